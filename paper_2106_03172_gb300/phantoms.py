@@ -1,0 +1,301 @@
+"""Seeded synthetic inputs for penalised PET reconstruction.
+
+This module is the only code that both the CUDA path and the FP64 oracle
+consume.  It holds none of the reconstruction arithmetic: no system matrix,
+no projector, no likelihood, no update rule.  It produces
+
+* the scanner/image geometry of each named workload (parallel-beam 2-D
+  sinograms, §5 of the paper uses the same kind of data with a Radon
+  transform forward model);
+* random-ellipse (and ellipsoid-stack) activity phantoms;
+* Poisson count data ``g ~ Poisson(p + w)`` (§2.1, Eq. (voxel_td)/(pdf)),
+  where ``p`` is the *analytic* line integral of the continuous ellipse
+  phantom (the closed-form Radon transform of an ellipse), so that the data
+  model never goes through the discrete projector under test;
+* the subset index sequences ``t_k`` that the stochastic methods draw
+  (§2.3: indices drawn uniformly at random), from SplitMix64 (Steele, Lea and
+  Flood, OOPSLA 2014) so that both sides consume the identical sequence.
+
+Units: lengths in mm, activity per pixel in arbitrary units scaled so that the
+expected trues sum to the requested total counts.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Geometry", "Workload", "WORKLOADS", "Ellipse", "random_ellipse_phantom",
+    "ellipsoid_stack_phantom", "rasterise", "analytic_sinogram", "make_data",
+    "splitmix64", "subset_sequence", "batched_workloads",
+]
+
+
+@dataclass(frozen=True)
+class Geometry:
+    """2-D parallel-beam geometry, optionally with ``nz`` independent slices.
+
+    Image: ``nx`` x ``ny`` square pixels of side ``pixel_mm`` centred on the
+    origin, stored row-major ``[iy][ix]`` (slice index innermost when nz > 1).
+    Sinogram: ``n_angles`` views at ``theta_i = i*pi/n_angles`` and
+    ``n_bins`` radial bins centred on the origin with spacing ``bin_mm``,
+    stored ``[view][bin]`` (slice index innermost when nz > 1).
+    """
+
+    nx: int
+    ny: int
+    n_angles: int
+    n_bins: int
+    pixel_mm: float = 2.0
+    bin_mm: float | None = None
+    nz: int = 1
+
+    @property
+    def ds(self) -> float:
+        return self.pixel_mm if self.bin_mm is None else self.bin_mm
+
+    @property
+    def n_pixels(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def n_rays(self) -> int:
+        return self.n_angles * self.n_bins
+
+
+@dataclass(frozen=True)
+class Workload:
+    """A named reconstruction workload: geometry, phantom recipe and method knobs."""
+
+    name: str
+    geometry: Geometry
+    n_subsets: int
+    counts: float
+    bg_frac: float
+    beta: float
+    n_ellipses: int
+    n_lesions: int = 0
+    epochs: int = 10
+    methods: tuple = ("osem", "svrem")
+    eta_svrg: int = 2
+    eta_svrem: int = 1
+    alpha_svrem: float = 0.7
+    alpha_saga: float = 2.0
+    alpha_svrg: float = 2.0
+    stack: bool = False
+    extra: dict = field(default_factory=dict)
+
+
+# Named workloads (sizes, counts, penalties and subset numbers of the
+# benchmark configurations; step sizes are the paper's brain-phantom values,
+# §5.1: alpha=2 for SAGA/SVRG with eta=2, alpha=0.7 and eta=1 for SVREM).
+WORKLOADS = {
+    "c64": Workload(
+        "c64", Geometry(64, 64, 60, 91), n_subsets=6, counts=1e5, bg_frac=0.10,
+        beta=0.01, n_ellipses=8, epochs=10, methods=("osem", "svrem")),
+    "c256": Workload(
+        "c256", Geometry(256, 256, 180, 367), n_subsets=21, counts=1e7, bg_frac=0.10,
+        beta=0.005, n_ellipses=20, n_lesions=6, epochs=50,
+        methods=("osem", "svrem", "saga", "svrg")),
+    "c128x47": Workload(
+        "c128x47", Geometry(128, 128, 252, 344, bin_mm=math.sqrt(2.0) * 128 * 2.0 / 344, nz=47),
+        n_subsets=14, counts=5e8, bg_frac=0.15, beta=0.002, n_ellipses=10, epochs=10,
+        methods=("svrg",), eta_svrg=2, stack=True),
+}
+
+
+@dataclass(frozen=True)
+class Ellipse:
+    cx: float
+    cy: float
+    a: float          # semi-axis along the rotated x' axis (mm)
+    b: float          # semi-axis along the rotated y' axis (mm)
+    phi: float        # rotation of x' from x (rad)
+    value: float      # activity added inside the ellipse
+
+
+def _contains(e: Ellipse, x, y):
+    c, s = math.cos(e.phi), math.sin(e.phi)
+    xr = (x - e.cx) * c + (y - e.cy) * s
+    yr = -(x - e.cx) * s + (y - e.cy) * c
+    return (xr / e.a) ** 2 + (yr / e.b) ** 2 <= 1.0
+
+
+def _value_at(ellipses, x, y) -> float:
+    return float(sum(e.value for e in ellipses if _contains(e, x, y)))
+
+
+def random_ellipse_phantom(geom: Geometry, seed: int, n_ellipses: int,
+                           n_lesions: int = 0) -> list:
+    """Body ellipse of activity 1 plus ``n_ellipses`` inner ellipses whose added
+    activity is U[0.5, 4], plus ``n_lesions`` hot disks of radius 3-6 pixels
+    at 4x the local activity (the lesion adds 3x the value at its centre)."""
+    rng = np.random.default_rng(seed)
+    half = 0.5 * min(geom.nx, geom.ny) * geom.pixel_mm
+    body = Ellipse(rng.uniform(-0.03, 0.03) * half, rng.uniform(-0.03, 0.03) * half,
+                   half * rng.uniform(0.80, 0.88), half * rng.uniform(0.62, 0.72),
+                   rng.uniform(-0.2, 0.2), 1.0)
+    out = [body]
+    for _ in range(n_ellipses):
+        for _try in range(100):
+            r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.7
+            ang = rng.uniform(0.0, 2.0 * math.pi)
+            cx = body.cx + r * body.a * math.cos(ang)
+            cy = body.cy + r * body.b * math.sin(ang)
+            a = half * rng.uniform(0.04, 0.22)
+            b = half * rng.uniform(0.04, 0.22)
+            e = Ellipse(cx, cy, a, b, rng.uniform(0.0, math.pi), rng.uniform(0.5, 4.0))
+            # keep the inner ellipse inside the body: test its 8 extreme points
+            pts = [(cx + a * math.cos(u) * math.cos(e.phi) - b * math.sin(u) * math.sin(e.phi),
+                    cy + a * math.cos(u) * math.sin(e.phi) + b * math.sin(u) * math.cos(e.phi))
+                   for u in np.linspace(0.0, 2.0 * math.pi, 8, endpoint=False)]
+            if all(_contains(body, px, py) for px, py in pts):
+                out.append(e)
+                break
+    for _ in range(n_lesions):
+        rad = rng.uniform(3.0, 6.0) * geom.pixel_mm
+        r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.6
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        cx = body.cx + r * body.a * math.cos(ang)
+        cy = body.cy + r * body.b * math.sin(ang)
+        local = _value_at(out, cx, cy)
+        out.append(Ellipse(cx, cy, rad, rad, 0.0, 3.0 * local))
+    return out
+
+
+def ellipsoid_stack_phantom(geom: Geometry, seed: int, n_ellipsoids: int) -> list:
+    """Per-slice ellipse lists of a random ellipsoid phantom sampled at the
+    ``nz`` slice centres (slice thickness = pixel size).  Each slice of an
+    ellipsoid with semi-axes (a, b, c) at height dz from its centre is the
+    ellipse with semi-axes scaled by sqrt(1 - (dz/c)^2)."""
+    rng = np.random.default_rng(seed)
+    half = 0.5 * min(geom.nx, geom.ny) * geom.pixel_mm
+    zhalf = 0.5 * geom.nz * geom.pixel_mm
+    solids = [(0.0, 0.0, 0.0, 0.85 * half, 0.66 * half, 1.05 * zhalf, 0.0, 1.0)]
+    for _ in range(n_ellipsoids):
+        r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.55
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        solids.append((r * 0.85 * half * math.cos(ang), r * 0.66 * half * math.sin(ang),
+                       rng.uniform(-0.5, 0.5) * zhalf, half * rng.uniform(0.05, 0.2),
+                       half * rng.uniform(0.05, 0.2), zhalf * rng.uniform(0.2, 0.6),
+                       rng.uniform(0.0, math.pi), rng.uniform(0.5, 4.0)))
+    slices = []
+    for k in range(geom.nz):
+        z = (k - 0.5 * (geom.nz - 1)) * geom.pixel_mm
+        cur = []
+        for (cx, cy, cz, a, b, c, phi, val) in solids:
+            t = 1.0 - ((z - cz) / c) ** 2
+            if t > 0.0:
+                sc = math.sqrt(t)
+                cur.append(Ellipse(cx, cy, a * sc, b * sc, phi, val))
+        slices.append(cur)
+    return slices
+
+
+def rasterise(ellipses, geom: Geometry) -> np.ndarray:
+    """Sample the phantom at pixel centres, ``[iy][ix]`` float64 (reference image only)."""
+    xs = (np.arange(geom.nx) - 0.5 * (geom.nx - 1)) * geom.pixel_mm
+    ys = (np.arange(geom.ny) - 0.5 * (geom.ny - 1)) * geom.pixel_mm
+    X, Y = np.meshgrid(xs, ys)
+    img = np.zeros((geom.ny, geom.nx))
+    for e in ellipses:
+        c, s = math.cos(e.phi), math.sin(e.phi)
+        xr = (X - e.cx) * c + (Y - e.cy) * s
+        yr = -(X - e.cx) * s + (Y - e.cy) * c
+        img += e.value * (((xr / e.a) ** 2 + (yr / e.b) ** 2) <= 1.0)
+    return img
+
+
+def analytic_sinogram(ellipses, geom: Geometry) -> np.ndarray:
+    """Closed-form line integrals of the continuous ellipse phantom,
+    ``[view][bin]`` float64, for the lines ``x cos(th) + y sin(th) = s``.
+
+    For an ellipse with semi-axes (a, b) rotated by phi and centred at c, the
+    chord of that line is ``2ab sqrt(q - s'^2) / q`` with
+    ``q = a^2 cos^2(th-phi) + b^2 sin^2(th-phi)`` and
+    ``s' = s - (cx cos th + cy sin th)`` (zero when ``s'^2 >= q``)."""
+    th = np.arange(geom.n_angles) * (math.pi / geom.n_angles)
+    s = (np.arange(geom.n_bins) - 0.5 * (geom.n_bins - 1)) * geom.ds
+    out = np.zeros((geom.n_angles, geom.n_bins))
+    for e in ellipses:
+        tp = th - e.phi
+        q = (e.a * np.cos(tp)) ** 2 + (e.b * np.sin(tp)) ** 2
+        sp = s[None, :] - (e.cx * np.cos(th) + e.cy * np.sin(th))[:, None]
+        rad = q[:, None] - sp * sp
+        chord = np.where(rad > 0.0, 2.0 * e.a * e.b * np.sqrt(np.maximum(rad, 0.0)) / q[:, None], 0.0)
+        out += e.value * chord
+    return out
+
+
+def make_data(work: Workload, seed: int):
+    """Phantom ``seed`` and Poisson data with noise seed ``seed + 1000``.
+
+    Returns a dict with
+      ``g``      float32 counts, ``[view][bin]`` (``[view][bin][z]`` for stacks);
+      ``w``      float background per bin (uniform: ``bg_frac`` x mean trues);
+      ``x_true`` float64 scaled reference image ``[iy][ix]`` (``[iy][ix][z]``);
+      ``scale``  the activity scale that makes the expected trues sum to ``counts``.
+    """
+    geom = work.geometry
+    if work.stack:
+        per_slice = ellipsoid_stack_phantom(geom, seed, work.n_ellipses)
+        sino = np.stack([analytic_sinogram(e, geom) for e in per_slice], axis=-1)
+        img = np.stack([rasterise(e, geom) for e in per_slice], axis=-1)
+    else:
+        ell = random_ellipse_phantom(geom, seed, work.n_ellipses, work.n_lesions)
+        sino = analytic_sinogram(ell, geom)
+        img = rasterise(ell, geom)
+    scale = work.counts / float(sino.sum())
+    trues = scale * sino
+    w = work.bg_frac * float(trues.mean())
+    rng = np.random.default_rng(seed + 1000)
+    g = rng.poisson(trues + w).astype(np.float32)
+    return {"g": g, "w": float(w), "x_true": scale * img, "scale": scale}
+
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> list:
+    """First ``n`` outputs of SplitMix64 started from ``seed`` (published
+    definition: add the golden gamma 0x9E3779B97F4A7C15, then two xor-shift
+    multiply rounds and a final xor-shift)."""
+    state = seed & _M64
+    out = []
+    for _ in range(n):
+        state = (state + 0x9E3779B97F4A7C15) & _M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def subset_sequence(seed: int, n_subsets: int, length: int) -> np.ndarray:
+    """i.i.d. uniform subset indices in ``[0, n_subsets)`` (with replacement),
+    ``floor(u * n_subsets)`` with ``u`` the top 53 bits of SplitMix64."""
+    if n_subsets <= 0 or length < 0:
+        raise ValueError("n_subsets must be positive and length nonnegative")
+    vals = splitmix64(seed, length)
+    return np.array([int(((v >> 11) * n_subsets) >> 53) for v in vals], dtype=np.int32)
+
+
+def batched_workloads(seed: int, count: int) -> list:
+    """Uneven batch of reconstruction geometries: N uniform in {64,128,192,256},
+    views round(1.4 N), bins the odd integer nearest 1.43 N, counts
+    log-uniform in [1e5, 1e7], subsets uniform in {6, 12, 21}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([64, 128, 192, 256]))
+        nb = int(round(1.43 * n))
+        if nb % 2 == 0:
+            nb += 1 if (1.43 * n) >= nb else -1
+        geom = Geometry(n, n, int(round(1.4 * n)), nb)
+        cnt = float(10.0 ** rng.uniform(5.0, 7.0))
+        out.append(Workload(f"batch{i}", geom, n_subsets=int(rng.choice([6, 12, 21])),
+                            counts=cnt, bg_frac=0.10, beta=0.005, n_ellipses=8,
+                            methods=("saga",)))
+    return out

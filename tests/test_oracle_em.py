@@ -1,0 +1,314 @@
+"""Pins for the oracle's likelihood, penalty and algorithms (CPU only).
+
+Each test checks the oracle against something the paper or the mathematics
+fixes independently of the oracle's own code: the Poisson pmf, finite
+differences, the majorisation property of the surrogate, a 1-D numerical
+maximiser, the MM monotonicity of EM, count conservation, the Appendix B closed
+form of the SVREM direction, an L-BFGS-B solution of the MAP problem, and
+library bfloat16 rounding.
+"""
+import numpy as np
+import pytest
+import scipy.optimize
+import scipy.stats
+import torch
+
+from oracle import em
+from oracle.penalty import POTENTIALS, Penalty, drho, gamma, m_step_root, rho
+from oracle.subsets import subset_rows, subset_views
+from paper_2106_03172_gb300.phantoms import Geometry
+
+from conftest import tiny_problem
+
+
+@pytest.fixture(scope="module")
+def prob_and_data():
+    return tiny_problem(Geometry(16, 16, 24, 23), seed=3)
+
+
+def _rand_image(prob, seed, lo=0.5, hi=3.0):
+    return np.random.default_rng(seed).uniform(lo, hi, size=(prob.N, prob.nz))
+
+
+def test_loglik_is_poisson_log_pmf(prob_and_data):
+    """L(f) + sum_m (-log g_m!) equals the Poisson log-likelihood of §2.1,
+    Eq. (pdf), with mean A f + w (pins the sign of w, reading C1)."""
+    prob, _ = prob_and_data
+    f = _rand_image(prob, 1)
+    mean = prob.A @ f + prob.w
+    ref = scipy.stats.poisson.logpmf(prob.g, mean).sum()
+    got = prob.loglik(f).sum() - scipy.special.gammaln(prob.g + 1.0).sum()
+    assert got == pytest.approx(ref, rel=1e-12)
+
+
+def test_grad_L_finite_difference(prob_and_data):
+    prob, _ = prob_and_data
+    f = _rand_image(prob, 2)
+    v = np.random.default_rng(5).standard_normal(f.shape)
+    h = 1e-5
+    fd = (prob.loglik(f + h * v).sum() - prob.loglik(f - h * v).sum()) / (2 * h)
+    assert float((prob.grad_L(f) * v).sum()) == pytest.approx(fd, rel=1e-6)
+    for t in range(prob.Ns):
+        rows = prob.subsets[t]
+        def Lt(x):
+            yh = prob.A[rows] @ x + prob.w[rows]
+            return float((prob.g[rows] * np.log(yh) - yh).sum())
+        fd_t = (Lt(f + h * v) - Lt(f - h * v)) / (2 * h)
+        assert float((prob.grad_L_t(f, t) * v).sum()) == pytest.approx(fd_t, rel=1e-6)
+
+
+@pytest.mark.parametrize("potential", POTENTIALS)
+def test_potential_table(potential):
+    """Table 1: rho' is the derivative of rho, gamma = rho'/t, rho even and
+    convex, gamma nonincreasing on t >= 0 with a finite nonzero limit at 0."""
+    delta = 0.7
+    t = np.linspace(-5, 5, 2001)
+    h = 1e-6
+    fd = (rho(t + h, potential, delta) - rho(t - h, potential, delta)) / (2 * h)
+    np.testing.assert_allclose(drho(t, potential, delta), fd, atol=1e-6)  # O(h) at the Huber kink
+    nz = np.abs(t) > 1e-3
+    np.testing.assert_allclose(gamma(t[nz], potential, delta), drho(t[nz], potential, delta) / t[nz], rtol=1e-12)
+    np.testing.assert_allclose(rho(t, potential, delta), rho(-t, potential, delta), rtol=1e-14)
+    g = gamma(t[t >= 0], potential, delta)
+    assert np.all(np.diff(g) <= 1e-15) and 0 < gamma(np.array([0.0]), potential, delta)[0] < np.inf
+    assert np.all(np.diff(drho(t, potential, delta)) >= -1e-15)
+
+
+@pytest.mark.parametrize("potential", POTENTIALS)
+def test_penalty_grad_finite_difference(potential):
+    pen = Penalty(7, 5, potential, 0.8)
+    rng = np.random.default_rng(0)
+    f = rng.uniform(0, 3, (35, 2))
+    v = rng.standard_normal(f.shape)
+    h = 1e-6
+    fd = (pen.value(f + h * v).sum() - pen.value(f - h * v).sum()) / (2 * h)
+    assert float((pen.grad(f) * v).sum()) == pytest.approx(fd, rel=1e-6)
+
+
+def test_quadratic_penalty_closed_form():
+    """Quadratic R = 1/2 sum_n sum_{j in N4} (f_n - f_j)^2 / 2 = sum over
+    unordered neighbour pairs of (f_n - f_j)^2 / 2."""
+    rng = np.random.default_rng(1)
+    img = rng.uniform(0, 2, (5, 6))
+    pairs = ((img[:, 1:] - img[:, :-1]) ** 2).sum() + ((img[1:, :] - img[:-1, :]) ** 2).sum()
+    pen = Penalty(6, 5)
+    assert pen.value(img.reshape(-1, 1))[0] == pytest.approx(0.5 * pairs, rel=1e-14)
+
+
+@pytest.mark.parametrize("potential", POTENTIALS)
+def test_surrogate_majorises_penalty(potential):
+    """§3: R_hat(.; f^k) >= R, with equality and equal gradient at f^k."""
+    pen = Penalty(6, 6, potential, 0.5)
+    rng = np.random.default_rng(2)
+    fk = rng.uniform(0, 3, (36, 1))
+    for _ in range(20):
+        f = rng.uniform(0, 3, (36, 1))
+        assert pen.surrogate_value(f, fk)[0] >= pen.value(f)[0] - 1e-12
+    assert pen.surrogate_value(fk, fk)[0] == pytest.approx(pen.value(fk)[0], rel=1e-14)
+    v = rng.standard_normal(fk.shape)
+    h = 1e-6
+    fd = (pen.surrogate_value(fk + h * v, fk)[0] - pen.surrogate_value(fk - h * v, fk)[0]) / (2 * h)
+    assert float((pen.grad(fk) * v).sum()) == pytest.approx(fd, rel=1e-6)
+
+
+@pytest.mark.parametrize("potential", ["quadratic", "huber", "logcosh"])
+def test_root_maximises_separable_surrogate(potential):
+    """The M-step root maximises, per pixel, a log f - S f - beta sum_j d_nj (f - mu_nj)^2
+    (the separable surrogate objective of §3); checked with a bounded 1-D
+    numerical maximiser, plus the residual of a/f - 2bf + c = 0."""
+    nx = ny = 5
+    pen = Penalty(nx, ny, potential, 0.6)
+    rng = np.random.default_rng(4)
+    fk = rng.uniform(0.1, 3, (nx * ny, 1))
+    a = rng.uniform(0.05, 5, fk.shape)
+    S = rng.uniform(0.5, 2, fk.shape)
+    beta = 0.7
+    root = m_step_root(a, fk, S, beta, pen)
+    d = gamma(fk[pen.src] - fk[pen.dst], potential, 0.6)[:, 0]
+    mu = 0.5 * (fk[pen.src] + fk[pen.dst])[:, 0]
+    for n in range(nx * ny):
+        sel = pen.src == n
+        def negh(x):
+            return -(a[n, 0] * np.log(x) - S[n, 0] * x - beta * np.sum(d[sel] * (x - mu[sel]) ** 2))
+        res = scipy.optimize.minimize_scalar(negh, bounds=(1e-9, 50.0), method="bounded",
+                                             options={"xatol": 1e-12})
+        assert root[n, 0] == pytest.approx(res.x, rel=1e-6)
+    sd, sdf = pen.surrogate_weights(fk)
+    b, c = beta * sd, beta * (fk * sd + sdf) - S
+    np.testing.assert_allclose(a / root - 2 * b * root + c, 0.0, atol=1e-12)
+    # beta = 0: the plain EM M-step a / S (the printed "-c/a" is a typo for -a/c)
+    np.testing.assert_allclose(m_step_root(a, fk, S, 0.0, pen), a / S, rtol=1e-15)
+    # nonpositive statistic -> 0 (zero-denominator remedy)
+    a2 = a.copy()
+    a2[:3] = -1.0
+    assert np.all(m_step_root(a2, fk, S, beta, pen)[:3] == 0.0)
+
+
+def test_subsets_partition():
+    views = subset_views(180, 21)
+    assert sorted(np.concatenate(views).tolist()) == list(range(180))
+    assert [len(v) for v in views].count(9) == 12 and [len(v) for v in views].count(8) == 9
+    rows = subset_rows(6, 5, 4)
+    assert sorted(np.concatenate(rows).tolist()) == list(range(30))
+    with pytest.raises(ValueError):
+        subset_views(5, 6)
+
+
+def test_osem_one_subset_is_mlem():
+    """§2.2: OSEM with N_s = 1 is MLEM."""
+    geom = Geometry(12, 12, 18, 17)
+    p1, _ = tiny_problem(geom, seed=5, n_subsets=1, beta=0.0)
+    f = p1.uniform_image()
+    for _ in range(3):
+        np.testing.assert_allclose(em.osem_step(p1, f, 0), em.mlem_step(p1, f), rtol=1e-13)
+        f = em.mlem_step(p1, f)
+
+
+def test_mlem_likelihood_monotone_and_nonnegative():
+    """MM property (§2.2): every MLEM iterate increases L and stays >= 0."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=6, n_subsets=1, beta=0.0)
+    f = p.uniform_image()
+    last = p.loglik(f).sum()
+    for _ in range(25):
+        f = em.mlem_step(p, f)
+        cur = p.loglik(f).sum()
+        assert cur >= last - 1e-9 * abs(last) and f.min() >= 0.0
+        last = cur
+
+
+def test_map_em_objective_monotone(prob_and_data):
+    """MM property with the parabolic surrogate (§3): MAP-EM increases Phi."""
+    prob, _ = prob_and_data
+    f = prob.uniform_image()
+    last = prob.objective(f)
+    for _ in range(25):
+        f = em.map_em_step(prob, f)
+        cur = prob.objective(f)
+        assert cur >= last - 1e-10 * abs(last) and f.min() >= 0.0
+        last = cur
+
+
+def test_count_conservation():
+    """w = 0, beta = 0: one OSEM step gives sum_n (A_t^T 1)_n f_n = sum g_m over
+    the rays of S_t that meet the image (textbook EM count conservation)."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=7, n_subsets=3, beta=0.0, w_zero=True)
+    f = p.uniform_image() + 0.1
+    for t in range(p.Ns):
+        f1 = em.osem_step(p, f, t)
+        hit = np.asarray(p.At[t].sum(axis=1)).ravel() > 0
+        assert (~hit).any()
+        assert float((p.sens_t[t] * f1).sum()) == pytest.approx(float(p.gt[t][hit].sum()), rel=1e-12)
+
+
+def test_statistic_identities(prob_and_data):
+    """Eq. (subsetstat) and Eq. (tau_t) agree, and s(f) = mean_t tau_t(f) (§2.3)."""
+    prob, _ = prob_and_data
+    f = _rand_image(prob, 8)
+    for t in range(prob.Ns):
+        np.testing.assert_allclose(prob.tau_t(f, t), prob.tau_t_from_gradient(f, t), rtol=1e-12, atol=1e-12)
+    mean = sum(prob.tau_t(f, t) for t in range(prob.Ns)) / prob.Ns
+    np.testing.assert_allclose(mean, prob.statistic(f), rtol=1e-12)
+
+
+def test_svrem_step_matches_appendix_b():
+    """Appendix B: at beta = 0 with s_hat^k = A^T 1 . f^k, one SVREM update
+    equals f^k + alpha h with the printed closed-form direction h."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=9, n_subsets=3, beta=0.0)
+    rng = np.random.default_rng(3)
+    fk = rng.uniform(0.5, 2.0, (p.N, 1))
+    f_anc = rng.uniform(0.5, 2.0, (p.N, 1))
+    alg = em.SVREM(p, f_anc, alpha=0.7, eta=1)
+    alg.refresh_anchor()
+    alg.f, alg.s_hat, alg.k = fk.copy(), p.sens * fk, 1
+    for t in range(p.Ns):
+        alg.f, alg.s_hat, alg.k = fk.copy(), p.sens * fk, 1
+        got = alg.step(t)
+        want = fk + 0.7 * em.svrem_direction_appendix_b(p, fk, f_anc, t)
+        np.testing.assert_allclose(got, np.maximum(want, 0.0), rtol=1e-11, atol=1e-12)
+
+
+def test_svrg_anchor_step_is_full_gradient_step(prob_and_data):
+    """§4: at an anchor iteration the SVRG direction is grad Phi(f)/N_s."""
+    prob, _ = prob_and_data
+    f0 = _rand_image(prob, 10)
+    alg = em.SVRG(prob, f0, alpha=1.5, eta=2)
+    f1 = alg.step(2)
+    want = np.maximum(f0 + 1.5 * alg.d * prob.grad_Phi(f0) / prob.Ns, 0.0)
+    np.testing.assert_allclose(f1, want, rtol=1e-12, atol=1e-14)
+
+
+def test_svrem_single_subset_alpha_one_is_map_em():
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=11, n_subsets=1, beta=0.05)
+    f = p.uniform_image()
+    alg = em.SVREM(p, f, alpha=1.0, eta=1)
+    for _ in range(4):
+        want = em.map_em_step(p, f)
+        f = alg.step(0)
+        np.testing.assert_allclose(f, want, rtol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def map_solution(prob_and_data):
+    """f* of max_{f>=0} Phi by L-BFGS-B (the paper's reference solver, §5.1)."""
+    prob, _ = prob_and_data
+    x0 = prob.initial_image().ravel()
+    res = scipy.optimize.minimize(
+        lambda x: -prob.objective(x.reshape(-1, 1)),
+        x0, jac=lambda x: -prob.grad_Phi(x.reshape(-1, 1)).ravel(),
+        method="L-BFGS-B", bounds=[(0, None)] * x0.size,
+        options={"maxiter": 20000, "ftol": 1e-16, "gtol": 1e-11, "maxcor": 30})
+    return res.x.reshape(-1, 1)
+
+
+def test_map_em_reaches_lbfgsb_maximiser(prob_and_data, map_solution):
+    """MAP-EM with the parabolic surrogate converges to the L-BFGS-B maximiser."""
+    prob, _ = prob_and_data
+    f, hist = em.map_em(prob, prob.initial_image(), max_iter=4000, tol=1e-15)
+    assert prob.objective(f) == pytest.approx(prob.objective(map_solution), rel=1e-9)
+    assert np.linalg.norm(f - map_solution) / np.linalg.norm(map_solution) < 2e-3
+    assert em.kkt_residual(prob, map_solution) < 1e-6
+
+
+def test_kkt_point_is_fixed_point_of_vr_methods(prob_and_data, map_solution):
+    """§4 stationarity: at the maximiser one SAGA step (table built there), one
+    SVRG step and one SVREM step leave f* unchanged; plain OSEM does not (the
+    limit cycle motivating variance reduction, §1)."""
+    prob, _ = prob_and_data
+    fs = map_solution
+    f0 = prob.initial_image()
+    d = em.preconditioner(prob, f0)
+    scale = np.linalg.norm(fs)
+    for t in range(prob.Ns):
+        saga = em.SAGA(prob, fs, alpha=2.0, d=d)
+        assert np.linalg.norm(saga.step(t) - fs) / scale < 1e-6
+        svrg = em.SVRG(prob, fs, alpha=2.0, eta=2, d=d)
+        assert np.linalg.norm(svrg.step(t) - fs) / scale < 1e-6
+        svrem = em.SVREM(prob, fs, alpha=0.7, eta=1)
+        assert np.linalg.norm(svrem.step(t) - fs) / scale < 1e-6
+    assert np.linalg.norm(em.osem_step(prob, fs, 0) - fs) / scale > 1e-4
+
+
+def test_bf16_round_matches_torch():
+    x = np.random.default_rng(0).standard_normal(10000) * np.logspace(-20, 20, 10000)
+    x = np.concatenate([x, [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 65504.0]])
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(em.bf16_round(x), want)
+
+
+def test_vr_methods_converge_towards_map(prob_and_data, map_solution):
+    """SVREM, SAGA and SVRG approach Phi* from the OSEM warm start (§5)."""
+    prob, _ = prob_and_data
+    phi_star = prob.objective(map_solution)
+    f0 = prob.initial_image()
+    gap0 = em.relative_gap(prob.objective(f0), phi_star)
+    from paper_2106_03172_gb300.phantoms import subset_sequence
+    seq = subset_sequence(2000, prob.Ns, 40 * prob.Ns)
+    for alg in (em.SVREM(prob, f0, 0.7, 1), em.SAGA(prob, f0, 1.0), em.SVRG(prob, f0, 1.0, 2)):
+        for t in seq:
+            f = alg.step(int(t))
+        gap = em.relative_gap(prob.objective(f), phi_star)
+        assert -1e-12 <= gap < 1e-3 * gap0
