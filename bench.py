@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the penalised stochastic-EM hot path on one GB300 per rank.
+
+Workload (default ``c256``): 256x256 image of 2 mm pixels, 180 views x 367
+bins, 21 angle-interleaved subsets, seeded 20-ellipse phantom with 6 hot
+lesions, 1e7 expected counts plus a 10% uniform background, quadratic
+penalty beta = 0.005.  The warm start is one unpenalised OSEM epoch.
+
+One step = one epoch (21 subset updates) of each of OSEM, SVREM (alpha 0.7,
+eta 1), SAGA (alpha 2, FP32 table) and SVRG (alpha 2, eta 2), each followed by
+its FP64 objective; anchor passes (SVREM every epoch, SVRG every second
+epoch) run inside the step when due.  The metric counts subset forward+back
+projection pairs (A_t f then A_t^T r): 84 per step plus 21 per anchor pass.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream; a 256 MiB buffer is written between steps (outside
+the events) so every step starts with a cold L2.  ``e2e`` repeats the steps
+through the public API with the counts copied in from pinned host memory and
+the four images and objectives copied back, inside the events.  Per-kernel
+durations for the roofline come from a separate profiled pass (event pairs
+around every projector launch).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+same step on the same workload), on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METHODS = ("osem", "svrem", "saga", "svrg")
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(work):
+    g = work.geometry
+    return {
+        "workload": f"{work.name}: {g.nx}x{g.ny} image ({g.pixel_mm:g} mm pixels), {g.n_angles} views x "
+                    f"{g.n_bins} bins, {work.n_subsets} angle-interleaved subsets, {work.counts:.0e} counts, "
+                    f"{int(round(work.bg_frac * 100))}% background, quadratic beta={work.beta}",
+        "step": "one epoch each of OSEM, SVREM(alpha=0.7, eta=1), SAGA(alpha=2, fp32 table), "
+                "SVRG(alpha=2, eta=2), each followed by its FP64 objective",
+        "l2": "flushed between steps (256 MiB write outside the timed events)",
+        "n_subsets": work.n_subsets,
+        "image": [g.ny, g.nx],
+        "sinogram": [g.n_angles, g.n_bins],
+    }
+
+
+def seqs_for_step(step: int, ns: int):
+    from paper_2106_03172_gb300.phantoms import subset_sequence
+    return [subset_sequence(2000 + 4 * step + i, ns, ns) for i in range(4)]
+
+
+def alphas(work):
+    return {"osem": (1.0, 1), "svrem": (work.alpha_svrem, work.eta_svrem),
+            "saga": (work.alpha_saga, 1), "svrg": (work.alpha_svrg, work.eta_svrg)}
+
+
+class Replica:
+    """Host bookkeeping of one rank's four reconstructions (counts anchor passes)."""
+
+    def __init__(self, work):
+        self.work = work
+        self.k = {m: 0 for m in METHODS}
+
+    def step_pairs(self):
+        ns = self.work.n_subsets
+        pairs = 4 * ns
+        anchors = []
+        for m in ("svrem", "svrg"):
+            eta = alphas(self.work)[m][1]
+            if self.k[m] % (eta * ns) == 0:
+                pairs += ns
+                anchors.append(m)
+        return pairs, anchors
+
+    def advance(self):
+        for m in METHODS:
+            self.k[m] += self.work.n_subsets
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def visible_index(torch):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    dev = torch.cuda.current_device()
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if dev < len(ids) and ids[dev].isdigit():
+            return int(ids[dev])
+    return dev
+
+
+# --------------------------------------------------------------------------- oracle timing
+
+def oracle_steps(work, data, n_steps: int, warmup: int = 0):
+    """Time ``n_steps`` oracle steps (the bench step in FP64 on the host);
+    returns (per-step seconds, per-step pairs, setup seconds)."""
+    from oracle import em
+    from oracle.em import build_problem
+    t0 = time.perf_counter()
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    f0 = prob.initial_image()
+    setup = time.perf_counter() - t0
+    a = alphas(work)
+    algs = {"svrem": em.SVREM(prob, f0, *a["svrem"]), "saga": em.SAGA(prob, f0, a["saga"][0]),
+            "svrg": em.SVRG(prob, f0, *a["svrg"])}
+    f_osem = f0.copy()
+    rep = Replica(work)
+    times, pairs = [], []
+    for step in range(warmup + n_steps):
+        seqs = seqs_for_step(step, work.n_subsets)
+        p, _ = rep.step_pairs()
+        t = time.perf_counter()
+        f_osem = em.osem_epoch(prob, f_osem, seqs[0])
+        prob.objective(f_osem)
+        for i, m in enumerate(("svrem", "saga", "svrg")):
+            for s in seqs[i + 1]:
+                algs[m].step(int(s))
+            prob.objective(algs[m].f)
+        dt = time.perf_counter() - t
+        rep.advance()
+        if step >= warmup:
+            times.append(dt)
+            pairs.append(p)
+    return times, pairs, setup
+
+
+def run_reference(args):
+    from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    work = WORKLOADS[args.workload]
+    data = make_data(work, 0)
+    times, pairs, setup = oracle_steps(work, data, args.steps, args.warmup)
+    total = sum(times)
+    value = sum(pairs) / total
+    unit = "subset fwd+back projections/s"
+    line = {
+        "impl": "reference",
+        "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
+        "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded ellipse phantom, Poisson counts)",
+        "config": workload_config(work),
+        "p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)),
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full bench steps after {args.warmup} warm-up steps "
+                                   f"(system matrix build and warm start, {setup:.1f} s, untimed)"},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_03172_gb300 import build as _build
+    from paper_2106_03172_gb300 import petvr
+    from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    petvr.lib()
+
+    work = WORKLOADS[args.workload]
+    geom = work.geometry
+    ns = work.n_subsets
+    data = make_data(work, 0)
+    g_host = torch.from_numpy(data["g"].ravel()).pin_memory()
+    g_dev = g_host.cuda()
+    plan = petvr.Plan(geom, ns)
+    prob = petvr.Problem(plan, g_dev, None, data["w"], work.beta)
+    f0 = torch.empty(geom.n_pixels * geom.nz, device="cuda")
+    petvr.pet_warm_start(prob.handle, f0)
+    imgs = {m: f0.clone() for m in METHODS}
+    states = {m: petvr.State(prob, m, imgs[m]) for m in METHODS}
+    phi = torch.zeros(4, 3, dtype=torch.float64, device="cuda")
+    a = alphas(work)
+    nnz_t = [petvr.pet_plan_nnz(plan.handle, t) for t in range(ns)]
+    nnz_all = petvr.pet_plan_nnz(plan.handle, -1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+    rep = Replica(work)
+
+    def one_step(step):
+        seqs = seqs_for_step(step, ns)
+        for i, m in enumerate(METHODS):
+            states[m].epoch(seqs[i], alpha=a[m][0], eta=a[m][1])
+            petvr.pet_objective_async(prob.handle, imgs[m], phi[i])
+        return seqs
+
+    for w in range(args.warmup):
+        one_step(w)
+        rep.advance()
+    torch.cuda.synchronize()
+
+    # ---- timed region (kernel-only: inputs resident in HBM)
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    pairs = 0
+    clocks = ClockSampler(visible_index(torch))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = petvr.pet_kernel_launches()
+    for k in range(args.steps):
+        flush.zero_()
+        p, _ = rep.step_pairs()
+        pairs += p
+        events[k][0].record(stream)
+        one_step(args.warmup + k)
+        events[k][1].record(stream)
+        rep.advance()
+    torch.cuda.synchronize()
+    launches = petvr.pet_kernel_launches() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in events]
+    total_ms = float(sum(step_ms))
+    phi_host = phi.cpu().numpy()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_max = float(t.item())
+        pt = torch.tensor([pairs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
+        pairs_all = float(pt.item())
+    else:
+        total_max, pairs_all = total_ms, float(pairs)
+    value = pairs_all / (total_max / 1e3)
+
+    # ---- profiled pass: per-kernel durations for the roofline
+    n_prof = min(args.steps, 8)
+    alg_flops = {0: 0.0, 1: 0.0, 2: 0.0}
+    alg_bytes = {0: 0.0, 1: 0.0, 2: 0.0}
+    N, M = geom.n_pixels, geom.n_rays
+    upd_bytes = {"osem": 12, "svrem": 32, "saga": 32, "svrg": 20}   # per pixel, see DESIGN
+    petvr.pet_profile_reset()
+    petvr.pet_profile_enable(True)
+    for k in range(n_prof):
+        flush.zero_()
+        p, anchors = rep.step_pairs()
+        seqs = one_step(args.warmup + args.steps + k)
+        for i, m in enumerate(METHODS):
+            for t in seqs[i]:
+                rays = plan.subset_rays(int(t))
+                alg_flops[0] += 2.0 * nnz_t[int(t)]
+                alg_bytes[0] += 4.0 * N + 8.0 * rays
+                alg_flops[1] += 2.0 * nnz_t[int(t)]
+                alg_bytes[1] += 4.0 * rays + upd_bytes[m] * N
+            alg_flops[0] += 2.0 * nnz_all                      # objective forward
+            alg_bytes[0] += 4.0 * N + 4.0 * M
+        for m in anchors:
+            alg_flops[0] += 2.0 * nnz_all
+            alg_bytes[0] += 4.0 * N + 8.0 * M
+            alg_flops[2] += 2.0 * nnz_all
+            alg_bytes[2] += 4.0 * M + 4.0 * N * ns
+        rep.advance()
+    torch.cuda.synchronize()
+    petvr.pet_profile_enable(False)
+    kinds = {}
+    for kind, name in ((0, "forward_kernel"), (1, "back_kernel (update epilogue)"), (2, "back_kernel (anchor)")):
+        n, ms = petvr.pet_profile_read(kind)
+        kinds[kind] = {"name": name, "launches": n, "total_ms": ms,
+                       "avg_us": 1e3 * ms / n if n else None}
+    petvr.pet_profile_reset()
+    tot = sum(v["total_ms"] for v in kinds.values()) or 1.0
+    for v in kinds.values():
+        v["share"] = v["total_ms"] / tot
+    dom = max(kinds, key=lambda k: kinds[k]["total_ms"])
+    peak_alu = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    achieved = alg_flops[dom] / (kinds[dom]["total_ms"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": kinds[dom]["name"], "achieved": achieved, "peak": peak_alu,
+                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)",
+                "hbm_achieved_gbs": alg_bytes[dom] / (kinds[dom]["total_ms"] / 1e3) / 1e9,
+                "kernels": {v["name"]: {k2: v[k2] for k2 in ("launches", "avg_us", "share")}
+                            for v in kinds.values()}}
+
+    # ---- end to end through the public API with host buffers
+    img_host = torch.empty(4, geom.n_pixels * geom.nz, dtype=torch.float32).pin_memory()
+    phi_host_buf = torch.empty(4, 3, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    e2e_pairs = 0
+    for k in range(args.steps):
+        flush.zero_()
+        p, _ = rep.step_pairs()
+        e2e_pairs += p
+        s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        g_dev.copy_(g_host, non_blocking=True)
+        petvr.pet_problem_update(prob.handle, g_dev, None, data["w"])
+        one_step(args.warmup + args.steps + n_prof + k)
+        for i, m in enumerate(METHODS):
+            img_host[i].copy_(imgs[m], non_blocking=True)
+        phi_host_buf.copy_(phi, non_blocking=True)
+        e_ev.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(s_ev.elapsed_time(e_ev))
+        rep.advance()
+    e2e_value = e2e_pairs / (sum(e2e_ms) / 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_value], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_value = float(t.item())
+    h2d = 4 * geom.n_rays * geom.nz
+    d2h = 4 * 4 * geom.n_pixels * geom.nz + 4 * 3 * 8
+
+    unit = "subset fwd+back projections/s"
+    line = {
+        "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
+        "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ellipse phantom, Poisson counts)",
+        "config": dict(workload_config(work), parallelism=f"replicas x{world}"),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "pairs_per_step": pairs / args.steps,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "objective_last_step": [float(x) for x in phi_host[:, 0]],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times, cpairs, setup = oracle_steps(work, data, 8)
+        line["cpu_baseline"] = {
+            "value": sum(cpairs) / sum(times), "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": f"8 bench steps of the FP64 oracle (about {sum(times):.0f} s; system matrix build "
+                      f"and warm start, {setup:.1f} s, untimed)"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * petvr.h -- C ABI of the GB300 (sm_103a) library for penalised PET
+ * reconstruction by (variance-reduced) stochastic EM.
+ *
+ * The method is the one of Kereta, Twyman, Arridge, Thielemans and Jin,
+ * "Stochastic EM methods with Variance Reduction for Penalised PET
+ * Reconstructions": maximise Phi(f) = L(f) - beta R(f) over f >= 0 (§3,
+ * Eq. (PET-MAP)) with the Poisson log-likelihood L of §2.1
+ * (Eq. (log_likelihood)) split over ordered subsets of the sinogram rows
+ * (§2.1, Eq. (subobjective)), by OSEM (§2.2, Eq. (Mstep)), SVREM (§2.3,
+ * Eq. (tempsvrem), with the surrogate M-step of §3, Eq. (svrsurder)), and
+ * preconditioned proximal SAGA / SVRG (§4, Eq. (saga_update),
+ * Eq. (svrg_update)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are CUDA device pointers (or managed memory) on the
+ *   current device; pointers named h_* are host pointers.  The caller owns
+ *   every buffer it passes; the library never frees them.  Objects created
+ *   here (plan, problem, state) own only the device tables they allocate and
+ *   borrow the caller's buffers, which must outlive them.
+ * - Images are float32, nz independent slices of nx*ny pixels, laid out
+ *   [iy][ix][z] (slice index innermost; nz = 1 is a plain [iy][ix] image).
+ *   Sinograms are float32 [view][bin][z].  A "subset sinogram" holds only the
+ *   views of one subset, in increasing view order ([view-in-subset][bin][z]).
+ * - `stream` is a cudaStream_t (0 = the legacy default stream).  Every call
+ *   is asynchronous on that stream unless documented as synchronising.
+ * - Every call returns a pet_status.  Argument errors are detected on the
+ *   host and returned immediately, with nothing enqueued.  CUDA launch or
+ *   allocation errors return PET_ERR_CUDA / PET_ERR_OOM.  Numeric problems
+ *   found by a kernel (a nonpositive expected count with positive data) are
+ *   latched in a device status word and returned by the next synchronising
+ *   call (pet_objective, pet_state_sync).  No call aborts the process.
+ *   pet_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef PETVR_H
+#define PETVR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PET_OK = 0,
+    PET_ERR_INVALID = 1, /* bad argument, size or object                    */
+    PET_ERR_OOM = 2,     /* device allocation failed                         */
+    PET_ERR_CUDA = 3,    /* a CUDA runtime call or kernel launch failed      */
+    PET_ERR_TIMEOUT = 4, /* reserved: a bounded device wait gave up          */
+    PET_ERR_NUMERIC = 5, /* latched device-side numeric error                */
+    PET_ERR_STATE = 6    /* call not valid for this object's algorithm/state */
+} pet_status;
+
+/* Algorithms (pet_state_create). */
+enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG = 3 };
+/* SAGA gradient-table storage (pet_state_create). */
+enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
+/* Potentials of the pairwise penalty (Table 1); quadratic is implemented. */
+enum { PET_POT_QUADRATIC = 0 };
+
+/* 2-D parallel-beam geometry (optionally a stack of nz independent slices).
+ * Pixel (ix, iy) is the half-open square [x_min + ix d, x_min + (ix+1) d) x
+ * [y_min + iy d, ...) with x_min = -nx d / 2, y_min = -ny d / 2, d = pixel_mm.
+ * View i is at theta_i = i pi / n_angles; bin j at s_j = (j - (n_bins-1)/2)
+ * bin_mm (bin_mm <= 0 means bin_mm = pixel_mm).  Ray (i, j) is the line
+ * x cos(theta_i) + y sin(theta_i) = s_j and a_mn is its length (mm) inside
+ * pixel n: the exact Siddon intersection length (the paper's forward model is
+ * a Radon transform, §5.1; A is any nonnegative system matrix, §2.1). */
+typedef struct {
+    int32_t nx, ny, nz;
+    double pixel_mm;
+    int32_t n_angles, n_bins;
+    double bin_mm;
+} pet_geometry;
+
+/* Ordered subsets (§2.1): scheme 0 = angle-interleaved, view i belongs to
+ * subset i mod n_subsets (1 <= n_subsets <= n_angles). */
+typedef struct {
+    int32_t n_subsets;
+    int32_t scheme;
+} pet_subsets;
+
+/* Penalty beta R(f), R = 1/2 sum_n sum_{j in N4(n)} rho(f_n - f_j) (§3). */
+typedef struct {
+    int32_t potential; /* PET_POT_QUADRATIC */
+    float beta;        /* >= 0 */
+    float delta;       /* unused by the quadratic potential */
+} pet_penalty;
+
+typedef struct pet_plan pet_plan;
+typedef struct pet_problem pet_problem;
+typedef struct pet_state pet_state;
+
+/* ---- plan: geometry tables and sensitivities ---------------------------- */
+
+/* Build the per-view and per-ray geometry tables on the current device and
+ * the subset sensitivities sens_t = A_t^T 1 and sens = A^T 1 (the
+ * denominators of §2.2, Eq. (Mstep)).  Synchronises the legacy stream once.
+ * *out is set on success and must be released with pet_plan_destroy. */
+pet_status pet_plan_create(const pet_geometry *geom, const pet_subsets *subsets, pet_plan **out);
+void pet_plan_destroy(pet_plan *plan);
+
+/* Number of views in subset t (t in [0, n_subsets)), or of all views for
+ * t = -1; the subset sinogram of t has n_views * n_bins * nz floats. */
+pet_status pet_plan_subset_views(const pet_plan *plan, int32_t t, int32_t *h_n_views);
+
+/* Number of nonzeros of A_t (t >= 0) or of A (t = -1) for one slice: the
+ * (ray, pixel) pairs with a positive intersection length, counted on the
+ * device when the plan is built.  This is the algorithmic work of one
+ * projection (one multiply-add per nonzero). */
+pet_status pet_plan_nnz(const pet_plan *plan, int32_t t, int64_t *h_nnz);
+
+/* Copy sens_t (t >= 0) or sens (t = -1), nx*ny floats, into d_out. */
+pet_status pet_plan_sensitivity(const pet_plan *plan, int32_t t, float *d_out, void *stream);
+
+/* ---- projectors ----------------------------------------------------------- */
+
+/* Forward projection y = A_t f + w (§2.1, Eq. (voxel_td)).  subset = -1
+ * projects every view into a full sinogram; subset = t writes the subset
+ * sinogram of t.  d_bg (same layout as d_sino) may be NULL, then the scalar
+ * bg is added to every ray.  d_img and d_sino must not overlap. */
+pet_status pet_forward(const pet_plan *plan, const float *d_img, const float *d_bg, float bg,
+                       int32_t subset, float *d_sino, void *stream);
+
+/* Back projection b = A_t^T y (the adjoint of pet_forward without the
+ * background; used in every update of §2.2-§4).  d_sino is the subset
+ * sinogram of t (full sinogram for subset = -1); d_img receives b. */
+pet_status pet_back(const pet_plan *plan, const float *d_sino, int32_t subset, float *d_img,
+                    void *stream);
+
+/* ---- problem: data, background and penalty -------------------------------- */
+
+/* Bind counts g (full sinogram, float32, [view][bin][z]), background w
+ * (full sinogram, or NULL for the scalar bg) and the penalty.  The data are
+ * copied into subset-major device order, so d_counts / d_bg may be freed
+ * after the call returns and the stream has drained. */
+pet_status pet_problem_create(const pet_plan *plan, const float *d_counts, const float *d_bg,
+                              float bg, const pet_penalty *pen, pet_problem **out, void *stream);
+void pet_problem_destroy(pet_problem *problem);
+
+/* Replace the counts (and background) of an existing problem in place, with
+ * the same layouts and rules as pet_problem_create; nothing is allocated.
+ * d_bg must be non-NULL exactly when the problem was created with a
+ * background sinogram. */
+pet_status pet_problem_update(pet_problem *problem, const float *d_counts, const float *d_bg, float bg,
+                              void *stream);
+
+/* Warm start (every method of §5.1 starts from one OSEM epoch): write the constant
+ * image f_u = sum_m max(g_m - w_m, 0) / sum_n (A^T 1)_n into d_img, then run
+ * one unpenalised OSEM epoch in cyclic subset order on it. */
+pet_status pet_warm_start(const pet_problem *problem, float *d_img, void *stream);
+
+/* Objective Phi(f) = sum_m (g_m log yhat_m - yhat_m) - beta R(f), with
+ * yhat = A f + w, reduced in FP64 (§2.1, Eq. (log_likelihood); §3,
+ * Eq. (PET-MAP)).  Synchronising: returns after *h_phi is written.  Returns
+ * PET_ERR_NUMERIC if some yhat_m <= 0 with g_m > 0. */
+pet_status pet_objective(const pet_problem *problem, const float *d_img, double *h_phi, void *stream);
+
+/* The same objective, enqueued only: d_phi (device, 3 doubles) receives
+ * {Phi, L, R} when the stream reaches it.  Numeric errors are latched and
+ * reported by the next synchronising call.  Calls on one problem share its
+ * reduction scratch, so they must be ordered on one stream. */
+pet_status pet_objective_async(const pet_problem *problem, const float *d_img, double *d_phi, void *stream);
+
+/* ---- state: one running reconstruction ------------------------------------ */
+
+/* Create the state of `algo` on the image d_img_inout (borrowed: every epoch
+ * call reads the current iterate from it and leaves the new one there).
+ * SAGA and SVRG freeze the preconditioner d = N_s f^(0) / A^T 1 at this
+ * image (§4: constant d = d(f^(0))); SAGA also fills its gradient table with
+ * grad Phi_t(f^(0)) for every t (one full pass), enqueued on `stream`.
+ * If out == NULL only *bytes_needed (device bytes this state would
+ * allocate) is computed: an admission query that allocates nothing. */
+pet_status pet_state_create(const pet_problem *problem, int32_t algo, int32_t table_dtype,
+                            float *d_img_inout, size_t *bytes_needed, pet_state **out,
+                            void *stream);
+pet_status pet_state_destroy(pet_state *state);
+
+/* n_iter updates (an epoch is n_iter = n_subsets) with subset indices
+ * h_subset_seq[0..n_iter-1], each in [0, n_subsets).  The update counter k
+ * persists across calls; anchors are refreshed when k mod (eta N_s) == 0.
+ *
+ * OSEM  (§2.2, Eq. (Mstep) with the penalised surrogate of §3):
+ *       f <- root(a = f . A_t^T(g_t / yhat_t), sens_t, beta / N_s).
+ * SVREM (§2.3, Eq. (tempsvrem); §3 M-step with sens and beta):
+ *       s <- (1-alpha) s + alpha (tau_t(f) - tau_t(f_anc) + s_anc).
+ * SAGA  (§4, Eq. (saga_update)): f <- P>=0(f + alpha d (q_new - q_t + mean q)).
+ * SVRG  (§4, Eq. (svrg_update)):
+ *       f <- P>=0(f + alpha d (grad Phi_t(f) - grad Phi_t(f_anc) + q~)).
+ * Returns PET_ERR_STATE if the state was created for another algorithm. */
+pet_status pet_osem_epoch(pet_state *state, const int32_t *h_subset_seq, int32_t n_iter, void *stream);
+pet_status pet_svrem_epoch(pet_state *state, float alpha, int32_t eta, const int32_t *h_subset_seq,
+                           int32_t n_iter, void *stream);
+pet_status pet_saga_epoch(pet_state *state, float alpha, const int32_t *h_subset_seq, int32_t n_iter,
+                          void *stream);
+pet_status pet_svrg_epoch(pet_state *state, float alpha, int32_t eta, const int32_t *h_subset_seq,
+                          int32_t n_iter, void *stream);
+
+/* Synchronise `stream` and return any latched device-side error. */
+pet_status pet_state_sync(pet_state *state, void *stream);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t pet_kernel_launches(void);
+
+/* Optional per-kernel timing for profiling: while enabled, every forward and
+ * back-projection launch is bracketed by two CUDA events on its stream.
+ * pet_profile_read synchronises those events and returns, for kernel kind
+ * `kind` (0 forward, 1 back projection with update epilogue, 2 multi-subset
+ * back projection of an anchor pass or table fill), the number of launches
+ * and their summed duration in ms since the last reset.  Not thread-safe
+ * with respect to concurrent launches from several host threads. */
+pet_status pet_profile_enable(int32_t on);
+pet_status pet_profile_reset(void);
+pet_status pet_profile_read(int32_t kind, int64_t *h_launches, double *h_total_ms);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char *pet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PETVR_H */

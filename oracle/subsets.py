@@ -2,9 +2,10 @@
 
 The rows are split by view into N_s disjoint, nonempty subsets whose union is
 every row.  Views are dealt out angle-interleaved (view i goes to subset
-i mod N_s), which keeps the subsets balanced and each subset's views spread
-over [0, pi) as the paper recommends ("perpendicular" ordering, §2.1;
-§5.1 bins the 180 views into 15/30/45 subsets of 12/6/4 views).  When N_s
+i mod N_s), which keeps the subsets balanced and spreads each subset's views over
+[0, pi), so that consecutive subsets see nearly orthogonal views as §2.1
+recommends (§5.1 splits its 180 views into 15/30/45 subsets of 12/6/4
+views).  When N_s
 does not divide the number of views, the first n_angles mod N_s subsets get
 one extra view.
 """

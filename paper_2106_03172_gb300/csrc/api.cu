@@ -1,0 +1,723 @@
+// Host side of the C ABI declared in include/petvr.h: argument checking,
+// geometry tables, object lifetime and the per-update launch sequences.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "petvr_internal.cuh"
+
+namespace petvr {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_error;
+
+pet_status set_error(pet_status code, const std::string &msg) {
+    t_error = msg;
+    return code;
+}
+
+namespace {
+struct ProfileRecord {
+    int kind;
+    cudaEvent_t a, b;
+};
+std::atomic<bool> g_profile{false};
+std::mutex g_profile_mu;
+std::vector<ProfileRecord> g_profile_records;
+}  // namespace
+
+ProfileScope::ProfileScope(int k, cudaStream_t s) : kind(k), stream(s) {
+    if (!g_profile.load(std::memory_order_relaxed)) return;
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        ev[0] = ev[1] = nullptr;
+        return;
+    }
+    cudaEventRecord(ev[0], stream);
+}
+
+ProfileScope::~ProfileScope() {
+    if (!ev[0]) return;
+    cudaEventRecord(ev[1], stream);
+    std::lock_guard<std::mutex> lk(g_profile_mu);
+    g_profile_records.push_back({kind, ev[0], ev[1]});
+}
+
+pet_status check_launch(const char *what) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(PET_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return PET_OK;
+}
+
+namespace {
+
+constexpr long long kMaxElems = (1LL << 31) - 1;
+
+template <typename T>
+pet_status dalloc(T **p, size_t count, const char *what) {
+    *p = nullptr;
+    if (count == 0) return PET_OK;
+    const cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(e == cudaErrorMemoryAllocation ? PET_ERR_OOM : PET_ERR_CUDA,
+                         std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+    }
+    return PET_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+pet_status cuda_ok(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) return set_error(PET_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return PET_OK;
+}
+
+#define PET_TRY(expr)                          \
+    do {                                       \
+        const pet_status _st = (expr);         \
+        if (_st != PET_OK) return _st;         \
+    } while (0)
+
+double snap(double v) {
+    if (std::fabs(v) < 1e-12) return 0.0;
+    if (std::fabs(v - 1.0) < 1e-12) return 1.0;
+    if (std::fabs(v + 1.0) < 1e-12) return -1.0;
+    return v;
+}
+
+int max_sub_rays(const pet_plan *pl) { return pl->max_sub_views * pl->nb; }
+
+FwdArgs fwd_args(const pet_plan *pl, const float *img, int subset, bool natural) {
+    FwdArgs a{};
+    a.views = pl->d_views;
+    a.uc = pl->d_uc;
+    a.order = natural ? pl->d_natural : pl->d_order;
+    if (subset < 0) {
+        a.v_begin = 0;
+        a.v_end = pl->na;
+    } else {
+        a.v_begin = pl->sub_off[subset];
+        a.v_end = pl->sub_off[subset + 1];
+    }
+    a.nx = pl->nx;
+    a.ny = pl->ny;
+    a.nz = pl->nz;
+    a.nb = pl->nb;
+    a.img = img;
+    return a;
+}
+
+BackArgs back_args(const pet_plan *pl, const float *r, int subset, bool natural) {
+    BackArgs a{};
+    a.views = pl->d_views;
+    a.uc = pl->d_uc;
+    a.order = natural ? pl->d_natural : pl->d_order;
+    a.sub_off = natural ? pl->d_all_off : pl->d_sub_off;
+    a.t0 = subset < 0 ? 0 : subset;
+    a.r_view0 = subset < 0 ? 0 : pl->sub_off[subset];
+    a.nx = pl->nx;
+    a.ny = pl->ny;
+    a.nz = pl->nz;
+    a.nb = pl->nb;
+    a.ns = pl->ns;
+    a.r = r;
+    a.sens_t = pl->d_sens_t;
+    a.sens = pl->d_sens;
+    return a;
+}
+
+long long plane_of(const pet_plan *pl) { return (long long)pl->N * pl->nz; }
+
+// Subset-t ratio r_t = g_t / (A_t f + w_t) into `ratio` (compact).
+pet_status ratio_subset(const pet_problem *p, const float *f, int t, float *ratio, cudaStream_t s) {
+    const pet_plan *pl = p->plan;
+    FwdArgs a = fwd_args(pl, f, t, false);
+    const long long off = (long long)pl->sub_off[t] * pl->nb * pl->nz;
+    a.g = p->d_g + off;
+    a.w = p->d_w ? p->d_w + off : nullptr;
+    a.w_scalar = p->w_scalar;
+    a.out = ratio;
+    a.status = p->d_status;
+    return launch_forward(a, FWD_RATIO, false, choose_group(pl), s, nullptr);
+}
+
+// Full-data ratio in subset-major order into `ratio` (M * nz).
+pet_status ratio_all(const pet_problem *p, const float *f, float *ratio, cudaStream_t s) {
+    const pet_plan *pl = p->plan;
+    FwdArgs a = fwd_args(pl, f, -1, false);
+    a.g = p->d_g;
+    a.w = p->d_w;
+    a.w_scalar = p->w_scalar;
+    a.out = ratio;
+    a.status = p->d_status;
+    return launch_forward(a, FWD_RATIO, false, choose_group(pl), s, nullptr);
+}
+
+// n_iter updates with the iterate ping-ponging between the caller's image and
+// `alt`, arranged so that the last update writes the caller's image.
+template <class Step>
+pet_status pingpong(float *user, float *alt, long long plane, int n_iter, cudaStream_t s, Step &&step) {
+    if (n_iter <= 0) return PET_OK;
+    float *a = user, *b = alt;
+    if (n_iter % 2 == 1) {
+        PET_TRY(cuda_ok(cudaMemcpyAsync(alt, user, (size_t)plane * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                        "cudaMemcpyAsync"));
+        a = alt;
+        b = user;
+    }
+    for (int i = 0; i < n_iter; ++i) {
+        const float *in = (i % 2 == 0) ? a : b;
+        float *out = (i % 2 == 0) ? b : a;
+        PET_TRY(step(i, in, out));
+    }
+    return PET_OK;
+}
+
+pet_status check_seq(const pet_plan *pl, const int32_t *seq, int32_t n_iter) {
+    if (n_iter < 0) return set_error(PET_ERR_INVALID, "n_iter must be >= 0");
+    if (n_iter > 0 && !seq) return set_error(PET_ERR_INVALID, "null subset sequence");
+    for (int i = 0; i < n_iter; ++i)
+        if (seq[i] < 0 || seq[i] >= pl->ns)
+            return set_error(PET_ERR_INVALID, "subset index out of range at position " + std::to_string(i));
+    return PET_OK;
+}
+
+pet_status read_status(const pet_problem *p, cudaStream_t s) {
+    int h = 0;
+    PET_TRY(cuda_ok(cudaMemcpyAsync(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy"));
+    PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    if (h != 0) {
+        PET_TRY(cuda_ok(cudaMemsetAsync(p->d_status, 0, sizeof(int), s), "status reset"));
+        return set_error((pet_status)h, "device reported a numeric error (nonpositive expected count)");
+    }
+    return PET_OK;
+}
+
+}  // namespace
+}  // namespace petvr
+
+using namespace petvr;
+
+extern "C" {
+
+const char *pet_last_error(void) { return t_error.c_str(); }
+
+uint64_t pet_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pet_status pet_profile_enable(int32_t on) {
+    g_profile.store(on != 0);
+    return PET_OK;
+}
+
+pet_status pet_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_profile_mu);
+    for (auto &r : g_profile_records) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_profile_records.clear();
+    return PET_OK;
+}
+
+pet_status pet_profile_read(int32_t kind, int64_t *h_launches, double *h_total_ms) {
+    if (!h_launches || !h_total_ms) return set_error(PET_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(g_profile_mu);
+    int64_t n = 0;
+    double total = 0.0;
+    for (auto &r : g_profile_records) {
+        if (r.kind != kind) continue;
+        PET_TRY(cuda_ok(cudaEventSynchronize(r.b), "cudaEventSynchronize"));
+        float ms = 0.0f;
+        PET_TRY(cuda_ok(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime"));
+        total += ms;
+        ++n;
+    }
+    *h_launches = n;
+    *h_total_ms = total;
+    return PET_OK;
+}
+
+void pet_plan_destroy(pet_plan *pl) {
+    if (!pl) return;
+    dfree(pl->d_views);
+    dfree(pl->d_uc);
+    dfree(pl->d_order);
+    dfree(pl->d_natural);
+    dfree(pl->d_sub_off);
+    dfree(pl->d_all_off);
+    dfree(pl->d_sens_t);
+    dfree(pl->d_sens);
+    delete pl;
+}
+
+pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_plan **out) {
+    if (!g || !sub || !out) return set_error(PET_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->n_angles < 1 || g->n_bins < 1)
+        return set_error(PET_ERR_INVALID, "geometry sizes must be >= 1");
+    if (g->nx > 16384 || g->ny > 16384) return set_error(PET_ERR_INVALID, "nx, ny must be <= 16384");
+    if (!(g->pixel_mm > 0.0) || !std::isfinite(g->pixel_mm) || !std::isfinite(g->bin_mm))
+        return set_error(PET_ERR_INVALID, "pixel_mm must be positive and finite");
+    if (sub->scheme != 0) return set_error(PET_ERR_INVALID, "only the interleaved subset scheme (0) exists");
+    if (sub->n_subsets < 1 || sub->n_subsets > g->n_angles)
+        return set_error(PET_ERR_INVALID, "need 1 <= n_subsets <= n_angles");
+    const long long N = (long long)g->nx * g->ny, M = (long long)g->n_angles * g->n_bins;
+    if (N * g->nz > kMaxElems || M * g->nz > kMaxElems)
+        return set_error(PET_ERR_INVALID, "image or sinogram larger than 2^31 - 1 elements");
+
+    pet_plan *pl = new (std::nothrow) pet_plan();
+    if (!pl) return set_error(PET_ERR_OOM, "host allocation failed");
+    pl->geom = *g;
+    pl->nx = g->nx;
+    pl->ny = g->ny;
+    pl->nz = g->nz;
+    pl->na = g->n_angles;
+    pl->nb = g->n_bins;
+    pl->ns = sub->n_subsets;
+    pl->N = (int)N;
+    pl->M = (int)M;
+    cudaGetDevice(&pl->device);
+    const double d = g->pixel_mm;
+    const double ds = g->bin_mm > 0.0 ? g->bin_mm : d;
+
+    // per-view parameters and per-ray centred minor coordinates (FP64 -> FP32)
+    std::vector<ViewParams> views(pl->na);
+    std::vector<float> uc((size_t)M);
+    for (int i = 0; i < pl->na; ++i) {
+        const double th = (double)i * M_PI / (double)pl->na;
+        const double c = snap(std::cos(th)), s = snap(std::sin(th));
+        ViewParams vp{};
+        vp.col = std::fabs(c) < std::fabs(s) ? 1 : 0;
+        const double cm = vp.col ? s : c;          // direction cosine of the major axis
+        const double cn = vp.col ? c : s;          // of the minor axis
+        const int n_minor = vp.col ? pl->ny : pl->nx;
+        vp.du = (float)(-cn / cm);
+        vp.L = (float)(d / std::fabs(cm));
+        vp.Lm = cn != 0.0 ? (float)(d / std::fabs(cn)) : 0.0f;
+        vp.K = (float)(ds / (cm * d));
+        const double off = (n_minor % 2) ? 0.5 : 0.0;
+        for (int j = 0; j < pl->nb; ++j) {
+            const double sj = ((double)j - 0.5 * (pl->nb - 1)) * ds;
+            uc[(size_t)i * pl->nb + j] = (float)(sj / (cm * d) + off);
+        }
+        vp.uc0 = uc[(size_t)i * pl->nb];
+        views[i] = vp;
+    }
+    // angle-interleaved subsets: view i -> subset i mod ns
+    pl->sub_off.assign(pl->ns + 1, 0);
+    for (int t = 0; t < pl->ns; ++t) {
+        for (int i = t; i < pl->na; i += pl->ns) pl->order.push_back(i);
+        pl->sub_off[t + 1] = (int)pl->order.size();
+        pl->max_sub_views = std::max(pl->max_sub_views, pl->sub_off[t + 1] - pl->sub_off[t]);
+    }
+    std::vector<int> natural(pl->na);
+    for (int i = 0; i < pl->na; ++i) natural[i] = i;
+    const int all_off[2] = {0, pl->na};
+
+    pet_status st = PET_OK;
+    float *ones = nullptr;
+    auto fail = [&](pet_status e) {
+        dfree(ones);
+        pet_plan_destroy(pl);
+        return e;
+    };
+    if ((st = dalloc(&pl->d_views, pl->na, "views")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_uc, (size_t)M, "uc")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_order, pl->na, "order")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_natural, pl->na, "natural")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_sub_off, pl->ns + 1, "sub_off")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_all_off, 2, "all_off")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_sens_t, (size_t)pl->ns * N, "sens_t")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_sens, (size_t)N, "sens")) != PET_OK) return fail(st);
+    if ((st = dalloc(&ones, (size_t)M, "ones")) != PET_OK) return fail(st);
+    cudaError_t e = cudaSuccess;
+    e = cudaMemcpy(pl->d_views, views.data(), sizeof(ViewParams) * pl->na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_uc, uc.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_order, pl->order.data(), sizeof(int) * pl->na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_natural, natural.data(), sizeof(int) * pl->na, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_sub_off, pl->sub_off.data(), sizeof(int) * (pl->ns + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_all_off, all_off, sizeof(int) * 2, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_ok(e, "table upload"));
+    {
+        std::vector<float> h1((size_t)M, 1.0f);
+        e = cudaMemcpy(ones, h1.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_ok(e, "ones upload"));
+    }
+    // sens_t = A_t^T 1 for every subset (one slice: the geometry is shared by all slices)
+    BackArgs b = back_args(pl, ones, -1, false);
+    b.nz = 1;
+    b.t0 = 0;
+    b.r_view0 = 0;
+    b.out = pl->d_sens_t;
+    if ((st = launch_back(b, EPI_ANCHOR, PET_TABLE_FP32, pl->ns, 0)) != PET_OK) return fail(st);
+    if ((st = launch_sum_sens(pl->d_sens_t, pl->d_sens, pl->ns, pl->N, 0)) != PET_OK) return fail(st);
+    // nonzeros per subset, counted with the projector's own geometry
+    {
+        unsigned long long *d_cnt = nullptr;
+        if ((st = dalloc(&d_cnt, (size_t)pl->ns, "nnz")) != PET_OK) return fail(st);
+        e = cudaMemset(d_cnt, 0, sizeof(unsigned long long) * pl->ns);
+        for (int t = 0; t < pl->ns && e == cudaSuccess && st == PET_OK; ++t) {
+            FwdArgs a = fwd_args(pl, nullptr, t, false);
+            a.nz = 1;
+            st = launch_count_nnz(a, d_cnt + t, 0);
+        }
+        std::vector<unsigned long long> h((size_t)pl->ns, 0);
+        if (e == cudaSuccess && st == PET_OK)
+            e = cudaMemcpy(h.data(), d_cnt, sizeof(unsigned long long) * pl->ns, cudaMemcpyDeviceToHost);
+        dfree(d_cnt);
+        if (st != PET_OK) return fail(st);
+        if (e != cudaSuccess) return fail(cuda_ok(e, "nnz count"));
+        pl->nnz.assign(h.begin(), h.end());
+    }
+    e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return fail(cuda_ok(e, "plan sensitivity"));
+    dfree(ones);
+    *out = pl;
+    return PET_OK;
+}
+
+pet_status pet_plan_subset_views(const pet_plan *pl, int32_t t, int32_t *h_n) {
+    if (!pl || !h_n) return set_error(PET_ERR_INVALID, "null argument");
+    if (t < -1 || t >= pl->ns) return set_error(PET_ERR_INVALID, "subset out of range");
+    *h_n = t < 0 ? pl->na : pl->sub_off[t + 1] - pl->sub_off[t];
+    return PET_OK;
+}
+
+pet_status pet_plan_nnz(const pet_plan *pl, int32_t t, int64_t *h_nnz) {
+    if (!pl || !h_nnz) return set_error(PET_ERR_INVALID, "null argument");
+    if (t < -1 || t >= pl->ns) return set_error(PET_ERR_INVALID, "subset out of range");
+    long long n = 0;
+    for (int i = 0; i < pl->ns; ++i)
+        if (t < 0 || i == t) n += pl->nnz[i];
+    *h_nnz = n;
+    return PET_OK;
+}
+
+pet_status pet_plan_sensitivity(const pet_plan *pl, int32_t t, float *d_out, void *stream) {
+    if (!pl || !d_out) return set_error(PET_ERR_INVALID, "null argument");
+    if (t < -1 || t >= pl->ns) return set_error(PET_ERR_INVALID, "subset out of range");
+    const float *src = t < 0 ? pl->d_sens : pl->d_sens_t + (size_t)t * pl->N;
+    return cuda_ok(cudaMemcpyAsync(d_out, src, sizeof(float) * pl->N, cudaMemcpyDeviceToDevice,
+                                   (cudaStream_t)stream),
+                   "sensitivity copy");
+}
+
+pet_status pet_forward(const pet_plan *pl, const float *d_img, const float *d_bg, float bg, int32_t subset,
+                       float *d_sino, void *stream) {
+    if (!pl || !d_img || !d_sino) return set_error(PET_ERR_INVALID, "null argument");
+    if (subset < -1 || subset >= pl->ns) return set_error(PET_ERR_INVALID, "subset out of range");
+    if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
+    FwdArgs a = fwd_args(pl, d_img, subset, subset < 0);
+    a.w = d_bg;
+    a.w_scalar = bg;
+    a.out = d_sino;
+    return launch_forward(a, FWD_YHAT, false, choose_group(pl), (cudaStream_t)stream, nullptr);
+}
+
+pet_status pet_back(const pet_plan *pl, const float *d_sino, int32_t subset, float *d_img, void *stream) {
+    if (!pl || !d_img || !d_sino) return set_error(PET_ERR_INVALID, "null argument");
+    if (subset < -1 || subset >= pl->ns) return set_error(PET_ERR_INVALID, "subset out of range");
+    BackArgs b = back_args(pl, d_sino, subset, subset < 0);
+    b.out = d_img;
+    return launch_back(b, EPI_PLAIN, PET_TABLE_FP32, 1, (cudaStream_t)stream);
+}
+
+void pet_problem_destroy(pet_problem *p) {
+    if (!p) return;
+    dfree(p->d_g);
+    dfree(p->d_w);
+    dfree(p->d_ratio);
+    dfree(p->d_alt);
+    dfree(p->d_part);
+    dfree(p->d_scalar);
+    dfree(p->d_status);
+    delete p;
+}
+
+pet_status pet_problem_create(const pet_plan *pl, const float *d_counts, const float *d_bg, float bg,
+                              const pet_penalty *pen, pet_problem **out, void *stream) {
+    if (!pl || !d_counts || !pen || !out) return set_error(PET_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (pen->potential != PET_POT_QUADRATIC) return set_error(PET_ERR_INVALID, "only the quadratic potential exists");
+    if (!(pen->beta >= 0.0f) || !std::isfinite(pen->beta)) return set_error(PET_ERR_INVALID, "beta must be >= 0");
+    if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    pet_problem *p = new (std::nothrow) pet_problem();
+    if (!p) return set_error(PET_ERR_OOM, "host allocation failed");
+    p->plan = pl;
+    p->pen = *pen;
+    p->w_scalar = bg;
+    const size_t Mz = (size_t)pl->M * pl->nz, Nz = (size_t)pl->N * pl->nz;
+    const int group = choose_group(pl);
+    p->n_part = forward_blocks(pl->M, pl->nz, group) + (int)((Nz + 255) / 256);
+    pet_status st;
+    auto fail = [&](pet_status e) {
+        pet_problem_destroy(p);
+        return e;
+    };
+    if ((st = dalloc(&p->d_g, Mz, "counts")) != PET_OK) return fail(st);
+    if (d_bg && (st = dalloc(&p->d_w, Mz, "background")) != PET_OK) return fail(st);
+    if ((st = dalloc(&p->d_ratio, Mz, "ratio")) != PET_OK) return fail(st);
+    if ((st = dalloc(&p->d_alt, Nz, "alt image")) != PET_OK) return fail(st);
+    if ((st = dalloc(&p->d_part, (size_t)p->n_part, "partials")) != PET_OK) return fail(st);
+    if ((st = dalloc(&p->d_scalar, (size_t)pl->nz + 8, "scalars")) != PET_OK) return fail(st);
+    if ((st = dalloc(&p->d_status, 1, "status")) != PET_OK) return fail(st);
+    if ((st = cuda_ok(cudaMemsetAsync(p->d_status, 0, sizeof(int), s), "memset")) != PET_OK) return fail(st);
+    if ((st = launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, pl->nz, s)) != PET_OK)
+        return fail(st);
+    if (d_bg && (st = launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, pl->nz, s)) != PET_OK)
+        return fail(st);
+    *out = p;
+    return PET_OK;
+}
+
+pet_status pet_problem_update(pet_problem *p, const float *d_counts, const float *d_bg, float bg, void *stream) {
+    if (!p || !d_counts) return set_error(PET_ERR_INVALID, "null argument");
+    if ((d_bg != nullptr) != (p->d_w != nullptr))
+        return set_error(PET_ERR_INVALID, "background kind differs from the one the problem was created with");
+    if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
+    const pet_plan *pl = p->plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->w_scalar = bg;
+    PET_TRY(launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, pl->nz, s));
+    if (d_bg) PET_TRY(launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, pl->nz, s));
+    return PET_OK;
+}
+
+pet_status pet_warm_start(const pet_problem *p, float *d_img, void *stream) {
+    if (!p || !d_img) return set_error(PET_ERR_INVALID, "null argument");
+    const pet_plan *pl = p->plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    PET_TRY(launch_uniform_image(p, d_img, s));
+    return pingpong(d_img, p->d_alt, plane_of(pl), pl->ns, s, [&](int i, const float *in, float *outp) {
+        PET_TRY(ratio_subset(p, in, i, p->d_ratio, s));
+        BackArgs b = back_args(pl, p->d_ratio, i, false);
+        b.f = in;
+        b.f_out = outp;
+        b.beta = 0.0f;
+        return launch_back(b, EPI_OSEM, PET_TABLE_FP32, 1, s);
+    });
+}
+
+pet_status pet_objective_async(const pet_problem *p, const float *d_img, double *d_phi, void *stream) {
+    if (!p || !d_img || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
+    const pet_plan *pl = p->plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    FwdArgs a = fwd_args(pl, d_img, -1, false);
+    a.g = p->d_g;
+    a.w = p->d_w;
+    a.w_scalar = p->w_scalar;
+    a.ll_partials = p->d_part;
+    a.status = p->d_status;
+    int n_ll = 0;
+    PET_TRY(launch_forward(a, FWD_NONE, true, choose_group(pl), s, &n_ll));
+    return launch_objective_finish(p, d_img, n_ll, d_phi, s);
+}
+
+pet_status pet_objective(const pet_problem *p, const float *d_img, double *h_phi, void *stream) {
+    if (!p || !d_img || !h_phi) return set_error(PET_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    PET_TRY(pet_objective_async(p, d_img, p->d_scalar, stream));
+    PET_TRY(cuda_ok(cudaMemcpyAsync(h_phi, p->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s), "phi copy"));
+    return read_status(p, s);
+}
+
+pet_status pet_state_destroy(pet_state *st) {
+    if (!st) return PET_OK;
+    dfree(st->alt);
+    dfree(st->ratio);
+    dfree(st->ratio_full);
+    dfree(st->s_hat);
+    dfree(st->f_anc);
+    dfree(st->s_anc);
+    dfree(st->B);
+    dfree(st->d);
+    dfree(st->qbar);
+    dfree(st->qtil);
+    if (st->table) cudaFree(st->table);
+    delete st;
+    return PET_OK;
+}
+
+pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dtype, float *d_img,
+                            size_t *bytes_needed, pet_state **out, void *stream) {
+    if (!p) return set_error(PET_ERR_INVALID, "null problem");
+    if (algo < PET_ALGO_OSEM || algo > PET_ALGO_SVRG) return set_error(PET_ERR_INVALID, "unknown algorithm");
+    if (table_dtype != PET_TABLE_FP32 && table_dtype != PET_TABLE_BF16)
+        return set_error(PET_ERR_INVALID, "unknown table dtype");
+    const pet_plan *pl = p->plan;
+    const size_t Nz = (size_t)pl->N * pl->nz;
+    const size_t table_bytes = (size_t)pl->ns * Nz * (table_dtype == PET_TABLE_BF16 ? 2 : 4);
+    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * pl->nz * 4;
+    if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
+    if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
+    if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
+    if (bytes_needed) *bytes_needed = bytes;
+    if (!out) return PET_OK;
+    *out = nullptr;
+    if (!d_img) return set_error(PET_ERR_INVALID, "null image");
+    cudaStream_t s = (cudaStream_t)stream;
+    pet_state *st = new (std::nothrow) pet_state();
+    if (!st) return set_error(PET_ERR_OOM, "host allocation failed");
+    st->prob = p;
+    st->algo = algo;
+    st->table_dtype = table_dtype;
+    st->img = d_img;
+    st->bytes = bytes;
+    pet_status e;
+    auto fail = [&](pet_status code) {
+        pet_state_destroy(st);
+        return code;
+    };
+    const size_t Mz = (size_t)pl->M * pl->nz;
+    if ((e = dalloc(&st->alt, Nz, "alt")) != PET_OK) return fail(e);
+    if ((e = dalloc(&st->ratio, (size_t)max_sub_rays(pl) * pl->nz, "ratio")) != PET_OK) return fail(e);
+    if (algo == PET_ALGO_SVREM) {
+        if ((e = dalloc(&st->s_hat, Nz, "s_hat")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->f_anc, Nz, "f_anc")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->s_anc, Nz, "s_anc")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->B, (size_t)pl->ns * Nz, "B")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->ratio_full, Mz, "full ratio")) != PET_OK) return fail(e);
+    } else if (algo == PET_ALGO_SVRG) {
+        if ((e = dalloc(&st->d, Nz, "d")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->qtil, Nz, "q_tilde")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->B, (size_t)pl->ns * Nz, "B")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->ratio_full, Mz, "full ratio")) != PET_OK) return fail(e);
+        if ((e = launch_precond(d_img, pl->d_sens, pl->ns, (long long)Nz, pl->nz, st->d, s)) != PET_OK)
+            return fail(e);
+    } else if (algo == PET_ALGO_SAGA) {
+        if ((e = dalloc(&st->d, Nz, "d")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->qbar, Nz, "qbar")) != PET_OK) return fail(e);
+        const cudaError_t ce = cudaMalloc(&st->table, table_bytes);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            st->table = nullptr;
+            return fail(set_error(PET_ERR_OOM, "cudaMalloc SAGA table"));
+        }
+        // table q_t = grad Phi_t(f^(0)) for all t, then qbar and d
+        if ((e = ratio_all(p, d_img, p->d_ratio, s)) != PET_OK) return fail(e);
+        BackArgs b = back_args(pl, p->d_ratio, -1, false);
+        b.t0 = 0;
+        b.r_view0 = 0;
+        b.f = d_img;
+        b.beta = p->pen.beta;
+        b.table = st->table;
+        if ((e = launch_back(b, EPI_SAGA_INIT, table_dtype, pl->ns, s)) != PET_OK) return fail(e);
+        if ((e = launch_saga_finish(st->table, table_dtype, pl->ns, (long long)Nz, pl->nz, d_img, pl->d_sens,
+                                    st->qbar, st->d, s)) != PET_OK)
+            return fail(e);
+    }
+    *out = st;
+    return PET_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Anchor pass at f: B_t = A_t^T r_t(f) for every t, into st->B, one forward
+// launch over all rays and one back launch over all subsets (grid.y = t).
+pet_status anchor_pass(pet_state *st, const float *f, float *ratio_full, cudaStream_t s) {
+    const pet_problem *p = st->prob;
+    const pet_plan *pl = p->plan;
+    PET_TRY(ratio_all(p, f, ratio_full, s));
+    BackArgs b = back_args(pl, ratio_full, -1, false);
+    b.t0 = 0;
+    b.r_view0 = 0;
+    b.out = st->B;
+    return launch_back(b, EPI_ANCHOR, PET_TABLE_FP32, pl->ns, s);
+}
+
+pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_iter, float alpha, int32_t eta,
+                        cudaStream_t s) {
+    if (!st) return set_error(PET_ERR_INVALID, "null state");
+    if (st->algo != algo) return set_error(PET_ERR_STATE, "state was created for another algorithm");
+    const pet_problem *p = st->prob;
+    const pet_plan *pl = p->plan;
+    PET_TRY(check_seq(pl, seq, n_iter));
+    if (!std::isfinite(alpha)) return set_error(PET_ERR_INVALID, "alpha must be finite");
+    if ((algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) && eta < 1)
+        return set_error(PET_ERR_INVALID, "eta must be >= 1");
+    const long long plane = plane_of(pl);
+    return pingpong(st->img, st->alt, plane, n_iter, s, [&](int i, const float *in, float *outp) {
+        const int t = seq[i];
+        const bool anchor = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) &&
+                            (st->k % ((long long)eta * pl->ns) == 0);
+        if (anchor && algo == PET_ALGO_SVREM) {
+            PET_TRY(cuda_ok(cudaMemcpyAsync(st->f_anc, in, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
+                            "anchor copy"));
+            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+            PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, st->f_anc, st->s_anc, st->s_hat,
+                                               st->k == 0, s));
+        } else if (anchor && algo == PET_ALGO_SVRG) {
+            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+            PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
+        }
+        PET_TRY(ratio_subset(p, in, t, st->ratio, s));
+        BackArgs b = back_args(pl, st->ratio, t, false);
+        b.f = in;
+        b.f_out = outp;
+        b.beta = p->pen.beta;
+        b.alpha = alpha;
+        int epi = EPI_OSEM;
+        if (algo == PET_ALGO_SVREM) {
+            epi = EPI_SVREM;
+            b.s_hat = st->s_hat;
+            b.f_anc = st->f_anc;
+            b.s_anc = st->s_anc;
+            b.B = st->B;
+        } else if (algo == PET_ALGO_SAGA) {
+            epi = EPI_SAGA;
+            b.d = st->d;
+            b.table = st->table;
+            b.qbar = st->qbar;
+        } else if (algo == PET_ALGO_SVRG) {
+            epi = EPI_SVRG;
+            b.d = st->d;
+            b.B = st->B;
+            b.qtil = st->qtil;
+        }
+        PET_TRY(launch_back(b, epi, st->table_dtype, 1, s));
+        st->k += 1;
+        return PET_OK;
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+pet_status pet_osem_epoch(pet_state *st, const int32_t *seq, int32_t n_iter, void *stream) {
+    return epoch_common(st, PET_ALGO_OSEM, seq, n_iter, 0.0f, 1, (cudaStream_t)stream);
+}
+
+pet_status pet_svrem_epoch(pet_state *st, float alpha, int32_t eta, const int32_t *seq, int32_t n_iter,
+                           void *stream) {
+    return epoch_common(st, PET_ALGO_SVREM, seq, n_iter, alpha, eta, (cudaStream_t)stream);
+}
+
+pet_status pet_saga_epoch(pet_state *st, float alpha, const int32_t *seq, int32_t n_iter, void *stream) {
+    return epoch_common(st, PET_ALGO_SAGA, seq, n_iter, alpha, 1, (cudaStream_t)stream);
+}
+
+pet_status pet_svrg_epoch(pet_state *st, float alpha, int32_t eta, const int32_t *seq, int32_t n_iter,
+                          void *stream) {
+    return epoch_common(st, PET_ALGO_SVRG, seq, n_iter, alpha, eta, (cudaStream_t)stream);
+}
+
+pet_status pet_state_sync(pet_state *st, void *stream) {
+    if (!st) return set_error(PET_ERR_INVALID, "null state");
+    return read_status(st->prob, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Back projection as a pixel-driven gather (K2), fused with the per-pixel
+// update of each method (K3).
+//
+// b_n = sum_{m in S_t} a_mn r_m: one thread per (pixel, slice) walks the
+// views of the subset; in each view only the 1-4 bins whose ray crosses the
+// pixel's major band near the pixel are candidates, found from the bin
+// spacing K, and each candidate's weight comes from band_weights(), the same
+// function the forward kernel uses, so A^T here is the exact transpose of A
+// there.  A gather (not atomics) keeps the result deterministic.
+//
+// The epilogue then applies, with b_n still in a register (§8 of the method's
+// update rules; the quadratic 4-neighbour penalty of §3 is read from f^k):
+//   OSEM   f' = root(a = f b, S = sens_t, beta / N_s)                (§2.2, §3)
+//   SVREM  s' = (1-alpha) s + alpha (N_s f b - N_s f_anc B_t + s_anc),
+//          f' = root(a = s', S = sens, beta)                        (§2.3, §3)
+//   SAGA   q = b - sens_t - (beta/N_s) grad R(f);
+//          f' = max(0, f + alpha d (q - q_t + qbar)); qbar += (q - q_t)/N_s;
+//          q_t = q                                                  (§4)
+//   SVRG   f' = max(0, f + alpha d (b - B_t - (beta/N_s) grad R(f) + q~))
+//          (the anchor's penalty terms cancel against those inside q~) (§4)
+//   ANCHOR B_t = b for every subset t at once (grid.y = t)
+//   SAGA_INIT table_t = b - sens_t - (beta/N_s) grad R(f) for every t.
+#include "petvr_internal.cuh"
+
+namespace petvr {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct Stencil {
+    float cnt;   // number of in-image 4-neighbours (sum_j d_nj for the quadratic potential)
+    float sum;   // sum_j f_j
+};
+
+__device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int nx, int ny, int nz,
+                                            int z) {
+    Stencil s{0.0f, 0.0f};
+    if (ix > 0) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)iy * nx + ix - 1) * nz + z); }
+    if (ix + 1 < nx) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)iy * nx + ix + 1) * nz + z); }
+    if (iy > 0) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)(iy - 1) * nx + ix) * nz + z); }
+    if (iy + 1 < ny) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)(iy + 1) * nx + ix) * nz + z); }
+    return s;
+}
+
+template <typename T> __device__ __forceinline__ float load_q(const void *p, long long i);
+template <> __device__ __forceinline__ float load_q<float>(const void *p, long long i) {
+    return static_cast<const float *>(p)[i];
+}
+template <> __device__ __forceinline__ float load_q<__nv_bfloat16>(const void *p, long long i) {
+    return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+}
+template <typename T> __device__ __forceinline__ float round_q(float x);
+template <> __device__ __forceinline__ float round_q<float>(float x) { return x; }
+template <> __device__ __forceinline__ float round_q<__nv_bfloat16>(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+template <typename T> __device__ __forceinline__ void store_q(void *p, long long i, float x);
+template <> __device__ __forceinline__ void store_q<float>(void *p, long long i, float x) {
+    static_cast<float *>(p)[i] = x;
+}
+template <> __device__ __forceinline__ void store_q<__nv_bfloat16>(void *p, long long i, float x) {
+    static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(x);
+}
+
+template <int EPI, typename TQ>
+__global__ void __launch_bounds__(kBlock) back_kernel(const BackArgs a) {
+    const long long plane = (long long)a.nx * a.ny * a.nz;
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;   // (pixel, slice)
+    if (i >= plane) return;
+    const int t = a.t0 + (int)blockIdx.y;
+    const int z = (int)(i % a.nz);
+    const int n = (int)(i / a.nz);
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+    const int vb = __ldg(a.sub_off + t);
+    const int ve = __ldg(a.sub_off + t + 1);
+
+    float acc = 0.0f;
+    for (int p = vb; p < ve; ++p) {
+        const int v = __ldg(a.order + p);
+        const ViewParams vp = a.views[v];
+        const int k = vp.col ? ix : iy;                 // major index
+        const int minor = vp.col ? iy : ix;
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const int mrel = minor - (n_minor >> 1);
+        const float kc = (float)k - 0.5f * (float)n_major;
+        // bins whose band interval can overlap [mrel, mrel + 1]
+        const float base = fmaf(kc, vp.du, vp.uc0);
+        const float e1 = ((float)mrel - fmaxf(vp.du, 0.0f) - base) / vp.K;
+        const float e2 = ((float)mrel + 1.0f - fminf(vp.du, 0.0f) - base) / vp.K;
+        const int jlo = max(0, (int)floorf(fminf(e1, e2)) - 1);
+        const int jhi = min(a.nb - 1, (int)ceilf(fmaxf(e1, e2)) + 1);
+        const float *rv = a.r + ((long long)(p - a.r_view0) * a.nb) * a.nz + z;
+        const float *ucv = a.uc + (long long)v * a.nb;
+        for (int j = jlo; j <= jhi; ++j) {
+            int c0;
+            float w0, w1;
+            band_weights(vp, __ldg(ucv + j), kc, c0, w0, w1);
+            const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
+            if (w != 0.0f) acc = fmaf(w, __ldg(rv + (long long)j * a.nz), acc);
+        }
+    }
+
+    const float inv_ns = 1.0f / (float)a.ns;
+    if (EPI == EPI_PLAIN) {
+        a.out[i] = acc;
+    } else if (EPI == EPI_ANCHOR) {
+        a.out[(long long)t * plane + i] = acc;
+    } else if (EPI == EPI_OSEM) {
+        const float fk = a.f[i];
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
+        const float bp = a.beta * inv_ns;
+        const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+        const float c = bp * fmaf(fk, st.cnt, st.sum) - S;
+        a.f_out[i] = m_step_root(fk * acc, S, bp * st.cnt, c);
+    } else if (EPI == EPI_SVREM) {
+        const float fk = a.f[i];
+        const float ns = (float)a.ns;
+        const float Bt = a.B[(long long)t * plane + i];
+        const float tau = ns * fk * acc - ns * a.f_anc[i] * Bt + a.s_anc[i];
+        const float s = fmaf(a.alpha, tau, (1.0f - a.alpha) * a.s_hat[i]);
+        a.s_hat[i] = s;
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
+        const float S = __ldg(a.sens + n);
+        const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
+        a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
+    } else if (EPI == EPI_SAGA || EPI == EPI_SAGA_INIT) {
+        const float fk = a.f[i];
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
+        const float gradR = fk * st.cnt - st.sum;
+        const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+        const float q = round_q<TQ>(acc - S - a.beta * inv_ns * gradR);
+        const long long qi = (long long)t * plane + i;
+        if (EPI == EPI_SAGA_INIT) {
+            store_q<TQ>(a.table, qi, q);
+        } else {
+            const float q_old = load_q<TQ>(a.table, qi);
+            const float qb = a.qbar[i];
+            const float step = fmaf(a.alpha * a.d[i], q - q_old + qb, fk);
+            a.f_out[i] = fmaxf(step, 0.0f);
+            a.qbar[i] = fmaf(q - q_old, inv_ns, qb);
+            store_q<TQ>(a.table, qi, q);
+        }
+    } else if (EPI == EPI_SVRG) {
+        const float fk = a.f[i];
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
+        const float gradR = fk * st.cnt - st.sum;
+        const float Bt = a.B[(long long)t * plane + i];
+        const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
+        a.f_out[i] = fmaxf(fmaf(a.alpha * a.d[i], dir, fk), 0.0f);
+    }
+}
+
+template <int EPI, typename TQ>
+pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s) {
+    const long long plane = (long long)a.nx * a.ny * a.nz;
+    const dim3 grid((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)ny_grid);
+    back_kernel<EPI, TQ><<<grid, kBlock, 0, s>>>(a);
+    return check_launch("back_kernel");
+}
+
+}  // namespace
+
+pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
+                       cudaStream_t s) {
+    const bool bf = table_dtype == PET_TABLE_BF16;
+    ProfileScope prof(n_subsets_grid > 1 ? 2 : 1, s);
+    switch (epi) {
+        case EPI_PLAIN: return go<EPI_PLAIN, float>(a, n_subsets_grid, s);
+        case EPI_OSEM: return go<EPI_OSEM, float>(a, n_subsets_grid, s);
+        case EPI_SVREM: return go<EPI_SVREM, float>(a, n_subsets_grid, s);
+        case EPI_SVRG: return go<EPI_SVRG, float>(a, n_subsets_grid, s);
+        case EPI_ANCHOR: return go<EPI_ANCHOR, float>(a, n_subsets_grid, s);
+        case EPI_SAGA:
+            return bf ? go<EPI_SAGA, __nv_bfloat16>(a, n_subsets_grid, s)
+                      : go<EPI_SAGA, float>(a, n_subsets_grid, s);
+        case EPI_SAGA_INIT:
+            return bf ? go<EPI_SAGA_INIT, __nv_bfloat16>(a, n_subsets_grid, s)
+                      : go<EPI_SAGA_INIT, float>(a, n_subsets_grid, s);
+        default: return set_error(PET_ERR_INVALID, "back: unknown epilogue");
+    }
+}
+
+}  // namespace petvr

@@ -1,0 +1,200 @@
+// Forward projection with the Poisson-ratio epilogue (K1).
+//
+// yhat_m = sum_n a_mn f_n + w_m for the rays m of a view range (§2.1,
+// Eq. (voxel_td)); in ratio mode the kernel writes r_m = g_m / yhat_m (the
+// ratio inside every E-step and gradient, §2.2 Eq. (EMsurrogate), §2.3
+// Eq. (tau_t), §4 Eq. (osem_additive)), 0 when yhat_m = 0 (§2.3 remedy), and
+// optionally reduces the FP64 log-likelihood sum_m g_m log yhat_m - yhat_m
+// (§2.1, Eq. (log_likelihood)) to one partial per block.
+//
+// Thread layout: GROUP consecutive lanes share one ray (single-slice images),
+// each walking a contiguous chunk of the ray's major bands, then an xor-
+// shuffle all-reduce combines the chunks in a fixed order (deterministic).
+// For slice stacks (nz > 1) lanes run along the slice index instead
+// (GROUP = 1): consecutive lanes read consecutive floats of one pixel column.
+#include "petvr_internal.cuh"
+
+namespace petvr {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int GROUP, int MODE, bool LL>
+__global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
+    const long long n_rays = (long long)(a.v_end - a.v_begin) * a.nb;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const int z = (int)(tid % a.nz);
+    const long long rest = tid / a.nz;
+    const int lane_g = (int)(rest % GROUP);
+    const long long ray = rest / GROUP;
+    const bool live = ray < n_rays;
+
+    float acc = 0.0f;
+    if (live) {
+        const int p = a.v_begin + (int)(ray / a.nb);
+        const int j = (int)(ray % a.nb);
+        const int v = __ldg(a.order + p);
+        const ViewParams vp = a.views[v];
+        const float uc = __ldg(a.uc + (long long)v * a.nb + j);
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const int s_major = vp.col ? 1 : a.nx;
+        const int s_minor = vp.col ? a.nx : 1;
+        const int mo = n_minor >> 1;
+        const float hm = 0.5f * (float)n_major;
+        // bands where the ray can meet the image (a superset; extra bands add 0)
+        int k_lo = 0, k_hi = n_major;
+        if (vp.du == 0.0f) {
+            if (!(uc >= (float)(-mo) && uc < (float)(n_minor - mo))) k_hi = 0;
+        } else {
+            const float ka = hm + ((float)(-mo - 1) - uc) / vp.du;
+            const float kb = hm + ((float)(n_minor - mo + 1) - uc) / vp.du;
+            const float kmax = (float)n_major + 1.0f;
+            const float klo = fminf(fmaxf(fminf(ka, kb), -1.0f), kmax);
+            const float khi = fmaxf(fminf(fmaxf(ka, kb), kmax), -1.0f);
+            k_lo = max(0, (int)floorf(klo) - 1);
+            k_hi = min(n_major, (int)ceilf(khi) + 1);
+        }
+        const int cnt = max(0, k_hi - k_lo);
+        const int per = (cnt + GROUP - 1) / GROUP;
+        const int kb = k_lo + lane_g * per;
+        const int ke = min(k_hi, kb + per);
+        const float *img = a.img + z;
+        const long long sm = (long long)s_minor * a.nz;
+        for (int k = kb; k < ke; ++k) {
+            int c0;
+            float w0, w1;
+            band_weights(vp, uc, (float)k - hm, c0, w0, w1);
+            const int m0 = c0 + mo;
+            const float *row = img + (long long)k * s_major * a.nz;
+            if ((unsigned)m0 < (unsigned)n_minor) acc = fmaf(w0, __ldg(row + m0 * sm), acc);
+            if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor)
+                acc = fmaf(w1, __ldg(row + (m0 + 1) * sm), acc);
+        }
+    }
+#pragma unroll
+    for (int o = GROUP / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+
+    double ll = 0.0;
+    if (live && lane_g == 0) {
+        const long long idx = ray * a.nz + z;
+        const float yhat = acc + (a.w ? __ldg(a.w + idx) : a.w_scalar);
+        if (MODE == FWD_YHAT) a.out[idx] = yhat;
+        if (MODE == FWD_RATIO || LL) {
+            const float g = __ldg(a.g + idx);
+            if (MODE == FWD_RATIO) a.out[idx] = (yhat != 0.0f) ? g / yhat : 0.0f;
+            if (LL) {
+                if (yhat > 0.0f) {
+                    const double y = (double)yhat;
+                    ll = (g > 0.0f ? (double)g * log(y) : 0.0) - y;
+                } else if (g > 0.0f) {
+                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
+                } else {
+                    ll = -(double)yhat;
+                }
+            }
+        }
+    }
+    if (LL) {
+        __shared__ double red[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < kBlock / 32; ++i) s += red[i];
+            a.ll_partials[blockIdx.x] = s;
+        }
+    }
+}
+
+// Nonzeros of the rays of a view range: band pieces of positive length that
+// fall inside the image (one thread per ray, same geometry as the projector).
+__global__ void __launch_bounds__(kBlock) count_nnz_kernel(const FwdArgs a, unsigned long long *count) {
+    const long long n_rays = (long long)(a.v_end - a.v_begin) * a.nb;
+    const long long ray = (long long)blockIdx.x * kBlock + threadIdx.x;
+    unsigned long long c = 0;
+    if (ray < n_rays) {
+        const int p = a.v_begin + (int)(ray / a.nb);
+        const int j = (int)(ray % a.nb);
+        const int v = a.order[p];
+        const ViewParams vp = a.views[v];
+        const float uc = a.uc[(long long)v * a.nb + j];
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const int mo = n_minor >> 1;
+        const float hm = 0.5f * (float)n_major;
+        for (int k = 0; k < n_major; ++k) {
+            int c0;
+            float w0, w1;
+            band_weights(vp, uc, (float)k - hm, c0, w0, w1);
+            const int m0 = c0 + mo;
+            c += (w0 > 0.0f && (unsigned)m0 < (unsigned)n_minor) ? 1 : 0;
+            c += (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+template <int GROUP>
+pet_status dispatch_mode(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    if (mode == FWD_YHAT && !ll)
+        forward_kernel<GROUP, FWD_YHAT, false><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && !ll)
+        forward_kernel<GROUP, FWD_RATIO, false><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && ll)
+        forward_kernel<GROUP, FWD_RATIO, true><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_NONE && ll)
+        forward_kernel<GROUP, FWD_NONE, true><<<blocks, kBlock, 0, s>>>(a);
+    else
+        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
+    return check_launch("forward_kernel");
+}
+
+}  // namespace
+
+pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s) {
+    const int n_rays = (a.v_end - a.v_begin) * a.nb;
+    if (n_rays == 0) return PET_OK;
+    count_nnz_kernel<<<(n_rays + kBlock - 1) / kBlock, kBlock, 0, s>>>(a, d_count);
+    return check_launch("count_nnz_kernel");
+}
+
+int forward_blocks(int n_rays, int nz, int group) {
+    const long long threads = (long long)n_rays * nz * group;
+    return (int)((threads + kBlock - 1) / kBlock);
+}
+
+int choose_group(const pet_plan *plan) {
+    if (plan->nz > 1) return 1;
+    const int n = plan->nx > plan->ny ? plan->nx : plan->ny;
+    if (n >= 384) return 32;
+    if (n >= 192) return 16;
+    if (n >= 96) return 8;
+    return 4;
+}
+
+pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s,
+                          int *n_blocks_out) {
+    const int n_rays = (a.v_end - a.v_begin) * a.nb;
+    const int blocks = forward_blocks(n_rays, a.nz, group);
+    if (n_blocks_out) *n_blocks_out = blocks;
+    if (blocks == 0) return PET_OK;
+    if (a.nz > 1 && group != 1) return set_error(PET_ERR_INVALID, "forward: slice stacks use group 1");
+    ProfileScope prof(0, s);
+    switch (group) {
+        case 1: return dispatch_mode<1>(a, mode, ll, blocks, s);
+        case 4: return dispatch_mode<4>(a, mode, ll, blocks, s);
+        case 8: return dispatch_mode<8>(a, mode, ll, blocks, s);
+        case 16: return dispatch_mode<16>(a, mode, ll, blocks, s);
+        case 32: return dispatch_mode<32>(a, mode, ll, blocks, s);
+        default: return set_error(PET_ERR_INVALID, "forward: unsupported lane group");
+    }
+}
+
+}  // namespace petvr

@@ -1,0 +1,225 @@
+// Small streaming kernels: data permutation, sensitivity sum, warm-start
+// image, FP64 objective reduction, anchor and table bookkeeping.
+#include "petvr_internal.cuh"
+
+namespace petvr {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// dst[p][j][z] = src[order[p]][j][z]: natural view order -> subset-major order.
+__global__ void permute_kernel(const float *src, float *dst, const int *order, int na, int nb, int nz) {
+    const long long row = (long long)nb * nz;
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= row * na) return;
+    const int p = (int)(i / row);
+    const long long r = i % row;
+    dst[i] = src[(long long)order[p] * row + r];
+}
+
+// sens = sum_t sens_t, summed in FP64.
+__global__ void sum_sens_kernel(const float *sens_t, float *sens, int ns, int N) {
+    const int n = blockIdx.x * kBlock + threadIdx.x;
+    if (n >= N) return;
+    double s = 0.0;
+    for (int t = 0; t < ns; ++t) s += sens_t[(long long)t * N + n];
+    sens[n] = (float)s;
+}
+
+// Block-wide FP64 sum (kBlock threads); result valid in thread 0.
+__device__ double block_sum(double v) {
+    __shared__ double red[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kBlock / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// out[z] = sum_m max(g_m - w_m, 0) for slice z (one block per slice), and
+// out[nz] = sum_n sens_n (block nz).
+__global__ void uniform_sums_kernel(const float *g, const float *w, float w_scalar, long long M, int nz,
+                                    const float *sens, int N, double *out) {
+    const int z = blockIdx.x;
+    double s = 0.0;
+    if (z < nz) {
+        for (long long m = threadIdx.x; m < M; m += kBlock) {
+            const long long idx = m * nz + z;
+            const float d = g[idx] - (w ? w[idx] : w_scalar);
+            s += d > 0.0f ? (double)d : 0.0;
+        }
+    } else {
+        for (int n = threadIdx.x; n < N; n += kBlock) s += sens[n];
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[z] = s;
+}
+
+__global__ void uniform_fill_kernel(float *img, long long plane, int nz, const double *sums) {
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= plane) return;
+    const double den = sums[nz];
+    img[i] = den > 0.0 ? (float)(sums[i % nz] / den) : 0.0f;
+}
+
+// Per-block partial of R(f) = 1/2 sum_n sum_{j in N4(n)} (f_n - f_j)^2 / 2.
+__global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, double *part) {
+    const long long plane = (long long)nx * ny * nz;
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    double r = 0.0;
+    if (i < plane) {
+        const int z = (int)(i % nz);
+        const int n = (int)(i / nz);
+        const int ix = n % nx, iy = n / nx;
+        const double fn = f[i];
+        double acc = 0.0;
+        if (ix > 0) { const double d = fn - f[i - nz]; acc += d * d; }
+        if (ix + 1 < nx) { const double d = fn - f[i + nz]; acc += d * d; }
+        if (iy > 0) { const double d = fn - f[i - (long long)nx * nz]; acc += d * d; }
+        if (iy + 1 < ny) { const double d = fn - f[i + (long long)nx * nz]; acc += d * d; }
+        r = 0.25 * acc;
+        (void)z;
+    }
+    r = block_sum(r);
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+
+// phi = sum(ll partials) - beta * sum(penalty partials), in one block, fixed order.
+__global__ void objective_final_kernel(const double *ll, int n_ll, const double *pen, int n_pen, double beta,
+                                       double *out) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n_ll; i += kBlock) a += ll[i];
+    for (int i = threadIdx.x; i < n_pen; i += kBlock) b += pen[i];
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        out[0] = a - beta * b;
+        out[1] = a;
+        out[2] = b;
+    }
+}
+
+__global__ void svrem_finish_kernel(const float *B, int ns, long long plane, const float *f_anc,
+                                    float *s_anc, float *s_hat, int init) {
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= plane) return;
+    double s = 0.0;
+    for (int t = 0; t < ns; ++t) s += B[(long long)t * plane + i];
+    const float sa = (float)((double)f_anc[i] * s);
+    s_anc[i] = sa;
+    if (init) s_hat[i] = sa;
+}
+
+__global__ void svrg_finish_kernel(const float *B, int ns, long long plane, int nz, const float *sens,
+                                   float *qtil) {
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= plane) return;
+    double s = 0.0;
+    for (int t = 0; t < ns; ++t) s += B[(long long)t * plane + i];
+    qtil[i] = (float)((s - (double)sens[i / nz]) / (double)ns);
+}
+
+template <typename TQ>
+__device__ __forceinline__ double table_at(const void *tab, long long i);
+template <> __device__ __forceinline__ double table_at<float>(const void *tab, long long i) {
+    return static_cast<const float *>(tab)[i];
+}
+template <> __device__ __forceinline__ double table_at<__nv_bfloat16>(const void *tab, long long i) {
+    return __bfloat162float(static_cast<const __nv_bfloat16 *>(tab)[i]);
+}
+
+template <typename TQ>
+__global__ void saga_finish_kernel(const void *tab, int ns, long long plane, float *qbar) {
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= plane) return;
+    double s = 0.0;
+    for (int t = 0; t < ns; ++t) s += table_at<TQ>(tab, (long long)t * plane + i);
+    qbar[i] = (float)(s / (double)ns);
+}
+
+// d = N_s f0 / sens (0 where sens = 0): the constant preconditioner of §4.
+__global__ void precond_kernel(const float *f0, const float *sens, int ns, long long plane, int nz, float *d) {
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i >= plane) return;
+    const float s = sens[i / nz];
+    d[i] = s > 0.0f ? (float)ns * f0[i] / s : 0.0f;
+}
+
+}  // namespace
+
+pet_status launch_permute_sino(const float *src, float *dst, const int *order, int na, int nb, int nz,
+                               cudaStream_t s) {
+    const long long n = (long long)na * nb * nz;
+    if (n == 0) return PET_OK;
+    permute_kernel<<<blocks_for(n), kBlock, 0, s>>>(src, dst, order, na, nb, nz);
+    return check_launch("permute_kernel");
+}
+
+pet_status launch_sum_sens(const float *sens_t, float *sens, int ns, int N, cudaStream_t s) {
+    sum_sens_kernel<<<blocks_for(N), kBlock, 0, s>>>(sens_t, sens, ns, N);
+    return check_launch("sum_sens_kernel");
+}
+
+pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s) {
+    const pet_plan *pl = p->plan;
+    uniform_sums_kernel<<<pl->nz + 1, kBlock, 0, s>>>(p->d_g, p->d_w, p->w_scalar, (long long)pl->M, pl->nz,
+                                                     pl->d_sens, pl->N, p->d_scalar + 4);
+    pet_status st = check_launch("uniform_sums_kernel");
+    if (st != PET_OK) return st;
+    const long long plane = (long long)pl->N * pl->nz;
+    uniform_fill_kernel<<<blocks_for(plane), kBlock, 0, s>>>(img, plane, pl->nz, p->d_scalar + 4);
+    return check_launch("uniform_fill_kernel");
+}
+
+pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks, double *d_out,
+                                   cudaStream_t s) {
+    const pet_plan *pl = p->plan;
+    const long long plane = (long long)pl->N * pl->nz;
+    const int n_pen = (int)blocks_for(plane);
+    double *pen_part = p->d_part + n_ll_blocks;
+    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, pl->nx, pl->ny, pl->nz, pen_part);
+    pet_status st = check_launch("penalty_partial_kernel");
+    if (st != PET_OK) return st;
+    objective_final_kernel<<<1, kBlock, 0, s>>>(p->d_part, n_ll_blocks, pen_part, n_pen, (double)p->pen.beta,
+                                                d_out);
+    return check_launch("objective_final_kernel");
+}
+
+pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz, const float *f_anc,
+                                      float *s_anc, float *s_hat, bool init, cudaStream_t s) {
+    (void)nz;
+    svrem_finish_kernel<<<blocks_for(plane), kBlock, 0, s>>>(B, ns, plane, f_anc, s_anc, s_hat, init ? 1 : 0);
+    return check_launch("svrem_finish_kernel");
+}
+
+pet_status launch_svrg_anchor_finish(const float *B, int ns, long long plane, int nz, const float *sens,
+                                     float *qtil, cudaStream_t s) {
+    svrg_finish_kernel<<<blocks_for(plane), kBlock, 0, s>>>(B, ns, plane, nz, sens, qtil);
+    return check_launch("svrg_finish_kernel");
+}
+
+pet_status launch_saga_finish(const void *table, int table_dtype, int ns, long long plane, int nz,
+                              const float *f0, const float *sens, float *qbar, float *d, cudaStream_t s) {
+    if (table_dtype == PET_TABLE_BF16)
+        saga_finish_kernel<__nv_bfloat16><<<blocks_for(plane), kBlock, 0, s>>>(table, ns, plane, qbar);
+    else
+        saga_finish_kernel<float><<<blocks_for(plane), kBlock, 0, s>>>(table, ns, plane, qbar);
+    pet_status st = check_launch("saga_finish_kernel");
+    if (st != PET_OK) return st;
+    return launch_precond(f0, sens, ns, plane, nz, d, s);
+}
+
+pet_status launch_precond(const float *f0, const float *sens, int ns, long long plane, int nz, float *d,
+                          cudaStream_t s) {
+    precond_kernel<<<blocks_for(plane), kBlock, 0, s>>>(f0, sens, ns, plane, nz, d);
+    return check_launch("precond_kernel");
+}
+
+}  // namespace petvr

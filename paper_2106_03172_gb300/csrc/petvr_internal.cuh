@@ -1,0 +1,226 @@
+// Internal declarations of libpetvr: object layouts, kernel argument blocks,
+// the shared ray-geometry device functions and the launch helpers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "petvr.h"
+
+namespace petvr {
+
+// ---------------------------------------------------------------------------
+// Ray geometry.
+//
+// For each view the traversal runs along the "major" image axis: rows (y)
+// when |cos theta| >= |sin theta|, columns (x) otherwise.  Along that axis
+// the line x cos + y sin = s moves by |du| <= 1 pixel in the "minor"
+// coordinate per pixel step, so inside one major step (one row band, or one
+// column band) it meets at most two pixels.  The part of the line inside a
+// major band has length L = d / max(|cos|, |sin|); if the band contains a
+// minor grid line at position c+1 the line is split there, the first piece
+// having length (c + 1 - u_lo) * Lm with Lm = L / |du|.  These are exactly
+// the Siddon intersection lengths (every piece between consecutive grid-line
+// crossings, charged to the pixel containing it), enumerated band by band.
+//
+// Minor coordinates u are in pixel units relative to the pixel edge nearest
+// the image centre (u in [-mo, n_minor - mo) is inside the image, with
+// mo = n_minor / 2), so that floor(u) + mo is the pixel index and axis-
+// aligned rays on grid lines land on integers exactly (half-open pixels: the
+// +x / +y pixel takes a ray lying on their shared edge).
+// ---------------------------------------------------------------------------
+struct ViewParams {
+    float du;    // minor displacement (pixels) per major step
+    float L;     // ray length (mm) per major step
+    float Lm;    // ray length (mm) per pixel of minor displacement (0 if du == 0)
+    float K;     // minor displacement (pixels) per bin step (never 0)
+    float uc0;   // centred minor coordinate of bin 0 at the central major line
+    int col;     // 1: major axis is x (columns); 0: major axis is y (rows)
+    int pad0, pad1;
+};
+
+// Weights of one ray in major band k: w0 for pixel (k, c0) and w1 for pixel
+// (k, c0 + 1), c0 relative to the centre edge (add mo for the index).
+// Forward and back projection both call this, so a_mn is bit-identical in
+// the two directions.
+__device__ __forceinline__ void band_weights(const ViewParams &vp, float uc, float kc, int &c0,
+                                             float &w0, float &w1) {
+    const float ua = fmaf(kc, vp.du, uc);
+    const float ub = fmaf(kc + 1.0f, vp.du, uc);
+    const float lo = fminf(ua, ub);
+    const float hi = fmaxf(ua, ub);
+    const float fl = floorf(lo);
+    c0 = (int)fl;
+    if (hi <= fl + 1.0f) {
+        w0 = vp.L;
+        w1 = 0.0f;
+    } else {
+        w0 = fminf((fl + 1.0f - lo) * vp.Lm, vp.L);
+        w1 = vp.L - w0;
+    }
+}
+
+// Nonnegative root of a/f - 2 b f + c = 0 (the surrogate M-step of §3,
+// Eq. (svrsurder)); cancellation-free in both signs of c, b = 0 allowed;
+// 0 when S <= 0 or a <= 0 (zero-denominator remedy of §2.3).
+__device__ __forceinline__ float m_step_root(float a, float S, float b, float c) {
+    if (!(S > 0.0f) || !(a > 0.0f)) return 0.0f;
+    const float D = sqrtf(fmaf(c, c, 8.0f * a * b));
+    return (c <= 0.0f) ? (2.0f * a) / (D - c) : (c + D) / (4.0f * b);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel argument blocks.
+// ---------------------------------------------------------------------------
+enum FwdMode { FWD_NONE = 0, FWD_YHAT = 1, FWD_RATIO = 2 };
+
+struct FwdArgs {
+    const ViewParams *views;  // [n_angles]
+    const float *uc;          // [n_angles * n_bins] centred minor coordinate per ray
+    const int *order;         // view order the ray range indexes
+    int v_begin, v_end;       // view positions [v_begin, v_end) of `order`
+    int nx, ny, nz, nb;
+    const float *img;         // [ny][nx][nz]
+    const float *g;           // counts of these rays (compact), FWD_RATIO / LL only
+    const float *w;           // background of these rays (compact) or null
+    float w_scalar;
+    float *out;               // compact output (yhat or ratio)
+    double *ll_partials;      // per-block partial log-likelihood (LL only)
+    int *status;              // device error latch (may be null)
+};
+
+enum BackEpi {
+    EPI_PLAIN = 0,       // out = A_t^T r
+    EPI_OSEM = 1,        // penalised OSEM M-step
+    EPI_SVREM = 2,       // SVREM statistic update + M-step
+    EPI_SAGA = 3,        // SAGA step (table dtype is a template parameter)
+    EPI_SVRG = 4,        // SVRG step
+    EPI_ANCHOR = 5,      // B[t] = A_t^T r_t for every t (grid.y = subset)
+    EPI_SAGA_INIT = 6,   // table[t] = grad Phi_t(f) for every t (grid.y = subset)
+};
+
+struct BackArgs {
+    const ViewParams *views;
+    const float *uc;
+    const int *order;
+    const int *sub_off;   // view offsets of subsets in `order`
+    int t0;               // subset of blockIdx.y == 0
+    int r_view0;          // view position of r[0]
+    int nx, ny, nz, nb, ns;
+    const float *r;       // ratio / sinogram, [view pos - r_view0][bin][z]
+    float *out;           // EPI_PLAIN: image; EPI_ANCHOR: B [ns][N*nz]
+    // update inputs
+    const float *f;       // current iterate f^k
+    float *f_out;         // next iterate f^{k+1}
+    const float *sens_t;  // [ns][N] subset sensitivities
+    const float *sens;    // [N] full sensitivity
+    float beta;           // penalty weight beta (full)
+    float alpha;
+    float *s_hat;         // SVREM running statistic
+    const float *f_anc;   // SVREM anchor image
+    const float *s_anc;   // SVREM anchor statistic
+    const float *B;       // SVREM/SVRG cached A_t^T r_t(f_anc), [ns][N*nz]
+    const float *d;       // SAGA/SVRG preconditioner
+    void *table;          // SAGA table [ns][N*nz] (float or bf16)
+    float *qbar;          // SAGA running mean of the table
+    const float *qtil;    // SVRG full-gradient term
+};
+
+// ---------------------------------------------------------------------------
+// Host objects.
+// ---------------------------------------------------------------------------
+}  // namespace petvr
+
+struct pet_plan {
+    pet_geometry geom;
+    int nx, ny, nz, na, nb, ns;
+    int N, M;                       // pixels and rays of one slice
+    int max_sub_views;
+    int device;
+    std::vector<int> order;         // subset-major view order
+    std::vector<int> sub_off;       // [ns + 1]
+    std::vector<long long> nnz;     // [ns] nonzeros of A_t (one slice)
+    petvr::ViewParams *d_views = nullptr;
+    float *d_uc = nullptr;
+    int *d_order = nullptr;         // subset-major
+    int *d_natural = nullptr;       // identity
+    int *d_sub_off = nullptr;       // [ns + 1]
+    int *d_all_off = nullptr;       // {0, na}
+    float *d_sens_t = nullptr;      // [ns][N]
+    float *d_sens = nullptr;        // [N]
+};
+
+struct pet_problem {
+    const pet_plan *plan;
+    pet_penalty pen;
+    float w_scalar;
+    float *d_g = nullptr;           // [M * nz], subset-major
+    float *d_w = nullptr;           // [M * nz], subset-major, or null
+    float *d_ratio = nullptr;       // [M * nz] scratch for full passes
+    float *d_alt = nullptr;         // [N * nz] scratch image (warm start)
+    double *d_part = nullptr;       // reduction partials
+    int n_part = 0;
+    double *d_scalar = nullptr;     // [4 + nz] reduction results
+    int *d_status = nullptr;        // device error latch
+};
+
+struct pet_state {
+    const pet_problem *prob;
+    int algo, table_dtype;
+    float *img;                     // caller's image (current iterate)
+    float *alt = nullptr;           // ping-pong partner
+    float *ratio = nullptr;         // [max subset rays * nz]
+    float *ratio_full = nullptr;    // [M * nz] anchor-pass ratio (SVREM, SVRG)
+    float *s_hat = nullptr, *f_anc = nullptr, *s_anc = nullptr;
+    float *B = nullptr, *d = nullptr, *qbar = nullptr, *qtil = nullptr;
+    void *table = nullptr;
+    long long k = 0;
+    size_t bytes = 0;
+};
+
+namespace petvr {
+
+// Launch accounting and error reporting.
+extern std::atomic<uint64_t> g_launches;
+// Optional event timing of kernel kinds (0 forward, 1 back+update, 2 multi-subset back).
+struct ProfileScope {
+    int kind;
+    cudaStream_t stream;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ProfileScope(int kind, cudaStream_t s);
+    ~ProfileScope();
+};
+pet_status set_error(pet_status code, const std::string &msg);
+pet_status check_launch(const char *what);
+
+// Kernel launchers (forward.cu / backward.cu / misc.cu).
+pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s,
+                          int *n_blocks_out);
+int forward_blocks(int n_rays, int nz, int group);
+int choose_group(const pet_plan *plan);
+pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
+                       cudaStream_t s);
+pet_status launch_permute_sino(const float *src, float *dst, const int *order, int na, int nb, int nz,
+                               cudaStream_t s);
+pet_status launch_sum_sens(const float *sens_t, float *sens, int ns, int N, cudaStream_t s);
+pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s);
+pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks,
+                                   double *d_out, cudaStream_t s);
+pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
+pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz,
+                                      const float *f_anc, float *s_anc, float *s_hat, bool init,
+                                      cudaStream_t s);
+pet_status launch_svrg_anchor_finish(const float *B, int ns, long long plane, int nz,
+                                     const float *sens, float *qtil, cudaStream_t s);
+pet_status launch_saga_finish(const void *table, int table_dtype, int ns, long long plane, int nz,
+                              const float *f0, const float *sens, float *qbar, float *d,
+                              cudaStream_t s);
+pet_status launch_precond(const float *f0, const float *sens, int ns, long long plane, int nz,
+                          float *d, cudaStream_t s);
+
+}  // namespace petvr

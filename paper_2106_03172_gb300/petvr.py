@@ -1,0 +1,289 @@
+"""Python binding of libpetvr (include/petvr.h): argument marshalling only.
+
+Every function named ``pet_*`` here calls the C entry point of the same name
+with device pointers taken from CUDA torch tensors and the current torch
+stream; every step of the reconstruction runs in the library's kernels.  The
+binding raises ``PetError`` on a nonzero status and refuses to run if the
+compiled library is missing: there is no fallback path.
+
+The small classes ``Plan``, ``Problem`` and ``State`` own the C handles and
+release them when garbage collected.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_float, c_int32, c_size_t, c_uint64, c_void_p
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpetvr.so")
+
+ALGO = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3}
+TABLE = {"fp32": 0, "bf16": 1}
+STATUS = {0: "PET_OK", 1: "PET_ERR_INVALID", 2: "PET_ERR_OOM", 3: "PET_ERR_CUDA",
+          4: "PET_ERR_TIMEOUT", 5: "PET_ERR_NUMERIC", 6: "PET_ERR_STATE"}
+
+
+class PetError(RuntimeError):
+    def __init__(self, func, status, msg):
+        super().__init__(f"{func} -> {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pet_geometry(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("pixel_mm", c_double),
+                ("n_angles", c_int32), ("n_bins", c_int32), ("bin_mm", c_double)]
+
+
+class pet_subsets(ctypes.Structure):
+    _fields_ = [("n_subsets", c_int32), ("scheme", c_int32)]
+
+
+class pet_penalty(ctypes.Structure):
+    _fields_ = [("potential", c_int32), ("beta", c_float), ("delta", c_float)]
+
+
+_SIGS = {
+    "pet_plan_create": (c_int32, [POINTER(pet_geometry), POINTER(pet_subsets), POINTER(c_void_p)]),
+    "pet_plan_destroy": (None, [c_void_p]),
+    "pet_plan_subset_views": (c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
+    "pet_plan_sensitivity": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    "pet_plan_nnz": (c_int32, [c_void_p, c_int32, POINTER(ctypes.c_int64)]),
+    "pet_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int32, c_void_p, c_void_p]),
+    "pet_back": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "pet_problem_create": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, POINTER(pet_penalty),
+                                     POINTER(c_void_p), c_void_p]),
+    "pet_problem_destroy": (None, [c_void_p]),
+    "pet_problem_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
+    "pet_profile_enable": (c_int32, [c_int32]),
+    "pet_profile_reset": (c_int32, []),
+    "pet_profile_read": (c_int32, [c_int32, POINTER(ctypes.c_int64), POINTER(c_double)]),
+    "pet_warm_start": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "pet_objective": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),
+    "pet_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pet_state_create": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_size_t),
+                                   POINTER(c_void_p), c_void_p]),
+    "pet_state_destroy": (c_int32, [c_void_p]),
+    "pet_osem_epoch": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "pet_svrem_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
+    "pet_saga_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
+    "pet_svrg_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
+    "pet_state_sync": (c_int32, [c_void_p, c_void_p]),
+    "pet_kernel_launches": (c_uint64, []),
+    "pet_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libpetvr.so (after torch has loaded the CUDA runtime)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = handle
+    return _lib
+
+
+def _call(name, *args):
+    st = getattr(lib(), name)(*args)
+    if st != 0:
+        raise PetError(name, st, lib().pet_last_error().decode())
+
+
+def _dev(t: torch.Tensor | None, dtype=torch.float32):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    return c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+def _seq(seq):
+    arr = (c_int32 * max(1, len(seq)))(*[int(x) for x in seq])
+    return arr, len(seq)
+
+
+# ---- thin wrappers with the C names ---------------------------------------------
+
+def pet_plan_create(geom, n_subsets: int) -> c_void_p:
+    g = pet_geometry(geom.nx, geom.ny, geom.nz, geom.pixel_mm, geom.n_angles, geom.n_bins,
+                     geom.bin_mm if geom.bin_mm is not None else 0.0)
+    h = c_void_p()
+    _call("pet_plan_create", byref(g), byref(pet_subsets(n_subsets, 0)), byref(h))
+    return h
+
+
+def pet_plan_subset_views(plan, t: int) -> int:
+    n = c_int32()
+    _call("pet_plan_subset_views", plan, t, byref(n))
+    return n.value
+
+
+def pet_plan_nnz(plan, t: int) -> int:
+    n = ctypes.c_int64()
+    _call("pet_plan_nnz", plan, t, byref(n))
+    return n.value
+
+
+def pet_plan_sensitivity(plan, t: int, out: torch.Tensor, stream=None):
+    _call("pet_plan_sensitivity", plan, t, _dev(out), _stream(stream))
+
+
+def pet_forward(plan, img, bg, bg_scalar: float, subset: int, sino, stream=None):
+    _call("pet_forward", plan, _dev(img), _dev(bg), bg_scalar, subset, _dev(sino), _stream(stream))
+
+
+def pet_back(plan, sino, subset: int, img, stream=None):
+    _call("pet_back", plan, _dev(sino), subset, _dev(img), _stream(stream))
+
+
+def pet_problem_create(plan, counts, bg, bg_scalar: float, beta: float, stream=None) -> c_void_p:
+    h = c_void_p()
+    _call("pet_problem_create", plan, _dev(counts), _dev(bg), bg_scalar,
+          byref(pet_penalty(0, beta, 1.0)), byref(h), _stream(stream))
+    return h
+
+
+def pet_problem_update(problem, counts, bg, bg_scalar: float, stream=None):
+    _call("pet_problem_update", problem, _dev(counts), _dev(bg), bg_scalar, _stream(stream))
+
+
+def pet_profile_enable(on: bool):
+    _call("pet_profile_enable", 1 if on else 0)
+
+
+def pet_profile_reset():
+    _call("pet_profile_reset")
+
+
+def pet_profile_read(kind: int):
+    """(launches, total ms) of kernel kind 0 forward, 1 back+update, 2 multi-subset back."""
+    n, ms = ctypes.c_int64(), c_double()
+    _call("pet_profile_read", kind, byref(n), byref(ms))
+    return n.value, ms.value
+
+
+def pet_warm_start(problem, img, stream=None):
+    _call("pet_warm_start", problem, _dev(img), _stream(stream))
+
+
+def pet_objective(problem, img, stream=None) -> float:
+    phi = c_double()
+    _call("pet_objective", problem, _dev(img), byref(phi), _stream(stream))
+    return phi.value
+
+
+def pet_objective_async(problem, img, phi_out: torch.Tensor, stream=None):
+    """Enqueue Phi, L, R of ``img`` into the float64 CUDA tensor ``phi_out`` (3 values)."""
+    _call("pet_objective_async", problem, _dev(img), _dev(phi_out, torch.float64), _stream(stream))
+
+
+def pet_state_bytes(problem, algo: str, table: str = "fp32") -> int:
+    n = c_size_t()
+    _call("pet_state_create", problem, ALGO[algo], TABLE[table], None, byref(n), None, None)
+    return n.value
+
+
+def pet_state_create(problem, algo: str, table: str, img, stream=None) -> c_void_p:
+    h = c_void_p()
+    n = c_size_t()
+    _call("pet_state_create", problem, ALGO[algo], TABLE[table], _dev(img), byref(n), byref(h),
+          _stream(stream))
+    return h
+
+
+def pet_osem_epoch(state, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_osem_epoch", state, arr, n, _stream(stream))
+
+
+def pet_svrem_epoch(state, alpha: float, eta: int, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_svrem_epoch", state, alpha, eta, arr, n, _stream(stream))
+
+
+def pet_saga_epoch(state, alpha: float, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_saga_epoch", state, alpha, arr, n, _stream(stream))
+
+
+def pet_svrg_epoch(state, alpha: float, eta: int, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_svrg_epoch", state, alpha, eta, arr, n, _stream(stream))
+
+
+def pet_state_sync(state, stream=None):
+    _call("pet_state_sync", state, _stream(stream))
+
+
+def pet_kernel_launches() -> int:
+    return int(lib().pet_kernel_launches())
+
+
+# ---- owning handles ------------------------------------------------------------
+
+class Plan:
+    """Geometry tables and sensitivities on the current CUDA device."""
+
+    def __init__(self, geom, n_subsets: int):
+        self.geom, self.n_subsets = geom, n_subsets
+        self.handle = pet_plan_create(geom, n_subsets)
+        self.subset_views = [pet_plan_subset_views(self.handle, t) for t in range(n_subsets)]
+
+    def subset_rays(self, t: int) -> int:
+        return self.subset_views[t] * self.geom.n_bins
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.pet_plan_destroy(self.handle)
+            self.handle = None
+
+
+class Problem:
+    """Counts, background and penalty bound to a plan (data copied on the device)."""
+
+    def __init__(self, plan: Plan, counts, bg, bg_scalar: float, beta: float, stream=None):
+        self.plan = plan
+        self.handle = pet_problem_create(plan.handle, counts, bg, bg_scalar, beta, stream)
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.pet_problem_destroy(self.handle)
+            self.handle = None
+
+
+class State:
+    """One running reconstruction of ``algo`` on the borrowed image ``img``."""
+
+    def __init__(self, problem: Problem, algo: str, img, table: str = "fp32", stream=None):
+        self.problem, self.algo, self.img = problem, algo, img
+        self.handle = pet_state_create(problem.handle, algo, table, img, stream)
+
+    def epoch(self, seq, alpha: float = 1.0, eta: int = 1, stream=None):
+        if self.algo == "osem":
+            pet_osem_epoch(self.handle, seq, stream)
+        elif self.algo == "svrem":
+            pet_svrem_epoch(self.handle, alpha, eta, seq, stream)
+        elif self.algo == "saga":
+            pet_saga_epoch(self.handle, alpha, seq, stream)
+        else:
+            pet_svrg_epoch(self.handle, alpha, eta, seq, stream)
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.pet_state_destroy(self.handle)
+            self.handle = None

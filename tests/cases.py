@@ -1,0 +1,37 @@
+"""Seeded parity cases shared by the GPU tests (inputs only; the oracle side is
+built here from ``oracle`` and the GPU side from the binding)."""
+from __future__ import annotations
+
+import functools
+from dataclasses import replace
+
+import numpy as np
+
+from paper_2106_03172_gb300.phantoms import WORKLOADS, Geometry, Workload, make_data
+
+CASES = {
+    # 64x64, 60 views x 91 bins, 6 subsets (the small benchmark configuration)
+    "c64": WORKLOADS["c64"],
+    # odd, non-square image, ragged subsets (23 views / 5 subsets), bins != pixels
+    "ragged": Workload("ragged", Geometry(37, 29, 23, 41, pixel_mm=1.7, bin_mm=1.3), n_subsets=5,
+                       counts=3e5, bg_frac=0.1, beta=0.02, n_ellipses=5),
+    # slice stack, slice index innermost
+    "stack": replace(WORKLOADS["c128x47"], name="stack",
+                     geometry=Geometry(24, 24, 18, 35, bin_mm=1.4, nz=5), n_subsets=3, counts=2e5),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_problem(name: str, seed: int = 0):
+    """(oracle Problem, data dict) for a named case or workload."""
+    from oracle.em import build_problem
+    work = CASES.get(name) or WORKLOADS[name]
+    data = make_data(work, seed)
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    return prob, data, work
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (float32 kernels against float64 oracle):
+  * projections: per element |gpu - oracle| <= 2e-5 |oracle| + 2e-6 max|oracle|
+    (FP32 accumulation along rays of up to ~2n pixels and FP32 ray geometry);
+  * one update from the same iterate: relative L2 <= 1e-5 (the stated
+    per-iterate tolerance);
+  * trajectories of several epochs: relative L2 <= 1e-4 and objective
+    |dPhi|/|Phi| <= 1e-7 (FP32 iterates, errors compound slowly);
+  * FP64 objective of a given image: relative 1e-7;
+  * BF16 SAGA table against the oracle's BF16 emulation: relative L2 <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from cases import CASES, oracle_problem, rel_l2
+from oracle import em
+from paper_2106_03172_gb300.phantoms import subset_sequence
+
+pytestmark = pytest.mark.gpu
+
+PROJ_RTOL, PROJ_ATOL = 2e-5, 2e-6
+METHOD_SEED = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3}
+
+
+def _pv():
+    from paper_2106_03172_gb300 import petvr
+    petvr.lib()
+    return petvr
+
+
+def _cuda(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def _assert_proj(gpu, ora):
+    ora = np.asarray(ora, dtype=np.float64)
+    tol = PROJ_RTOL * np.abs(ora) + PROJ_ATOL * np.abs(ora).max()
+    err = np.abs(gpu - ora)
+    assert np.all(err <= tol), f"max err {err.max():.3e}, worst ratio {(err / tol).max():.2f}"
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    pv = _pv()
+    prob, data, work = oracle_problem(request.param)
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    return pv, prob, data, work, plan
+
+
+def test_forward_parity(case):
+    pv, prob, data, work, plan = case
+    geom = work.geometry
+    f = np.random.default_rng(1).uniform(0.5, 3.0, (prob.N, prob.nz))
+    fd = _cuda(f)
+    out = torch.empty(geom.n_rays * geom.nz, device="cuda")
+    pv.pet_forward(plan.handle, fd, None, 0.25, -1, out)
+    _assert_proj(_host(out).reshape(-1, geom.nz), prob.A @ f + 0.25)
+    bg = np.random.default_rng(2).uniform(0.0, 1.0, (prob.M, prob.nz))
+    for t in range(work.n_subsets):
+        rows = prob.subsets[t]
+        sub = torch.empty(len(rows) * geom.nz, device="cuda")
+        pv.pet_forward(plan.handle, fd, _cuda(bg[rows]), 0.0, t, sub)
+        _assert_proj(_host(sub).reshape(-1, geom.nz), prob.At[t] @ f + bg[rows])
+
+
+def test_back_parity_and_adjoint(case):
+    pv, prob, data, work, plan = case
+    geom = work.geometry
+    y = np.random.default_rng(3).uniform(0.0, 2.0, (prob.M, prob.nz))
+    img = torch.empty(prob.N * prob.nz, device="cuda")
+    pv.pet_back(plan.handle, _cuda(y), -1, img)
+    _assert_proj(_host(img).reshape(-1, geom.nz), prob.A.T @ y)
+    for t in range(work.n_subsets):
+        rows = prob.subsets[t]
+        pv.pet_back(plan.handle, _cuda(y[rows]), t, img)
+        _assert_proj(_host(img).reshape(-1, geom.nz), prob.At[t].T @ y[rows])
+    # adjoint identity <A x, y> = <x, A^T y>, both sides on the GPU
+    x = np.random.default_rng(4).uniform(0.0, 1.0, (prob.N, prob.nz))
+    ax = torch.empty(prob.M * prob.nz, device="cuda")
+    pv.pet_forward(plan.handle, _cuda(x), None, 0.0, -1, ax)
+    pv.pet_back(plan.handle, _cuda(y), -1, img)
+    lhs = float((_host(ax) * y.ravel().astype(np.float32)).sum())
+    rhs = float((_host(img) * x.ravel().astype(np.float32)).sum())
+    assert lhs == pytest.approx(rhs, rel=2e-6)
+
+
+def test_nonzero_counts(case):
+    """The library's nonzero count of every A_t equals the oracle's CSR nnz."""
+    pv, prob, data, work, plan = case
+    for t in range(work.n_subsets):
+        assert pv.pet_plan_nnz(plan.handle, t) == prob.At[t].nnz
+    assert pv.pet_plan_nnz(plan.handle, -1) == prob.A.nnz
+
+
+def test_sensitivities(case):
+    pv, prob, data, work, plan = case
+    out = torch.empty(prob.N, device="cuda")
+    pv.pet_plan_sensitivity(plan.handle, -1, out)
+    _assert_proj(_host(out), prob.sens[:, 0])
+    for t in range(work.n_subsets):
+        pv.pet_plan_sensitivity(plan.handle, t, out)
+        _assert_proj(_host(out), prob.sens_t[t][:, 0])
+
+
+def _gpu_problem(pv, plan, data, work):
+    return pv.Problem(plan, _cuda(data["g"]), None, data["w"], work.beta)
+
+
+def test_objective_and_warm_start(case):
+    pv, prob, data, work, plan = case
+    gp = _gpu_problem(pv, plan, data, work)
+    img = torch.empty(prob.N * prob.nz, device="cuda")
+    pv.pet_warm_start(gp.handle, img)
+    f0 = prob.initial_image()
+    assert rel_l2(_host(img), f0) <= 1e-5
+    f = f0.astype(np.float32).astype(np.float64)
+    phi_gpu = pv.pet_objective(gp.handle, _cuda(f))
+    assert phi_gpu == pytest.approx(prob.objective(f), rel=1e-7)
+
+
+def _oracle_alg(prob, method, f0, work, table="fp32"):
+    if method == "osem":
+        return None
+    if method == "svrem":
+        return em.SVREM(prob, f0, work.alpha_svrem, work.eta_svrem)
+    if method == "saga":
+        return em.SAGA(prob, f0, work.alpha_saga, table=table)
+    return em.SVRG(prob, f0, work.alpha_svrg, work.eta_svrg)
+
+
+def _gpu_step(state, method, t, work):
+    state.epoch([t], alpha={"svrem": work.alpha_svrem, "saga": work.alpha_saga,
+                            "svrg": work.alpha_svrg}.get(method, 1.0),
+                eta={"svrem": work.eta_svrem, "svrg": work.eta_svrg}.get(method, 1))
+
+
+@pytest.mark.parametrize("method", ["osem", "svrem", "saga", "svrg"])
+def test_update_parity(case, method):
+    """One update from the same iterate within 1e-5; then two epochs step by
+    step within 1e-4 and the objective within 1e-7."""
+    pv, prob, data, work, plan = case
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, method, img)
+    alg = _oracle_alg(prob, method, f0, work)
+    seq = subset_sequence(2000 + METHOD_SEED[method], work.n_subsets, 2 * work.n_subsets)
+    f = f0
+    for k, t in enumerate(seq):
+        _gpu_step(state, method, int(t), work)
+        f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
+        err = rel_l2(_host(img), f)
+        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+    phi_gpu = pv.pet_objective(gp.handle, img)
+    assert phi_gpu == pytest.approx(prob.objective(f), rel=1e-7)
+    assert _host(img).min() >= 0.0
+
+
+def test_saga_bf16_table():
+    pv = _pv()
+    prob, data, work = oracle_problem("c64")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, "saga", img, table="bf16")
+    alg = em.SAGA(prob, f0, work.alpha_saga, table="bf16")
+    for t in subset_sequence(7, work.n_subsets, 3 * work.n_subsets):
+        _gpu_step(state, "saga", int(t), work)
+        f = alg.step(int(t))
+    assert rel_l2(_host(img), f) <= 1e-4
+
+
+def test_epoch_calls_equal_step_calls():
+    """An epoch call equals the same updates issued one call at a time
+    (ping-pong buffering and the anchor counter are invisible to the caller)."""
+    pv = _pv()
+    prob, data, work = oracle_problem("ragged")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32)
+    seq = subset_sequence(11, work.n_subsets, 3 * work.n_subsets)
+    for method in ("osem", "svrem", "saga", "svrg"):
+        a, b = _cuda(f0), _cuda(f0)
+        sa, sb = pv.State(gp, method, a), pv.State(gp, method, b)
+        sa.epoch(seq, alpha=0.7, eta=1)
+        for t in seq:
+            sb.epoch([int(t)], alpha=0.7, eta=1)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), method
+
+
+def test_error_handling():
+    pv = _pv()
+    from paper_2106_03172_gb300.phantoms import Geometry
+    with pytest.raises(pv.PetError) as e:
+        pv.Plan(Geometry(0, 8, 10, 11), 2)
+    assert e.value.status == 1
+    with pytest.raises(pv.PetError):
+        pv.Plan(Geometry(8, 8, 4, 11), 5)          # more subsets than views
+    prob, data, work = oracle_problem("ragged")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    out = torch.empty(10, device="cuda")
+    with pytest.raises(pv.PetError):
+        pv.pet_forward(plan.handle, _cuda(np.ones(prob.N)), None, 0.0, work.n_subsets, out)
+    gp = _gpu_problem(pv, plan, data, work)
+    img = _cuda(prob.initial_image())
+    before = img.clone()
+    st = pv.State(gp, "osem", img)
+    st.epoch([])                                      # zero updates: a no-op
+    torch.cuda.synchronize()
+    assert torch.equal(img, before)
+    with pytest.raises(pv.PetError) as e:
+        pv.pet_svrem_epoch(st.handle, 0.5, 1, [0])   # wrong algorithm for this state
+    assert e.value.status == 6
+    with pytest.raises(pv.PetError) as e:
+        st.epoch([0, 99])                             # out-of-range subset: nothing enqueued
+    assert e.value.status == 1
+    torch.cuda.synchronize()
+    assert torch.equal(img, before)
+    assert pv.pet_state_bytes(gp.handle, "saga", "bf16") < pv.pet_state_bytes(gp.handle, "saga", "fp32")
+
+
+@pytest.fixture(scope="module")
+def full256():
+    pv = _pv()
+    prob, data, work = oracle_problem("c256")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    return pv, prob, data, work, plan
+
+
+def test_full_size_projection_parity(full256):
+    """256x256, 180 views x 367 bins, 21 subsets: every subset's forward and
+    back projection in the launch configuration the benchmark times."""
+    pv, prob, data, work, plan = full256
+    f = prob.initial_image()
+    fd = _cuda(f)
+    y = np.random.default_rng(5).uniform(0.0, 2.0, (prob.M, 1))
+    img = torch.empty(prob.N, device="cuda")
+    for t in range(work.n_subsets):
+        rows = prob.subsets[t]
+        sub = torch.empty(len(rows), device="cuda")
+        pv.pet_forward(plan.handle, fd, None, data["w"], t, sub)
+        _assert_proj(_host(sub).reshape(-1, 1), prob.At[t] @ f + data["w"])
+        pv.pet_back(plan.handle, _cuda(y[rows]), t, img)
+        _assert_proj(_host(img).reshape(-1, 1), prob.At[t].T @ y[rows])
+
+
+@pytest.mark.parametrize("method", ["osem", "svrem", "saga", "svrg"])
+def test_full_size_one_epoch(full256, method):
+    pv, prob, data, work, plan = full256
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, method, img)
+    alg = _oracle_alg(prob, method, f0, work)
+    seq = subset_sequence(2000, work.n_subsets, work.n_subsets)
+    _gpu_step(state, method, int(seq[0]), work)
+    f = em.osem_step(prob, f0, int(seq[0])) if alg is None else alg.step(int(seq[0]))
+    assert rel_l2(_host(img), f) <= 1e-5
+    state.epoch(seq[1:], alpha={"svrem": work.alpha_svrem, "saga": work.alpha_saga,
+                                "svrg": work.alpha_svrg}.get(method, 1.0),
+                eta={"svrem": work.eta_svrem, "svrg": work.eta_svrg}.get(method, 1))
+    for t in seq[1:]:
+        f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
+    assert rel_l2(_host(img), f) <= 1e-4
+
+
+def test_full_size_stack_projection():
+    """128x128 x 47 slices, 252 views x 344 bins: forward and back of every
+    slice through one traversal."""
+    pv = _pv()
+    from oracle.siddon import system_matrix
+    from paper_2106_03172_gb300.phantoms import WORKLOADS
+    work = WORKLOADS["c128x47"]
+    geom = work.geometry
+    A = system_matrix(geom)
+    plan = pv.Plan(geom, work.n_subsets)
+    f = np.random.default_rng(6).uniform(0.0, 2.0, (geom.n_pixels, geom.nz))
+    out = torch.empty(geom.n_rays * geom.nz, device="cuda")
+    pv.pet_forward(plan.handle, _cuda(f), None, 0.0, -1, out)
+    _assert_proj(_host(out).reshape(-1, geom.nz), A @ f)
+    y = np.random.default_rng(7).uniform(0.0, 2.0, (geom.n_rays, geom.nz))
+    img = torch.empty(geom.n_pixels * geom.nz, device="cuda")
+    pv.pet_back(plan.handle, _cuda(y), -1, img)
+    _assert_proj(_host(img).reshape(-1, geom.nz), A.T @ y)
