@@ -7,7 +7,7 @@ lesions, 1e7 expected counts plus a 10% uniform background, quadratic
 penalty beta = 0.005.  The warm start is one unpenalised OSEM epoch.
 
 One step = one epoch (21 subset updates) of each of OSEM, SVREM (alpha 0.7,
-eta 1), SAGA (alpha 2, FP32 table) and SVRG (alpha 2, eta 2), each followed by
+eta 1), SAGA (alpha 1, FP32 table) and SVRG (alpha 2, eta 2), each followed by
 its FP64 objective; anchor passes (SVREM every epoch, SVRG every second
 epoch) run inside the step when due.  The metric counts subset forward+back
 projection pairs (A_t f then A_t^T r): 84 per step plus 21 per anchor pass.
@@ -18,7 +18,9 @@ the events) so every step starts with a cold L2.  ``e2e`` repeats the steps
 through the public API with the counts copied in from pinned host memory and
 the four images and objectives copied back, inside the events.  Per-kernel
 durations for the roofline come from a separate profiled pass (event pairs
-around every projector launch).
+around every projector launch, methods run one after another, no graphs).
+The four reconstructions of a step are independent and run on four streams;
+each method's epoch is one captured CUDA graph.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
 same step on the same workload), on rank 0 only.
@@ -65,8 +67,9 @@ def workload_config(work):
         "workload": f"{work.name}: {g.nx}x{g.ny} image ({g.pixel_mm:g} mm pixels), {g.n_angles} views x "
                     f"{g.n_bins} bins, {work.n_subsets} angle-interleaved subsets, {work.counts:.0e} counts, "
                     f"{int(round(work.bg_frac * 100))}% background, quadratic beta={work.beta}",
-        "step": "one epoch each of OSEM, SVREM(alpha=0.7, eta=1), SAGA(alpha=2, fp32 table), "
-                "SVRG(alpha=2, eta=2), each followed by its FP64 objective",
+        "step": f"one epoch each of OSEM, SVREM(alpha={work.alpha_svrem}, eta={work.eta_svrem}), "
+                f"SAGA(alpha={work.alpha_saga}, fp32 table), SVRG(alpha={work.alpha_svrg}, eta={work.eta_svrg}), "
+                "each followed by its FP64 objective",
         "l2": "flushed between steps (256 MiB write outside the timed events)",
         "n_subsets": work.n_subsets,
         "image": [g.ny, g.nx],
@@ -271,11 +274,22 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     rep = Replica(work)
 
-    def one_step(step):
+    side = {m: torch.cuda.Stream() for m in METHODS}
+
+    def one_step(step, concurrent=True):
+        """The four reconstructions are independent: each runs on its own
+        stream (forked from and joined back into the timing stream)."""
         seqs = seqs_for_step(step, ns)
+        fork = torch.cuda.Event()
+        fork.record(stream)
         for i, m in enumerate(METHODS):
-            states[m].epoch(seqs[i], alpha=a[m][0], eta=a[m][1])
-            petvr.pet_objective_async(prob.handle, imgs[m], phi[i])
+            s = side[m] if concurrent else stream
+            s.wait_event(fork)
+            states[m].epoch(seqs[i], alpha=a[m][0], eta=a[m][1], stream=s)
+            petvr.pet_state_objective_async(states[m].handle, phi[i], stream=s)
+        if concurrent:
+            for m in METHODS:
+                stream.wait_stream(side[m])
         return seqs
 
     for w in range(args.warmup):
@@ -331,7 +345,7 @@ def run_ours(args):
     for k in range(n_prof):
         flush.zero_()
         p, anchors = rep.step_pairs()
-        seqs = one_step(args.warmup + args.steps + k)
+        seqs = one_step(args.warmup + args.steps + k, concurrent=False)
         for i, m in enumerate(METHODS):
             for t in seqs[i]:
                 rays = plan.subset_rays(int(t))

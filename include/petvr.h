@@ -189,7 +189,15 @@ pet_status pet_state_destroy(pet_state *state);
  * SAGA  (§4, Eq. (saga_update)): f <- P>=0(f + alpha d (q_new - q_t + mean q)).
  * SVRG  (§4, Eq. (svrg_update)):
  *       f <- P>=0(f + alpha d (grad Phi_t(f) - grad Phi_t(f_anc) + q~)).
- * Returns PET_ERR_STATE if the state was created for another algorithm. */
+ * Returns PET_ERR_STATE if the state was created for another algorithm.
+ *
+ * The subset sequence is copied to the device first; the launches of an
+ * epoch are captured once into a CUDA graph (keyed by n_iter, alpha, eta and
+ * where anchors fall) and replayed on later calls with the same key, so the
+ * first call with a new key costs a capture.  All calls on one state must be
+ * ordered on one stream, and a state's first call with a new key should not
+ * come while `stream` is itself being captured.  Setting the environment
+ * variable PETVR_NO_GRAPHS=1 issues the launches directly instead. */
 pet_status pet_osem_epoch(pet_state *state, const int32_t *h_subset_seq, int32_t n_iter, void *stream);
 pet_status pet_svrem_epoch(pet_state *state, float alpha, int32_t eta, const int32_t *h_subset_seq,
                            int32_t n_iter, void *stream);
@@ -197,6 +205,11 @@ pet_status pet_saga_epoch(pet_state *state, float alpha, const int32_t *h_subset
                           void *stream);
 pet_status pet_svrg_epoch(pet_state *state, float alpha, int32_t eta, const int32_t *h_subset_seq,
                           int32_t n_iter, void *stream);
+
+/* Objective {Phi, L, R} of the state's current image into d_phi (device,
+ * 3 doubles), enqueued only, using the state's own reduction scratch (so
+ * states of one problem may evaluate it on different streams). */
+pet_status pet_state_objective_async(pet_state *state, double *d_phi, void *stream);
 
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);

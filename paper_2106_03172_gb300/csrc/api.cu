@@ -28,6 +28,8 @@ std::mutex g_profile_mu;
 std::vector<ProfileRecord> g_profile_records;
 }  // namespace
 
+bool profiling_enabled() { return g_profile.load(std::memory_order_relaxed); }
+
 ProfileScope::ProfileScope(int k, cudaStream_t s) : kind(k), stream(s) {
     if (!g_profile.load(std::memory_order_relaxed)) return;
     if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
@@ -202,6 +204,21 @@ pet_status read_status(const pet_problem *p, cudaStream_t s) {
     return PET_OK;
 }
 
+// Phi, L, R of d_img into d_phi (3 doubles), using `part` as block-partial scratch.
+pet_status objective_enqueue(const pet_problem *p, const float *d_img, double *d_phi, double *part,
+                             cudaStream_t s) {
+    const pet_plan *pl = p->plan;
+    FwdArgs a = fwd_args(pl, d_img, -1, false);
+    a.g = p->d_g;
+    a.w = p->d_w;
+    a.w_scalar = p->w_scalar;
+    a.ll_partials = part;
+    a.status = p->d_status;
+    int n_ll = 0;
+    PET_TRY(launch_forward(a, FWD_NONE, true, choose_group(pl), s, &n_ll));
+    return launch_objective_finish(p, d_img, n_ll, part, d_phi, s);
+}
+
 }  // namespace
 }  // namespace petvr
 
@@ -289,9 +306,9 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     const double d = g->pixel_mm;
     const double ds = g->bin_mm > 0.0 ? g->bin_mm : d;
 
-    // per-view parameters and per-ray centred minor coordinates (FP64 -> FP32)
+    // per-view parameters and per-ray centred minor offsets (FP64 -> FP32)
     std::vector<ViewParams> views(pl->na);
-    std::vector<float> uc((size_t)M);
+    std::vector<float2> uc((size_t)M);
     for (int i = 0; i < pl->na; ++i) {
         const double th = (double)i * M_PI / (double)pl->na;
         const double c = snap(std::cos(th)), s = snap(std::sin(th));
@@ -300,16 +317,21 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
         const double cm = vp.col ? s : c;          // direction cosine of the major axis
         const double cn = vp.col ? c : s;          // of the minor axis
         const int n_minor = vp.col ? pl->ny : pl->nx;
-        vp.du = (float)(-cn / cm);
+        const double du = -cn / cm;
+        vp.du = (float)du;
+        vp.du_lo = (float)(du - (double)vp.du);
         vp.L = (float)(d / std::fabs(cm));
         vp.Lm = cn != 0.0 ? (float)(d / std::fabs(cn)) : 0.0f;
         vp.K = (float)(ds / (cm * d));
+        vp.invK = (float)(cm * d / ds);
         const double off = (n_minor % 2) ? 0.5 : 0.0;
         for (int j = 0; j < pl->nb; ++j) {
             const double sj = ((double)j - 0.5 * (pl->nb - 1)) * ds;
-            uc[(size_t)i * pl->nb + j] = (float)(sj / (cm * d) + off);
+            const double u = sj / (cm * d) + off;
+            const double ui = std::nearbyint(u);
+            uc[(size_t)i * pl->nb + j] = make_float2((float)ui, (float)(u - ui));
+            if (j == 0) vp.uc0 = (float)u;
         }
-        vp.uc0 = uc[(size_t)i * pl->nb];
         views[i] = vp;
     }
     // angle-interleaved subsets: view i -> subset i mod ns
@@ -341,7 +363,7 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     if ((st = dalloc(&ones, (size_t)M, "ones")) != PET_OK) return fail(st);
     cudaError_t e = cudaSuccess;
     e = cudaMemcpy(pl->d_views, views.data(), sizeof(ViewParams) * pl->na, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(pl->d_uc, uc.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_uc, uc.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_order, pl->order.data(), sizeof(int) * pl->na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_natural, natural.data(), sizeof(int) * pl->na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -359,7 +381,7 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     b.t0 = 0;
     b.r_view0 = 0;
     b.out = pl->d_sens_t;
-    if ((st = launch_back(b, EPI_ANCHOR, PET_TABLE_FP32, pl->ns, 0)) != PET_OK) return fail(st);
+    if ((st = launch_back(b, EPI_ANCHOR, PET_TABLE_FP32, pl->ns, 0, pl->max_sub_views)) != PET_OK) return fail(st);
     if ((st = launch_sum_sens(pl->d_sens_t, pl->d_sens, pl->ns, pl->N, 0)) != PET_OK) return fail(st);
     // nonzeros per subset, counted with the projector's own geometry
     {
@@ -429,7 +451,8 @@ pet_status pet_back(const pet_plan *pl, const float *d_sino, int32_t subset, flo
     if (subset < -1 || subset >= pl->ns) return set_error(PET_ERR_INVALID, "subset out of range");
     BackArgs b = back_args(pl, d_sino, subset, subset < 0);
     b.out = d_img;
-    return launch_back(b, EPI_PLAIN, PET_TABLE_FP32, 1, (cudaStream_t)stream);
+    return launch_back(b, EPI_PLAIN, PET_TABLE_FP32, 1, (cudaStream_t)stream,
+                       subset < 0 ? pl->na : pl->max_sub_views);
 }
 
 void pet_problem_destroy(pet_problem *p) {
@@ -505,23 +528,13 @@ pet_status pet_warm_start(const pet_problem *p, float *d_img, void *stream) {
         b.f = in;
         b.f_out = outp;
         b.beta = 0.0f;
-        return launch_back(b, EPI_OSEM, PET_TABLE_FP32, 1, s);
+        return launch_back(b, EPI_OSEM, PET_TABLE_FP32, 1, s, pl->max_sub_views);
     });
 }
 
 pet_status pet_objective_async(const pet_problem *p, const float *d_img, double *d_phi, void *stream) {
     if (!p || !d_img || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
-    const pet_plan *pl = p->plan;
-    cudaStream_t s = (cudaStream_t)stream;
-    FwdArgs a = fwd_args(pl, d_img, -1, false);
-    a.g = p->d_g;
-    a.w = p->d_w;
-    a.w_scalar = p->w_scalar;
-    a.ll_partials = p->d_part;
-    a.status = p->d_status;
-    int n_ll = 0;
-    PET_TRY(launch_forward(a, FWD_NONE, true, choose_group(pl), s, &n_ll));
-    return launch_objective_finish(p, d_img, n_ll, d_phi, s);
+    return objective_enqueue(p, d_img, d_phi, p->d_part, (cudaStream_t)stream);
 }
 
 pet_status pet_objective(const pet_problem *p, const float *d_img, double *h_phi, void *stream) {
@@ -545,6 +558,10 @@ pet_status pet_state_destroy(pet_state *st) {
     dfree(st->qbar);
     dfree(st->qtil);
     if (st->table) cudaFree(st->table);
+    dfree(st->d_seq);
+    dfree(st->d_part);
+    for (auto &g : st->graphs) cudaGraphExecDestroy(g.second);
+    if (st->cap) cudaStreamDestroy(st->cap);
     delete st;
     return PET_OK;
 }
@@ -558,7 +575,7 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     const pet_plan *pl = p->plan;
     const size_t Nz = (size_t)pl->N * pl->nz;
     const size_t table_bytes = (size_t)pl->ns * Nz * (table_dtype == PET_TABLE_BF16 ? 2 : 4);
-    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * pl->nz * 4;
+    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * pl->nz * 4 + (size_t)p->n_part * 8;
     if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
     if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
     if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
@@ -581,6 +598,8 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     };
     const size_t Mz = (size_t)pl->M * pl->nz;
     if ((e = dalloc(&st->alt, Nz, "alt")) != PET_OK) return fail(e);
+    st->n_part = p->n_part;
+    if ((e = dalloc(&st->d_part, (size_t)st->n_part, "objective partials")) != PET_OK) return fail(e);
     if ((e = dalloc(&st->ratio, (size_t)max_sub_rays(pl) * pl->nz, "ratio")) != PET_OK) return fail(e);
     if (algo == PET_ALGO_SVREM) {
         if ((e = dalloc(&st->s_hat, Nz, "s_hat")) != PET_OK) return fail(e);
@@ -612,7 +631,7 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
         b.f = d_img;
         b.beta = p->pen.beta;
         b.table = st->table;
-        if ((e = launch_back(b, EPI_SAGA_INIT, table_dtype, pl->ns, s)) != PET_OK) return fail(e);
+        if ((e = launch_back(b, EPI_SAGA_INIT, table_dtype, pl->ns, s, pl->max_sub_views)) != PET_OK) return fail(e);
         if ((e = launch_saga_finish(st->table, table_dtype, pl->ns, (long long)Nz, pl->nz, d_img, pl->d_sens,
                                     st->qbar, st->d, s)) != PET_OK)
             return fail(e);
@@ -635,7 +654,103 @@ pet_status anchor_pass(pet_state *st, const float *f, float *ratio_full, cudaStr
     b.t0 = 0;
     b.r_view0 = 0;
     b.out = st->B;
-    return launch_back(b, EPI_ANCHOR, PET_TABLE_FP32, pl->ns, s);
+    return launch_back(b, EPI_ANCHOR, PET_TABLE_FP32, pl->ns, s, pl->max_sub_views);
+}
+
+// One update on subset *t_dev (device-resident index) from `in` to `outp`.
+pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float *in, float *outp, float alpha,
+                          cudaStream_t s) {
+    const pet_problem *p = st->prob;
+    const pet_plan *pl = p->plan;
+    FwdArgs a = fwd_args(pl, in, -1, false);
+    a.t_dev = t_dev;
+    a.sub_off = pl->d_sub_off;
+    a.g = p->d_g;
+    a.w = p->d_w;
+    a.w_scalar = p->w_scalar;
+    a.out = st->ratio;
+    a.status = p->d_status;
+    PET_TRY(launch_forward(a, FWD_RATIO, false, choose_group(pl), s, nullptr, max_sub_rays(pl)));
+    BackArgs b = back_args(pl, st->ratio, 0, false);
+    b.t_dev = t_dev;
+    b.f = in;
+    b.f_out = outp;
+    b.beta = p->pen.beta;
+    b.alpha = alpha;
+    int epi = EPI_OSEM;
+    if (algo == PET_ALGO_SVREM) {
+        epi = EPI_SVREM;
+        b.s_hat = st->s_hat;
+        b.f_anc = st->f_anc;
+        b.s_anc = st->s_anc;
+        b.B = st->B;
+    } else if (algo == PET_ALGO_SAGA) {
+        epi = EPI_SAGA;
+        b.d = st->d;
+        b.table = st->table;
+        b.qbar = st->qbar;
+    } else if (algo == PET_ALGO_SVRG) {
+        epi = EPI_SVRG;
+        b.d = st->d;
+        b.B = st->B;
+        b.qtil = st->qtil;
+    }
+    return launch_back(b, epi, st->table_dtype, 1, s, pl->max_sub_views);
+}
+
+// The whole epoch's launch sequence (anchors where `anchors[i]`), on stream s.
+pet_status enqueue_epoch(pet_state *st, int algo, int32_t n_iter, float alpha, const std::vector<uint8_t> &anchors,
+                         cudaStream_t s) {
+    const pet_plan *pl = st->prob->plan;
+    const long long plane = plane_of(pl);
+    return pingpong(st->img, st->alt, plane, n_iter, s, [&](int i, const float *in, float *outp) {
+        if (anchors[i] && algo == PET_ALGO_SVREM) {
+            PET_TRY(cuda_ok(cudaMemcpyAsync(st->f_anc, in, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
+                            "anchor copy"));
+            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+            PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, st->f_anc, st->s_anc, st->s_hat,
+                                               !st->s_hat_ready, s));
+            st->s_hat_ready = true;
+        } else if (anchors[i] && algo == PET_ALGO_SVRG) {
+            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+            PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
+        }
+        return enqueue_update(st, algo, st->d_seq + i, in, outp, alpha, s);
+    });
+}
+
+bool use_graphs() {
+    static const bool on = [] {
+        const char *e = std::getenv("PETVR_NO_GRAPHS");
+        return !(e && e[0] && e[0] != '0');
+    }();
+    return on;
+}
+
+// Capture `enqueue` once on the state's private stream, cache the executable
+// graph under `key`, and launch it on `s`.
+template <class Enqueue>
+pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_t s, Enqueue &&enqueue) {
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : st->graphs)
+        if (g.first == key) exec = g.second;
+    if (!exec) {
+        if (!st->cap) PET_TRY(cuda_ok(cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking), "capture stream"));
+        PET_TRY(cuda_ok(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal), "begin capture"));
+        const pet_status est = enqueue(st->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st->cap, &graph);
+        if (est != PET_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return est;
+        }
+        PET_TRY(cuda_ok(ce, "end capture"));
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        PET_TRY(cuda_ok(ie, "graph instantiate"));
+        st->graphs.emplace_back(key, exec);
+    }
+    return cuda_ok(cudaGraphLaunch(exec, s), "graph launch");
 }
 
 pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_iter, float alpha, int32_t eta,
@@ -648,49 +763,38 @@ pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_i
     if (!std::isfinite(alpha)) return set_error(PET_ERR_INVALID, "alpha must be finite");
     if ((algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) && eta < 1)
         return set_error(PET_ERR_INVALID, "eta must be >= 1");
-    const long long plane = plane_of(pl);
-    return pingpong(st->img, st->alt, plane, n_iter, s, [&](int i, const float *in, float *outp) {
-        const int t = seq[i];
-        const bool anchor = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) &&
-                            (st->k % ((long long)eta * pl->ns) == 0);
-        if (anchor && algo == PET_ALGO_SVREM) {
-            PET_TRY(cuda_ok(cudaMemcpyAsync(st->f_anc, in, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
-                            "anchor copy"));
-            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
-            PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, st->f_anc, st->s_anc, st->s_hat,
-                                               st->k == 0, s));
-        } else if (anchor && algo == PET_ALGO_SVRG) {
-            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
-            PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
+    if (n_iter == 0) return PET_OK;
+    if (n_iter > st->seq_cap) {
+        int *grown = nullptr;
+        PET_TRY(dalloc(&grown, (size_t)n_iter, "subset sequence"));
+        // the old buffer may still be read by enqueued work: release it after the stream drains
+        if (st->d_seq) {
+            PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+            dfree(st->d_seq);
         }
-        PET_TRY(ratio_subset(p, in, t, st->ratio, s));
-        BackArgs b = back_args(pl, st->ratio, t, false);
-        b.f = in;
-        b.f_out = outp;
-        b.beta = p->pen.beta;
-        b.alpha = alpha;
-        int epi = EPI_OSEM;
-        if (algo == PET_ALGO_SVREM) {
-            epi = EPI_SVREM;
-            b.s_hat = st->s_hat;
-            b.f_anc = st->f_anc;
-            b.s_anc = st->s_anc;
-            b.B = st->B;
-        } else if (algo == PET_ALGO_SAGA) {
-            epi = EPI_SAGA;
-            b.d = st->d;
-            b.table = st->table;
-            b.qbar = st->qbar;
-        } else if (algo == PET_ALGO_SVRG) {
-            epi = EPI_SVRG;
-            b.d = st->d;
-            b.B = st->B;
-            b.qtil = st->qtil;
-        }
-        PET_TRY(launch_back(b, epi, st->table_dtype, 1, s));
-        st->k += 1;
-        return PET_OK;
-    });
+        st->d_seq = grown;
+        st->seq_cap = n_iter;
+        for (auto &g : st->graphs) cudaGraphExecDestroy(g.second);
+        st->graphs.clear();
+    }
+    PET_TRY(cuda_ok(cudaMemcpyAsync(st->d_seq, seq, sizeof(int32_t) * n_iter, cudaMemcpyHostToDevice, s),
+                    "subset sequence copy"));
+    std::vector<uint8_t> anchors((size_t)n_iter, 0);
+    if (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG)
+        for (int i = 0; i < n_iter; ++i) anchors[i] = ((st->k + i) % ((long long)eta * pl->ns) == 0) ? 1 : 0;
+    pet_status rc;
+    // SVREM's first anchor also initialises s_hat: that epoch shape is enqueued directly
+    const bool first_svrem = algo == PET_ALGO_SVREM && !st->s_hat_ready;
+    if (!use_graphs() || profiling_enabled() || first_svrem) {
+        rc = enqueue_epoch(st, algo, n_iter, alpha, anchors, s);
+    } else {
+        std::vector<int64_t> key = {n_iter, (int64_t)std::llround((double)alpha * 1e9), eta};
+        for (int i = 0; i < n_iter; ++i)
+            if (anchors[i]) key.push_back(i);
+        rc = run_graph(st, key, s, [&](cudaStream_t cs) { return enqueue_epoch(st, algo, n_iter, alpha, anchors, cs); });
+    }
+    if (rc == PET_OK) st->k += n_iter;
+    return rc;
 }
 
 }  // namespace
@@ -713,6 +817,17 @@ pet_status pet_saga_epoch(pet_state *st, float alpha, const int32_t *seq, int32_
 pet_status pet_svrg_epoch(pet_state *st, float alpha, int32_t eta, const int32_t *seq, int32_t n_iter,
                           void *stream) {
     return epoch_common(st, PET_ALGO_SVRG, seq, n_iter, alpha, eta, (cudaStream_t)stream);
+}
+
+pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream) {
+    if (!st || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!use_graphs() || profiling_enabled())
+        return objective_enqueue(st->prob, st->img, d_phi, st->d_part, s);
+    const std::vector<int64_t> key = {-1, (int64_t)(intptr_t)d_phi};
+    return run_graph(st, key, s, [&](cudaStream_t cs) {
+        return objective_enqueue(st->prob, st->img, d_phi, st->d_part, cs);
+    });
 }
 
 pet_status pet_state_sync(pet_state *st, void *stream) {

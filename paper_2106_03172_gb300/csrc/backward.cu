@@ -1,12 +1,14 @@
 // Back projection as a pixel-driven gather (K2), fused with the per-pixel
 // update of each method (K3).
 //
-// b_n = sum_{m in S_t} a_mn r_m: one thread per (pixel, slice) walks the
-// views of the subset; in each view only the 1-4 bins whose ray crosses the
-// pixel's major band near the pixel are candidates, found from the bin
-// spacing K, and each candidate's weight comes from band_weights(), the same
-// function the forward kernel uses, so A^T here is the exact transpose of A
-// there.  A gather (not atomics) keeps the result deterministic.
+// b_n = sum_{m in S_t} a_mn r_m: four lanes per (pixel, slice) share the
+// views of the subset (lane l takes views l, l+4, ...) and combine with an
+// xor-shuffle in a fixed order.  In each view only the bins whose ray can
+// cross the pixel's major band at the pixel are candidates (usually 2-3),
+// found from the bin spacing K, and each candidate's weight comes from
+// band_point() / band_split(), the functions the forward kernel uses, so A^T
+// here is the exact transpose of A there.  A gather (not atomics) keeps the
+// result deterministic.
 //
 // The epilogue then applies, with b_n still in a register (§8 of the method's
 // update rules; the quadratic 4-neighbour penalty of §3 is read from f^k):
@@ -27,6 +29,8 @@ namespace petvr {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kLanes = 4;           // lanes per (pixel, slice); each takes every 4th view
+constexpr float kCandEps = 1e-3f;   // candidate-bin margin (pixels)
 
 struct Stencil {
     float cnt;   // number of in-image 4-neighbours (sum_j d_nj for the quadratic potential)
@@ -65,43 +69,64 @@ template <> __device__ __forceinline__ void store_q<__nv_bfloat16>(void *p, long
 
 template <int EPI, typename TQ>
 __global__ void __launch_bounds__(kBlock) back_kernel(const BackArgs a) {
+    // the subset's view table, staged once per block
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    for (int q = threadIdx.x; q < nv; q += kBlock) {
+        const int v = __ldg(a.order + vb + q);
+        s_vid[q] = v;
+        s_views[q] = a.views[v];
+    }
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
     const long long plane = (long long)a.nx * a.ny * a.nz;
-    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;   // (pixel, slice)
-    if (i >= plane) return;
-    const int t = a.t0 + (int)blockIdx.y;
+    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const long long i = gid / kLanes;                    // (pixel, slice)
+    const int lane = (int)(gid % kLanes);
+    const bool live = i < plane;
     const int z = (int)(i % a.nz);
     const int n = (int)(i / a.nz);
     const int ix = n % a.nx;
     const int iy = n / a.nx;
-    const int vb = __ldg(a.sub_off + t);
-    const int ve = __ldg(a.sub_off + t + 1);
 
     float acc = 0.0f;
-    for (int p = vb; p < ve; ++p) {
-        const int v = __ldg(a.order + p);
-        const ViewParams vp = a.views[v];
-        const int k = vp.col ? ix : iy;                 // major index
-        const int minor = vp.col ? iy : ix;
-        const int n_major = vp.col ? a.nx : a.ny;
-        const int n_minor = vp.col ? a.ny : a.nx;
-        const int mrel = minor - (n_minor >> 1);
-        const float kc = (float)k - 0.5f * (float)n_major;
-        // bins whose band interval can overlap [mrel, mrel + 1]
-        const float base = fmaf(kc, vp.du, vp.uc0);
-        const float e1 = ((float)mrel - fmaxf(vp.du, 0.0f) - base) / vp.K;
-        const float e2 = ((float)mrel + 1.0f - fminf(vp.du, 0.0f) - base) / vp.K;
-        const int jlo = max(0, (int)floorf(fminf(e1, e2)) - 1);
-        const int jhi = min(a.nb - 1, (int)ceilf(fmaxf(e1, e2)) + 1);
-        const float *rv = a.r + ((long long)(p - a.r_view0) * a.nb) * a.nz + z;
-        const float *ucv = a.uc + (long long)v * a.nb;
-        for (int j = jlo; j <= jhi; ++j) {
-            int c0;
-            float w0, w1;
-            band_weights(vp, __ldg(ucv + j), kc, c0, w0, w1);
-            const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
-            if (w != 0.0f) acc = fmaf(w, __ldg(rv + (long long)j * a.nz), acc);
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            // bins whose band interval can overlap [mrel, mrel + 1], with a margin
+            // far above the rounding of the approximate bin positions
+            const float base = fmaf(kc, vp.du, vp.uc0);
+            const float e1 = ((float)mrel - fmaxf(vp.du, 0.0f) - base - kCandEps) * vp.invK;
+            const float e2 = ((float)mrel + 1.0f - fminf(vp.du, 0.0f) - base + kCandEps) * vp.invK;
+            const int jlo = max(0, (int)ceilf(fminf(e1, e2)));
+            const int jhi = min(a.nb - 1, (int)floorf(fmaxf(e1, e2)));
+            const float2 *ucv = a.uc + (long long)v * a.nb;
+            const float *rv = a.r + ((long long)(vb + q - r_view0) * a.nb) * a.nz + z;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
+                if (w != 0.0f) acc = fmaf(w, __ldg(rv + (long long)j * a.nz), acc);
+            }
         }
     }
+#pragma unroll
+    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!live || lane != 0) return;
 
     const float inv_ns = 1.0f / (float)a.ns;
     if (EPI == EPI_PLAIN) {
@@ -154,31 +179,31 @@ __global__ void __launch_bounds__(kBlock) back_kernel(const BackArgs a) {
 }
 
 template <int EPI, typename TQ>
-pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s) {
-    const long long plane = (long long)a.nx * a.ny * a.nz;
-    const dim3 grid((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)ny_grid);
-    back_kernel<EPI, TQ><<<grid, kBlock, 0, s>>>(a);
+pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
+    const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
+    const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
+    const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
+    back_kernel<EPI, TQ><<<grid, kBlock, smem, s>>>(a);
     return check_launch("back_kernel");
 }
 
 }  // namespace
 
 pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
-                       cudaStream_t s) {
+                       cudaStream_t s, int max_views) {
     const bool bf = table_dtype == PET_TABLE_BF16;
-    ProfileScope prof(n_subsets_grid > 1 ? 2 : 1, s);
+    const int g = n_subsets_grid;
+    const int mv = max_views;
+    ProfileScope prof(g > 1 ? 2 : 1, s);
     switch (epi) {
-        case EPI_PLAIN: return go<EPI_PLAIN, float>(a, n_subsets_grid, s);
-        case EPI_OSEM: return go<EPI_OSEM, float>(a, n_subsets_grid, s);
-        case EPI_SVREM: return go<EPI_SVREM, float>(a, n_subsets_grid, s);
-        case EPI_SVRG: return go<EPI_SVRG, float>(a, n_subsets_grid, s);
-        case EPI_ANCHOR: return go<EPI_ANCHOR, float>(a, n_subsets_grid, s);
-        case EPI_SAGA:
-            return bf ? go<EPI_SAGA, __nv_bfloat16>(a, n_subsets_grid, s)
-                      : go<EPI_SAGA, float>(a, n_subsets_grid, s);
+        case EPI_PLAIN: return go<EPI_PLAIN, float>(a, g, s, mv);
+        case EPI_OSEM: return go<EPI_OSEM, float>(a, g, s, mv);
+        case EPI_SVREM: return go<EPI_SVREM, float>(a, g, s, mv);
+        case EPI_SVRG: return go<EPI_SVRG, float>(a, g, s, mv);
+        case EPI_ANCHOR: return go<EPI_ANCHOR, float>(a, g, s, mv);
+        case EPI_SAGA: return bf ? go<EPI_SAGA, __nv_bfloat16>(a, g, s, mv) : go<EPI_SAGA, float>(a, g, s, mv);
         case EPI_SAGA_INIT:
-            return bf ? go<EPI_SAGA_INIT, __nv_bfloat16>(a, n_subsets_grid, s)
-                      : go<EPI_SAGA_INIT, float>(a, n_subsets_grid, s);
+            return bf ? go<EPI_SAGA_INIT, __nv_bfloat16>(a, g, s, mv) : go<EPI_SAGA_INIT, float>(a, g, s, mv);
         default: return set_error(PET_ERR_INVALID, "back: unknown epilogue");
     }
 }

@@ -12,6 +12,11 @@
 // shuffle all-reduce combines the chunks in a fixed order (deterministic).
 // For slice stacks (nz > 1) lanes run along the slice index instead
 // (GROUP = 1): consecutive lanes read consecutive floats of one pixel column.
+//
+// The view range is either given on the host (v_begin/v_end) or, when
+// a.t_dev is set, read on the device from the subset offsets, so that one
+// captured launch serves any subset; the grid then covers the largest subset
+// and surplus threads only take part in the reduction.
 #include "petvr_internal.cuh"
 
 namespace petvr {
@@ -20,9 +25,30 @@ namespace {
 
 constexpr int kBlock = 256;
 
+struct RayRange {
+    int v_begin, v_end;
+    long long off;   // element offset of the range's first ray in g / w (compact layouts)
+};
+
+__device__ __forceinline__ RayRange ray_range(const FwdArgs &a) {
+    RayRange r;
+    if (a.t_dev) {
+        const int t = __ldg(a.t_dev);
+        r.v_begin = __ldg(a.sub_off + t);
+        r.v_end = __ldg(a.sub_off + t + 1);
+        r.off = (long long)r.v_begin * a.nb * a.nz;
+    } else {
+        r.v_begin = a.v_begin;
+        r.v_end = a.v_end;
+        r.off = 0;
+    }
+    return r;
+}
+
 template <int GROUP, int MODE, bool LL>
 __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
-    const long long n_rays = (long long)(a.v_end - a.v_begin) * a.nb;
+    const RayRange rr = ray_range(a);
+    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     const int z = (int)(tid % a.nz);
     const long long rest = tid / a.nz;
@@ -32,17 +58,16 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
 
     float acc = 0.0f;
     if (live) {
-        const int p = a.v_begin + (int)(ray / a.nb);
+        const int p = rr.v_begin + (int)(ray / a.nb);
         const int j = (int)(ray % a.nb);
         const int v = __ldg(a.order + p);
         const ViewParams vp = a.views[v];
-        const float uc = __ldg(a.uc + (long long)v * a.nb + j);
+        const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
         const int n_major = vp.col ? a.nx : a.ny;
         const int n_minor = vp.col ? a.ny : a.nx;
-        const int s_major = vp.col ? 1 : a.nx;
-        const int s_minor = vp.col ? a.nx : 1;
         const int mo = n_minor >> 1;
         const float hm = 0.5f * (float)n_major;
+        const float uc = u.x + u.y;
         // bands where the ray can meet the image (a superset; extra bands add 0)
         int k_lo = 0, k_hi = n_major;
         if (vp.du == 0.0f) {
@@ -60,17 +85,26 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
         const int per = (cnt + GROUP - 1) / GROUP;
         const int kb = k_lo + lane_g * per;
         const int ke = min(k_hi, kb + per);
-        const float *img = a.img + z;
-        const long long sm = (long long)s_minor * a.nz;
-        for (int k = kb; k < ke; ++k) {
-            int c0;
-            float w0, w1;
-            band_weights(vp, uc, (float)k - hm, c0, w0, w1);
-            const int m0 = c0 + mo;
-            const float *row = img + (long long)k * s_major * a.nz;
-            if ((unsigned)m0 < (unsigned)n_minor) acc = fmaf(w0, __ldg(row + m0 * sm), acc);
-            if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor)
-                acc = fmaf(w1, __ldg(row + (m0 + 1) * sm), acc);
+        if (kb < ke) {
+            // 32-bit strides: images are below 2^31 elements (checked at plan time)
+            const int s_major = (vp.col ? 1 : a.nx) * a.nz;
+            const int s_minor = (vp.col ? a.nx : 1) * a.nz;
+            const int ui = (int)u.x + mo;              // pixel index of fractional position 0
+            const float *rowp = a.img + z + kb * s_major;
+            float kc = (float)kb - hm;
+            float va = band_point(vp, u.y, kc);
+            for (int k = kb; k < ke; ++k) {
+                kc += 1.0f;
+                const float vb = band_point(vp, u.y, kc);
+                float fl, w0, w1;
+                band_split(vp, va, vb, fl, w0, w1);
+                const int m0 = (int)fl + ui;
+                if ((unsigned)m0 < (unsigned)n_minor) acc = fmaf(w0, __ldg(rowp + m0 * s_minor), acc);
+                if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor)
+                    acc = fmaf(w1, __ldg(rowp + (m0 + 1) * s_minor), acc);
+                va = vb;
+                rowp += s_major;
+            }
         }
     }
 #pragma unroll
@@ -79,10 +113,11 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
     double ll = 0.0;
     if (live && lane_g == 0) {
         const long long idx = ray * a.nz + z;
-        const float yhat = acc + (a.w ? __ldg(a.w + idx) : a.w_scalar);
+        const long long gi = rr.off + idx;
+        const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
         if (MODE == FWD_YHAT) a.out[idx] = yhat;
         if (MODE == FWD_RATIO || LL) {
-            const float g = __ldg(a.g + idx);
+            const float g = __ldg(a.g + gi);
             if (MODE == FWD_RATIO) a.out[idx] = (yhat != 0.0f) ? g / yhat : 0.0f;
             if (LL) {
                 if (yhat > 0.0f) {
@@ -122,18 +157,22 @@ __global__ void __launch_bounds__(kBlock) count_nnz_kernel(const FwdArgs a, unsi
         const int j = (int)(ray % a.nb);
         const int v = a.order[p];
         const ViewParams vp = a.views[v];
-        const float uc = a.uc[(long long)v * a.nb + j];
+        const float2 u = a.uc[(long long)v * a.nb + j];
         const int n_major = vp.col ? a.nx : a.ny;
         const int n_minor = vp.col ? a.ny : a.nx;
-        const int mo = n_minor >> 1;
+        const int ui = (int)u.x + (n_minor >> 1);
         const float hm = 0.5f * (float)n_major;
+        float kc = -hm;
+        float va = band_point(vp, u.y, kc);
         for (int k = 0; k < n_major; ++k) {
-            int c0;
-            float w0, w1;
-            band_weights(vp, uc, (float)k - hm, c0, w0, w1);
-            const int m0 = c0 + mo;
+            kc += 1.0f;
+            const float vb = band_point(vp, u.y, kc);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
             c += (w0 > 0.0f && (unsigned)m0 < (unsigned)n_minor) ? 1 : 0;
             c += (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor) ? 1 : 0;
+            va = vb;
         }
     }
 #pragma unroll
@@ -173,15 +212,14 @@ int forward_blocks(int n_rays, int nz, int group) {
 int choose_group(const pet_plan *plan) {
     if (plan->nz > 1) return 1;
     const int n = plan->nx > plan->ny ? plan->nx : plan->ny;
-    if (n >= 384) return 32;
-    if (n >= 192) return 16;
-    if (n >= 96) return 8;
-    return 4;
+    if (n >= 160) return 32;
+    if (n >= 80) return 16;
+    return 8;
 }
 
-pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s,
-                          int *n_blocks_out) {
-    const int n_rays = (a.v_end - a.v_begin) * a.nb;
+pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s, int *n_blocks_out,
+                          int rays_for_grid) {
+    const int n_rays = rays_for_grid >= 0 ? rays_for_grid : (a.v_end - a.v_begin) * a.nb;
     const int blocks = forward_blocks(n_rays, a.nz, group);
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
@@ -189,7 +227,6 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
     ProfileScope prof(0, s);
     switch (group) {
         case 1: return dispatch_mode<1>(a, mode, ll, blocks, s);
-        case 4: return dispatch_mode<4>(a, mode, ll, blocks, s);
         case 8: return dispatch_mode<8>(a, mode, ll, blocks, s);
         case 16: return dispatch_mode<16>(a, mode, ll, blocks, s);
         case 32: return dispatch_mode<32>(a, mode, ll, blocks, s);

@@ -178,16 +178,16 @@ pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s
     return check_launch("uniform_fill_kernel");
 }
 
-pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks, double *d_out,
-                                   cudaStream_t s) {
+pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks, double *part,
+                                   double *d_out, cudaStream_t s) {
     const pet_plan *pl = p->plan;
     const long long plane = (long long)pl->N * pl->nz;
     const int n_pen = (int)blocks_for(plane);
-    double *pen_part = p->d_part + n_ll_blocks;
+    double *pen_part = part + n_ll_blocks;
     penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, pl->nx, pl->ny, pl->nz, pen_part);
     pet_status st = check_launch("penalty_partial_kernel");
     if (st != PET_OK) return st;
-    objective_final_kernel<<<1, kBlock, 0, s>>>(p->d_part, n_ll_blocks, pen_part, n_pen, (double)p->pen.beta,
+    objective_final_kernel<<<1, kBlock, 0, s>>>(part, n_ll_blocks, pen_part, n_pen, (double)p->pen.beta,
                                                 d_out);
     return check_launch("objective_final_kernel");
 }

@@ -7,7 +7,9 @@
 
 #include <atomic>
 #include <cstdint>
+#include <cstdlib>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "petvr.h"
@@ -33,29 +35,40 @@ namespace petvr {
 // mo = n_minor / 2), so that floor(u) + mo is the pixel index and axis-
 // aligned rays on grid lines land on integers exactly (half-open pixels: the
 // +x / +y pixel takes a ray lying on their shared edge).
+//
+// Precision: near-axis views (|du| small) turn an error e in u into an error
+// e / |du| in where the ray crosses the nearly parallel grid line.  Each ray
+// therefore carries its offset as an integer ui plus a fraction uf in
+// [-1/2, 1/2] (both from FP64 on the host), the slope as du + du_lo (FP32
+// value and its FP64 rounding residual), and u - ui is evaluated as
+// uf + kc (du + du_lo), whose magnitude stays small exactly when |du| is.
 // ---------------------------------------------------------------------------
 struct ViewParams {
-    float du;    // minor displacement (pixels) per major step
-    float L;     // ray length (mm) per major step
-    float Lm;    // ray length (mm) per pixel of minor displacement (0 if du == 0)
-    float K;     // minor displacement (pixels) per bin step (never 0)
-    float uc0;   // centred minor coordinate of bin 0 at the central major line
-    int col;     // 1: major axis is x (columns); 0: major axis is y (rows)
-    int pad0, pad1;
+    float du;     // minor displacement (pixels) per major step (FP32 value)
+    float du_lo;  // FP64 residual du_exact - du
+    float L;      // ray length (mm) per major step
+    float Lm;     // ray length (mm) per pixel of minor displacement (0 if du == 0)
+    float K;      // minor displacement (pixels) per bin step (never 0)
+    float invK;   // 1 / K
+    float uc0;    // centred minor coordinate of bin 0 at the central major line (approx.)
+    int col;      // 1: major axis is x (columns); 0: major axis is y (rows)
 };
 
-// Weights of one ray in major band k: w0 for pixel (k, c0) and w1 for pixel
-// (k, c0 + 1), c0 relative to the centre edge (add mo for the index).
-// Forward and back projection both call this, so a_mn is bit-identical in
-// the two directions.
-__device__ __forceinline__ void band_weights(const ViewParams &vp, float uc, float kc, int &c0,
-                                             float &w0, float &w1) {
-    const float ua = fmaf(kc, vp.du, uc);
-    const float ub = fmaf(kc + 1.0f, vp.du, uc);
-    const float lo = fminf(ua, ub);
-    const float hi = fmaxf(ua, ub);
-    const float fl = floorf(lo);
-    c0 = (int)fl;
+// Fractional minor position u - ui of a ray at band boundary kc (centred
+// major coordinate).  Both projectors evaluate exactly this expression.
+__device__ __forceinline__ float band_point(const ViewParams &vp, float uf, float kc) {
+    return fmaf(kc, vp.du, fmaf(kc, vp.du_lo, uf));
+}
+
+// Split of one major band between the two minor pixels it can touch, given
+// the fractional positions va, vb at its two boundaries: pixel fl (relative
+// to ui) gets w0, pixel fl + 1 gets w1.  Forward and back projection both call
+// this, so a_mn is bit-identical in the two directions.
+__device__ __forceinline__ void band_split(const ViewParams &vp, float va, float vb, float &fl, float &w0,
+                                           float &w1) {
+    const float lo = fminf(va, vb);
+    const float hi = fmaxf(va, vb);
+    fl = floorf(lo);
     if (hi <= fl + 1.0f) {
         w0 = vp.L;
         w1 = 0.0f;
@@ -81,9 +94,12 @@ enum FwdMode { FWD_NONE = 0, FWD_YHAT = 1, FWD_RATIO = 2 };
 
 struct FwdArgs {
     const ViewParams *views;  // [n_angles]
-    const float *uc;          // [n_angles * n_bins] centred minor coordinate per ray
+    const float2 *uc;         // [n_angles * n_bins] (ui, uf) centred minor offset per ray
     const int *order;         // view order the ray range indexes
     int v_begin, v_end;       // view positions [v_begin, v_end) of `order`
+    const int *t_dev;         // if set: subset index on the device; the range is
+    const int *sub_off;       //   [sub_off[t], sub_off[t+1]) and g / w are the full
+                              //   subset-major arrays (offset applied on the device)
     int nx, ny, nz, nb;
     const float *img;         // [ny][nx][nz]
     const float *g;           // counts of these rays (compact), FWD_RATIO / LL only
@@ -106,11 +122,13 @@ enum BackEpi {
 
 struct BackArgs {
     const ViewParams *views;
-    const float *uc;
+    const float2 *uc;
     const int *order;
     const int *sub_off;   // view offsets of subsets in `order`
     int t0;               // subset of blockIdx.y == 0
-    int r_view0;          // view position of r[0]
+    const int *t_dev;     // if set: the subset index is read here (grid.y must be 1)
+    int r_view0;          // view position of r[0] (ignored when t_dev is set: r is
+                          //   then the compact ratio of subset *t_dev)
     int nx, ny, nz, nb, ns;
     const float *r;       // ratio / sinogram, [view pos - r_view0][bin][z]
     float *out;           // EPI_PLAIN: image; EPI_ANCHOR: B [ns][N*nz]
@@ -146,7 +164,7 @@ struct pet_plan {
     std::vector<int> sub_off;       // [ns + 1]
     std::vector<long long> nnz;     // [ns] nonzeros of A_t (one slice)
     petvr::ViewParams *d_views = nullptr;
-    float *d_uc = nullptr;
+    float2 *d_uc = nullptr;
     int *d_order = nullptr;         // subset-major
     int *d_natural = nullptr;       // identity
     int *d_sub_off = nullptr;       // [ns + 1]
@@ -181,6 +199,13 @@ struct pet_state {
     void *table = nullptr;
     long long k = 0;
     size_t bytes = 0;
+    bool s_hat_ready = false;       // SVREM: s_hat initialised by the first anchor
+    int *d_seq = nullptr;           // device copy of the current call's subset sequence
+    int seq_cap = 0;
+    double *d_part = nullptr;       // objective reduction scratch of this state
+    int n_part = 0;
+    cudaStream_t cap = nullptr;     // private stream for graph capture
+    std::vector<std::pair<std::vector<int64_t>, cudaGraphExec_t>> graphs;   // captured epochs
 };
 
 namespace petvr {
@@ -197,20 +222,21 @@ struct ProfileScope {
 };
 pet_status set_error(pet_status code, const std::string &msg);
 pet_status check_launch(const char *what);
+bool profiling_enabled();
 
 // Kernel launchers (forward.cu / backward.cu / misc.cu).
 pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s,
-                          int *n_blocks_out);
+                          int *n_blocks_out, int rays_for_grid = -1);
 int forward_blocks(int n_rays, int nz, int group);
 int choose_group(const pet_plan *plan);
 pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
-                       cudaStream_t s);
+                       cudaStream_t s, int max_views);
 pet_status launch_permute_sino(const float *src, float *dst, const int *order, int na, int nb, int nz,
                                cudaStream_t s);
 pet_status launch_sum_sens(const float *sens_t, float *sens, int ns, int N, cudaStream_t s);
 pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s);
 pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks,
-                                   double *d_out, cudaStream_t s);
+                                   double *part, double *d_out, cudaStream_t s);
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
 pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz,
                                       const float *f_anc, float *s_anc, float *s_hat, bool init,

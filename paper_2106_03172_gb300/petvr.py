@@ -71,6 +71,7 @@ _SIGS = {
     "pet_saga_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
     "pet_svrg_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
     "pet_state_sync": (c_int32, [c_void_p, c_void_p]),
+    "pet_state_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
     "pet_last_error": (ctypes.c_char_p, []),
 }
@@ -224,6 +225,11 @@ def pet_saga_epoch(state, alpha: float, seq, stream=None):
 def pet_svrg_epoch(state, alpha: float, eta: int, seq, stream=None):
     arr, n = _seq(seq)
     _call("pet_svrg_epoch", state, alpha, eta, arr, n, _stream(stream))
+
+
+def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):
+    """Enqueue Phi, L, R of the state's current image into ``phi_out`` (3 float64)."""
+    _call("pet_state_objective_async", state, _dev(phi_out, torch.float64), _stream(stream))
 
 
 def pet_state_sync(state, stream=None):
