@@ -67,7 +67,9 @@ enum { PET_POT_QUADRATIC = 0 };
  * bin_mm (bin_mm <= 0 means bin_mm = pixel_mm).  Ray (i, j) is the line
  * x cos(theta_i) + y sin(theta_i) = s_j and a_mn is its length (mm) inside
  * pixel n: the exact Siddon intersection length (the paper's forward model is
- * a Radon transform, §5.1; A is any nonnegative system matrix, §2.1). */
+ * a Radon transform, §5.1; A is any nonnegative system matrix, §2.1).
+ * Limits: nx, ny <= 16384, n_angles <= 1024, nx*ny*nz and n_angles*n_bins*nz
+ * below 2^31. */
 typedef struct {
     int32_t nx, ny, nz;
     double pixel_mm;
@@ -178,6 +180,13 @@ pet_status pet_state_create(const pet_problem *problem, int32_t algo, int32_t ta
                             void *stream);
 pet_status pet_state_destroy(pet_state *state);
 
+/* Restart the state from the image currently in its d_img_inout buffer, as
+ * pet_state_create would (update counter to 0, SAGA table / SVRG and SAGA
+ * preconditioner recomputed, SVREM statistic re-initialised at the next
+ * anchor), without allocating: a slot can serve a new reconstruction.
+ * Enqueued on `stream`. */
+pet_status pet_state_reset(pet_state *state, void *stream);
+
 /* n_iter updates (an epoch is n_iter = n_subsets) with subset indices
  * h_subset_seq[0..n_iter-1], each in [0, n_subsets).  The update counter k
  * persists across calls; anchors are refreshed when k mod (eta N_s) == 0.
@@ -214,7 +223,8 @@ pet_status pet_state_objective_async(pet_state *state, double *d_phi, void *stre
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);
 
-/* Number of kernels this library has launched in this process (all threads). */
+/* Number of kernels this library has launched in this process (all threads),
+ * kernels replayed from its captured graphs included. */
 uint64_t pet_kernel_launches(void);
 
 /* Optional per-kernel timing for profiling: while enabled, every forward and

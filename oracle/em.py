@@ -184,6 +184,22 @@ def map_em(prob: Problem, f, max_iter=100000, tol=1e-10):
     return f, hist
 
 
+def map_reference(prob: Problem, f0=None, maxiter=20000):
+    """Maximiser f* and Phi* of max_{f>=0} Phi by bounded L-BFGS-B, the kind of
+    reference solver the paper uses for its error curves (§5.1).  Returns
+    (f*, Phi*, KKT residual)."""
+    import scipy.optimize
+    x0 = (prob.initial_image() if f0 is None else f0).ravel()
+    shape = (prob.N, prob.nz)
+    res = scipy.optimize.minimize(
+        lambda x: -prob.objective(x.reshape(shape)), x0,
+        jac=lambda x: -prob.grad_Phi(x.reshape(shape)).ravel(), method="L-BFGS-B",
+        bounds=[(0.0, None)] * x0.size,
+        options={"maxiter": maxiter, "ftol": 1e-16, "gtol": 1e-10, "maxcor": 30})
+    fs = res.x.reshape(shape)
+    return fs, prob.objective(fs), kkt_residual(prob, fs)
+
+
 def kkt_residual(prob: Problem, f):
     """|| f - P_{>=0}(f + D grad Phi(f)) || / ||f|| with the EM scaling
     D = f / A^T 1: zero exactly at a KKT point of max_{f>=0} Phi."""

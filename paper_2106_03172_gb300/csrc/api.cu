@@ -204,6 +204,29 @@ pet_status read_status(const pet_problem *p, cudaStream_t s) {
     return PET_OK;
 }
 
+// (Re)initialise an allocated state at its current image: update counter,
+// SVREM statistic flag, SAGA table/mean/preconditioner, SVRG preconditioner.
+pet_status state_init(pet_state *st, cudaStream_t s) {
+    const pet_problem *p = st->prob;
+    const pet_plan *pl = p->plan;
+    const long long Nz = plane_of(pl);
+    st->k = 0;
+    st->s_hat_ready = false;
+    if (st->algo == PET_ALGO_SVRG) return launch_precond(st->img, pl->d_sens, pl->ns, Nz, pl->nz, st->d, s);
+    if (st->algo != PET_ALGO_SAGA) return PET_OK;
+    // table q_t = grad Phi_t(f^(0)) for all t, then qbar and d
+    PET_TRY(ratio_all(p, st->img, p->d_ratio, s));
+    BackArgs b = back_args(pl, p->d_ratio, -1, false);
+    b.t0 = 0;
+    b.r_view0 = 0;
+    b.f = st->img;
+    b.beta = p->pen.beta;
+    b.table = st->table;
+    PET_TRY(launch_back(b, EPI_SAGA_INIT, st->table_dtype, pl->ns, s, pl->max_sub_views));
+    return launch_saga_finish(st->table, st->table_dtype, pl->ns, Nz, pl->nz, st->img, pl->d_sens, st->qbar, st->d,
+                              s);
+}
+
 // Phi, L, R of d_img into d_phi (3 doubles), using `part` as block-partial scratch.
 pet_status objective_enqueue(const pet_problem *p, const float *d_img, double *d_phi, double *part,
                              cudaStream_t s) {
@@ -282,6 +305,7 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->n_angles < 1 || g->n_bins < 1)
         return set_error(PET_ERR_INVALID, "geometry sizes must be >= 1");
     if (g->nx > 16384 || g->ny > 16384) return set_error(PET_ERR_INVALID, "nx, ny must be <= 16384");
+    if (g->n_angles > 1024) return set_error(PET_ERR_INVALID, "n_angles must be <= 1024");
     if (!(g->pixel_mm > 0.0) || !std::isfinite(g->pixel_mm) || !std::isfinite(g->bin_mm))
         return set_error(PET_ERR_INVALID, "pixel_mm must be positive and finite");
     if (sub->scheme != 0) return set_error(PET_ERR_INVALID, "only the interleaved subset scheme (0) exists");
@@ -560,7 +584,7 @@ pet_status pet_state_destroy(pet_state *st) {
     if (st->table) cudaFree(st->table);
     dfree(st->d_seq);
     dfree(st->d_part);
-    for (auto &g : st->graphs) cudaGraphExecDestroy(g.second);
+    for (auto &g : st->graphs) cudaGraphExecDestroy(g.exec);
     if (st->cap) cudaStreamDestroy(st->cap);
     delete st;
     return PET_OK;
@@ -612,8 +636,6 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
         if ((e = dalloc(&st->qtil, Nz, "q_tilde")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->B, (size_t)pl->ns * Nz, "B")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->ratio_full, Mz, "full ratio")) != PET_OK) return fail(e);
-        if ((e = launch_precond(d_img, pl->d_sens, pl->ns, (long long)Nz, pl->nz, st->d, s)) != PET_OK)
-            return fail(e);
     } else if (algo == PET_ALGO_SAGA) {
         if ((e = dalloc(&st->d, Nz, "d")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->qbar, Nz, "qbar")) != PET_OK) return fail(e);
@@ -623,19 +645,8 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
             st->table = nullptr;
             return fail(set_error(PET_ERR_OOM, "cudaMalloc SAGA table"));
         }
-        // table q_t = grad Phi_t(f^(0)) for all t, then qbar and d
-        if ((e = ratio_all(p, d_img, p->d_ratio, s)) != PET_OK) return fail(e);
-        BackArgs b = back_args(pl, p->d_ratio, -1, false);
-        b.t0 = 0;
-        b.r_view0 = 0;
-        b.f = d_img;
-        b.beta = p->pen.beta;
-        b.table = st->table;
-        if ((e = launch_back(b, EPI_SAGA_INIT, table_dtype, pl->ns, s, pl->max_sub_views)) != PET_OK) return fail(e);
-        if ((e = launch_saga_finish(st->table, table_dtype, pl->ns, (long long)Nz, pl->nz, d_img, pl->d_sens,
-                                    st->qbar, st->d, s)) != PET_OK)
-            return fail(e);
     }
+    if ((e = state_init(st, s)) != PET_OK) return fail(e);
     *out = st;
     return PET_OK;
 }
@@ -731,13 +742,17 @@ bool use_graphs() {
 // graph under `key`, and launch it on `s`.
 template <class Enqueue>
 pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_t s, Enqueue &&enqueue) {
-    cudaGraphExec_t exec = nullptr;
+    pet_state::Graph *hit = nullptr;
     for (auto &g : st->graphs)
-        if (g.first == key) exec = g.second;
-    if (!exec) {
+        if (g.key == key) hit = &g;
+    if (!hit) {
         if (!st->cap) PET_TRY(cuda_ok(cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking), "capture stream"));
         PET_TRY(cuda_ok(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal), "begin capture"));
+        const uint64_t before = g_launches.load();
         const pet_status est = enqueue(st->cap);
+        // launches recorded into the graph are counted when the graph runs
+        const uint64_t kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);
         cudaGraph_t graph = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(st->cap, &graph);
         if (est != PET_OK) {
@@ -745,12 +760,16 @@ pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_
             return est;
         }
         PET_TRY(cuda_ok(ce, "end capture"));
+        cudaGraphExec_t exec = nullptr;
         const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         PET_TRY(cuda_ok(ie, "graph instantiate"));
-        st->graphs.emplace_back(key, exec);
+        st->graphs.push_back({key, exec, kernels});
+        hit = &st->graphs.back();
     }
-    return cuda_ok(cudaGraphLaunch(exec, s), "graph launch");
+    PET_TRY(cuda_ok(cudaGraphLaunch(hit->exec, s), "graph launch"));
+    g_launches.fetch_add(hit->kernels);
+    return PET_OK;
 }
 
 pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_iter, float alpha, int32_t eta,
@@ -774,7 +793,7 @@ pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_i
         }
         st->d_seq = grown;
         st->seq_cap = n_iter;
-        for (auto &g : st->graphs) cudaGraphExecDestroy(g.second);
+        for (auto &g : st->graphs) cudaGraphExecDestroy(g.exec);
         st->graphs.clear();
     }
     PET_TRY(cuda_ok(cudaMemcpyAsync(st->d_seq, seq, sizeof(int32_t) * n_iter, cudaMemcpyHostToDevice, s),
@@ -828,6 +847,11 @@ pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream)
     return run_graph(st, key, s, [&](cudaStream_t cs) {
         return objective_enqueue(st->prob, st->img, d_phi, st->d_part, cs);
     });
+}
+
+pet_status pet_state_reset(pet_state *st, void *stream) {
+    if (!st) return set_error(PET_ERR_INVALID, "null state");
+    return state_init(st, (cudaStream_t)stream);
 }
 
 pet_status pet_state_sync(pet_state *st, void *stream) {

@@ -29,8 +29,12 @@ namespace petvr {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kLanes = 4;           // lanes per (pixel, slice); each takes every 4th view
+constexpr int kLanes = 4;           // slice stacks: lanes per (pixel, slice); each takes every 4th view
 constexpr float kCandEps = 1e-3f;   // candidate-bin margin (pixels)
+constexpr int kTile = 16;           // single slice: a block owns a kTile x kTile tile (kTile^2 == kBlock)
+constexpr int kRun = 8;             // pixels per run along a view's minor axis
+constexpr int kChunk = 16;          // views per shared-memory pass
+static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
 
 struct Stencil {
     float cnt;   // number of in-image 4-neighbours (sum_j d_nj for the quadratic potential)
@@ -67,67 +71,11 @@ template <> __device__ __forceinline__ void store_q<__nv_bfloat16>(void *p, long
     static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(x);
 }
 
+// Per-pixel update after the gather: b = acc is A_t^T r_t at (pixel n, slice z).
 template <int EPI, typename TQ>
-__global__ void __launch_bounds__(kBlock) back_kernel(const BackArgs a) {
-    // the subset's view table, staged once per block
-    extern __shared__ unsigned char smem_raw[];
-    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
-    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
-    const int vb = __ldg(a.sub_off + t);
-    const int nv = __ldg(a.sub_off + t + 1) - vb;
-    int *s_vid = reinterpret_cast<int *>(s_views + nv);
-    for (int q = threadIdx.x; q < nv; q += kBlock) {
-        const int v = __ldg(a.order + vb + q);
-        s_vid[q] = v;
-        s_views[q] = a.views[v];
-    }
-    __syncthreads();
-    const int r_view0 = a.t_dev ? vb : a.r_view0;
-
+__device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long long i, int n, int ix, int iy,
+                                               int z, float acc) {
     const long long plane = (long long)a.nx * a.ny * a.nz;
-    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const long long i = gid / kLanes;                    // (pixel, slice)
-    const int lane = (int)(gid % kLanes);
-    const bool live = i < plane;
-    const int z = (int)(i % a.nz);
-    const int n = (int)(i / a.nz);
-    const int ix = n % a.nx;
-    const int iy = n / a.nx;
-
-    float acc = 0.0f;
-    if (live) {
-        for (int q = lane; q < nv; q += kLanes) {
-            const ViewParams vp = s_views[q];
-            const int v = s_vid[q];
-            const int k = vp.col ? ix : iy;              // major index
-            const int minor = vp.col ? iy : ix;
-            const int n_major = vp.col ? a.nx : a.ny;
-            const int n_minor = vp.col ? a.ny : a.nx;
-            const int mrel = minor - (n_minor >> 1);
-            const float kc = (float)k - 0.5f * (float)n_major;
-            // bins whose band interval can overlap [mrel, mrel + 1], with a margin
-            // far above the rounding of the approximate bin positions
-            const float base = fmaf(kc, vp.du, vp.uc0);
-            const float e1 = ((float)mrel - fmaxf(vp.du, 0.0f) - base - kCandEps) * vp.invK;
-            const float e2 = ((float)mrel + 1.0f - fminf(vp.du, 0.0f) - base + kCandEps) * vp.invK;
-            const int jlo = max(0, (int)ceilf(fminf(e1, e2)));
-            const int jhi = min(a.nb - 1, (int)floorf(fmaxf(e1, e2)));
-            const float2 *ucv = a.uc + (long long)v * a.nb;
-            const float *rv = a.r + ((long long)(vb + q - r_view0) * a.nb) * a.nz + z;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float2 u = __ldg(ucv + j);
-                float fl, w0, w1;
-                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
-                const int c0 = (int)fl + (int)u.x;
-                const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
-                if (w != 0.0f) acc = fmaf(w, __ldg(rv + (long long)j * a.nz), acc);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (!live || lane != 0) return;
-
     const float inv_ns = 1.0f / (float)a.ns;
     if (EPI == EPI_PLAIN) {
         a.out[i] = acc;
@@ -178,13 +126,173 @@ __global__ void __launch_bounds__(kBlock) back_kernel(const BackArgs a) {
     }
 }
 
+// Candidate bins of view vp whose band-kc interval can overlap the minor
+// pixels [m_lo, m_hi): the bin positions uc0 + j K are approximate, so the
+// range carries a margin far above their rounding.
+__device__ __forceinline__ void candidate_bins(const ViewParams &vp, float kc, float m_lo, float m_hi, int nb,
+                                               int &jlo, int &jhi) {
+    const float base = fmaf(kc, vp.du, vp.uc0);
+    const float e1 = (m_lo - fmaxf(vp.du, 0.0f) - base - kCandEps) * vp.invK;
+    const float e2 = (m_hi - fminf(vp.du, 0.0f) - base + kCandEps) * vp.invK;
+    jlo = max(0, (int)ceilf(fminf(e1, e2)));
+    jhi = min(nb - 1, (int)floorf(fmaxf(e1, e2)));
+}
+
+// Stage the views [vb, vb + nv) of `order` into shared memory.
+__device__ __forceinline__ void stage_views(const BackArgs &a, int vb, int nv, ViewParams *s_views, int *s_vid) {
+    for (int q = threadIdx.x; q < nv; q += kBlock) {
+        const int v = __ldg(a.order + vb + q);
+        s_vid[q] = v;
+        s_views[q] = a.views[v];
+    }
+}
+
+// General path (slice stacks): kLanes lanes per (pixel, slice) share the
+// subset's views and combine with an xor-shuffle in a fixed order.
+template <int EPI, typename TQ>
+__global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    stage_views(a, vb, nv, s_views, s_vid);
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    const long long plane = (long long)a.nx * a.ny * a.nz;
+    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const long long i = gid / kLanes;                    // (pixel, slice)
+    const int lane = (int)(gid % kLanes);
+    const bool live = i < plane;
+    const int z = (int)(i % a.nz);
+    const int n = (int)(i / a.nz);
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+
+    float acc = 0.0f;
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
+            const float2 *ucv = a.uc + (long long)v * a.nb;
+            const float *rv = a.r + ((long long)(vb + q - r_view0) * a.nb) * a.nz + z;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
+                if (w != 0.0f) acc = fmaf(w, __ldg(rv + (long long)j * a.nz), acc);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!live || lane != 0) return;
+    apply_epilogue<EPI, TQ>(a, t, i, n, ix, iy, z, acc);
+}
+
+// Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
+// the tile's bands are cut into runs of kRun pixels along the view's minor
+// axis; one thread walks the rays that can cross a run in band order and
+// adds each ray's two band pieces into per-view partial sums in shared
+// memory (every (view, pixel) slot has exactly one writer, so no atomics).
+// Then each thread sums its pixel's partials over the views in a fixed order
+// and applies the update.  Each ray-band split is evaluated once per run
+// instead of once per pixel it touches.  Views are processed in chunks of
+// kChunk to bound shared memory.
+template <int EPI, typename TQ>
+__global__ void __launch_bounds__(kBlock) back_tile_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    float *s_part = reinterpret_cast<float *>(smem_raw);                       // [kChunk][kTile*kTile]
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(s_part + kChunk * kTile * kTile);   // [kChunk]
+    int *s_vid = reinterpret_cast<int *>(s_views + kChunk);
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    const int tiles_x = (a.nx + kTile - 1) / kTile;
+    const int x0 = (blockIdx.x % tiles_x) * kTile;
+    const int y0 = (blockIdx.x / tiles_x) * kTile;
+    constexpr int kRunsPerBand = kTile / kRun;
+    constexpr int kRunsPerView = kTile * kRunsPerBand;
+
+    float acc = 0.0f;
+    for (int q0 = 0; q0 < nv; q0 += kChunk) {
+        const int nq = min(kChunk, nv - q0);
+        stage_views(a, vb + q0, nq, s_views, s_vid);
+        for (int e = threadIdx.x; e < nq * kTile * kTile; e += kBlock) s_part[e] = 0.0f;
+        __syncthreads();
+        for (int run = threadIdx.x; run < nq * kRunsPerView; run += kBlock) {
+            const int ql = run / kRunsPerView;
+            const int rem = run - ql * kRunsPerView;
+            const int band = rem / kRunsPerBand;          // band offset inside the tile
+            const int seg = rem - band * kRunsPerBand;
+            const ViewParams vp = s_views[ql];
+            const int v = s_vid[ql];
+            const int k = (vp.col ? x0 : y0) + band;      // major index
+            const int mstart = (vp.col ? y0 : x0) + seg * kRun;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mlen = min(kRun, n_minor - mstart);
+            if (k >= n_major || mlen <= 0) continue;
+            const int m0rel = mstart - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)m0rel, (float)(m0rel + mlen), a.nb, jlo, jhi);
+            // local pixel index of minor offset c inside the run: row-driven runs
+            // go along x, column-driven runs along y
+            const int lbase = vp.col ? (seg * kRun) * kTile + band : band * kTile + seg * kRun;
+            const int lstep = vp.col ? kTile : 1;
+            float *pp = s_part + ql * kTile * kTile + lbase;
+            const float2 *ucv = a.uc + v * a.nb;
+            const float *rv = a.r + (vb + q0 + ql - r_view0) * a.nb;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c = (int)fl + (int)u.x - m0rel;
+                const float r = __ldg(rv + j);
+                if ((unsigned)c < (unsigned)mlen) pp[c * lstep] += w0 * r;
+                if (w1 > 0.0f && (unsigned)(c + 1) < (unsigned)mlen) pp[(c + 1) * lstep] += w1 * r;
+            }
+        }
+        __syncthreads();
+        for (int ql = 0; ql < nq; ++ql) acc += s_part[ql * kTile * kTile + threadIdx.x];
+        __syncthreads();
+    }
+    const int ix = x0 + (threadIdx.x % kTile);
+    const int iy = y0 + (threadIdx.x / kTile);
+    if (ix >= a.nx || iy >= a.ny) return;
+    const int n = iy * a.nx + ix;
+    apply_epilogue<EPI, TQ>(a, t, n, n, ix, iy, 0, acc);
+}
+
 template <int EPI, typename TQ>
 pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
+    if (a.nz == 1) {
+        const int tiles = ((a.nx + kTile - 1) / kTile) * ((a.ny + kTile - 1) / kTile);
+        const dim3 grid((unsigned)tiles, (unsigned)ny_grid);
+        const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
+        back_tile_kernel<EPI, TQ><<<grid, kBlock, smem, s>>>(a);
+        return check_launch("back_tile_kernel");
+    }
     const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
     const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
     const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
-    back_kernel<EPI, TQ><<<grid, kBlock, smem, s>>>(a);
-    return check_launch("back_kernel");
+    back_pixel_kernel<EPI, TQ><<<grid, kBlock, smem, s>>>(a);
+    return check_launch("back_pixel_kernel");
 }
 
 }  // namespace

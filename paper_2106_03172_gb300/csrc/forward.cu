@@ -4,8 +4,8 @@
 // Eq. (voxel_td)); in ratio mode the kernel writes r_m = g_m / yhat_m (the
 // ratio inside every E-step and gradient, §2.2 Eq. (EMsurrogate), §2.3
 // Eq. (tau_t), §4 Eq. (osem_additive)), 0 when yhat_m = 0 (§2.3 remedy), and
-// optionally reduces the FP64 log-likelihood sum_m g_m log yhat_m - yhat_m
-// (§2.1, Eq. (log_likelihood)) to one partial per block.
+// optionally reduces the log-likelihood sum_m g_m log yhat_m - yhat_m (§2.1,
+// Eq. (log_likelihood)) in FP64 to one partial per block.
 //
 // Thread layout: GROUP consecutive lanes share one ray (single-slice images),
 // each walking a contiguous chunk of the ray's major bands, then an xor-
@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
             if (MODE == FWD_RATIO) a.out[idx] = (yhat != 0.0f) ? g / yhat : 0.0f;
             if (LL) {
                 if (yhat > 0.0f) {
-                    const double y = (double)yhat;
-                    ll = (g > 0.0f ? (double)g * log(y) : 0.0) - y;
+                    // per-ray term with an FP32 log (GB300's FP64 pipe is too slow for a
+                    // log per ray; the term's error, ~g ulp(log yhat), is far below the
+                    // FP32 rounding of yhat itself), reduced in FP64
+                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
                 } else if (g > 0.0f) {
                     if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
                 } else {

@@ -205,7 +205,12 @@ struct pet_state {
     double *d_part = nullptr;       // objective reduction scratch of this state
     int n_part = 0;
     cudaStream_t cap = nullptr;     // private stream for graph capture
-    std::vector<std::pair<std::vector<int64_t>, cudaGraphExec_t>> graphs;   // captured epochs
+    struct Graph {
+        std::vector<int64_t> key;
+        cudaGraphExec_t exec;
+        uint64_t kernels;           // kernel nodes, counted at capture
+    };
+    std::vector<Graph> graphs;      // captured epochs / objectives
 };
 
 namespace petvr {

@@ -66,6 +66,7 @@ _SIGS = {
     "pet_state_create": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_size_t),
                                    POINTER(c_void_p), c_void_p]),
     "pet_state_destroy": (c_int32, [c_void_p]),
+    "pet_state_reset": (c_int32, [c_void_p, c_void_p]),
     "pet_osem_epoch": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
     "pet_svrem_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
     "pet_saga_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
@@ -207,6 +208,10 @@ def pet_state_create(problem, algo: str, table: str, img, stream=None) -> c_void
     return h
 
 
+def pet_state_reset(state, stream=None):
+    _call("pet_state_reset", state, _stream(stream))
+
+
 def pet_osem_epoch(state, seq, stream=None):
     arr, n = _seq(seq)
     _call("pet_osem_epoch", state, arr, n, _stream(stream))
@@ -288,6 +293,12 @@ class State:
             pet_saga_epoch(self.handle, alpha, seq, stream)
         else:
             pet_svrg_epoch(self.handle, alpha, eta, seq, stream)
+
+    def reset(self, stream=None):
+        pet_state_reset(self.handle, stream)
+
+    def objective_async(self, phi_out, stream=None):
+        pet_state_objective_async(self.handle, phi_out, stream)
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

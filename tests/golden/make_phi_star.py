@@ -1,0 +1,45 @@
+"""Write tests/golden/phi_star.json: the MAP objective Phi* of the named
+workloads (seed 0) from the FP64 oracle's L-BFGS-B solve, with a SHA-256 of
+the generated counts so a consumer can tell whether its inputs are the ones
+these values belong to.  Calls only the oracle and the input generator.
+
+    python tests/golden/make_phi_star.py [workload ...]
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle.em import build_problem, map_reference  # noqa: E402
+from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data  # noqa: E402
+
+OUT = os.path.join(HERE, "phi_star.json")
+
+
+def counts_sha256(g) -> str:
+    return hashlib.sha256(g.astype("<f4").tobytes()).hexdigest()
+
+
+def main(names):
+    table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in names:
+        work = WORKLOADS[name]
+        data = make_data(work, 0)
+        prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+        t = time.time()
+        _, phi, kkt = map_reference(prob)
+        table[name] = {"seed": 0, "phi_star": phi, "kkt_residual": kkt,
+                       "counts_sha256": counts_sha256(data["g"]),
+                       "solver": "scipy L-BFGS-B on the FP64 oracle objective",
+                       "seconds": round(time.time() - t, 1)}
+        print(name, table[name])
+    with open(OUT, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["c64", "c256"])
