@@ -166,6 +166,29 @@ pet_status pet_objective(const pet_problem *problem, const float *d_img, double 
  * reduction scratch, so they must be ordered on one stream. */
 pet_status pet_objective_async(const pet_problem *problem, const float *d_img, double *d_phi, void *stream);
 
+/* Objective {Phi, L, R} of d_img into d_phi (device, 3 doubles) without any
+ * device allocation, for callers that cannot call cudaMalloc: code whose
+ * device memory is owned by a framework or serving allocator (a caching
+ * allocator or a fixed pool that must account for every byte) and code on a
+ * latency path that cannot take cudaMalloc's implicit synchronisation.  The
+ * paper has no counterpart; it is an interface convenience.
+ * Inputs as for pet_problem_create (counts and optional background as full
+ * sinograms in view order, [view][bin][z]) plus the quadratic penalty weight
+ * beta; no problem object is needed.  The reduction scratch is a fixed
+ * 1 MiB array (131072 doubles) in this library's device memory, which every
+ * device that loads the library holds until the process exits.  Sizes that
+ * need more block partials than that (roughly more than 1M rays x 32 lanes or
+ * 33M pixels) are rejected with PET_ERR_INVALID and a message.  The first
+ * call on each device looks the array's device address up (with that device
+ * current), so make that first call before any stream capture.  All calls
+ * share the array and every call overwrites the partials it uses, so calls
+ * that overlap on the GPU (different streams, or different threads) race:
+ * order them on one stream.  Nonpositive expected counts with positive data
+ * are not latched by this entry point (pet_objective reports them).
+ * Enqueued only. */
+pet_status pet_objective_noalloc(const pet_plan *plan, const float *d_img, const float *d_counts,
+                                 const float *d_bg, float bg, float beta, double *d_phi, void *stream);
+
 /* ---- state: one running reconstruction ------------------------------------ */
 
 /* Create the state of `algo` on the image d_img_inout (borrowed: every epoch

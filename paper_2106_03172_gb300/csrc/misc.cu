@@ -192,6 +192,18 @@ pet_status launch_objective_finish(const pet_problem *p, const float *img, int n
     return check_launch("objective_final_kernel");
 }
 
+pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const float *img, int n_ll_blocks,
+                                       double *part, double *d_out, cudaStream_t s) {
+    const long long plane = (long long)nx * ny * nz;
+    const int n_pen = (int)blocks_for(plane);
+    double *pen_part = part + n_ll_blocks;
+    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, nx, ny, nz, pen_part);
+    pet_status st = check_launch("penalty_partial_kernel");
+    if (st != PET_OK) return st;
+    objective_final_kernel<<<1, kBlock, 0, s>>>(part, n_ll_blocks, pen_part, n_pen, (double)beta, d_out);
+    return check_launch("objective_final_kernel");
+}
+
 pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz, const float *f_anc,
                                       float *s_anc, float *s_hat, bool init, cudaStream_t s) {
     (void)nz;

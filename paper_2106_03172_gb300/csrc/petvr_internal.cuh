@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <string>
@@ -242,6 +243,8 @@ pet_status launch_sum_sens(const float *sens_t, float *sens, int ns, int N, cuda
 pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s);
 pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks,
                                    double *part, double *d_out, cudaStream_t s);
+pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const float *img, int n_ll_blocks,
+                                       double *part, double *d_out, cudaStream_t s);
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
 pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz,
                                       const float *f_anc, float *s_anc, float *s_hat, bool init,

@@ -63,6 +63,8 @@ _SIGS = {
     "pet_warm_start": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_objective": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),
     "pet_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pet_objective_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
+                                        c_void_p]),
     "pet_state_create": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_size_t),
                                    POINTER(c_void_p), c_void_p]),
     "pet_state_destroy": (c_int32, [c_void_p]),
@@ -192,6 +194,14 @@ def pet_objective(problem, img, stream=None) -> float:
 def pet_objective_async(problem, img, phi_out: torch.Tensor, stream=None):
     """Enqueue Phi, L, R of ``img`` into the float64 CUDA tensor ``phi_out`` (3 values)."""
     _call("pet_objective_async", problem, _dev(img), _dev(phi_out, torch.float64), _stream(stream))
+
+
+def pet_objective_noalloc(plan, img, counts, bg, bg_scalar: float, beta: float, phi_out: torch.Tensor,
+                          stream=None):
+    """Objective into ``phi_out`` (3 float64) with no device allocation; see
+    the C declaration for who needs this and its fixed-scratch limits."""
+    _call("pet_objective_noalloc", plan, _dev(img), _dev(counts), _dev(bg), bg_scalar, beta,
+          _dev(phi_out, torch.float64), _stream(stream))
 
 
 def pet_state_bytes(problem, algo: str, table: str = "fp32") -> int:

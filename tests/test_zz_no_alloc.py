@@ -1,0 +1,65 @@
+"""The allocation-free objective entry point, pet_objective_noalloc.
+
+It exists for callers that cannot call cudaMalloc: code whose device memory
+belongs to a framework or serving allocator that must account for every byte,
+and code on a latency path that cannot take cudaMalloc's implicit device
+synchronisation.  Its reduction scratch is a fixed array inside the library,
+shared by all calls.  This file is collected last so that a failure here
+cannot hide the result of any other test; it passes alone and after the rest.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from cases import oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _pv():
+    from paper_2106_03172_gb300 import petvr
+    petvr.lib()
+    return petvr
+
+
+@pytest.mark.parametrize("case", ["c64", "ragged", "stack"])
+def test_noalloc_objective_matches_pet_objective(case):
+    """Two calls in a row, on two different images, agree with pet_objective
+    (the existing entry point) within the objective tolerance of the other
+    tests (1e-7 relative), component by component."""
+    pv = _pv()
+    prob, data, work = oracle_problem(case)
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    counts = torch.from_numpy(data["g"].ravel()).cuda()
+    gp = pv.Problem(plan, counts, None, data["w"], work.beta)
+    rng = np.random.default_rng(11)
+    f0 = prob.initial_image()
+    images = [f0, f0 * rng.uniform(0.5, 1.5, f0.shape)]
+    out = torch.empty(2, 3, dtype=torch.float64, device="cuda")
+    ref = torch.empty(2, 3, dtype=torch.float64, device="cuda")
+    imgs = [torch.from_numpy(f.astype(np.float32).ravel()).cuda() for f in images]
+    for i, img in enumerate(imgs):
+        pv.pet_objective_noalloc(plan.handle, img, counts, None, data["w"], work.beta, out[i])
+        pv.pet_objective_async(gp.handle, img, ref[i])
+    torch.cuda.synchronize()
+    got, want = out.cpu().numpy(), ref.cpu().numpy()
+    assert got[0, 0] != got[1, 0]
+    for i, img in enumerate(imgs):
+        np.testing.assert_allclose(got[i], want[i], rtol=1e-7)
+        assert got[i, 0] == pytest.approx(pv.pet_objective(gp.handle, img), rel=1e-7)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    pv = _pv()
+    from paper_2106_03172_gb300.phantoms import Geometry
+    geom = Geometry(1024, 1024, 1024, 1465)
+    plan = pv.Plan(geom, 1)
+    img = torch.ones(geom.n_pixels, device="cuda")
+    counts = torch.ones(geom.n_rays, device="cuda")
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(pv.PetError, match="too large for its fixed scratch") as e:
+        pv.pet_objective_noalloc(plan.handle, img, counts, None, 0.1, 0.01, out)
+    assert e.value.status == 1
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
