@@ -34,6 +34,7 @@ constexpr float kCandEps = 1e-3f;   // candidate-bin margin (pixels)
 constexpr int kTile = 16;           // single slice: a block owns a kTile x kTile tile (kTile^2 == kBlock)
 constexpr int kRun = 8;             // pixels per run along a view's minor axis
 constexpr int kChunk = 16;          // views per shared-memory pass
+constexpr int kTileBlockMax = 512;  // threads of a tile block: 32 per view of a chunk
 static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
 
 struct Stencil {
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
 // instead of once per pixel it touches.  Views are processed in chunks of
 // kChunk to bound shared memory.
 template <int EPI, typename TQ>
-__global__ void __launch_bounds__(kBlock) back_tile_kernel(const BackArgs a) {
+__global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {
     extern __shared__ unsigned char smem_raw[];
     const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
     const int vb = __ldg(a.sub_off + t);
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(kBlock) back_tile_kernel(const BackArgs a) {
     ViewParams *s_views = reinterpret_cast<ViewParams *>(s_part + kChunk * kTile * kTile);   // [kChunk]
     int *s_vid = reinterpret_cast<int *>(s_views + kChunk);
     const int r_view0 = a.t_dev ? vb : a.r_view0;
+    const int nthr = blockDim.x;                  // >= kTile * kTile; one run per thread when nv <= nthr / 32
 
     const int tiles_x = (a.nx + kTile - 1) / kTile;
     const int x0 = (blockIdx.x % tiles_x) * kTile;
@@ -231,10 +233,14 @@ __global__ void __launch_bounds__(kBlock) back_tile_kernel(const BackArgs a) {
     float acc = 0.0f;
     for (int q0 = 0; q0 < nv; q0 += kChunk) {
         const int nq = min(kChunk, nv - q0);
-        stage_views(a, vb + q0, nq, s_views, s_vid);
-        for (int e = threadIdx.x; e < nq * kTile * kTile; e += kBlock) s_part[e] = 0.0f;
+        for (int q = threadIdx.x; q < nq; q += nthr) {
+            const int v = __ldg(a.order + vb + q0 + q);
+            s_vid[q] = v;
+            s_views[q] = a.views[v];
+        }
+        for (int e = threadIdx.x; e < nq * kTile * kTile; e += nthr) s_part[e] = 0.0f;
         __syncthreads();
-        for (int run = threadIdx.x; run < nq * kRunsPerView; run += kBlock) {
+        for (int run = threadIdx.x; run < nq * kRunsPerView; run += nthr) {
             const int ql = run / kRunsPerView;
             const int rem = run - ql * kRunsPerView;
             const int band = rem / kRunsPerBand;          // band offset inside the tile
@@ -269,9 +275,11 @@ __global__ void __launch_bounds__(kBlock) back_tile_kernel(const BackArgs a) {
             }
         }
         __syncthreads();
-        for (int ql = 0; ql < nq; ++ql) acc += s_part[ql * kTile * kTile + threadIdx.x];
+        if (threadIdx.x < kTile * kTile)
+            for (int ql = 0; ql < nq; ++ql) acc += s_part[ql * kTile * kTile + threadIdx.x];
         __syncthreads();
     }
+    if (threadIdx.x >= kTile * kTile) return;
     const int ix = x0 + (threadIdx.x % kTile);
     const int iy = y0 + (threadIdx.x / kTile);
     if (ix >= a.nx || iy >= a.ny) return;
@@ -285,7 +293,10 @@ pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
         const int tiles = ((a.nx + kTile - 1) / kTile) * ((a.ny + kTile - 1) / kTile);
         const dim3 grid((unsigned)tiles, (unsigned)ny_grid);
         const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
-        back_tile_kernel<EPI, TQ><<<grid, kBlock, smem, s>>>(a);
+        // one thread per run: 32 runs per view, so 32 threads per view of the largest chunk
+        const int per_view = kTile * (kTile / kRun);
+        const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
+        back_tile_kernel<EPI, TQ><<<grid, threads, smem, s>>>(a);
         return check_launch("back_tile_kernel");
     }
     const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;

@@ -148,6 +148,124 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
     }
 }
 
+// Single-slice forward: a block takes RAYS adjacent rays of the view range
+// and splits each ray's bands into CHUNKS contiguous chunks (RAYS * CHUNKS =
+// kBlock).  Inside a warp, lane = 8 * chunk + ray: the 32 lanes are 8
+// adjacent rays times 4 chunks, so one warp load touches 4 image rows with
+// 8 neighbouring pixels each.  Chunk sums are reduced by xor-shuffles
+// (within the warp) and then over warps through shared memory, always in the
+// same order, so the result is deterministic.
+template <int CHUNKS, int MODE, bool LL>
+__global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
+    constexpr int RAYS = kBlock / CHUNKS;        // rays per block
+    constexpr int WPG = CHUNKS / 4;              // warps per group of 8 rays
+    const RayRange rr = ray_range(a);
+    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int r8 = lane & 7;
+    const int chunk = 4 * (warp % WPG) + (lane >> 3);
+    const int ray_local = 8 * (warp / WPG) + r8;
+    const long long ray = (long long)blockIdx.x * RAYS + ray_local;
+
+    float acc = 0.0f;
+    if (ray < n_rays) {
+        const int p = rr.v_begin + (int)(ray / a.nb);
+        const int j = (int)(ray % a.nb);
+        const int v = __ldg(a.order + p);
+        const ViewParams vp = a.views[v];
+        const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const int mo = n_minor >> 1;
+        const float hm = 0.5f * (float)n_major;
+        const float uc = u.x + u.y;
+        int k_lo = 0, k_hi = n_major;
+        if (vp.du == 0.0f) {
+            if (!(uc >= (float)(-mo) && uc < (float)(n_minor - mo))) k_hi = 0;
+        } else {
+            const float ka = hm + ((float)(-mo - 1) - uc) / vp.du;
+            const float kb = hm + ((float)(n_minor - mo + 1) - uc) / vp.du;
+            const float kmax = (float)n_major + 1.0f;
+            const float klo = fminf(fmaxf(fminf(ka, kb), -1.0f), kmax);
+            const float khi = fmaxf(fminf(fmaxf(ka, kb), kmax), -1.0f);
+            k_lo = max(0, (int)floorf(klo) - 1);
+            k_hi = min(n_major, (int)ceilf(khi) + 1);
+        }
+        // chunks are aligned to the same bands for every ray of the view, so
+        // neighbouring lanes read the same image rows
+        const int per = (n_major + CHUNKS - 1) / CHUNKS;
+        const int kb = max(k_lo, chunk * per);
+        const int ke = min(k_hi, (chunk + 1) * per);
+        if (kb < ke) {
+            const int s_major = vp.col ? 1 : a.nx;
+            const int s_minor = vp.col ? a.nx : 1;
+            const int ui = (int)u.x + mo;
+            const float *rowp = a.img + kb * s_major;
+            float kc = (float)kb - hm;
+            float va = band_point(vp, u.y, kc);
+            for (int k = kb; k < ke; ++k) {
+                kc += 1.0f;
+                const float vb = band_point(vp, u.y, kc);
+                float fl, w0, w1;
+                band_split(vp, va, vb, fl, w0, w1);
+                const int m0 = (int)fl + ui;
+                if ((unsigned)m0 < (unsigned)n_minor) acc = fmaf(w0, __ldg(rowp + m0 * s_minor), acc);
+                if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor)
+                    acc = fmaf(w1, __ldg(rowp + (m0 + 1) * s_minor), acc);
+                va = vb;
+                rowp += s_major;
+            }
+        }
+    }
+    // the 4 chunks of each ray in this warp, then the warps of its group
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    __shared__ float red[kBlock / 32][8];
+    if (lane < 8) red[warp][lane] = acc;
+    __syncthreads();
+
+    double ll = 0.0;
+    if (threadIdx.x < RAYS) {
+        const int g = threadIdx.x >> 3;
+        float sum = 0.0f;
+#pragma unroll
+        for (int w = 0; w < WPG; ++w) sum += red[g * WPG + w][threadIdx.x & 7];
+        const long long ray_f = (long long)blockIdx.x * RAYS + threadIdx.x;
+        if (ray_f < n_rays) {
+            const long long gi = rr.off + ray_f;
+            const float yhat = sum + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+            if (MODE == FWD_YHAT) a.out[ray_f] = yhat;
+            if (MODE == FWD_RATIO || LL) {
+                const float g = __ldg(a.g + gi);
+                if (MODE == FWD_RATIO) a.out[ray_f] = (yhat != 0.0f) ? g / yhat : 0.0f;
+                if (LL) {
+                    if (yhat > 0.0f) {
+                        ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
+                    } else if (g > 0.0f) {
+                        if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
+                    } else {
+                        ll = -(double)yhat;
+                    }
+                }
+            }
+        }
+    }
+    if (LL) {
+        __shared__ double dred[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if (lane == 0) dred[warp] = ll;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < kBlock / 32; ++i) s += dred[i];
+            a.ll_partials[blockIdx.x] = s;
+        }
+    }
+}
+
 // Nonzeros of the rays of a view range: band pieces of positive length that
 // fall inside the image (one thread per ray, same geometry as the projector).
 __global__ void __launch_bounds__(kBlock) count_nnz_kernel(const FwdArgs a, unsigned long long *count) {
@@ -197,6 +315,21 @@ pet_status dispatch_mode(const FwdArgs &a, int mode, bool ll, int blocks, cudaSt
     return check_launch("forward_kernel");
 }
 
+template <int CHUNKS>
+pet_status dispatch_tile(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    if (mode == FWD_YHAT && !ll)
+        forward_tile_kernel<CHUNKS, FWD_YHAT, false><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && !ll)
+        forward_tile_kernel<CHUNKS, FWD_RATIO, false><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && ll)
+        forward_tile_kernel<CHUNKS, FWD_RATIO, true><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_NONE && ll)
+        forward_tile_kernel<CHUNKS, FWD_NONE, true><<<blocks, kBlock, 0, s>>>(a);
+    else
+        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
+    return check_launch("forward_tile_kernel");
+}
+
 }  // namespace
 
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s) {
@@ -211,6 +344,8 @@ int forward_blocks(int n_rays, int nz, int group) {
     return (int)((threads + kBlock - 1) / kBlock);
 }
 
+// Lanes per ray: slice stacks put lanes along z (1 per ray); single slices
+// split each ray into chunks of about 8 bands, as many as the image needs.
 int choose_group(const pet_plan *plan) {
     if (plan->nz > 1) return 1;
     const int n = plan->nx > plan->ny ? plan->nx : plan->ny;
@@ -225,15 +360,17 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
     const int blocks = forward_blocks(n_rays, a.nz, group);
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
-    if (a.nz > 1 && group != 1) return set_error(PET_ERR_INVALID, "forward: slice stacks use group 1");
     ProfileScope prof(0, s);
-    switch (group) {
-        case 1: return dispatch_mode<1>(a, mode, ll, blocks, s);
-        case 8: return dispatch_mode<8>(a, mode, ll, blocks, s);
-        case 16: return dispatch_mode<16>(a, mode, ll, blocks, s);
-        case 32: return dispatch_mode<32>(a, mode, ll, blocks, s);
-        default: return set_error(PET_ERR_INVALID, "forward: unsupported lane group");
+    if (a.nz == 1) {
+        switch (group) {
+            case 8: return dispatch_tile<8>(a, mode, ll, blocks, s);
+            case 16: return dispatch_tile<16>(a, mode, ll, blocks, s);
+            case 32: return dispatch_tile<32>(a, mode, ll, blocks, s);
+            default: return set_error(PET_ERR_INVALID, "forward: unsupported lane group");
+        }
     }
+    if (group != 1) return set_error(PET_ERR_INVALID, "forward: slice stacks use group 1");
+    return dispatch_mode<1>(a, mode, ll, blocks, s);
 }
 
 }  // namespace petvr
