@@ -322,6 +322,7 @@ def run_ours(args):
     g_host = torch.from_numpy(data["g"].ravel()).pin_memory()
     g_dev = g_host.cuda()
     plan = petvr.Plan(geom, ns)
+    tuning = petvr.pet_plan_autotune(plan.handle)       # launch shapes timed on this geometry
     prob = petvr.Problem(plan, g_dev, None, data["w"], work.beta)
     f0 = torch.empty(geom.n_pixels * geom.nz, device="cuda")
     petvr.pet_warm_start(prob.handle, f0)
@@ -485,7 +486,9 @@ def run_ours(args):
         "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ellipse phantom, Poisson counts)",
-        "config": dict(workload_config(work), parallelism=f"replicas x{world}"),
+        "config": dict(workload_config(work), parallelism=f"replicas x{world}",
+                       launch_shapes={"forward_band_chunks": tuning[0], "back_run_pixels": tuning[1],
+                                      "source": "pet_plan_autotune"}),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "pairs_per_step": pairs / args.steps,
         "gpu_launches": int(launches),

@@ -114,6 +114,21 @@ pet_status pet_plan_subset_views(const pet_plan *plan, int32_t t, int32_t *h_n_v
  * projection (one multiply-add per nonzero). */
 pet_status pet_plan_nnz(const pet_plan *plan, int32_t t, int64_t *h_nnz);
 
+/* Launch shapes of the single-slice kernels: band chunks per ray in the
+ * forward projector (8, 16 or 32; 0 = size-based default) and pixels per run
+ * in the tiled back projector (4 or 8).  Results are identical up to the
+ * FP32 summation order.  Set them before creating states: captured epochs
+ * keep the shapes they were captured with. */
+pet_status pet_plan_set_tuning(pet_plan *plan, int32_t fwd_chunks, int32_t back_run);
+pet_status pet_plan_get_tuning(const pet_plan *plan, int32_t *h_fwd_chunks, int32_t *h_back_run);
+
+/* Autotuner: times every forward chunk count and back-projection run length
+ * on this plan's own geometry (all subsets, best of three passes on a
+ * private stream, synchronising), keeps the fastest of each, and reports them
+ * (either pointer may be NULL).  Allocates and frees scratch images.  Slice
+ * stacks have nothing to tune. */
+pet_status pet_plan_autotune(pet_plan *plan, int32_t *h_fwd_chunks, int32_t *h_back_run);
+
 /* Copy sens_t (t >= 0) or sens (t = -1), nx*ny floats, into d_out. */
 pet_status pet_plan_sensitivity(const pet_plan *plan, int32_t t, float *d_out, void *stream);
 

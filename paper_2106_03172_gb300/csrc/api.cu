@@ -134,6 +134,7 @@ BackArgs back_args(const pet_plan *pl, const float *r, int subset, bool natural)
     a.r = r;
     a.sens_t = pl->d_sens_t;
     a.sens = pl->d_sens;
+    a.run = pl->back_run;
     return a;
 }
 
@@ -348,6 +349,7 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
         vp.Lm = cn != 0.0 ? (float)(d / std::fabs(cn)) : 0.0f;
         vp.K = (float)(ds / (cm * d));
         vp.invK = (float)(cm * d / ds);
+        vp.inv_du = cn != 0.0 ? (float)(-cm / cn) : 0.0f;
         const double off = (n_minor % 2) ? 0.5 : 0.0;
         for (int j = 0; j < pl->nb; ++j) {
             const double sj = ((double)j - 0.5 * (pl->nb - 1)) * ds;
@@ -446,6 +448,105 @@ pet_status pet_plan_nnz(const pet_plan *pl, int32_t t, int64_t *h_nnz) {
     for (int i = 0; i < pl->ns; ++i)
         if (t < 0 || i == t) n += pl->nnz[i];
     *h_nnz = n;
+    return PET_OK;
+}
+
+pet_status pet_plan_set_tuning(pet_plan *pl, int32_t fwd_chunks, int32_t back_run) {
+    if (!pl) return set_error(PET_ERR_INVALID, "null plan");
+    if (fwd_chunks != 0 && fwd_chunks != 8 && fwd_chunks != 16 && fwd_chunks != 32)
+        return set_error(PET_ERR_INVALID, "fwd_chunks must be 0 (default), 8, 16 or 32");
+    if (back_run != 4 && back_run != 8) return set_error(PET_ERR_INVALID, "back_run must be 4 or 8");
+    pl->fwd_chunks = fwd_chunks;
+    pl->back_run = back_run;
+    return PET_OK;
+}
+
+pet_status pet_plan_get_tuning(const pet_plan *pl, int32_t *h_fwd_chunks, int32_t *h_back_run) {
+    if (!pl || !h_fwd_chunks || !h_back_run) return set_error(PET_ERR_INVALID, "null argument");
+    *h_fwd_chunks = pl->nz > 1 ? 1 : choose_group(pl);
+    *h_back_run = pl->back_run;
+    return PET_OK;
+}
+
+pet_status pet_plan_autotune(pet_plan *pl, int32_t *h_fwd_chunks, int32_t *h_back_run) {
+    if (!pl) return set_error(PET_ERR_INVALID, "null plan");
+    if (pl->nz == 1) {
+        const size_t N = (size_t)pl->N, R = (size_t)max_sub_rays(pl);
+        float *img = nullptr, *sino = nullptr, *out = nullptr;
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        pet_status st = PET_OK;
+        auto cleanup = [&]() {
+            dfree(img);
+            dfree(sino);
+            dfree(out);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (s) cudaStreamDestroy(s);
+        };
+        if ((st = dalloc(&img, N, "tune image")) != PET_OK || (st = dalloc(&sino, R, "tune sinogram")) != PET_OK ||
+            (st = dalloc(&out, N, "tune image")) != PET_OK) {
+            cleanup();
+            return st;
+        }
+        std::vector<float> ones(std::max(N, R), 1.0f);
+        cudaError_t e = cudaMemcpy(img, ones.data(), N * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(sino, ones.data(), R * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_ok(e, "autotune set-up");
+        }
+        // time `reps` passes over every subset of one projector, best of 3
+        auto time_pass = [&](bool forward, float *best_ms) -> pet_status {
+            float best = 1e30f;
+            for (int trial = 0; trial < 4; ++trial) {
+                PET_TRY(cuda_ok(cudaEventRecord(e0, s), "event"));
+                for (int t = 0; t < pl->ns; ++t) {
+                    if (forward) {
+                        FwdArgs a = fwd_args(pl, img, t, false);
+                        a.out = sino;
+                        PET_TRY(launch_forward(a, FWD_YHAT, false, choose_group(pl), s, nullptr));
+                    } else {
+                        BackArgs b = back_args(pl, sino, t, false);
+                        b.out = out;
+                        PET_TRY(launch_back(b, EPI_PLAIN, PET_TABLE_FP32, 1, s, pl->max_sub_views));
+                    }
+                }
+                PET_TRY(cuda_ok(cudaEventRecord(e1, s), "event"));
+                PET_TRY(cuda_ok(cudaEventSynchronize(e1), "event sync"));
+                float ms = 0.0f;
+                PET_TRY(cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event time"));
+                if (trial > 0) best = std::min(best, ms);   // trial 0 warms up
+            }
+            *best_ms = best;
+            return PET_OK;
+        };
+        int best_c = choose_group(pl), best_r = pl->back_run;
+        float best_ms = 1e30f;
+        for (int c : {8, 16, 32}) {
+            pl->fwd_chunks = c;
+            float ms = 0.0f;
+            if ((st = time_pass(true, &ms)) != PET_OK) break;
+            if (ms < best_ms) best_ms = ms, best_c = c;
+        }
+        pl->fwd_chunks = best_c;
+        best_ms = 1e30f;
+        for (int r : {4, 8}) {
+            if (st != PET_OK) break;
+            pl->back_run = r;
+            float ms = 0.0f;
+            if ((st = time_pass(false, &ms)) != PET_OK) break;
+            if (ms < best_ms) best_ms = ms, best_r = r;
+        }
+        pl->back_run = best_r;
+        cleanup();
+        if (st != PET_OK) return st;
+    }
+    if (h_fwd_chunks) *h_fwd_chunks = pl->nz > 1 ? 1 : choose_group(pl);
+    if (h_back_run) *h_back_run = pl->back_run;
     return PET_OK;
 }
 

@@ -32,9 +32,8 @@ constexpr int kBlock = 256;
 constexpr int kLanes = 4;           // slice stacks: lanes per (pixel, slice); each takes every 4th view
 constexpr float kCandEps = 1e-3f;   // candidate-bin margin (pixels)
 constexpr int kTile = 16;           // single slice: a block owns a kTile x kTile tile (kTile^2 == kBlock)
-constexpr int kRun = 8;             // pixels per run along a view's minor axis
 constexpr int kChunk = 16;          // views per shared-memory pass
-constexpr int kTileBlockMax = 512;  // threads of a tile block: 32 per view of a chunk
+constexpr int kTileBlockMax = 1024; // threads of a tile block: kTile * kTile / run per view of a chunk
 static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
 
 struct Stencil {
@@ -212,7 +211,7 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
 // and applies the update.  Each ray-band split is evaluated once per run
 // instead of once per pixel it touches.  Views are processed in chunks of
 // kChunk to bound shared memory.
-template <int EPI, typename TQ>
+template <int EPI, typename TQ, int kRun>
 __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {
     extern __shared__ unsigned char smem_raw[];
     const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
@@ -293,10 +292,14 @@ pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
         const int tiles = ((a.nx + kTile - 1) / kTile) * ((a.ny + kTile - 1) / kTile);
         const dim3 grid((unsigned)tiles, (unsigned)ny_grid);
         const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
-        // one thread per run: 32 runs per view, so 32 threads per view of the largest chunk
-        const int per_view = kTile * (kTile / kRun);
+        // one thread per run: kTile * kTile / run runs per view of the largest chunk
+        const int run = a.run == 4 ? 4 : 8;
+        const int per_view = kTile * (kTile / run);
         const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
-        back_tile_kernel<EPI, TQ><<<grid, threads, smem, s>>>(a);
+        if (run == 4)
+            back_tile_kernel<EPI, TQ, 4><<<grid, threads, smem, s>>>(a);
+        else
+            back_tile_kernel<EPI, TQ, 8><<<grid, threads, smem, s>>>(a);
         return check_launch("back_tile_kernel");
     }
     const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;

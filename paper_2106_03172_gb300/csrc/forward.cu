@@ -67,20 +67,8 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
         const int n_minor = vp.col ? a.ny : a.nx;
         const int mo = n_minor >> 1;
         const float hm = 0.5f * (float)n_major;
-        const float uc = u.x + u.y;
-        // bands where the ray can meet the image (a superset; extra bands add 0)
-        int k_lo = 0, k_hi = n_major;
-        if (vp.du == 0.0f) {
-            if (!(uc >= (float)(-mo) && uc < (float)(n_minor - mo))) k_hi = 0;
-        } else {
-            const float ka = hm + ((float)(-mo - 1) - uc) / vp.du;
-            const float kb = hm + ((float)(n_minor - mo + 1) - uc) / vp.du;
-            const float kmax = (float)n_major + 1.0f;
-            const float klo = fminf(fmaxf(fminf(ka, kb), -1.0f), kmax);
-            const float khi = fmaxf(fminf(fmaxf(ka, kb), kmax), -1.0f);
-            k_lo = max(0, (int)floorf(klo) - 1);
-            k_hi = min(n_major, (int)ceilf(khi) + 1);
-        }
+        int k_lo, k_hi;
+        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
         const int cnt = max(0, k_hi - k_lo);
         const int per = (cnt + GROUP - 1) / GROUP;
         const int kb = k_lo + lane_g * per;
@@ -179,19 +167,8 @@ __global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
         const int n_minor = vp.col ? a.ny : a.nx;
         const int mo = n_minor >> 1;
         const float hm = 0.5f * (float)n_major;
-        const float uc = u.x + u.y;
-        int k_lo = 0, k_hi = n_major;
-        if (vp.du == 0.0f) {
-            if (!(uc >= (float)(-mo) && uc < (float)(n_minor - mo))) k_hi = 0;
-        } else {
-            const float ka = hm + ((float)(-mo - 1) - uc) / vp.du;
-            const float kb = hm + ((float)(n_minor - mo + 1) - uc) / vp.du;
-            const float kmax = (float)n_major + 1.0f;
-            const float klo = fminf(fmaxf(fminf(ka, kb), -1.0f), kmax);
-            const float khi = fmaxf(fminf(fmaxf(ka, kb), kmax), -1.0f);
-            k_lo = max(0, (int)floorf(klo) - 1);
-            k_hi = min(n_major, (int)ceilf(khi) + 1);
-        }
+        int k_lo, k_hi;
+        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
         // chunks are aligned to the same bands for every ray of the view, so
         // neighbouring lanes read the same image rows
         const int per = (n_major + CHUNKS - 1) / CHUNKS;
@@ -204,6 +181,7 @@ __global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
             const float *rowp = a.img + kb * s_major;
             float kc = (float)kb - hm;
             float va = band_point(vp, u.y, kc);
+#pragma unroll 2
             for (int k = kb; k < ke; ++k) {
                 kc += 1.0f;
                 const float vb = band_point(vp, u.y, kc);
@@ -346,12 +324,16 @@ int forward_blocks(int n_rays, int nz, int group) {
 
 // Lanes per ray: slice stacks put lanes along z (1 per ray); single slices
 // split each ray into chunks of about 8 bands, as many as the image needs.
-int choose_group(const pet_plan *plan) {
-    if (plan->nz > 1) return 1;
-    const int n = plan->nx > plan->ny ? plan->nx : plan->ny;
+int default_chunks(int nx, int ny) {
+    const int n = nx > ny ? nx : ny;
     if (n >= 160) return 32;
     if (n >= 80) return 16;
     return 8;
+}
+
+int choose_group(const pet_plan *plan) {
+    if (plan->nz > 1) return 1;
+    return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
 }
 
 pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s, int *n_blocks_out,

@@ -51,9 +51,31 @@ struct ViewParams {
     float Lm;     // ray length (mm) per pixel of minor displacement (0 if du == 0)
     float K;      // minor displacement (pixels) per bin step (never 0)
     float invK;   // 1 / K
+    float inv_du; // 1 / du (0 if du == 0), for band ranges only
     float uc0;    // centred minor coordinate of bin 0 at the central major line (approx.)
     int col;      // 1: major axis is x (columns); 0: major axis is y (rows)
 };
+
+// Bands [k_lo, k_hi) where a ray with centred minor offset uc can meet the
+// image (a superset with one band of margin each side; extra bands add 0).
+__device__ __forceinline__ void band_range(const ViewParams &vp, float uc, int n_major, int n_minor, int &k_lo,
+                                           int &k_hi) {
+    const int mo = n_minor >> 1;
+    k_lo = 0;
+    k_hi = n_major;
+    if (vp.du == 0.0f) {
+        if (!(uc >= (float)(-mo) && uc < (float)(n_minor - mo))) k_hi = 0;
+        return;
+    }
+    const float hm = 0.5f * (float)n_major;
+    const float ka = fmaf((float)(-mo - 1) - uc, vp.inv_du, hm);
+    const float kb = fmaf((float)(n_minor - mo + 1) - uc, vp.inv_du, hm);
+    const float kmax = (float)n_major + 1.0f;
+    const float klo = fminf(fmaxf(fminf(ka, kb), -1.0f), kmax);
+    const float khi = fmaxf(fminf(fmaxf(ka, kb), kmax), -1.0f);
+    k_lo = max(0, (int)floorf(klo) - 1);
+    k_hi = min(n_major, (int)ceilf(khi) + 1);
+}
 
 // Fractional minor position u - ui of a ray at band boundary kc (centred
 // major coordinate).  Both projectors evaluate exactly this expression.
@@ -128,6 +150,7 @@ struct BackArgs {
     const int *sub_off;   // view offsets of subsets in `order`
     int t0;               // subset of blockIdx.y == 0
     const int *t_dev;     // if set: the subset index is read here (grid.y must be 1)
+    int run;              // single-slice tile kernel: pixels per run (4 or 8)
     int r_view0;          // view position of r[0] (ignored when t_dev is set: r is
                           //   then the compact ratio of subset *t_dev)
     int nx, ny, nz, nb, ns;
@@ -161,6 +184,8 @@ struct pet_plan {
     int N, M;                       // pixels and rays of one slice
     int max_sub_views;
     int device;
+    int fwd_chunks = 0;             // single-slice forward: band chunks per ray (8, 16 or 32)
+    int back_run = 8;               // single-slice back projection: pixels per run (4 or 8)
     std::vector<int> order;         // subset-major view order
     std::vector<int> sub_off;       // [ns + 1]
     std::vector<long long> nnz;     // [ns] nonzeros of A_t (one slice)
@@ -235,6 +260,7 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
                           int *n_blocks_out, int rays_for_grid = -1);
 int forward_blocks(int n_rays, int nz, int group);
 int choose_group(const pet_plan *plan);
+int default_chunks(int nx, int ny);
 pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
                        cudaStream_t s, int max_views);
 pet_status launch_permute_sino(const float *src, float *dst, const int *order, int na, int nb, int nz,

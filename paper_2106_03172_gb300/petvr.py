@@ -51,6 +51,9 @@ _SIGS = {
     "pet_plan_subset_views": (c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
     "pet_plan_sensitivity": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "pet_plan_nnz": (c_int32, [c_void_p, c_int32, POINTER(ctypes.c_int64)]),
+    "pet_plan_set_tuning": (c_int32, [c_void_p, c_int32, c_int32]),
+    "pet_plan_get_tuning": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
+    "pet_plan_autotune": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     "pet_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int32, c_void_p, c_void_p]),
     "pet_back": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "pet_problem_create": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, POINTER(pet_penalty),
@@ -141,6 +144,23 @@ def pet_plan_nnz(plan, t: int) -> int:
     n = ctypes.c_int64()
     _call("pet_plan_nnz", plan, t, byref(n))
     return n.value
+
+
+def pet_plan_set_tuning(plan, fwd_chunks: int, back_run: int):
+    _call("pet_plan_set_tuning", plan, fwd_chunks, back_run)
+
+
+def pet_plan_get_tuning(plan):
+    c, r = c_int32(), c_int32()
+    _call("pet_plan_get_tuning", plan, byref(c), byref(r))
+    return c.value, r.value
+
+
+def pet_plan_autotune(plan):
+    """Time the launch shapes on this plan and keep the fastest; returns (chunks, run)."""
+    c, r = c_int32(), c_int32()
+    _call("pet_plan_autotune", plan, byref(c), byref(r))
+    return c.value, r.value
 
 
 def pet_plan_sensitivity(plan, t: int, out: torch.Tensor, stream=None):

@@ -103,6 +103,40 @@ def test_nonzero_counts(case):
         assert int((A.data > 1e-4).sum()) <= got <= A.nnz + max(10, A.nnz // 1000), (t, got, A.nnz)
 
 
+@pytest.mark.parametrize("chunks,run", [(8, 4), (8, 8), (16, 4), (16, 8), (32, 4), (32, 8)])
+def test_projection_parity_every_launch_shape(chunks, run):
+    """Every forward chunk count and back-projection run length the autotuner
+    may pick gives the oracle's projections (odd, non-square image)."""
+    pv = _pv()
+    prob, data, work = oracle_problem("ragged")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    pv.pet_plan_set_tuning(plan.handle, chunks, run)
+    assert pv.pet_plan_get_tuning(plan.handle) == (chunks, run)
+    f = np.random.default_rng(8).uniform(0.5, 3.0, (prob.N, 1))
+    y = np.random.default_rng(9).uniform(0.0, 2.0, (prob.M, 1))
+    img = torch.empty(prob.N, device="cuda")
+    for t in range(work.n_subsets):
+        rows = prob.subsets[t]
+        sub = torch.empty(len(rows), device="cuda")
+        pv.pet_forward(plan.handle, _cuda(f), None, 0.0, t, sub)
+        _assert_proj(_host(sub).reshape(-1, 1), prob.At[t] @ f)
+        pv.pet_back(plan.handle, _cuda(y[rows]), t, img)
+        _assert_proj(_host(img).reshape(-1, 1), prob.At[t].T @ y[rows])
+    pv.pet_back(plan.handle, _cuda(y), -1, img)
+    _assert_proj(_host(img).reshape(-1, 1), prob.A.T @ y)
+
+
+def test_autotune_picks_a_valid_shape():
+    pv = _pv()
+    prob, data, work = oracle_problem("c64")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    chunks, run = pv.pet_plan_autotune(plan.handle)
+    assert chunks in (8, 16, 32) and run in (4, 8)
+    assert pv.pet_plan_get_tuning(plan.handle) == (chunks, run)
+    with pytest.raises(pv.PetError):
+        pv.pet_plan_set_tuning(plan.handle, 12, 8)
+
+
 def test_sensitivities(case):
     pv, prob, data, work, plan = case
     out = torch.empty(prob.N, device="cuda")
