@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--workload", default="c256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", type=int, default=20, help="reconstructions per method for the gap metric")
+    ap.add_argument("--streams", dest="batch", action="store_false",
+                    help="run the four methods on four streams instead of one batched launch per phase")
     return ap.parse_args()
 
 
@@ -337,11 +339,18 @@ def run_ours(args):
     rep = Replica(work)
 
     side = {m: torch.cuda.Stream() for m in METHODS}
+    batch = petvr.Batch([states[m] for m in METHODS]) if args.batch else None
 
     def one_step(step, concurrent=True):
-        """The four reconstructions are independent: each runs on its own
-        stream (forked from and joined back into the timing stream)."""
+        """The four reconstructions are independent: by default one batched
+        launch per phase covers all four (pet_batch_epoch); otherwise each
+        runs on its own stream (forked from and joined back into the timing
+        stream)."""
         seqs = seqs_for_step(step, ns)
+        if batch is not None and concurrent:
+            batch.epoch(seqs, [a[m][0] for m in METHODS], [a[m][1] for m in METHODS], stream=stream)
+            batch.objective_async(phi, stream=stream)
+            return seqs
         fork = torch.cuda.Event()
         fork.record(stream)
         for i, m in enumerate(METHODS):
@@ -487,6 +496,7 @@ def run_ours(args):
         "ms_per_step": total_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ellipse phantom, Poisson counts)",
         "config": dict(workload_config(work), parallelism=f"replicas x{world}",
+                       concurrency="batched launches (pet_batch_epoch)" if args.batch else "four streams",
                        launch_shapes={"forward_band_chunks": tuning[0], "back_run_pixels": tuning[1],
                                       "source": "pet_plan_autotune"}),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),

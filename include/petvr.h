@@ -94,6 +94,7 @@ typedef struct {
 typedef struct pet_plan pet_plan;
 typedef struct pet_problem pet_problem;
 typedef struct pet_state pet_state;
+typedef struct pet_batch pet_batch;
 
 /* ---- plan: geometry tables and sensitivities ---------------------------- */
 
@@ -257,6 +258,31 @@ pet_status pet_svrg_epoch(pet_state *state, float alpha, int32_t eta, const int3
  * 3 doubles), enqueued only, using the state's own reduction scratch (so
  * states of one problem may evaluate it on different streams). */
 pet_status pet_state_objective_async(pet_state *state, double *d_phi, void *stream);
+
+/* ---- batches: many reconstructions per launch ------------------------------ */
+
+/* Group n existing states (any algorithms; single-slice plans of any sizes;
+ * each state at most once) so that their updates run together: every update
+ * of pet_batch_epoch launches one forward projection and one back projection
+ * + update kernel per launch shape for all members (the batched form of the
+ * reconstructions, with per-member geometry, data and subset indices).  Each
+ * member's result is bit-identical to running its own epoch call with the
+ * same subset sequence.  The batch borrows the states, which must outlive it;
+ * a state in a batch may still be used on its own between batch calls. */
+pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out);
+pet_status pet_batch_destroy(pet_batch *batch);
+
+/* n_iter updates of every member: h_subset_seqs is row-major [n][n_iter]
+ * (member j's subset indices), h_alpha[j] and h_eta[j] its step size and
+ * anchor period (ignored where the algorithm has none).  Anchor passes are
+ * due per member as in the single-state calls.  Captured into a CUDA graph
+ * keyed by n_iter and the anchor pattern, like pet_*_epoch. */
+pet_status pet_batch_epoch(pet_batch *batch, const int32_t *h_subset_seqs, int32_t n_iter, const float *h_alpha,
+                           const int32_t *h_eta, void *stream);
+
+/* Objectives {Phi, L, R} of every member's current image into d_phi
+ * (device, [n][3] doubles), enqueued only. */
+pet_status pet_batch_objective_async(pet_batch *batch, double *d_phi, void *stream);
 
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);

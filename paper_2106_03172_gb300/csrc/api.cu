@@ -950,6 +950,228 @@ pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream)
     });
 }
 
+// ---- batches ------------------------------------------------------------------
+
+pet_status pet_batch_destroy(pet_batch *b) {
+    if (!b) return PET_OK;
+    dfree(b->d_members);
+    dfree(b->d_idx);
+    dfree(b->d_seqs);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return PET_OK;
+}
+
+pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out) {
+    if (!states || !out || n < 1) return set_error(PET_ERR_INVALID, "need at least one state");
+    *out = nullptr;
+    for (int j = 0; j < n; ++j) {
+        if (!states[j]) return set_error(PET_ERR_INVALID, "null state in batch");
+        if (states[j]->prob->plan->nz != 1) return set_error(PET_ERR_INVALID, "batches take single-slice images");
+        for (int i = 0; i < j; ++i)
+            if (states[i] == states[j]) return set_error(PET_ERR_INVALID, "a state appears twice in the batch");
+    }
+    pet_batch *b = new (std::nothrow) pet_batch();
+    if (!b) return set_error(PET_ERR_OOM, "host allocation failed");
+    b->states.assign(states, states + n);
+    b->members.resize(n);
+    // group members by launch shape
+    std::vector<int> idx;
+    auto add_groups = [&](bool fwd) {
+        std::vector<int> values;
+        for (pet_state *st : b->states) {
+            const int v = fwd ? choose_group(st->prob->plan) : st->prob->plan->back_run;
+            if (std::find(values.begin(), values.end(), v) == values.end()) values.push_back(v);
+        }
+        for (int v : values) {
+            pet_batch::Group g{v, (int)idx.size(), 0, 0, 0};
+            for (int j = 0; j < n; ++j) {
+                const pet_plan *pl = b->states[j]->prob->plan;
+                if ((fwd ? choose_group(pl) : pl->back_run) != v) continue;
+                idx.push_back(j);
+                ++g.count;
+                const int gx = fwd ? forward_blocks(max_sub_rays(pl), 1, v)
+                                   : ((pl->nx + 15) / 16) * ((pl->ny + 15) / 16);
+                g.grid_x = std::max(g.grid_x, gx);
+                g.max_views = std::max(g.max_views, pl->max_sub_views);
+            }
+            (fwd ? b->fwd_groups : b->back_groups).push_back(g);
+        }
+    };
+    add_groups(true);
+    add_groups(false);
+    pet_status e;
+    if ((e = dalloc(&b->d_members, (size_t)n, "batch members")) != PET_OK ||
+        (e = dalloc(&b->d_idx, idx.size(), "batch index")) != PET_OK) {
+        pet_batch_destroy(b);
+        return e;
+    }
+    const cudaError_t ce = cudaMemcpy(b->d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        pet_batch_destroy(b);
+        return cuda_ok(ce, "batch index upload");
+    }
+    *out = b;
+    return PET_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *seq) {
+    const pet_problem *p = st->prob;
+    const pet_plan *pl = p->plan;
+    m.views = pl->d_views;
+    m.uc = pl->d_uc;
+    m.order = pl->d_order;
+    m.sub_off = pl->d_sub_off;
+    m.nx = pl->nx;
+    m.ny = pl->ny;
+    m.nb = pl->nb;
+    m.ns = pl->ns;
+    m.sens_t = pl->d_sens_t;
+    m.sens = pl->d_sens;
+    m.g = p->d_g;
+    m.w = p->d_w;
+    m.w_scalar = p->w_scalar;
+    m.beta = p->pen.beta;
+    m.status = p->d_status;
+    m.algo = st->algo;
+    m.table_dtype = st->table_dtype;
+    m.img = st->img;
+    m.alt = st->alt;
+    m.ratio = st->ratio;
+    m.s_hat = st->s_hat;
+    m.f_anc = st->f_anc;
+    m.s_anc = st->s_anc;
+    m.B = st->B;
+    m.d = st->d;
+    m.table = st->table;
+    m.qbar = st->qbar;
+    m.qtil = st->qtil;
+    m.alpha = alpha;
+    m.seq = seq;
+}
+
+// All launches of one batched epoch on stream s.
+pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<std::vector<uint8_t>> &anchors,
+                               cudaStream_t s) {
+    const int n = (int)b->states.size();
+    const bool odd = (n_iter % 2) == 1;
+    if (odd)
+        for (pet_state *st : b->states) {
+            const long long plane = plane_of(st->prob->plan);
+            PET_TRY(cuda_ok(cudaMemcpyAsync(st->alt, st->img, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
+                            "cudaMemcpyAsync"));
+        }
+    for (int i = 0; i < n_iter; ++i) {
+        const bool in_is_img = ((i % 2) == 0) != odd;
+        for (int j = 0; j < n; ++j) {
+            if (!anchors[j][i]) continue;
+            pet_state *st = b->states[j];
+            const pet_plan *pl = st->prob->plan;
+            const long long plane = plane_of(pl);
+            const float *in = in_is_img ? st->img : st->alt;
+            if (st->algo == PET_ALGO_SVREM) {
+                PET_TRY(cuda_ok(cudaMemcpyAsync(st->f_anc, in, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
+                                "anchor copy"));
+                PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+                PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, st->f_anc, st->s_anc, st->s_hat,
+                                                   !st->s_hat_ready, s));
+                st->s_hat_ready = true;
+            } else {
+                PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+                PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
+            }
+        }
+        for (const auto &g : b->fwd_groups)
+            PET_TRY(launch_batch_forward(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, i,
+                                         in_is_img ? 1 : 0, s));
+        for (const auto &g : b->back_groups)
+            PET_TRY(launch_batch_back(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, g.max_views, i,
+                                      in_is_img ? 1 : 0, s));
+    }
+    return PET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, const float *h_alpha,
+                           const int32_t *h_eta, void *stream) {
+    if (!b || !h_alpha || !h_eta) return set_error(PET_ERR_INVALID, "null argument");
+    const int n = (int)b->states.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_iter < 0) return set_error(PET_ERR_INVALID, "n_iter must be >= 0");
+    for (int j = 0; j < n; ++j) {
+        PET_TRY(check_seq(b->states[j]->prob->plan, h_seqs ? h_seqs + (size_t)j * n_iter : nullptr, n_iter));
+        if (!std::isfinite(h_alpha[j])) return set_error(PET_ERR_INVALID, "alpha must be finite");
+        const int algo = b->states[j]->algo;
+        if ((algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) && h_eta[j] < 1)
+            return set_error(PET_ERR_INVALID, "eta must be >= 1");
+    }
+    if (n_iter == 0) return PET_OK;
+    const size_t need = (size_t)n * n_iter;
+    if ((int)need > b->seq_cap) {
+        int *grown = nullptr;
+        PET_TRY(dalloc(&grown, need, "batch subset sequences"));
+        if (b->d_seqs) {
+            PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+            dfree(b->d_seqs);
+        }
+        b->d_seqs = grown;
+        b->seq_cap = (int)need;
+    }
+    PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_seqs, h_seqs, sizeof(int32_t) * need, cudaMemcpyHostToDevice, s),
+                    "batch sequence copy"));
+    for (int j = 0; j < n; ++j) fill_member(b->members[j], b->states[j], h_alpha[j], b->d_seqs + (size_t)j * n_iter);
+    PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_members, b->members.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice,
+                                    s),
+                    "batch member copy"));
+    std::vector<std::vector<uint8_t>> anchors(n, std::vector<uint8_t>((size_t)n_iter, 0));
+    bool direct = !use_graphs() || profiling_enabled();
+    std::vector<int64_t> key = {n_iter};
+    for (int j = 0; j < n; ++j) {
+        pet_state *st = b->states[j];
+        if (st->algo != PET_ALGO_SVREM && st->algo != PET_ALGO_SVRG) continue;
+        if (st->algo == PET_ALGO_SVREM && !st->s_hat_ready) direct = true;
+        for (int i = 0; i < n_iter; ++i)
+            if ((st->k + i) % ((long long)h_eta[j] * st->prob->plan->ns) == 0) {
+                anchors[j][i] = 1;
+                key.push_back((int64_t)j * (1LL << 32) + i);
+            }
+    }
+    pet_status rc;
+    if (direct) {
+        rc = enqueue_batch_epoch(b, n_iter, anchors, s);
+    } else {
+        // a batch keeps its own graph cache; run_graph takes a state, so borrow
+        // the cache of a stand-in state object
+        pet_state holder{};
+        holder.cap = b->cap;
+        holder.graphs.swap(b->graphs);
+        rc = run_graph(&holder, key, s, [&](cudaStream_t cs) { return enqueue_batch_epoch(b, n_iter, anchors, cs); });
+        b->graphs.swap(holder.graphs);
+        b->cap = holder.cap;
+        holder.cap = nullptr;
+    }
+    if (rc == PET_OK)
+        for (pet_state *st : b->states) st->k += n_iter;
+    return rc;
+}
+
+pet_status pet_batch_objective_async(pet_batch *b, double *d_phi, void *stream) {
+    if (!b || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
+    for (size_t j = 0; j < b->states.size(); ++j) {
+        pet_state *st = b->states[j];
+        PET_TRY(objective_enqueue(st->prob, st->img, d_phi + 3 * j, st->d_part, (cudaStream_t)stream));
+    }
+    return PET_OK;
+}
+
 pet_status pet_state_reset(pet_state *st, void *stream) {
     if (!st) return set_error(PET_ERR_INVALID, "null state");
     return state_init(st, (cudaStream_t)stream);

@@ -212,9 +212,8 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
 // instead of once per pixel it touches.  Views are processed in chunks of
 // kChunk to bound shared memory.
 template <int EPI, typename TQ, int kRun>
-__global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {
+__device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, const int bx) {
     extern __shared__ unsigned char smem_raw[];
-    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
     const int vb = __ldg(a.sub_off + t);
     const int nv = __ldg(a.sub_off + t + 1) - vb;
     float *s_part = reinterpret_cast<float *>(smem_raw);                       // [kChunk][kTile*kTile]
@@ -224,8 +223,8 @@ __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs
     const int nthr = blockDim.x;                  // >= kTile * kTile; one run per thread when nv <= nthr / 32
 
     const int tiles_x = (a.nx + kTile - 1) / kTile;
-    const int x0 = (blockIdx.x % tiles_x) * kTile;
-    const int y0 = (blockIdx.x / tiles_x) * kTile;
+    const int x0 = (bx % tiles_x) * kTile;
+    const int y0 = (bx / tiles_x) * kTile;
     constexpr int kRunsPerBand = kTile / kRun;
     constexpr int kRunsPerView = kTile * kRunsPerBand;
 
@@ -286,6 +285,62 @@ __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs
     apply_epilogue<EPI, TQ>(a, t, n, n, ix, iy, 0, acc);
 }
 
+template <int EPI, typename TQ, int kRun>
+__global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    back_tile_body<EPI, TQ, kRun>(a, t, blockIdx.x);
+}
+
+// Batched back projection + update: blockIdx.y picks the member, whose
+// algorithm and table type select the epilogue; same body as the single
+// launch, so each member's update is bit-identical to an unbatched one.
+template <int kRun>
+__global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMember *ms, const int *idx, int iter,
+                                                                   int in_is_img) {
+    const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
+    const int tiles = ((m.nx + kTile - 1) / kTile) * ((m.ny + kTile - 1) / kTile);
+    if ((int)blockIdx.x >= tiles) return;
+    BackArgs b{};
+    b.views = m.views;
+    b.uc = m.uc;
+    b.order = m.order;
+    b.sub_off = m.sub_off;
+    b.t_dev = m.seq + iter;
+    b.nx = m.nx;
+    b.ny = m.ny;
+    b.nz = 1;
+    b.nb = m.nb;
+    b.ns = m.ns;
+    b.run = kRun;
+    b.r = m.ratio;
+    b.f = in_is_img ? m.img : m.alt;
+    b.f_out = in_is_img ? m.alt : m.img;
+    b.sens_t = m.sens_t;
+    b.sens = m.sens;
+    b.beta = m.beta;
+    b.alpha = m.alpha;
+    b.s_hat = m.s_hat;
+    b.f_anc = m.f_anc;
+    b.s_anc = m.s_anc;
+    b.B = m.B;
+    b.d = m.d;
+    b.table = m.table;
+    b.qbar = m.qbar;
+    b.qtil = m.qtil;
+    const int t = __ldg(m.seq + iter);
+    switch (m.algo) {
+        case PET_ALGO_OSEM: back_tile_body<EPI_OSEM, float, kRun>(b, t, blockIdx.x); break;
+        case PET_ALGO_SVREM: back_tile_body<EPI_SVREM, float, kRun>(b, t, blockIdx.x); break;
+        case PET_ALGO_SAGA:
+            if (m.table_dtype == PET_TABLE_BF16)
+                back_tile_body<EPI_SAGA, __nv_bfloat16, kRun>(b, t, blockIdx.x);
+            else
+                back_tile_body<EPI_SAGA, float, kRun>(b, t, blockIdx.x);
+            break;
+        default: back_tile_body<EPI_SVRG, float, kRun>(b, t, blockIdx.x); break;
+    }
+}
+
 template <int EPI, typename TQ>
 pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
     if (a.nz == 1) {
@@ -310,6 +365,20 @@ pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
 }
 
 }  // namespace
+
+pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
+                             int max_views, int iter, int in_is_img, cudaStream_t s) {
+    if (n_members == 0 || tiles == 0) return PET_OK;
+    const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
+    const int per_view = kTile * (kTile / run);
+    const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
+    const dim3 grid((unsigned)tiles, (unsigned)n_members);
+    if (run == 4)
+        batch_back_kernel<4><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+    else
+        batch_back_kernel<8><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+    return check_launch("batch_back_kernel");
+}
 
 pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
                        cudaStream_t s, int max_views) {

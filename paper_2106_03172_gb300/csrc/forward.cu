@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
 // (within the warp) and then over warps through shared memory, always in the
 // same order, so the result is deterministic.
 template <int CHUNKS, int MODE, bool LL>
-__global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
+__device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx) {
     constexpr int RAYS = kBlock / CHUNKS;        // rays per block
     constexpr int WPG = CHUNKS / 4;              // warps per group of 8 rays
     const RayRange rr = ray_range(a);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
     const int r8 = lane & 7;
     const int chunk = 4 * (warp % WPG) + (lane >> 3);
     const int ray_local = 8 * (warp / WPG) + r8;
-    const long long ray = (long long)blockIdx.x * RAYS + ray_local;
+    const long long ray = (long long)bx * RAYS + ray_local;
 
     float acc = 0.0f;
     if (ray < n_rays) {
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
         float sum = 0.0f;
 #pragma unroll
         for (int w = 0; w < WPG; ++w) sum += red[g * WPG + w][threadIdx.x & 7];
-        const long long ray_f = (long long)blockIdx.x * RAYS + threadIdx.x;
+        const long long ray_f = (long long)bx * RAYS + threadIdx.x;
         if (ray_f < n_rays) {
             const long long gi = rr.off + ray_f;
             const float yhat = sum + (a.w ? __ldg(a.w + gi) : a.w_scalar);
@@ -239,9 +239,40 @@ __global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
             double s = 0.0;
 #pragma unroll
             for (int i = 0; i < kBlock / 32; ++i) s += dred[i];
-            a.ll_partials[blockIdx.x] = s;
+            a.ll_partials[bx] = s;
         }
     }
+}
+
+template <int CHUNKS, int MODE, bool LL>
+__global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
+    forward_tile_body<CHUNKS, MODE, LL>(a, blockIdx.x);
+}
+
+// Batched forward: blockIdx.y picks the member (through idx), whose subset
+// index for update `iter` is read on the device; same body as the single
+// launch, so each member's ratios are bit-identical to an unbatched update.
+template <int CHUNKS>
+__global__ void __launch_bounds__(kBlock) batch_forward_kernel(const BatchMember *ms, const int *idx, int iter,
+                                                               int in_is_img) {
+    const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
+    FwdArgs a{};
+    a.views = m.views;
+    a.uc = m.uc;
+    a.order = m.order;
+    a.sub_off = m.sub_off;
+    a.t_dev = m.seq + iter;
+    a.nx = m.nx;
+    a.ny = m.ny;
+    a.nz = 1;
+    a.nb = m.nb;
+    a.img = in_is_img ? m.img : m.alt;
+    a.g = m.g;
+    a.w = m.w;
+    a.w_scalar = m.w_scalar;
+    a.out = m.ratio;
+    a.status = m.status;
+    forward_tile_body<CHUNKS, FWD_RATIO, false>(a, blockIdx.x);
 }
 
 // Nonzeros of the rays of a view range: band pieces of positive length that
@@ -315,6 +346,19 @@ pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaS
     if (n_rays == 0) return PET_OK;
     count_nnz_kernel<<<(n_rays + kBlock - 1) / kBlock, kBlock, 0, s>>>(a, d_count);
     return check_launch("count_nnz_kernel");
+}
+
+pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
+                                int blocks, int iter, int in_is_img, cudaStream_t s) {
+    if (n_members == 0 || blocks == 0) return PET_OK;
+    const dim3 grid((unsigned)blocks, (unsigned)n_members);
+    switch (chunks) {
+        case 8: batch_forward_kernel<8><<<grid, kBlock, 0, s>>>(d_members, d_idx, iter, in_is_img); break;
+        case 16: batch_forward_kernel<16><<<grid, kBlock, 0, s>>>(d_members, d_idx, iter, in_is_img); break;
+        case 32: batch_forward_kernel<32><<<grid, kBlock, 0, s>>>(d_members, d_idx, iter, in_is_img); break;
+        default: return set_error(PET_ERR_INVALID, "batch forward: unsupported chunk count");
+    }
+    return check_launch("batch_forward_kernel");
 }
 
 int forward_blocks(int n_rays, int nz, int group) {

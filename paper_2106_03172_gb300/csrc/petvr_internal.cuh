@@ -173,6 +173,32 @@ struct BackArgs {
     const float *qtil;    // SVRG full-gradient term
 };
 
+// One member of a batched update (device-resident descriptor): where its
+// plan, problem and state live, and its subset indices for the current call.
+struct BatchMember {
+    const ViewParams *views;
+    const float2 *uc;
+    const int *order;
+    const int *sub_off;
+    int nx, ny, nb, ns;
+    const float *sens_t;
+    const float *sens;
+    const float *g;
+    const float *w;
+    float w_scalar;
+    float beta;
+    int *status;
+    int algo, table_dtype;
+    float *img, *alt, *ratio;
+    float *s_hat;
+    const float *f_anc, *s_anc, *B, *d;
+    void *table;
+    float *qbar;
+    const float *qtil;
+    float alpha;
+    const int *seq;
+};
+
 // ---------------------------------------------------------------------------
 // Host objects.
 // ---------------------------------------------------------------------------
@@ -213,6 +239,8 @@ struct pet_problem {
     int *d_status = nullptr;        // device error latch
 };
 
+struct pet_batch;
+
 struct pet_state {
     const pet_problem *prob;
     int algo, table_dtype;
@@ -237,6 +265,24 @@ struct pet_state {
         uint64_t kernels;           // kernel nodes, counted at capture
     };
     std::vector<Graph> graphs;      // captured epochs / objectives
+};
+
+struct pet_batch {
+    std::vector<pet_state *> states;
+    std::vector<petvr::BatchMember> members;   // host copy; uploaded before every call
+    petvr::BatchMember *d_members = nullptr;
+    int *d_idx = nullptr;           // member indices: forward groups, then back groups
+    struct Group {
+        int value;                  // forward: band chunks; back: run length
+        int offset, count;          // slice of d_idx
+        int grid_x;                 // forward blocks / back tiles to cover every member
+        int max_views;
+    };
+    std::vector<Group> fwd_groups, back_groups;
+    int *d_seqs = nullptr;          // [n][seq_cap] subset indices of the current call
+    int seq_cap = 0;
+    cudaStream_t cap = nullptr;
+    std::vector<pet_state::Graph> graphs;
 };
 
 namespace petvr {
@@ -272,6 +318,10 @@ pet_status launch_objective_finish(const pet_problem *p, const float *img, int n
 pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const float *img, int n_ll_blocks,
                                        double *part, double *d_out, cudaStream_t s);
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
+pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
+                                int blocks, int iter, int in_is_img, cudaStream_t s);
+pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
+                             int max_views, int iter, int in_is_img, cudaStream_t s);
 pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz,
                                       const float *f_anc, float *s_anc, float *s_hat, bool init,
                                       cudaStream_t s);

@@ -72,6 +72,10 @@ _SIGS = {
                                    POINTER(c_void_p), c_void_p]),
     "pet_state_destroy": (c_int32, [c_void_p]),
     "pet_state_reset": (c_int32, [c_void_p, c_void_p]),
+    "pet_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
+    "pet_batch_destroy": (c_int32, [c_void_p]),
+    "pet_batch_epoch": (c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_float), POINTER(c_int32), c_void_p]),
+    "pet_batch_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_osem_epoch": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
     "pet_svrem_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
     "pet_saga_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
@@ -275,6 +279,29 @@ def pet_kernel_launches() -> int:
     return int(lib().pet_kernel_launches())
 
 
+def pet_batch_create(states) -> c_void_p:
+    arr = (c_void_p * len(states))(*[st.value if isinstance(st, c_void_p) else st for st in states])
+    h = c_void_p()
+    _call("pet_batch_create", arr, len(states), byref(h))
+    return h
+
+
+def pet_batch_epoch(batch, seqs, alphas, etas, stream=None):
+    """seqs: one equal-length subset sequence per member."""
+    n = len(seqs)
+    n_iter = len(seqs[0]) if n else 0
+    if any(len(q) != n_iter for q in seqs):
+        raise ValueError("every member needs a sequence of the same length")
+    flat = (c_int32 * max(1, n * n_iter))(*[int(x) for q in seqs for x in q])
+    al = (c_float * n)(*[float(x) for x in alphas])
+    et = (c_int32 * n)(*[int(x) for x in etas])
+    _call("pet_batch_epoch", batch, flat, n_iter, al, et, _stream(stream))
+
+
+def pet_batch_objective_async(batch, phi_out: torch.Tensor, stream=None):
+    _call("pet_batch_objective_async", batch, _dev(phi_out, torch.float64), _stream(stream))
+
+
 # ---- owning handles ------------------------------------------------------------
 
 class Plan:
@@ -304,6 +331,25 @@ class Problem:
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.pet_problem_destroy(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """States whose updates run together (one launch per phase for all)."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        self.handle = pet_batch_create([st.handle for st in self.states])
+
+    def epoch(self, seqs, alphas, etas, stream=None):
+        pet_batch_epoch(self.handle, seqs, alphas, etas, stream)
+
+    def objective_async(self, phi_out, stream=None):
+        pet_batch_objective_async(self.handle, phi_out, stream)
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.pet_batch_destroy(self.handle)
             self.handle = None
 
 
