@@ -1007,6 +1007,7 @@ pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out
         pet_batch_destroy(b);
         return e;
     }
+    b->h_idx = idx;
     const cudaError_t ce = cudaMemcpy(b->d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
         pet_batch_destroy(b);
@@ -1053,6 +1054,9 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.qtil = st->qtil;
     m.alpha = alpha;
     m.seq = seq;
+    m.na = pl->na;
+    m.n_ll = forward_blocks(pl->M, 1, choose_group(pl));
+    m.part = st->d_part;
 }
 
 // All launches of one batched epoch on stream s.
@@ -1165,11 +1169,25 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
 
 pet_status pet_batch_objective_async(pet_batch *b, double *d_phi, void *stream) {
     if (!b || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
-    for (size_t j = 0; j < b->states.size(); ++j) {
-        pet_state *st = b->states[j];
-        PET_TRY(objective_enqueue(st->prob, st->img, d_phi + 3 * j, st->d_part, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)b->states.size();
+    // descriptors with the output slots (the subset sequences are not read here)
+    int pen_blocks = 0;
+    for (int j = 0; j < n; ++j) {
+        fill_member(b->members[j], b->states[j], b->members[j].alpha, b->members[j].seq);
+        b->members[j].phi = d_phi + 3 * j;
+        const pet_plan *pl = b->states[j]->prob->plan;
+        pen_blocks = std::max(pen_blocks, (pl->N + 255) / 256);
     }
-    return PET_OK;
+    PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_members, b->members.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice,
+                                    s),
+                    "batch member copy"));
+    for (const auto &g : b->fwd_groups) {
+        int blocks = 0;
+        for (int q = 0; q < g.count; ++q) blocks = std::max(blocks, b->members[b->h_idx[g.offset + q]].n_ll);
+        PET_TRY(launch_batch_objective(b->d_members, b->d_idx + g.offset, g.count, g.value, blocks, 0, s));
+    }
+    return launch_batch_objective_finish(b->d_members, n, pen_blocks, s);
 }
 
 pet_status pet_state_reset(pet_state *st, void *stream) {

@@ -361,6 +361,45 @@ pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, 
     return check_launch("batch_forward_kernel");
 }
 
+// Batched full-data objective pass: log-likelihood partials of every member's
+// current image over all its rays (blockIdx.y = member), into member.part.
+template <int CHUNKS>
+__global__ void __launch_bounds__(kBlock) batch_objective_kernel(const BatchMember *ms, const int *idx) {
+    const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
+    if ((int)blockIdx.x >= m.n_ll) return;
+    FwdArgs a{};
+    a.views = m.views;
+    a.uc = m.uc;
+    a.order = m.order;
+    a.v_begin = 0;
+    a.v_end = m.na;
+    a.nx = m.nx;
+    a.ny = m.ny;
+    a.nz = 1;
+    a.nb = m.nb;
+    a.img = m.img;
+    a.g = m.g;
+    a.w = m.w;
+    a.w_scalar = m.w_scalar;
+    a.ll_partials = m.part;
+    a.status = m.status;
+    forward_tile_body<CHUNKS, FWD_NONE, true>(a, blockIdx.x);
+}
+
+pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
+                                  int fwd_blocks, int pen_blocks, cudaStream_t s) {
+    (void)pen_blocks;
+    if (n_members == 0 || fwd_blocks == 0) return PET_OK;
+    const dim3 grid((unsigned)fwd_blocks, (unsigned)n_members);
+    switch (chunks) {
+        case 8: batch_objective_kernel<8><<<grid, kBlock, 0, s>>>(d_members, d_idx); break;
+        case 16: batch_objective_kernel<16><<<grid, kBlock, 0, s>>>(d_members, d_idx); break;
+        case 32: batch_objective_kernel<32><<<grid, kBlock, 0, s>>>(d_members, d_idx); break;
+        default: return set_error(PET_ERR_INVALID, "batch objective: unsupported chunk count");
+    }
+    return check_launch("batch_objective_kernel");
+}
+
 int forward_blocks(int n_rays, int nz, int group) {
     const long long threads = (long long)n_rays * nz * group;
     return (int)((threads + kBlock - 1) / kBlock);

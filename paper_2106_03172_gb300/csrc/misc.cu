@@ -152,7 +152,55 @@ __global__ void precond_kernel(const float *f0, const float *sens, int ns, long 
     d[i] = s > 0.0f ? (float)ns * f0[i] / s : 0.0f;
 }
 
+// Batched penalty partials (blockIdx.y = member) after the member's
+// log-likelihood partials, then one block per member for the final sums.
+__global__ void batch_penalty_kernel(const BatchMember *ms) {
+    const BatchMember &m = ms[blockIdx.y];
+    const int plane = m.nx * m.ny;
+    if ((int)blockIdx.x * kBlock >= plane) return;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    double r = 0.0;
+    if (i < plane) {
+        const float *f = m.img;
+        const int ix = i % m.nx, iy = i / m.nx;
+        const double fn = f[i];
+        double acc = 0.0;
+        if (ix > 0) { const double d = fn - f[i - 1]; acc += d * d; }
+        if (ix + 1 < m.nx) { const double d = fn - f[i + 1]; acc += d * d; }
+        if (iy > 0) { const double d = fn - f[i - m.nx]; acc += d * d; }
+        if (iy + 1 < m.ny) { const double d = fn - f[i + m.nx]; acc += d * d; }
+        r = 0.25 * acc;
+    }
+    r = block_sum(r);
+    if (threadIdx.x == 0) m.part[m.n_ll + blockIdx.x] = r;
+}
+
+__global__ void batch_objective_final_kernel(const BatchMember *ms) {
+    const BatchMember &m = ms[blockIdx.x];
+    const int n_pen = (m.nx * m.ny + kBlock - 1) / kBlock;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < m.n_ll; i += kBlock) a += m.part[i];
+    for (int i = threadIdx.x; i < n_pen; i += kBlock) b += m.part[m.n_ll + i];
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        m.phi[0] = a - (double)m.beta * b;
+        m.phi[1] = a;
+        m.phi[2] = b;
+    }
+}
+
 }  // namespace
+
+pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_members, int pen_blocks,
+                                         cudaStream_t s) {
+    if (n_members == 0) return PET_OK;
+    batch_penalty_kernel<<<dim3((unsigned)pen_blocks, (unsigned)n_members), kBlock, 0, s>>>(d_members);
+    pet_status st = check_launch("batch_penalty_kernel");
+    if (st != PET_OK) return st;
+    batch_objective_final_kernel<<<n_members, kBlock, 0, s>>>(d_members);
+    return check_launch("batch_objective_final_kernel");
+}
 
 pet_status launch_permute_sino(const float *src, float *dst, const int *order, int na, int nb, int nz,
                                cudaStream_t s) {

@@ -197,6 +197,10 @@ struct BatchMember {
     const float *qtil;
     float alpha;
     const int *seq;
+    int na;                // views (full-data passes)
+    int n_ll;              // forward blocks of a full pass (objective partial count)
+    double *part;          // objective partials of this member
+    double *phi;           // objective output {Phi, L, R}
 };
 
 // ---------------------------------------------------------------------------
@@ -272,6 +276,7 @@ struct pet_batch {
     std::vector<petvr::BatchMember> members;   // host copy; uploaded before every call
     petvr::BatchMember *d_members = nullptr;
     int *d_idx = nullptr;           // member indices: forward groups, then back groups
+    std::vector<int> h_idx;
     struct Group {
         int value;                  // forward: band chunks; back: run length
         int offset, count;          // slice of d_idx
@@ -320,6 +325,10 @@ pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
 pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
                                 int blocks, int iter, int in_is_img, cudaStream_t s);
+pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
+                                  int fwd_blocks, int pen_blocks, cudaStream_t s);
+pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_members, int pen_blocks,
+                                         cudaStream_t s);
 pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
                              int max_views, int iter, int in_is_img, cudaStream_t s);
 pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz,
