@@ -113,6 +113,21 @@ class Replica:
             self.k[m] += self.work.n_subsets
 
 
+def combine_ranks(total_ms: float, units: float, device=None):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed, summed, over the slowest rank's time (max over ranks).
+    Returns (value per second, max ms, summed units)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / (total_ms / 1e3), total_ms, units
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) / 1e3), float(t.item()), float(u.item())
+
+
 # --------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -394,16 +409,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in events]
     total_ms = float(sum(step_ms))
     phi_host = phi.cpu().numpy()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_max = float(t.item())
-        pt = torch.tensor([pairs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
-        pairs_all = float(pt.item())
-    else:
-        total_max, pairs_all = total_ms, float(pairs)
-    value = pairs_all / (total_max / 1e3)
+    value, total_max, pairs_all = combine_ranks(total_ms, float(pairs), device="cuda")
 
     # ---- profiled pass: per-kernel durations for the roofline
     n_prof = min(args.steps, 8)
@@ -474,11 +480,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append(s_ev.elapsed_time(e_ev))
         rep.advance()
-    e2e_value = e2e_pairs / (sum(e2e_ms) / 1e3)
-    if world > 1:
-        t = torch.tensor([e2e_value], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_value = float(t.item())
+    e2e_value, _, _ = combine_ranks(float(sum(e2e_ms)), float(e2e_pairs), device="cuda")
     h2d = 4 * geom.n_rays * geom.nz
     d2h = 4 * 4 * geom.n_pixels * geom.nz + 4 * 3 * 8
 
@@ -595,6 +597,13 @@ def run_batch64(args):
     same = all(torch.equal(m["img"], m["solo_img"]) for m in members)
     pairs_step = len(members) * n_iter
     value = pairs_step * args.steps / (sum(t_batch) / 1e3)
+    # algorithmic work of the timed steps: 2 nnz(A_t) per update (forward + back), nnz(A) per objective
+    nnz_steps = 0
+    for k in range(args.steps):
+        for m, q in zip(members, seqs(args.warmup + k)):
+            nz_t = [petvr.pet_plan_nnz(m["plan"].handle, t) for t in range(m["work"].n_subsets)]
+            nnz_steps += sum(2 * nz_t[int(t)] for t in q) + petvr.pet_plan_nnz(m["plan"].handle, -1)
+    flops = 2.0 * nnz_steps / (sum(t_batch) / 1e3) / 1e12
     solo_value = pairs_step * args.steps / (sum(t_solo) / 1e3)
     sizes = sorted({m["work"].geometry.nx for m in members})
     line = {
@@ -613,6 +622,8 @@ def run_batch64(args):
         "sequential": {"value": solo_value, "ms_per_step": float(np.mean(t_solo)),
                        "how": "the same 64 states stepped one after another on one stream (graph per state)"},
         "speedup_vs_sequential": value / solo_value,
+        "algorithmic": {"nonzeros_per_step": nnz_steps / args.steps, "achieved_tflops": flops,
+                        "note": "2 flops per system-matrix nonzero per projection"},
         "bit_identical_to_sequential": bool(same),
     }
     print(json.dumps(line), flush=True)
