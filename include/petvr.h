@@ -57,8 +57,11 @@ typedef enum {
 enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG = 3 };
 /* SAGA gradient-table storage (pet_state_create). */
 enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
-/* Potentials of the pairwise penalty (Table 1); quadratic is implemented. */
-enum { PET_POT_QUADRATIC = 0 };
+/* Potentials of the pairwise penalty (Table 1, t = f_n - f_j, delta > 0):
+ * quadratic t^2/2; Huber t^2/2 for |t| <= delta else delta|t| - delta^2/2;
+ * log cosh delta^2 log cosh(t/delta); hyperbola delta^2 (sqrt(1+(t/delta)^2) - 1)
+ * (the form whose derivative is Table 1's t / sqrt(1+(t/delta)^2)). */
+enum { PET_POT_QUADRATIC = 0, PET_POT_HUBER = 1, PET_POT_LOGCOSH = 2, PET_POT_HYPERBOLA = 3 };
 
 /* 2-D parallel-beam geometry (optionally a stack of nz independent slices).
  * Pixel (ix, iy) is the half-open square [x_min + ix d, x_min + (ix+1) d) x
@@ -86,9 +89,9 @@ typedef struct {
 
 /* Penalty beta R(f), R = 1/2 sum_n sum_{j in N4(n)} rho(f_n - f_j) (§3). */
 typedef struct {
-    int32_t potential; /* PET_POT_QUADRATIC */
+    int32_t potential; /* PET_POT_* */
     float beta;        /* >= 0 */
-    float delta;       /* unused by the quadratic potential */
+    float delta;       /* > 0; unused by the quadratic potential */
 } pet_penalty;
 
 typedef struct pet_plan pet_plan;

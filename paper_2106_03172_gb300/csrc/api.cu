@@ -222,6 +222,8 @@ pet_status state_init(pet_state *st, cudaStream_t s) {
     b.r_view0 = 0;
     b.f = st->img;
     b.beta = p->pen.beta;
+    b.pot = p->pen.potential;
+    b.delta = p->pen.delta;
     b.table = st->table;
     PET_TRY(launch_back(b, EPI_SAGA_INIT, st->table_dtype, pl->ns, s, pl->max_sub_views));
     return launch_saga_finish(st->table, st->table_dtype, pl->ns, Nz, pl->nz, st->img, pl->d_sens, st->qbar, st->d,
@@ -596,7 +598,10 @@ pet_status pet_problem_create(const pet_plan *pl, const float *d_counts, const f
                               const pet_penalty *pen, pet_problem **out, void *stream) {
     if (!pl || !d_counts || !pen || !out) return set_error(PET_ERR_INVALID, "null argument");
     *out = nullptr;
-    if (pen->potential != PET_POT_QUADRATIC) return set_error(PET_ERR_INVALID, "only the quadratic potential exists");
+    if (pen->potential < PET_POT_QUADRATIC || pen->potential > PET_POT_HYPERBOLA)
+        return set_error(PET_ERR_INVALID, "unknown potential");
+    if (pen->potential != PET_POT_QUADRATIC && !(pen->delta > 0.0f && std::isfinite(pen->delta)))
+        return set_error(PET_ERR_INVALID, "delta must be positive and finite");
     if (!(pen->beta >= 0.0f) || !std::isfinite(pen->beta)) return set_error(PET_ERR_INVALID, "beta must be >= 0");
     if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
     cudaStream_t s = (cudaStream_t)stream;
@@ -788,6 +793,8 @@ pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float
     b.f = in;
     b.f_out = outp;
     b.beta = p->pen.beta;
+    b.pot = p->pen.potential;
+    b.delta = p->pen.delta;
     b.alpha = alpha;
     int epi = EPI_OSEM;
     if (algo == PET_ALGO_SVREM) {
@@ -1038,6 +1045,8 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.w = p->d_w;
     m.w_scalar = p->w_scalar;
     m.beta = p->pen.beta;
+    m.pot = p->pen.potential;
+    m.delta = p->pen.delta;
     m.status = p->d_status;
     m.algo = st->algo;
     m.table_dtype = st->table_dtype;

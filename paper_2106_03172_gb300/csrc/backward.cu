@@ -37,17 +37,41 @@ constexpr int kTileBlockMax = 1024; // threads of a tile block: kTile * kTile / 
 static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
 
 struct Stencil {
-    float cnt;   // number of in-image 4-neighbours (sum_j d_nj for the quadratic potential)
-    float sum;   // sum_j f_j
+    float cnt;   // sum_j d_nj, d_nj = gamma(f_n - f_j) (quadratic: the number of in-image neighbours)
+    float sum;   // sum_j d_nj f_j
+    float grad;  // dR/df_n = sum_j rho'(f_n - f_j)
 };
 
-__device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int nx, int ny, int nz,
-                                            int z) {
-    Stencil s{0.0f, 0.0f};
-    if (ix > 0) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)iy * nx + ix - 1) * nz + z); }
-    if (ix + 1 < nx) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)iy * nx + ix + 1) * nz + z); }
-    if (iy > 0) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)(iy - 1) * nx + ix) * nz + z); }
-    if (iy + 1 < ny) { s.cnt += 1.0f; s.sum += __ldg(f + ((long long)(iy + 1) * nx + ix) * nz + z); }
+// 4-neighbourhood of pixel (ix, iy) in slice z: surrogate weights and
+// penalty gradient at f^k (out-of-image neighbours are dropped).
+__device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int nx, int ny, int nz, int z,
+                                            float fk, int pot, float delta) {
+    Stencil s{0.0f, 0.0f, 0.0f};
+    float nb[4];
+    int cnt = 0;
+    if (ix > 0) nb[cnt++] = __ldg(f + ((long long)iy * nx + ix - 1) * nz + z);
+    if (ix + 1 < nx) nb[cnt++] = __ldg(f + ((long long)iy * nx + ix + 1) * nz + z);
+    if (iy > 0) nb[cnt++] = __ldg(f + ((long long)(iy - 1) * nx + ix) * nz + z);
+    if (iy + 1 < ny) nb[cnt++] = __ldg(f + ((long long)(iy + 1) * nx + ix) * nz + z);
+    if (pot == PET_POT_QUADRATIC) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < cnt) {
+                s.cnt += 1.0f;
+                s.sum += nb[q];
+            }
+        s.grad = fk * s.cnt - s.sum;
+        return s;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (q < cnt) {
+            float dr, g;
+            potential_dg(pot, delta, fk - nb[q], dr, g);
+            s.cnt += g;
+            s.sum += g * nb[q];
+            s.grad += dr;
+        }
     return s;
 }
 
@@ -83,7 +107,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         a.out[(long long)t * plane + i] = acc;
     } else if (EPI == EPI_OSEM) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float bp = a.beta * inv_ns;
         const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
         const float c = bp * fmaf(fk, st.cnt, st.sum) - S;
@@ -95,14 +119,14 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float tau = ns * fk * acc - ns * a.f_anc[i] * Bt + a.s_anc[i];
         const float s = fmaf(a.alpha, tau, (1.0f - a.alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float S = __ldg(a.sens + n);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
     } else if (EPI == EPI_SAGA || EPI == EPI_SAGA_INIT) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
-        const float gradR = fk * st.cnt - st.sum;
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const float gradR = st.grad;
         const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
         const float q = round_q<TQ>(acc - S - a.beta * inv_ns * gradR);
         const long long qi = (long long)t * plane + i;
@@ -118,8 +142,8 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         }
     } else if (EPI == EPI_SVRG) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z);
-        const float gradR = fk * st.cnt - st.sum;
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const float gradR = st.grad;
         const float Bt = a.B[(long long)t * plane + i];
         const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
         a.f_out[i] = fmaxf(fmaf(a.alpha * a.d[i], dir, fk), 0.0f);
@@ -318,6 +342,8 @@ __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMe
     b.sens_t = m.sens_t;
     b.sens = m.sens;
     b.beta = m.beta;
+    b.pot = m.pot;
+    b.delta = m.delta;
     b.alpha = m.alpha;
     b.s_hat = m.s_hat;
     b.f_anc = m.f_anc;

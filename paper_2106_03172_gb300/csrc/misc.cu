@@ -69,23 +69,32 @@ __global__ void uniform_fill_kernel(float *img, long long plane, int nz, const d
     img[i] = den > 0.0 ? (float)(sums[i % nz] / den) : 0.0f;
 }
 
-// Per-block partial of R(f) = 1/2 sum_n sum_{j in N4(n)} (f_n - f_j)^2 / 2.
-__global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, double *part) {
+// Per-block partial of R(f) = 1/2 sum_n sum_{j in N4(n)} rho(f_n - f_j): each
+// pixel adds half its four potential terms (rho in FP32, sums in FP64).
+__global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, int pot, float delta, double *part) {
     const long long plane = (long long)nx * ny * nz;
     const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
     double r = 0.0;
     if (i < plane) {
-        const int z = (int)(i % nz);
         const int n = (int)(i / nz);
         const int ix = n % nx, iy = n / nx;
-        const double fn = f[i];
-        double acc = 0.0;
-        if (ix > 0) { const double d = fn - f[i - nz]; acc += d * d; }
-        if (ix + 1 < nx) { const double d = fn - f[i + nz]; acc += d * d; }
-        if (iy > 0) { const double d = fn - f[i - (long long)nx * nz]; acc += d * d; }
-        if (iy + 1 < ny) { const double d = fn - f[i + (long long)nx * nz]; acc += d * d; }
-        r = 0.25 * acc;
-        (void)z;
+        const float fn = f[i];
+        if (pot == PET_POT_QUADRATIC) {
+            const double fd = fn;
+            double acc = 0.0;
+            if (ix > 0) { const double d = fd - f[i - nz]; acc += d * d; }
+            if (ix + 1 < nx) { const double d = fd - f[i + nz]; acc += d * d; }
+            if (iy > 0) { const double d = fd - f[i - (long long)nx * nz]; acc += d * d; }
+            if (iy + 1 < ny) { const double d = fd - f[i + (long long)nx * nz]; acc += d * d; }
+            r = 0.25 * acc;
+        } else {
+            double acc = 0.0;
+            if (ix > 0) acc += potential_rho(pot, delta, fn - f[i - nz]);
+            if (ix + 1 < nx) acc += potential_rho(pot, delta, fn - f[i + nz]);
+            if (iy > 0) acc += potential_rho(pot, delta, fn - f[i - (long long)nx * nz]);
+            if (iy + 1 < ny) acc += potential_rho(pot, delta, fn - f[i + (long long)nx * nz]);
+            r = 0.5 * acc;
+        }
     }
     r = block_sum(r);
     if (threadIdx.x == 0) part[blockIdx.x] = r;
@@ -163,13 +172,23 @@ __global__ void batch_penalty_kernel(const BatchMember *ms) {
     if (i < plane) {
         const float *f = m.img;
         const int ix = i % m.nx, iy = i / m.nx;
-        const double fn = f[i];
-        double acc = 0.0;
-        if (ix > 0) { const double d = fn - f[i - 1]; acc += d * d; }
-        if (ix + 1 < m.nx) { const double d = fn - f[i + 1]; acc += d * d; }
-        if (iy > 0) { const double d = fn - f[i - m.nx]; acc += d * d; }
-        if (iy + 1 < m.ny) { const double d = fn - f[i + m.nx]; acc += d * d; }
-        r = 0.25 * acc;
+        const float fn = f[i];
+        if (m.pot == PET_POT_QUADRATIC) {
+            const double fd = fn;
+            double acc = 0.0;
+            if (ix > 0) { const double d = fd - f[i - 1]; acc += d * d; }
+            if (ix + 1 < m.nx) { const double d = fd - f[i + 1]; acc += d * d; }
+            if (iy > 0) { const double d = fd - f[i - m.nx]; acc += d * d; }
+            if (iy + 1 < m.ny) { const double d = fd - f[i + m.nx]; acc += d * d; }
+            r = 0.25 * acc;
+        } else {
+            double acc = 0.0;
+            if (ix > 0) acc += potential_rho(m.pot, m.delta, fn - f[i - 1]);
+            if (ix + 1 < m.nx) acc += potential_rho(m.pot, m.delta, fn - f[i + 1]);
+            if (iy > 0) acc += potential_rho(m.pot, m.delta, fn - f[i - m.nx]);
+            if (iy + 1 < m.ny) acc += potential_rho(m.pot, m.delta, fn - f[i + m.nx]);
+            r = 0.5 * acc;
+        }
     }
     r = block_sum(r);
     if (threadIdx.x == 0) m.part[m.n_ll + blockIdx.x] = r;
@@ -232,7 +251,8 @@ pet_status launch_objective_finish(const pet_problem *p, const float *img, int n
     const long long plane = (long long)pl->N * pl->nz;
     const int n_pen = (int)blocks_for(plane);
     double *pen_part = part + n_ll_blocks;
-    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, pl->nx, pl->ny, pl->nz, pen_part);
+    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, pl->nx, pl->ny, pl->nz, p->pen.potential, p->pen.delta,
+                                                    pen_part);
     pet_status st = check_launch("penalty_partial_kernel");
     if (st != PET_OK) return st;
     objective_final_kernel<<<1, kBlock, 0, s>>>(part, n_ll_blocks, pen_part, n_pen, (double)p->pen.beta,
@@ -245,7 +265,7 @@ pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const
     const long long plane = (long long)nx * ny * nz;
     const int n_pen = (int)blocks_for(plane);
     double *pen_part = part + n_ll_blocks;
-    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, nx, ny, nz, pen_part);
+    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, nx, ny, nz, PET_POT_QUADRATIC, 1.0f, pen_part);
     pet_status st = check_launch("penalty_partial_kernel");
     if (st != PET_OK) return st;
     objective_final_kernel<<<1, kBlock, 0, s>>>(part, n_ll_blocks, pen_part, n_pen, (double)beta, d_out);

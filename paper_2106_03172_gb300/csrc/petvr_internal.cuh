@@ -110,6 +110,46 @@ __device__ __forceinline__ float m_step_root(float a, float S, float b, float c)
     return (c <= 0.0f) ? (2.0f * a) / (D - c) : (c + D) / (4.0f * b);
 }
 
+// Pairwise potentials of Table 1 (t = f_n - f_j, delta > 0): rho, rho' and
+// the curvature gamma = rho'(t)/t with its finite limit 1 at t = 0.  The
+// hyperbola is delta^2 (sqrt(1 + (t/delta)^2) - 1), the form whose derivative
+// is the printed rho' (the printed rho lacks a factor delta).
+__device__ __forceinline__ void potential_dg(int pot, float delta, float t, float &drho, float &gam) {
+    if (pot == PET_POT_HUBER) {
+        const float a = fabsf(t);
+        drho = fminf(fmaxf(t, -delta), delta);
+        gam = a <= delta ? 1.0f : delta / a;
+    } else if (pot == PET_POT_LOGCOSH) {
+        const float th = tanhf(t / delta);
+        drho = delta * th;
+        gam = t != 0.0f ? delta * th / t : 1.0f;
+    } else if (pot == PET_POT_HYPERBOLA) {
+        const float q = t / delta;
+        gam = rsqrtf(fmaf(q, q, 1.0f));
+        drho = t * gam;
+    } else {
+        drho = t;
+        gam = 1.0f;
+    }
+}
+
+__device__ __forceinline__ float potential_rho(int pot, float delta, float t) {
+    if (pot == PET_POT_HUBER) {
+        const float a = fabsf(t);
+        return a <= delta ? 0.5f * t * t : delta * a - 0.5f * delta * delta;
+    }
+    if (pot == PET_POT_LOGCOSH) {
+        // delta^2 log cosh(t/delta) = delta^2 (|u| + log1p(exp(-2|u|)) - log 2)
+        const float u = fabsf(t / delta);
+        return delta * delta * (u + log1pf(expf(-2.0f * u)) - 0.69314718055994531f);
+    }
+    if (pot == PET_POT_HYPERBOLA) {
+        const float q = t / delta;
+        return delta * delta * (sqrtf(fmaf(q, q, 1.0f)) - 1.0f);
+    }
+    return 0.5f * t * t;
+}
+
 // ---------------------------------------------------------------------------
 // Kernel argument blocks.
 // ---------------------------------------------------------------------------
@@ -162,6 +202,8 @@ struct BackArgs {
     const float *sens_t;  // [ns][N] subset sensitivities
     const float *sens;    // [N] full sensitivity
     float beta;           // penalty weight beta (full)
+    int pot;              // potential (PET_POT_*)
+    float delta;          // its transition parameter
     float alpha;
     float *s_hat;         // SVREM running statistic
     const float *f_anc;   // SVREM anchor image
@@ -187,6 +229,8 @@ struct BatchMember {
     const float *w;
     float w_scalar;
     float beta;
+    int pot;
+    float delta;
     int *status;
     int algo, table_dtype;
     float *img, *alt, *ratio;

@@ -179,10 +179,14 @@ def pet_back(plan, sino, subset: int, img, stream=None):
     _call("pet_back", plan, _dev(sino), subset, _dev(img), _stream(stream))
 
 
-def pet_problem_create(plan, counts, bg, bg_scalar: float, beta: float, stream=None) -> c_void_p:
+POTENTIAL = {"quadratic": 0, "huber": 1, "logcosh": 2, "hyperbola": 3}
+
+
+def pet_problem_create(plan, counts, bg, bg_scalar: float, beta: float, stream=None,
+                       potential: str = "quadratic", delta: float = 1.0) -> c_void_p:
     h = c_void_p()
     _call("pet_problem_create", plan, _dev(counts), _dev(bg), bg_scalar,
-          byref(pet_penalty(0, beta, 1.0)), byref(h), _stream(stream))
+          byref(pet_penalty(POTENTIAL[potential], beta, delta)), byref(h), _stream(stream))
     return h
 
 
@@ -324,9 +328,10 @@ class Plan:
 class Problem:
     """Counts, background and penalty bound to a plan (data copied on the device)."""
 
-    def __init__(self, plan: Plan, counts, bg, bg_scalar: float, beta: float, stream=None):
+    def __init__(self, plan: Plan, counts, bg, bg_scalar: float, beta: float, stream=None,
+                 potential: str = "quadratic", delta: float = 1.0):
         self.plan = plan
-        self.handle = pet_problem_create(plan.handle, counts, bg, bg_scalar, beta, stream)
+        self.handle = pet_problem_create(plan.handle, counts, bg, bg_scalar, beta, stream, potential, delta)
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

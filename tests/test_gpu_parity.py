@@ -329,3 +329,44 @@ def test_full_size_stack_projection():
     img = torch.empty(geom.n_pixels * geom.nz, device="cuda")
     pv.pet_back(plan.handle, _cuda(y), -1, img)
     _assert_proj(_host(img).reshape(-1, geom.nz), A.T @ y)
+
+
+@pytest.fixture(scope="module", params=[("huber", 0.05), ("logcosh", 0.05), ("hyperbola", 0.05)])
+def potential_case(request):
+    """64x64 workload with an edge-preserving potential of Table 1 (the paper's
+    experiments use log cosh) and a penalty weight large enough to matter."""
+    from oracle.em import build_problem
+    from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data
+    pv = _pv()
+    pot, delta = request.param
+    work = WORKLOADS["c64"]
+    data = make_data(work, 0)
+    beta = 0.5
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, beta, pot, delta)
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    gp = pv.Problem(plan, _cuda(data["g"]), None, data["w"], beta, potential=pot, delta=delta)
+    return pv, prob, work, plan, gp
+
+
+@pytest.mark.parametrize("method", ["osem", "svrem", "saga", "svrg"])
+def test_edge_preserving_potential_updates(potential_case, method):
+    pv, prob, work, plan, gp = potential_case
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, method, img)
+    alg = _oracle_alg(prob, method, f0, work)
+    seq = subset_sequence(3000 + METHOD_SEED[method], work.n_subsets, 2 * work.n_subsets)
+    f = f0
+    for k, t in enumerate(seq):
+        _gpu_step(state, method, int(t), work)
+        f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
+        err = rel_l2(_host(img), f)
+        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+    assert pv.pet_objective(gp.handle, img) == pytest.approx(prob.objective(f), rel=1e-7)
+
+
+def test_edge_preserving_potential_objective(potential_case):
+    pv, prob, work, plan, gp = potential_case
+    f = np.random.default_rng(12).uniform(0.05, 0.6, (prob.N, 1)).astype(np.float32).astype(np.float64)
+    assert pv.pet_objective(gp.handle, _cuda(f)) == pytest.approx(prob.objective(f), rel=1e-7)
+    assert prob.pen.value(f)[0] > 0.0
