@@ -54,7 +54,8 @@ typedef enum {
 } pet_status;
 
 /* Algorithms (pet_state_create). */
-enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG = 3 };
+enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG = 3,
+       PET_ALGO_SGA = 4, PET_ALGO_SEM = 5 };
 /* SAGA gradient-table storage (pet_state_create). */
 enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
 /* Potentials of the pairwise penalty (Table 1, t = f_n - f_j, delta > 0):
@@ -286,6 +287,19 @@ pet_status pet_batch_epoch(pet_batch *batch, const int32_t *h_subset_seqs, int32
 /* Objectives {Phi, L, R} of every member's current image into d_phi
  * (device, [n][3] doubles), enqueued only. */
 pet_status pet_batch_objective_async(pet_batch *batch, double *d_phi, void *stream);
+
+/* The paper's non-variance-reduced baselines on the same kernels (§5.1),
+ * with step alpha_k = alpha0 / (decay k + 1), k the state's update counter:
+ * SGA   (§4, Eq. (sga)): f <- P>=0(f + alpha_k (f / A_t^T 1) . grad Phi_t(f));
+ *       decay = 0, alpha0 = 1 is SGA; decay = 0.001 is the subset-dependent
+ *       BSREM of §5.1.  State algorithm PET_ALGO_SGA.
+ * SEM   (§2.3, Eq. (tempsem)): s <- (1 - alpha_k) s + alpha_k tau_t(f), then
+ *       the M-step of §3 with A^T 1 and beta; s starts at s(f^(0)) (one full
+ *       pass on the first call).  State algorithm PET_ALGO_SEM. */
+pet_status pet_sga_epoch(pet_state *state, float alpha0, float decay, const int32_t *h_subset_seq,
+                         int32_t n_iter, void *stream);
+pet_status pet_sem_epoch(pet_state *state, float alpha0, float decay, const int32_t *h_subset_seq,
+                         int32_t n_iter, void *stream);
 
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);

@@ -208,6 +208,30 @@ def kkt_residual(prob: Problem, f):
     return float(np.linalg.norm(step) / np.linalg.norm(f))
 
 
+def bsrem_schedule(k):
+    """Decaying step (0.001 k + 1)^{-1} used for SEM and BSREM in §5.1."""
+    return 1.0 / (0.001 * k + 1.0)
+
+
+class SGA:
+    """Preconditioned stochastic gradient ascent (§4, Eq. (sga)) with the
+    subset preconditioner d_t(f) = f / A_t^T 1 (§4, Eq. (preconditioners)) and
+    the projection P_{>=0}:
+        f^{k+1} = P_{>=0}(f^k + alpha_k d_t(f^k) . (grad L_t(f^k) - (beta/N_s) grad R(f^k))).
+    alpha_k = 1 is SGA; alpha_k = (0.001 k + 1)^{-1} is the subset-dependent
+    BSREM variant of §5.1."""
+
+    def __init__(self, prob: Problem, f0, schedule=lambda k: 1.0):
+        self.p, self.f, self.k, self.alpha = prob, f0.copy(), 0, schedule
+
+    def step(self, t):
+        S = self.p.sens_t[t]
+        d = np.where(S > 0, self.f / np.where(S > 0, S, 1.0), 0.0)
+        self.f = np.maximum(self.f + self.alpha(self.k) * d * self.p.grad_Phi_t(self.f, t), 0.0)
+        self.k += 1
+        return self.f
+
+
 class SEM:
     """Stochastic EM (§2.3, Eq. (tempsem)): s_hat <- (1-alpha_k) s_hat + alpha_k tau_t(f)."""
 

@@ -689,6 +689,7 @@ pet_status pet_state_destroy(pet_state *st) {
     dfree(st->qtil);
     if (st->table) cudaFree(st->table);
     dfree(st->d_seq);
+    dfree(st->d_alpha);
     dfree(st->d_part);
     for (auto &g : st->graphs) cudaGraphExecDestroy(g.exec);
     if (st->cap) cudaStreamDestroy(st->cap);
@@ -699,7 +700,7 @@ pet_status pet_state_destroy(pet_state *st) {
 pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dtype, float *d_img,
                             size_t *bytes_needed, pet_state **out, void *stream) {
     if (!p) return set_error(PET_ERR_INVALID, "null problem");
-    if (algo < PET_ALGO_OSEM || algo > PET_ALGO_SVRG) return set_error(PET_ERR_INVALID, "unknown algorithm");
+    if (algo < PET_ALGO_OSEM || algo > PET_ALGO_SEM) return set_error(PET_ERR_INVALID, "unknown algorithm");
     if (table_dtype != PET_TABLE_FP32 && table_dtype != PET_TABLE_BF16)
         return set_error(PET_ERR_INVALID, "unknown table dtype");
     const pet_plan *pl = p->plan;
@@ -709,6 +710,7 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
     if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
     if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
+    if (algo == PET_ALGO_SEM) bytes += Nz * 4 + (size_t)pl->M * pl->nz * 4;
     if (bytes_needed) *bytes_needed = bytes;
     if (!out) return PET_OK;
     *out = nullptr;
@@ -736,6 +738,9 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
         if ((e = dalloc(&st->f_anc, Nz, "f_anc")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->s_anc, Nz, "s_anc")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->B, (size_t)pl->ns * Nz, "B")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->ratio_full, Mz, "full ratio")) != PET_OK) return fail(e);
+    } else if (algo == PET_ALGO_SEM) {
+        if ((e = dalloc(&st->s_hat, Nz, "s_hat")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->ratio_full, Mz, "full ratio")) != PET_OK) return fail(e);
     } else if (algo == PET_ALGO_SVRG) {
         if ((e = dalloc(&st->d, Nz, "d")) != PET_OK) return fail(e);
@@ -775,8 +780,8 @@ pet_status anchor_pass(pet_state *st, const float *f, float *ratio_full, cudaStr
 }
 
 // One update on subset *t_dev (device-resident index) from `in` to `outp`.
-pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float *in, float *outp, float alpha,
-                          cudaStream_t s) {
+pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float *alpha_dev, const float *in,
+                          float *outp, cudaStream_t s) {
     const pet_problem *p = st->prob;
     const pet_plan *pl = p->plan;
     FwdArgs a = fwd_args(pl, in, -1, false);
@@ -795,7 +800,7 @@ pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float
     b.beta = p->pen.beta;
     b.pot = p->pen.potential;
     b.delta = p->pen.delta;
-    b.alpha = alpha;
+    b.alpha_dev = alpha_dev;
     int epi = EPI_OSEM;
     if (algo == PET_ALGO_SVREM) {
         epi = EPI_SVREM;
@@ -813,12 +818,31 @@ pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float
         b.d = st->d;
         b.B = st->B;
         b.qtil = st->qtil;
+    } else if (algo == PET_ALGO_SGA) {
+        epi = EPI_SGA;
+    } else if (algo == PET_ALGO_SEM) {
+        epi = EPI_SEM;
+        b.s_hat = st->s_hat;
     }
     return launch_back(b, epi, st->table_dtype, 1, s, pl->max_sub_views);
 }
 
+// SEM start: s_hat = f . A^T(g / (A f + w)), the full statistic at f (one pass).
+pet_status sem_init(pet_state *st, const float *f, cudaStream_t s) {
+    const pet_problem *p = st->prob;
+    const pet_plan *pl = p->plan;
+    PET_TRY(ratio_all(p, f, st->ratio_full, s));
+    BackArgs b = back_args(pl, st->ratio_full, -1, false);
+    b.sub_off = pl->d_all_off;            // every view, in the subset-major order of the ratio
+    b.t0 = 0;
+    b.r_view0 = 0;
+    b.f = f;
+    b.s_hat = st->s_hat;
+    return launch_back(b, EPI_SEM_INIT, PET_TABLE_FP32, 1, s, pl->na);
+}
+
 // The whole epoch's launch sequence (anchors where `anchors[i]`), on stream s.
-pet_status enqueue_epoch(pet_state *st, int algo, int32_t n_iter, float alpha, const std::vector<uint8_t> &anchors,
+pet_status enqueue_epoch(pet_state *st, int algo, int32_t n_iter, const std::vector<uint8_t> &anchors,
                          cudaStream_t s) {
     const pet_plan *pl = st->prob->plan;
     const long long plane = plane_of(pl);
@@ -834,7 +858,11 @@ pet_status enqueue_epoch(pet_state *st, int algo, int32_t n_iter, float alpha, c
             PET_TRY(anchor_pass(st, in, st->ratio_full, s));
             PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
         }
-        return enqueue_update(st, algo, st->d_seq + i, in, outp, alpha, s);
+        if (algo == PET_ALGO_SEM && !st->s_hat_ready) {
+            PET_TRY(sem_init(st, in, s));
+            st->s_hat_ready = true;
+        }
+        return enqueue_update(st, algo, st->d_seq + i, st->d_alpha + i, in, outp, s);
     });
 }
 
@@ -880,45 +908,57 @@ pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_
     return PET_OK;
 }
 
-pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_iter, float alpha, int32_t eta,
-                        cudaStream_t s) {
+pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_iter, float alpha0, float decay,
+                        int32_t eta, cudaStream_t s) {
     if (!st) return set_error(PET_ERR_INVALID, "null state");
     if (st->algo != algo) return set_error(PET_ERR_STATE, "state was created for another algorithm");
     const pet_problem *p = st->prob;
     const pet_plan *pl = p->plan;
     PET_TRY(check_seq(pl, seq, n_iter));
-    if (!std::isfinite(alpha)) return set_error(PET_ERR_INVALID, "alpha must be finite");
+    if (!std::isfinite(alpha0) || !std::isfinite(decay) || decay < 0.0f)
+        return set_error(PET_ERR_INVALID, "alpha must be finite and decay >= 0");
     if ((algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) && eta < 1)
         return set_error(PET_ERR_INVALID, "eta must be >= 1");
     if (n_iter == 0) return PET_OK;
     if (n_iter > st->seq_cap) {
         int *grown = nullptr;
+        float *grown_a = nullptr;
         PET_TRY(dalloc(&grown, (size_t)n_iter, "subset sequence"));
-        // the old buffer may still be read by enqueued work: release it after the stream drains
+        if (dalloc(&grown_a, (size_t)n_iter, "step sizes") != PET_OK) {
+            dfree(grown);
+            return PET_ERR_OOM;
+        }
+        // the old buffers may still be read by enqueued work: release them after the stream drains
         if (st->d_seq) {
             PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
             dfree(st->d_seq);
+            dfree(st->d_alpha);
         }
         st->d_seq = grown;
+        st->d_alpha = grown_a;
         st->seq_cap = n_iter;
         for (auto &g : st->graphs) cudaGraphExecDestroy(g.exec);
         st->graphs.clear();
     }
+    std::vector<float> alphas((size_t)n_iter);
+    for (int i = 0; i < n_iter; ++i) alphas[i] = (float)((double)alpha0 / ((double)decay * (double)(st->k + i) + 1.0));
     PET_TRY(cuda_ok(cudaMemcpyAsync(st->d_seq, seq, sizeof(int32_t) * n_iter, cudaMemcpyHostToDevice, s),
                     "subset sequence copy"));
+    PET_TRY(cuda_ok(cudaMemcpyAsync(st->d_alpha, alphas.data(), sizeof(float) * n_iter, cudaMemcpyHostToDevice, s),
+                    "step size copy"));
     std::vector<uint8_t> anchors((size_t)n_iter, 0);
     if (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG)
         for (int i = 0; i < n_iter; ++i) anchors[i] = ((st->k + i) % ((long long)eta * pl->ns) == 0) ? 1 : 0;
     pet_status rc;
-    // SVREM's first anchor also initialises s_hat: that epoch shape is enqueued directly
-    const bool first_svrem = algo == PET_ALGO_SVREM && !st->s_hat_ready;
-    if (!use_graphs() || profiling_enabled() || first_svrem) {
-        rc = enqueue_epoch(st, algo, n_iter, alpha, anchors, s);
+    // a first SVREM anchor / SEM start also initialises s_hat: that call is enqueued directly
+    const bool first = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SEM) && !st->s_hat_ready;
+    if (!use_graphs() || profiling_enabled() || first) {
+        rc = enqueue_epoch(st, algo, n_iter, anchors, s);
     } else {
-        std::vector<int64_t> key = {n_iter, (int64_t)std::llround((double)alpha * 1e9), eta};
+        std::vector<int64_t> key = {n_iter, eta};
         for (int i = 0; i < n_iter; ++i)
             if (anchors[i]) key.push_back(i);
-        rc = run_graph(st, key, s, [&](cudaStream_t cs) { return enqueue_epoch(st, algo, n_iter, alpha, anchors, cs); });
+        rc = run_graph(st, key, s, [&](cudaStream_t cs) { return enqueue_epoch(st, algo, n_iter, anchors, cs); });
     }
     if (rc == PET_OK) st->k += n_iter;
     return rc;
@@ -929,21 +969,31 @@ pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_i
 extern "C" {
 
 pet_status pet_osem_epoch(pet_state *st, const int32_t *seq, int32_t n_iter, void *stream) {
-    return epoch_common(st, PET_ALGO_OSEM, seq, n_iter, 0.0f, 1, (cudaStream_t)stream);
+    return epoch_common(st, PET_ALGO_OSEM, seq, n_iter, 0.0f, 0.0f, 1, (cudaStream_t)stream);
 }
 
 pet_status pet_svrem_epoch(pet_state *st, float alpha, int32_t eta, const int32_t *seq, int32_t n_iter,
                            void *stream) {
-    return epoch_common(st, PET_ALGO_SVREM, seq, n_iter, alpha, eta, (cudaStream_t)stream);
+    return epoch_common(st, PET_ALGO_SVREM, seq, n_iter, alpha, 0.0f, eta, (cudaStream_t)stream);
 }
 
 pet_status pet_saga_epoch(pet_state *st, float alpha, const int32_t *seq, int32_t n_iter, void *stream) {
-    return epoch_common(st, PET_ALGO_SAGA, seq, n_iter, alpha, 1, (cudaStream_t)stream);
+    return epoch_common(st, PET_ALGO_SAGA, seq, n_iter, alpha, 0.0f, 1, (cudaStream_t)stream);
 }
 
 pet_status pet_svrg_epoch(pet_state *st, float alpha, int32_t eta, const int32_t *seq, int32_t n_iter,
                           void *stream) {
-    return epoch_common(st, PET_ALGO_SVRG, seq, n_iter, alpha, eta, (cudaStream_t)stream);
+    return epoch_common(st, PET_ALGO_SVRG, seq, n_iter, alpha, 0.0f, eta, (cudaStream_t)stream);
+}
+
+pet_status pet_sga_epoch(pet_state *st, float alpha0, float decay, const int32_t *seq, int32_t n_iter,
+                         void *stream) {
+    return epoch_common(st, PET_ALGO_SGA, seq, n_iter, alpha0, decay, 1, (cudaStream_t)stream);
+}
+
+pet_status pet_sem_epoch(pet_state *st, float alpha0, float decay, const int32_t *seq, int32_t n_iter,
+                         void *stream) {
+    return epoch_common(st, PET_ALGO_SEM, seq, n_iter, alpha0, decay, 1, (cudaStream_t)stream);
 }
 
 pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream) {
@@ -964,6 +1014,7 @@ pet_status pet_batch_destroy(pet_batch *b) {
     dfree(b->d_members);
     dfree(b->d_idx);
     dfree(b->d_seqs);
+    dfree(b->d_alphas);
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -1063,6 +1114,7 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.qtil = st->qtil;
     m.alpha = alpha;
     m.seq = seq;
+    m.alphas = nullptr;
     m.na = pl->na;
     m.n_ll = forward_blocks(pl->M, 1, choose_group(pl));
     m.part = st->d_part;
@@ -1082,8 +1134,12 @@ pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<s
     for (int i = 0; i < n_iter; ++i) {
         const bool in_is_img = ((i % 2) == 0) != odd;
         for (int j = 0; j < n; ++j) {
-            if (!anchors[j][i]) continue;
             pet_state *st = b->states[j];
+            if (st->algo == PET_ALGO_SEM && !st->s_hat_ready) {
+                PET_TRY(sem_init(st, in_is_img ? st->img : st->alt, s));
+                st->s_hat_ready = true;
+            }
+            if (!anchors[j][i]) continue;
             const pet_plan *pl = st->prob->plan;
             const long long plane = plane_of(pl);
             const float *in = in_is_img ? st->img : st->alt;
@@ -1130,17 +1186,32 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
     const size_t need = (size_t)n * n_iter;
     if ((int)need > b->seq_cap) {
         int *grown = nullptr;
+        float *grown_a = nullptr;
         PET_TRY(dalloc(&grown, need, "batch subset sequences"));
+        if (dalloc(&grown_a, need, "batch step sizes") != PET_OK) {
+            dfree(grown);
+            return PET_ERR_OOM;
+        }
         if (b->d_seqs) {
             PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
             dfree(b->d_seqs);
+            dfree(b->d_alphas);
         }
         b->d_seqs = grown;
+        b->d_alphas = grown_a;
         b->seq_cap = (int)need;
     }
+    std::vector<float> alphas(need);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n_iter; ++i) alphas[(size_t)j * n_iter + i] = h_alpha[j];
     PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_seqs, h_seqs, sizeof(int32_t) * need, cudaMemcpyHostToDevice, s),
                     "batch sequence copy"));
-    for (int j = 0; j < n; ++j) fill_member(b->members[j], b->states[j], h_alpha[j], b->d_seqs + (size_t)j * n_iter);
+    PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_alphas, alphas.data(), sizeof(float) * need, cudaMemcpyHostToDevice, s),
+                    "batch step size copy"));
+    for (int j = 0; j < n; ++j) {
+        fill_member(b->members[j], b->states[j], h_alpha[j], b->d_seqs + (size_t)j * n_iter);
+        b->members[j].alphas = b->d_alphas + (size_t)j * n_iter;
+    }
     PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_members, b->members.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice,
                                     s),
                     "batch member copy"));
@@ -1149,8 +1220,8 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
     std::vector<int64_t> key = {n_iter};
     for (int j = 0; j < n; ++j) {
         pet_state *st = b->states[j];
+        if ((st->algo == PET_ALGO_SVREM || st->algo == PET_ALGO_SEM) && !st->s_hat_ready) direct = true;
         if (st->algo != PET_ALGO_SVREM && st->algo != PET_ALGO_SVRG) continue;
-        if (st->algo == PET_ALGO_SVREM && !st->s_hat_ready) direct = true;
         for (int i = 0; i < n_iter; ++i)
             if ((st->k + i) % ((long long)h_eta[j] * st->prob->plan->ns) == 0) {
                 anchors[j][i] = 1;

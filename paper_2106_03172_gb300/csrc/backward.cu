@@ -101,6 +101,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
                                                int z, float acc) {
     const long long plane = (long long)a.nx * a.ny * a.nz;
     const float inv_ns = 1.0f / (float)a.ns;
+    const float alpha = a.alpha_dev ? __ldg(a.alpha_dev) : a.alpha;
     if (EPI == EPI_PLAIN) {
         a.out[i] = acc;
     } else if (EPI == EPI_ANCHOR) {
@@ -117,7 +118,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float ns = (float)a.ns;
         const float Bt = a.B[(long long)t * plane + i];
         const float tau = ns * fk * acc - ns * a.f_anc[i] * Bt + a.s_anc[i];
-        const float s = fmaf(a.alpha, tau, (1.0f - a.alpha) * a.s_hat[i]);
+        const float s = fmaf(alpha, tau, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
         const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float S = __ldg(a.sens + n);
@@ -135,7 +136,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         } else {
             const float q_old = load_q<TQ>(a.table, qi);
             const float qb = a.qbar[i];
-            const float step = fmaf(a.alpha * a.d[i], q - q_old + qb, fk);
+            const float step = fmaf(alpha * a.d[i], q - q_old + qb, fk);
             a.f_out[i] = fmaxf(step, 0.0f);
             a.qbar[i] = fmaf(q - q_old, inv_ns, qb);
             store_q<TQ>(a.table, qi, q);
@@ -146,7 +147,24 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float gradR = st.grad;
         const float Bt = a.B[(long long)t * plane + i];
         const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
-        a.f_out[i] = fmaxf(fmaf(a.alpha * a.d[i], dir, fk), 0.0f);
+        a.f_out[i] = fmaxf(fmaf(alpha * a.d[i], dir, fk), 0.0f);
+    } else if (EPI == EPI_SGA) {
+        const float fk = a.f[i];
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+        const float dir = acc - S - a.beta * inv_ns * st.grad;      // grad Phi_t
+        const float dt = S > 0.0f ? fk / S : 0.0f;                  // d_t(f) = f / A_t^T 1
+        a.f_out[i] = fmaxf(fmaf(alpha * dt, dir, fk), 0.0f);
+    } else if (EPI == EPI_SEM) {
+        const float fk = a.f[i];
+        const float s = fmaf(alpha, (float)a.ns * fk * acc, (1.0f - alpha) * a.s_hat[i]);
+        a.s_hat[i] = s;
+        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const float S = __ldg(a.sens + n);
+        const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
+        a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
+    } else if (EPI == EPI_SEM_INIT) {
+        a.s_hat[i] = a.f[i] * acc;
     }
 }
 
@@ -345,6 +363,7 @@ __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMe
     b.pot = m.pot;
     b.delta = m.delta;
     b.alpha = m.alpha;
+    b.alpha_dev = m.alphas ? m.alphas + iter : nullptr;
     b.s_hat = m.s_hat;
     b.f_anc = m.f_anc;
     b.s_anc = m.s_anc;
@@ -363,6 +382,8 @@ __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMe
             else
                 back_tile_body<EPI_SAGA, float, kRun>(b, t, blockIdx.x);
             break;
+        case PET_ALGO_SGA: back_tile_body<EPI_SGA, float, kRun>(b, t, blockIdx.x); break;
+        case PET_ALGO_SEM: back_tile_body<EPI_SEM, float, kRun>(b, t, blockIdx.x); break;
         default: back_tile_body<EPI_SVRG, float, kRun>(b, t, blockIdx.x); break;
     }
 }
@@ -421,6 +442,9 @@ pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subset
         case EPI_SAGA: return bf ? go<EPI_SAGA, __nv_bfloat16>(a, g, s, mv) : go<EPI_SAGA, float>(a, g, s, mv);
         case EPI_SAGA_INIT:
             return bf ? go<EPI_SAGA_INIT, __nv_bfloat16>(a, g, s, mv) : go<EPI_SAGA_INIT, float>(a, g, s, mv);
+        case EPI_SGA: return go<EPI_SGA, float>(a, g, s, mv);
+        case EPI_SEM: return go<EPI_SEM, float>(a, g, s, mv);
+        case EPI_SEM_INIT: return go<EPI_SEM_INIT, float>(a, g, s, mv);
         default: return set_error(PET_ERR_INVALID, "back: unknown epilogue");
     }
 }

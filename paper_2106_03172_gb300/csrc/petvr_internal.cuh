@@ -181,6 +181,9 @@ enum BackEpi {
     EPI_SVRG = 4,        // SVRG step
     EPI_ANCHOR = 5,      // B[t] = A_t^T r_t for every t (grid.y = subset)
     EPI_SAGA_INIT = 6,   // table[t] = grad Phi_t(f) for every t (grid.y = subset)
+    EPI_SGA = 7,         // preconditioned gradient step (SGA / BSREM)
+    EPI_SEM = 8,         // stochastic EM statistic update + M-step
+    EPI_SEM_INIT = 9,    // s_hat = f . A^T r over all views
 };
 
 struct BackArgs {
@@ -205,7 +208,8 @@ struct BackArgs {
     int pot;              // potential (PET_POT_*)
     float delta;          // its transition parameter
     float alpha;
-    float *s_hat;         // SVREM running statistic
+    const float *alpha_dev;  // if set: this update's step size (device), else alpha
+    float *s_hat;         // SVREM / SEM running statistic
     const float *f_anc;   // SVREM anchor image
     const float *s_anc;   // SVREM anchor statistic
     const float *B;       // SVREM/SVRG cached A_t^T r_t(f_anc), [ns][N*nz]
@@ -241,6 +245,7 @@ struct BatchMember {
     const float *qtil;
     float alpha;
     const int *seq;
+    const float *alphas;   // this member's step size per update of the current call
     int na;                // views (full-data passes)
     int n_ll;              // forward blocks of a full pass (objective partial count)
     double *part;          // objective partials of this member
@@ -303,6 +308,7 @@ struct pet_state {
     size_t bytes = 0;
     bool s_hat_ready = false;       // SVREM: s_hat initialised by the first anchor
     int *d_seq = nullptr;           // device copy of the current call's subset sequence
+    float *d_alpha = nullptr;       // and of its step size per update
     int seq_cap = 0;
     double *d_part = nullptr;       // objective reduction scratch of this state
     int n_part = 0;
@@ -329,6 +335,7 @@ struct pet_batch {
     };
     std::vector<Group> fwd_groups, back_groups;
     int *d_seqs = nullptr;          // [n][seq_cap] subset indices of the current call
+    float *d_alphas = nullptr;      // [n][seq_cap] step sizes of the current call
     int seq_cap = 0;
     cudaStream_t cap = nullptr;
     std::vector<pet_state::Graph> graphs;

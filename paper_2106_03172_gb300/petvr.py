@@ -20,7 +20,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpetvr.so")
 
-ALGO = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3}
+ALGO = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3, "sga": 4, "sem": 5}
 TABLE = {"fp32": 0, "bf16": 1}
 STATUS = {0: "PET_OK", 1: "PET_ERR_INVALID", 2: "PET_ERR_OOM", 3: "PET_ERR_CUDA",
           4: "PET_ERR_TIMEOUT", 5: "PET_ERR_NUMERIC", 6: "PET_ERR_STATE"}
@@ -80,6 +80,8 @@ _SIGS = {
     "pet_svrem_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
     "pet_saga_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
     "pet_svrg_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
+    "pet_sga_epoch": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_int32, c_void_p]),
+    "pet_sem_epoch": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_int32, c_void_p]),
     "pet_state_sync": (c_int32, [c_void_p, c_void_p]),
     "pet_state_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
@@ -270,6 +272,16 @@ def pet_svrg_epoch(state, alpha: float, eta: int, seq, stream=None):
     _call("pet_svrg_epoch", state, alpha, eta, arr, n, _stream(stream))
 
 
+def pet_sga_epoch(state, alpha0: float, decay: float, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_sga_epoch", state, alpha0, decay, arr, n, _stream(stream))
+
+
+def pet_sem_epoch(state, alpha0: float, decay: float, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_sem_epoch", state, alpha0, decay, arr, n, _stream(stream))
+
+
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):
     """Enqueue Phi, L, R of the state's current image into ``phi_out`` (3 float64)."""
     _call("pet_state_objective_async", state, _dev(phi_out, torch.float64), _stream(stream))
@@ -365,9 +377,13 @@ class State:
         self.problem, self.algo, self.img = problem, algo, img
         self.handle = pet_state_create(problem.handle, algo, table, img, stream)
 
-    def epoch(self, seq, alpha: float = 1.0, eta: int = 1, stream=None):
+    def epoch(self, seq, alpha: float = 1.0, eta: int = 1, stream=None, decay: float = 0.0):
         if self.algo == "osem":
             pet_osem_epoch(self.handle, seq, stream)
+        elif self.algo == "sga":
+            pet_sga_epoch(self.handle, alpha, decay, seq, stream)
+        elif self.algo == "sem":
+            pet_sem_epoch(self.handle, alpha, decay, seq, stream)
         elif self.algo == "svrem":
             pet_svrem_epoch(self.handle, alpha, eta, seq, stream)
         elif self.algo == "saga":

@@ -370,3 +370,23 @@ def test_edge_preserving_potential_objective(potential_case):
     f = np.random.default_rng(12).uniform(0.05, 0.6, (prob.N, 1)).astype(np.float32).astype(np.float64)
     assert pv.pet_objective(gp.handle, _cuda(f)) == pytest.approx(prob.objective(f), rel=1e-7)
     assert prob.pen.value(f)[0] > 0.0
+
+
+@pytest.mark.parametrize("method,alpha0,decay", [("sga", 1.0, 0.0), ("sga", 1.0, 0.001), ("sem", 1.0, 0.001)])
+def test_non_vr_baseline_updates(case, method, alpha0, decay):
+    """The paper's baselines on the same kernels (§5.1): SGA, the subset
+    BSREM (SGA with alpha_k = (0.001 k + 1)^-1) and SEM, against the oracle."""
+    pv, prob, data, work, plan = case
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, method, img)
+    sched = lambda k: alpha0 / (decay * k + 1.0)
+    alg = em.SGA(prob, f0, sched) if method == "sga" else em.SEM(prob, f0, sched)
+    seq = subset_sequence(4000, work.n_subsets, 2 * work.n_subsets)
+    for k, t in enumerate(seq):
+        state.epoch([int(t)], alpha=alpha0, decay=decay)
+        f = alg.step(int(t))
+        err = rel_l2(_host(img), f)
+        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+    assert _host(img).min() >= 0.0

@@ -312,3 +312,31 @@ def test_vr_methods_converge_towards_map(prob_and_data, map_solution):
             f = alg.step(int(t))
         gap = em.relative_gap(prob.objective(f), phi_star)
         assert -1e-12 <= gap < 1e-3 * gap0
+
+
+def test_sga_at_beta_zero_is_osem():
+    """§4, Eq. (osem_additive): with beta = 0 and alpha = 1, the preconditioned
+    gradient step f + (f / A_t^T 1) grad L_t(f) is the OSEM M-step."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=13, n_subsets=3, beta=0.0)
+    f = p.uniform_image()
+    alg = em.SGA(p, f)
+    for t in (0, 2, 1, 1):
+        want = em.osem_step(p, alg.f, t)
+        np.testing.assert_allclose(alg.step(t), want, rtol=1e-12, atol=1e-14)
+
+
+def test_sem_full_step_single_subset_is_map_em():
+    """SEM with alpha_k = 1 and one subset replaces s_hat by s(f): MAP-EM."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=14, n_subsets=1, beta=0.05)
+    f = p.uniform_image()
+    alg = em.SEM(p, f, schedule=lambda k: 1.0)
+    for _ in range(3):
+        want = em.map_em_step(p, alg.f)
+        np.testing.assert_allclose(alg.step(0), want, rtol=1e-12)
+
+
+def test_bsrem_schedule_and_monotone_decay():
+    assert em.bsrem_schedule(0) == 1.0
+    assert em.bsrem_schedule(1000) == pytest.approx(0.5)
