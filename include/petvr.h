@@ -55,7 +55,7 @@ typedef enum {
 
 /* Algorithms (pet_state_create). */
 enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG = 3,
-       PET_ALGO_SGA = 4, PET_ALGO_SEM = 5 };
+       PET_ALGO_SGA = 4, PET_ALGO_SEM = 5, PET_ALGO_SAGAEM = 6 };
 /* SAGA gradient-table storage (pet_state_create). */
 enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
 /* Potentials of the pairwise penalty (Table 1, t = f_n - f_j, delta > 0):
@@ -301,6 +301,13 @@ pet_status pet_sga_epoch(pet_state *state, float alpha0, float decay, const int3
 pet_status pet_sem_epoch(pet_state *state, float alpha0, float decay, const int32_t *h_subset_seq,
                          int32_t n_iter, void *stream);
 
+/* SAGA on the EM statistic (§2.3, the remark after Eq. (tempsvrem)):
+ * s <- (1-alpha) s + alpha (tau_t(f) - T_t + mean_t T_t), the M-step of §3,
+ * then T_t <- tau_t(f) for the subset just used; the table starts at
+ * tau_t(f^(0)) (one full pass at state creation).  PET_ALGO_SAGAEM. */
+pet_status pet_sagaem_epoch(pet_state *state, float alpha, const int32_t *h_subset_seq, int32_t n_iter,
+                            void *stream);
+
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);
 
@@ -311,8 +318,9 @@ uint64_t pet_kernel_launches(void);
 /* Optional per-kernel timing for profiling: while enabled, every forward and
  * back-projection launch is bracketed by two CUDA events on its stream.
  * pet_profile_read synchronises those events and returns, for kernel kind
- * `kind` (0 forward, 1 back projection with update epilogue, 2 multi-subset
- * back projection of an anchor pass or table fill), the number of launches
+ * `kind` (0 forward projection of an update's subset, 1 back projection with
+ * update epilogue, 2 multi-subset back projection of an anchor pass or table
+ * fill, 3 forward projection of all rays or an API call), the number of launches
  * and their summed duration in ms since the last reset.  Not thread-safe
  * with respect to concurrent launches from several host threads. */
 pet_status pet_profile_enable(int32_t on);

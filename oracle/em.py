@@ -277,6 +277,30 @@ class SVREM:
         return self.f
 
 
+class SAGAEM:
+    """SAGA applied to the EM statistic (§2.3, the remark after
+    Eq. (tempsvrem)), with the surrogate M-step of §3:
+        s_hat <- (1-alpha) s_hat + alpha (tau_t(f^k) - T_t + (1/N_s) sum_t' T_t')
+        f^{k+1} = argmax zeta(f)^T s_hat - U(f) - beta R_hat(f; f^k);  T_t <- tau_t(f^k)
+    The table starts at T_t = tau_t(f^(0)) and s_hat at their mean s(f^(0)).
+    Reading: the remark refreshes the entry of an independently drawn index;
+    here the refreshed entry is the subset just used (as SAGA of §4 does),
+    so an update costs one subset pass."""
+
+    def __init__(self, prob: Problem, f0, alpha: float):
+        self.p, self.f, self.alpha = prob, f0.copy(), alpha
+        self.T = [prob.tau_t(self.f, t) for t in range(prob.Ns)]
+        self.s_hat = sum(self.T) / prob.Ns
+
+    def step(self, t):
+        tau = self.p.tau_t(self.f, t)
+        mean_old = sum(self.T) / self.p.Ns
+        self.s_hat = (1.0 - self.alpha) * self.s_hat + self.alpha * (tau - self.T[t] + mean_old)
+        self.f = m_step_root(self.s_hat, self.f, self.p.sens, self.p.beta, self.p.pen)
+        self.T[t] = tau
+        return self.f
+
+
 def preconditioner(prob: Problem, f0):
     """Constant d = N_s f^(0) / A^T 1 (0 where A^T 1 = 0) (§4, reading C13)."""
     pos = prob.sens > 0

@@ -214,6 +214,19 @@ pet_status state_init(pet_state *st, cudaStream_t s) {
     st->k = 0;
     st->s_hat_ready = false;
     if (st->algo == PET_ALGO_SVRG) return launch_precond(st->img, pl->d_sens, pl->ns, Nz, pl->nz, st->d, s);
+    if (st->algo == PET_ALGO_SAGAEM) {
+        // table T_t = tau_t(f^(0)) for all t, its mean, and s_hat = mean = s(f^(0))
+        PET_TRY(ratio_all(p, st->img, p->d_ratio, s));
+        BackArgs b = back_args(pl, p->d_ratio, -1, false);
+        b.t0 = 0;
+        b.r_view0 = 0;
+        b.f = st->img;
+        b.table = st->table;
+        PET_TRY(launch_back(b, EPI_SAGAEM_INIT, PET_TABLE_FP32, pl->ns, s, pl->max_sub_views));
+        PET_TRY(launch_table_mean(st->table, PET_TABLE_FP32, pl->ns, Nz, st->qbar, s));
+        return cuda_ok(cudaMemcpyAsync(st->s_hat, st->qbar, (size_t)Nz * 4, cudaMemcpyDeviceToDevice, s),
+                       "statistic copy");
+    }
     if (st->algo != PET_ALGO_SAGA) return PET_OK;
     // table q_t = grad Phi_t(f^(0)) for all t, then qbar and d
     PET_TRY(ratio_all(p, st->img, p->d_ratio, s));
@@ -700,7 +713,9 @@ pet_status pet_state_destroy(pet_state *st) {
 pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dtype, float *d_img,
                             size_t *bytes_needed, pet_state **out, void *stream) {
     if (!p) return set_error(PET_ERR_INVALID, "null problem");
-    if (algo < PET_ALGO_OSEM || algo > PET_ALGO_SEM) return set_error(PET_ERR_INVALID, "unknown algorithm");
+    if (algo < PET_ALGO_OSEM || algo > PET_ALGO_SAGAEM) return set_error(PET_ERR_INVALID, "unknown algorithm");
+    if (algo == PET_ALGO_SAGAEM && table_dtype != PET_TABLE_FP32)
+        return set_error(PET_ERR_INVALID, "the SAGA-EM statistic table is FP32");
     if (table_dtype != PET_TABLE_FP32 && table_dtype != PET_TABLE_BF16)
         return set_error(PET_ERR_INVALID, "unknown table dtype");
     const pet_plan *pl = p->plan;
@@ -711,6 +726,7 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
     if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
     if (algo == PET_ALGO_SEM) bytes += Nz * 4 + (size_t)pl->M * pl->nz * 4;
+    if (algo == PET_ALGO_SAGAEM) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4;
     if (bytes_needed) *bytes_needed = bytes;
     if (!out) return PET_OK;
     *out = nullptr;
@@ -742,6 +758,15 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     } else if (algo == PET_ALGO_SEM) {
         if ((e = dalloc(&st->s_hat, Nz, "s_hat")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->ratio_full, Mz, "full ratio")) != PET_OK) return fail(e);
+    } else if (algo == PET_ALGO_SAGAEM) {
+        if ((e = dalloc(&st->s_hat, Nz, "s_hat")) != PET_OK) return fail(e);
+        if ((e = dalloc(&st->qbar, Nz, "table mean")) != PET_OK) return fail(e);
+        const cudaError_t ce = cudaMalloc(&st->table, (size_t)pl->ns * Nz * 4);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            st->table = nullptr;
+            return fail(set_error(PET_ERR_OOM, "cudaMalloc SAGA-EM table"));
+        }
     } else if (algo == PET_ALGO_SVRG) {
         if ((e = dalloc(&st->d, Nz, "d")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->qtil, Nz, "q_tilde")) != PET_OK) return fail(e);
@@ -823,6 +848,11 @@ pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float
     } else if (algo == PET_ALGO_SEM) {
         epi = EPI_SEM;
         b.s_hat = st->s_hat;
+    } else if (algo == PET_ALGO_SAGAEM) {
+        epi = EPI_SAGAEM;
+        b.s_hat = st->s_hat;
+        b.table = st->table;
+        b.qbar = st->qbar;
     }
     return launch_back(b, epi, st->table_dtype, 1, s, pl->max_sub_views);
 }
@@ -994,6 +1024,10 @@ pet_status pet_sga_epoch(pet_state *st, float alpha0, float decay, const int32_t
 pet_status pet_sem_epoch(pet_state *st, float alpha0, float decay, const int32_t *seq, int32_t n_iter,
                          void *stream) {
     return epoch_common(st, PET_ALGO_SEM, seq, n_iter, alpha0, decay, 1, (cudaStream_t)stream);
+}
+
+pet_status pet_sagaem_epoch(pet_state *st, float alpha, const int32_t *seq, int32_t n_iter, void *stream) {
+    return epoch_common(st, PET_ALGO_SAGAEM, seq, n_iter, alpha, 0.0f, 1, (cudaStream_t)stream);
 }
 
 pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream) {

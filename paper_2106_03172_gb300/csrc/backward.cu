@@ -165,6 +165,25 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
     } else if (EPI == EPI_SEM_INIT) {
         a.s_hat[i] = a.f[i] * acc;
+    } else if (EPI == EPI_SAGAEM || EPI == EPI_SAGAEM_INIT) {
+        const float fk = a.f[i];
+        const float tau = (float)a.ns * fk * acc;                   // tau_t(f^k)
+        float *T = static_cast<float *>(a.table);
+        const long long ti = (long long)t * plane + i;
+        if (EPI == EPI_SAGAEM_INIT) {
+            T[ti] = tau;
+        } else {
+            const float T_old = T[ti];
+            const float Tb = a.qbar[i];
+            const float s = fmaf(alpha, tau - T_old + Tb, (1.0f - alpha) * a.s_hat[i]);
+            a.s_hat[i] = s;
+            const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+            const float S = __ldg(a.sens + n);
+            const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
+            a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
+            a.qbar[i] = fmaf(tau - T_old, inv_ns, Tb);
+            T[ti] = tau;
+        }
     }
 }
 
@@ -384,6 +403,7 @@ __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMe
             break;
         case PET_ALGO_SGA: back_tile_body<EPI_SGA, float, kRun>(b, t, blockIdx.x); break;
         case PET_ALGO_SEM: back_tile_body<EPI_SEM, float, kRun>(b, t, blockIdx.x); break;
+        case PET_ALGO_SAGAEM: back_tile_body<EPI_SAGAEM, float, kRun>(b, t, blockIdx.x); break;
         default: back_tile_body<EPI_SVRG, float, kRun>(b, t, blockIdx.x); break;
     }
 }
@@ -445,6 +465,8 @@ pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subset
         case EPI_SGA: return go<EPI_SGA, float>(a, g, s, mv);
         case EPI_SEM: return go<EPI_SEM, float>(a, g, s, mv);
         case EPI_SEM_INIT: return go<EPI_SEM_INIT, float>(a, g, s, mv);
+        case EPI_SAGAEM: return go<EPI_SAGAEM, float>(a, g, s, mv);
+        case EPI_SAGAEM_INIT: return go<EPI_SAGAEM_INIT, float>(a, g, s, mv);
         default: return set_error(PET_ERR_INVALID, "back: unknown epilogue");
     }
 }

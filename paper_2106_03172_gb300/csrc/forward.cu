@@ -425,7 +425,7 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
     const int blocks = forward_blocks(n_rays, a.nz, group);
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
-    ProfileScope prof(0, s);
+    ProfileScope prof(a.t_dev ? 0 : 3, s);     // 0: subset update forward, 3: full-data / API forward
     if (a.nz == 1) {
         switch (group) {
             case 8: return dispatch_tile<8>(a, mode, ll, blocks, s);

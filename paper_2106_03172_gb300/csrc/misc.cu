@@ -296,6 +296,15 @@ pet_status launch_saga_finish(const void *table, int table_dtype, int ns, long l
     return launch_precond(f0, sens, ns, plane, nz, d, s);
 }
 
+pet_status launch_table_mean(const void *table, int table_dtype, int ns, long long plane, float *mean,
+                             cudaStream_t s) {
+    if (table_dtype == PET_TABLE_BF16)
+        saga_finish_kernel<__nv_bfloat16><<<blocks_for(plane), kBlock, 0, s>>>(table, ns, plane, mean);
+    else
+        saga_finish_kernel<float><<<blocks_for(plane), kBlock, 0, s>>>(table, ns, plane, mean);
+    return check_launch("table_mean_kernel");
+}
+
 pet_status launch_precond(const float *f0, const float *sens, int ns, long long plane, int nz, float *d,
                           cudaStream_t s) {
     precond_kernel<<<blocks_for(plane), kBlock, 0, s>>>(f0, sens, ns, plane, nz, d);

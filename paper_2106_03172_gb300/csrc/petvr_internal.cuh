@@ -184,6 +184,8 @@ enum BackEpi {
     EPI_SGA = 7,         // preconditioned gradient step (SGA / BSREM)
     EPI_SEM = 8,         // stochastic EM statistic update + M-step
     EPI_SEM_INIT = 9,    // s_hat = f . A^T r over all views
+    EPI_SAGAEM = 10,     // SAGA on the EM statistic + M-step
+    EPI_SAGAEM_INIT = 11,  // table[t] = tau_t(f) for every t (grid.y = subset)
 };
 
 struct BackArgs {
@@ -390,6 +392,8 @@ pet_status launch_svrg_anchor_finish(const float *B, int ns, long long plane, in
 pet_status launch_saga_finish(const void *table, int table_dtype, int ns, long long plane, int nz,
                               const float *f0, const float *sens, float *qbar, float *d,
                               cudaStream_t s);
+pet_status launch_table_mean(const void *table, int table_dtype, int ns, long long plane, float *mean,
+                             cudaStream_t s);
 pet_status launch_precond(const float *f0, const float *sens, int ns, long long plane, int nz,
                           float *d, cudaStream_t s);
 

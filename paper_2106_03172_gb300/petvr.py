@@ -20,7 +20,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpetvr.so")
 
-ALGO = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3, "sga": 4, "sem": 5}
+ALGO = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3, "sga": 4, "sem": 5, "sagaem": 6}
 TABLE = {"fp32": 0, "bf16": 1}
 STATUS = {0: "PET_OK", 1: "PET_ERR_INVALID", 2: "PET_ERR_OOM", 3: "PET_ERR_CUDA",
           4: "PET_ERR_TIMEOUT", 5: "PET_ERR_NUMERIC", 6: "PET_ERR_STATE"}
@@ -82,6 +82,7 @@ _SIGS = {
     "pet_svrg_epoch": (c_int32, [c_void_p, c_float, c_int32, c_void_p, c_int32, c_void_p]),
     "pet_sga_epoch": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_int32, c_void_p]),
     "pet_sem_epoch": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_int32, c_void_p]),
+    "pet_sagaem_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
     "pet_state_sync": (c_int32, [c_void_p, c_void_p]),
     "pet_state_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
@@ -282,6 +283,11 @@ def pet_sem_epoch(state, alpha0: float, decay: float, seq, stream=None):
     _call("pet_sem_epoch", state, alpha0, decay, arr, n, _stream(stream))
 
 
+def pet_sagaem_epoch(state, alpha: float, seq, stream=None):
+    arr, n = _seq(seq)
+    _call("pet_sagaem_epoch", state, alpha, arr, n, _stream(stream))
+
+
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):
     """Enqueue Phi, L, R of the state's current image into ``phi_out`` (3 float64)."""
     _call("pet_state_objective_async", state, _dev(phi_out, torch.float64), _stream(stream))
@@ -384,6 +390,8 @@ class State:
             pet_sga_epoch(self.handle, alpha, decay, seq, stream)
         elif self.algo == "sem":
             pet_sem_epoch(self.handle, alpha, decay, seq, stream)
+        elif self.algo == "sagaem":
+            pet_sagaem_epoch(self.handle, alpha, seq, stream)
         elif self.algo == "svrem":
             pet_svrem_epoch(self.handle, alpha, eta, seq, stream)
         elif self.algo == "saga":

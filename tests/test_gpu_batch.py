@@ -31,7 +31,8 @@ def _setup(pv, name, run=None):
 
 MEMBERS = [("c64", "osem", "fp32", 1.0, 1), ("c64", "svrem", "fp32", 0.7, 1), ("c64", "saga", "bf16", 1.0, 1),
            ("c64", "svrg", "fp32", 2.0, 2), ("ragged", "svrem", "fp32", 0.7, 1), ("ragged", "saga", "fp32", 1.0, 1),
-           ("c256", "svrg", "fp32", 2.0, 1), ("c64", "sga", "fp32", 0.8, 1), ("ragged", "sem", "fp32", 0.5, 1)]
+           ("c256", "svrg", "fp32", 2.0, 1), ("c64", "sga", "fp32", 0.8, 1), ("ragged", "sem", "fp32", 0.5, 1),
+           ("c64", "sagaem", "fp32", 0.7, 1)]
 
 
 def test_batch_equals_individual_epochs():

@@ -390,3 +390,18 @@ def test_non_vr_baseline_updates(case, method, alpha0, decay):
         err = rel_l2(_host(img), f)
         assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
     assert _host(img).min() >= 0.0
+
+
+def test_sagaem_updates(case):
+    """SAGA on the EM statistic (§2.3 remark) against the oracle."""
+    pv, prob, data, work, plan = case
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, "sagaem", img)
+    alg = em.SAGAEM(prob, f0, 0.7)
+    for k, t in enumerate(subset_sequence(4100, work.n_subsets, 2 * work.n_subsets)):
+        state.epoch([int(t)], alpha=0.7)
+        f = alg.step(int(t))
+        err = rel_l2(_host(img), f)
+        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"

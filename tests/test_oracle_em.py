@@ -340,3 +340,21 @@ def test_sem_full_step_single_subset_is_map_em():
 def test_bsrem_schedule_and_monotone_decay():
     assert em.bsrem_schedule(0) == 1.0
     assert em.bsrem_schedule(1000) == pytest.approx(0.5)
+
+
+def test_sagaem_single_subset_alpha_one_is_map_em():
+    """SAGA-EM with one subset and alpha = 1 replaces s_hat by s(f^k): MAP-EM."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=15, n_subsets=1, beta=0.05)
+    f = p.uniform_image()
+    alg = em.SAGAEM(p, f, alpha=1.0)
+    for _ in range(3):
+        want = em.map_em_step(p, alg.f)
+        np.testing.assert_allclose(alg.step(0), want, rtol=1e-12)
+
+
+def test_sagaem_statistic_starts_at_full_statistic(prob_and_data):
+    prob, _ = prob_and_data
+    f = _rand_image(prob, 16)
+    alg = em.SAGAEM(prob, f, alpha=0.5)
+    np.testing.assert_allclose(alg.s_hat, prob.statistic(f), rtol=1e-12)
