@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--workload", default="c256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", type=int, default=20, help="reconstructions per method for the gap metric")
+    ap.add_argument("--tuning", default="", help="pin launch shapes 'chunks,run' instead of autotuning")
     ap.add_argument("--batch", dest="batch", action="store_true",
                     help="run the four methods as one batch (one launch per phase) instead of four streams")
     return ap.parse_args()
@@ -367,7 +368,14 @@ def run_ours(args):
     g_host = torch.from_numpy(data["g"].ravel()).pin_memory()
     g_dev = g_host.cuda()
     plan = petvr.Plan(geom, ns)
-    tuning = petvr.pet_plan_autotune(plan.handle)       # launch shapes timed on this geometry
+    if args.tuning:                                     # pinned launch shapes (e.g. for profiler runs)
+        c, r = (int(x) for x in args.tuning.split(","))
+        petvr.pet_plan_set_tuning(plan.handle, c, r)
+        tuning = petvr.pet_plan_get_tuning(plan.handle)
+        tune_src = "pinned by --tuning"
+    else:
+        tuning = petvr.pet_plan_autotune(plan.handle)   # launch shapes timed on this geometry
+        tune_src = "pet_plan_autotune"
     prob = petvr.Problem(plan, g_dev, None, data["w"], work.beta)
     f0 = torch.empty(geom.n_pixels * geom.nz, device="cuda")
     petvr.pet_warm_start(prob.handle, f0)
@@ -531,7 +539,7 @@ def run_ours(args):
         "config": dict(workload_config(work), parallelism=f"replicas x{world}",
                        concurrency="one batch (pet_batch_epoch)" if args.batch else "four streams",
                        launch_shapes={"forward_band_chunks": tuning[0], "back_run_pixels": tuning[1],
-                                      "source": "pet_plan_autotune"}),
+                                      "source": tune_src}),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "pairs_per_step": pairs / args.steps,
         "gpu_launches": int(launches),

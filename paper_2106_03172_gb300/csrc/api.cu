@@ -1192,9 +1192,13 @@ pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<s
         for (const auto &g : b->fwd_groups)
             PET_TRY(launch_batch_forward(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, i,
                                          in_is_img ? 1 : 0, s));
-        for (const auto &g : b->back_groups)
+        for (const auto &g : b->back_groups) {
+            bool general = false;
+            for (int q = 0; q < g.count; ++q)
+                general |= b->states[b->h_idx[g.offset + q]]->prob->pen.potential != PET_POT_QUADRATIC;
             PET_TRY(launch_batch_back(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, g.max_views, i,
-                                      in_is_img ? 1 : 0, s));
+                                      in_is_img ? 1 : 0, general, s));
+        }
     }
     return PET_OK;
 }

@@ -43,35 +43,29 @@ struct Stencil {
 };
 
 // 4-neighbourhood of pixel (ix, iy) in slice z: surrogate weights and
-// penalty gradient at f^k (out-of-image neighbours are dropped).
+// penalty gradient at f^k (out-of-image neighbours are dropped).  GENPOT
+// selects the edge-preserving potentials (runtime pot); otherwise quadratic.
+template <bool GENPOT>
 __device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int nx, int ny, int nz, int z,
                                             float fk, int pot, float delta) {
+    const bool hl = ix > 0, hr = ix + 1 < nx, hd = iy > 0, hu = iy + 1 < ny;
+    const float fl = hl ? __ldg(f + ((long long)iy * nx + ix - 1) * nz + z) : 0.0f;
+    const float fr = hr ? __ldg(f + ((long long)iy * nx + ix + 1) * nz + z) : 0.0f;
+    const float fd = hd ? __ldg(f + ((long long)(iy - 1) * nx + ix) * nz + z) : 0.0f;
+    const float fu = hu ? __ldg(f + ((long long)(iy + 1) * nx + ix) * nz + z) : 0.0f;
     Stencil s{0.0f, 0.0f, 0.0f};
-    float nb[4];
-    int cnt = 0;
-    if (ix > 0) nb[cnt++] = __ldg(f + ((long long)iy * nx + ix - 1) * nz + z);
-    if (ix + 1 < nx) nb[cnt++] = __ldg(f + ((long long)iy * nx + ix + 1) * nz + z);
-    if (iy > 0) nb[cnt++] = __ldg(f + ((long long)(iy - 1) * nx + ix) * nz + z);
-    if (iy + 1 < ny) nb[cnt++] = __ldg(f + ((long long)(iy + 1) * nx + ix) * nz + z);
-    if (pot == PET_POT_QUADRATIC) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q < cnt) {
-                s.cnt += 1.0f;
-                s.sum += nb[q];
-            }
+    if (!GENPOT) {
+        // missing neighbours add exact zeros
+        s.cnt = (float)((int)hl + (int)hr + (int)hd + (int)hu);
+        s.sum = ((fl + fr) + fd) + fu;
         s.grad = fk * s.cnt - s.sum;
         return s;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (q < cnt) {
-            float dr, g;
-            potential_dg(pot, delta, fk - nb[q], dr, g);
-            s.cnt += g;
-            s.sum += g * nb[q];
-            s.grad += dr;
-        }
+    float dr, g;
+    if (hl) { potential_dg(pot, delta, fk - fl, dr, g); s.cnt += g; s.sum += g * fl; s.grad += dr; }
+    if (hr) { potential_dg(pot, delta, fk - fr, dr, g); s.cnt += g; s.sum += g * fr; s.grad += dr; }
+    if (hd) { potential_dg(pot, delta, fk - fd, dr, g); s.cnt += g; s.sum += g * fd; s.grad += dr; }
+    if (hu) { potential_dg(pot, delta, fk - fu, dr, g); s.cnt += g; s.sum += g * fu; s.grad += dr; }
     return s;
 }
 
@@ -96,7 +90,7 @@ template <> __device__ __forceinline__ void store_q<__nv_bfloat16>(void *p, long
 }
 
 // Per-pixel update after the gather: b = acc is A_t^T r_t at (pixel n, slice z).
-template <int EPI, typename TQ>
+template <int EPI, typename TQ, bool GENPOT>
 __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long long i, int n, int ix, int iy,
                                                int z, float acc) {
     const long long plane = (long long)a.nx * a.ny * a.nz;
@@ -108,7 +102,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         a.out[(long long)t * plane + i] = acc;
     } else if (EPI == EPI_OSEM) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float bp = a.beta * inv_ns;
         const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
         const float c = bp * fmaf(fk, st.cnt, st.sum) - S;
@@ -120,13 +114,13 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float tau = ns * fk * acc - ns * a.f_anc[i] * Bt + a.s_anc[i];
         const float s = fmaf(alpha, tau, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float S = __ldg(a.sens + n);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
     } else if (EPI == EPI_SAGA || EPI == EPI_SAGA_INIT) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float gradR = st.grad;
         const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
         const float q = round_q<TQ>(acc - S - a.beta * inv_ns * gradR);
@@ -143,14 +137,14 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         }
     } else if (EPI == EPI_SVRG) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float gradR = st.grad;
         const float Bt = a.B[(long long)t * plane + i];
         const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
         a.f_out[i] = fmaxf(fmaf(alpha * a.d[i], dir, fk), 0.0f);
     } else if (EPI == EPI_SGA) {
         const float fk = a.f[i];
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
         const float dir = acc - S - a.beta * inv_ns * st.grad;      // grad Phi_t
         const float dt = S > 0.0f ? fk / S : 0.0f;                  // d_t(f) = f / A_t^T 1
@@ -159,7 +153,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float fk = a.f[i];
         const float s = fmaf(alpha, (float)a.ns * fk * acc, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
         const float S = __ldg(a.sens + n);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
@@ -177,7 +171,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
             const float Tb = a.qbar[i];
             const float s = fmaf(alpha, tau - T_old + Tb, (1.0f - alpha) * a.s_hat[i]);
             a.s_hat[i] = s;
-            const Stencil st = stencil4(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+            const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
             const float S = __ldg(a.sens + n);
             const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
             a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
@@ -210,7 +204,7 @@ __device__ __forceinline__ void stage_views(const BackArgs &a, int vb, int nv, V
 
 // General path (slice stacks): kLanes lanes per (pixel, slice) share the
 // subset's views and combine with an xor-shuffle in a fixed order.
-template <int EPI, typename TQ>
+template <int EPI, typename TQ, bool GENPOT>
 __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
     extern __shared__ unsigned char smem_raw[];
     ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
@@ -260,7 +254,7 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
 #pragma unroll
     for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (!live || lane != 0) return;
-    apply_epilogue<EPI, TQ>(a, t, i, n, ix, iy, z, acc);
+    apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, z, acc);
 }
 
 // Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
@@ -272,7 +266,7 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
 // and applies the update.  Each ray-band split is evaluated once per run
 // instead of once per pixel it touches.  Views are processed in chunks of
 // kChunk to bound shared memory.
-template <int EPI, typename TQ, int kRun>
+template <int EPI, typename TQ, int kRun, bool GENPOT>
 __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, const int bx) {
     extern __shared__ unsigned char smem_raw[];
     const int vb = __ldg(a.sub_off + t);
@@ -343,19 +337,19 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
     const int iy = y0 + (threadIdx.x / kTile);
     if (ix >= a.nx || iy >= a.ny) return;
     const int n = iy * a.nx + ix;
-    apply_epilogue<EPI, TQ>(a, t, n, n, ix, iy, 0, acc);
+    apply_epilogue<EPI, TQ, GENPOT>(a, t, n, n, ix, iy, 0, acc);
 }
 
-template <int EPI, typename TQ, int kRun>
+template <int EPI, typename TQ, int kRun, bool GENPOT>
 __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {
     const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
-    back_tile_body<EPI, TQ, kRun>(a, t, blockIdx.x);
+    back_tile_body<EPI, TQ, kRun, GENPOT>(a, t, blockIdx.x);
 }
 
 // Batched back projection + update: blockIdx.y picks the member, whose
 // algorithm and table type select the epilogue; same body as the single
 // launch, so each member's update is bit-identical to an unbatched one.
-template <int kRun>
+template <int kRun, bool GENPOT>
 __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMember *ms, const int *idx, int iter,
                                                                    int in_is_img) {
     const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
@@ -393,23 +387,28 @@ __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMe
     b.qtil = m.qtil;
     const int t = __ldg(m.seq + iter);
     switch (m.algo) {
-        case PET_ALGO_OSEM: back_tile_body<EPI_OSEM, float, kRun>(b, t, blockIdx.x); break;
-        case PET_ALGO_SVREM: back_tile_body<EPI_SVREM, float, kRun>(b, t, blockIdx.x); break;
+        case PET_ALGO_OSEM: back_tile_body<EPI_OSEM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
+        case PET_ALGO_SVREM: back_tile_body<EPI_SVREM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
         case PET_ALGO_SAGA:
             if (m.table_dtype == PET_TABLE_BF16)
-                back_tile_body<EPI_SAGA, __nv_bfloat16, kRun>(b, t, blockIdx.x);
+                back_tile_body<EPI_SAGA, __nv_bfloat16, kRun, GENPOT>(b, t, blockIdx.x);
             else
-                back_tile_body<EPI_SAGA, float, kRun>(b, t, blockIdx.x);
+                back_tile_body<EPI_SAGA, float, kRun, GENPOT>(b, t, blockIdx.x);
             break;
-        case PET_ALGO_SGA: back_tile_body<EPI_SGA, float, kRun>(b, t, blockIdx.x); break;
-        case PET_ALGO_SEM: back_tile_body<EPI_SEM, float, kRun>(b, t, blockIdx.x); break;
-        case PET_ALGO_SAGAEM: back_tile_body<EPI_SAGAEM, float, kRun>(b, t, blockIdx.x); break;
-        default: back_tile_body<EPI_SVRG, float, kRun>(b, t, blockIdx.x); break;
+        case PET_ALGO_SGA: back_tile_body<EPI_SGA, float, kRun, GENPOT>(b, t, blockIdx.x); break;
+        case PET_ALGO_SEM: back_tile_body<EPI_SEM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
+        case PET_ALGO_SAGAEM: back_tile_body<EPI_SAGAEM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
+        default: back_tile_body<EPI_SVRG, float, kRun, GENPOT>(b, t, blockIdx.x); break;
     }
 }
 
-template <int EPI, typename TQ>
-pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
+constexpr bool uses_stencil(int epi) {
+    return epi == EPI_OSEM || epi == EPI_SVREM || epi == EPI_SAGA || epi == EPI_SVRG || epi == EPI_SGA ||
+           epi == EPI_SEM || epi == EPI_SAGAEM;
+}
+
+template <int EPI, typename TQ, bool GENPOT>
+pet_status go_impl(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
     if (a.nz == 1) {
         const int tiles = ((a.nx + kTile - 1) / kTile) * ((a.ny + kTile - 1) / kTile);
         const dim3 grid((unsigned)tiles, (unsigned)ny_grid);
@@ -419,31 +418,46 @@ pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
         const int per_view = kTile * (kTile / run);
         const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
         if (run == 4)
-            back_tile_kernel<EPI, TQ, 4><<<grid, threads, smem, s>>>(a);
+            back_tile_kernel<EPI, TQ, 4, GENPOT><<<grid, threads, smem, s>>>(a);
         else
-            back_tile_kernel<EPI, TQ, 8><<<grid, threads, smem, s>>>(a);
+            back_tile_kernel<EPI, TQ, 8, GENPOT><<<grid, threads, smem, s>>>(a);
         return check_launch("back_tile_kernel");
     }
     const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
     const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
     const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
-    back_pixel_kernel<EPI, TQ><<<grid, kBlock, smem, s>>>(a);
+    back_pixel_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
     return check_launch("back_pixel_kernel");
+}
+
+template <int EPI, typename TQ>
+pet_status go(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
+    if constexpr (uses_stencil(EPI)) {
+        if (a.pot != PET_POT_QUADRATIC) return go_impl<EPI, TQ, true>(a, ny_grid, s, max_views);
+    }
+    return go_impl<EPI, TQ, false>(a, ny_grid, s, max_views);
 }
 
 }  // namespace
 
 pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
-                             int max_views, int iter, int in_is_img, cudaStream_t s) {
+                             int max_views, int iter, int in_is_img, bool general_potential, cudaStream_t s) {
     if (n_members == 0 || tiles == 0) return PET_OK;
     const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
     const int per_view = kTile * (kTile / run);
     const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
     const dim3 grid((unsigned)tiles, (unsigned)n_members);
-    if (run == 4)
-        batch_back_kernel<4><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
-    else
-        batch_back_kernel<8><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+    if (general_potential) {
+        if (run == 4)
+            batch_back_kernel<4, true><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+        else
+            batch_back_kernel<8, true><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+    } else {
+        if (run == 4)
+            batch_back_kernel<4, false><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+        else
+            batch_back_kernel<8, false><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
+    }
     return check_launch("batch_back_kernel");
 }
 
