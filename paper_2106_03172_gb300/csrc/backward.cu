@@ -403,8 +403,8 @@ __global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMe
 }
 
 constexpr bool uses_stencil(int epi) {
-    return epi == EPI_OSEM || epi == EPI_SVREM || epi == EPI_SAGA || epi == EPI_SVRG || epi == EPI_SGA ||
-           epi == EPI_SEM || epi == EPI_SAGAEM;
+    return epi == EPI_OSEM || epi == EPI_SVREM || epi == EPI_SAGA || epi == EPI_SAGA_INIT || epi == EPI_SVRG ||
+           epi == EPI_SGA || epi == EPI_SEM || epi == EPI_SAGAEM;
 }
 
 template <int EPI, typename TQ, bool GENPOT>
