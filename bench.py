@@ -275,9 +275,10 @@ def dram_traffic_record(kind: int):
         if ":" in line and not line.startswith("#"):
             key, val = line.split(":", 1)
             rec[key.strip()] = val.strip()
-    if rec.get("source_sha256") != kernel_source_digest() or rec.get("kind") != str(kind):
+    key = f"kind{kind}_dram_bytes_per_launch"
+    if rec.get("source_sha256") != kernel_source_digest() or key not in rec:
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return float(rec[key])
 
 
 # --------------------------------------------------------------------------- objective gap
