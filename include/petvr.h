@@ -134,6 +134,14 @@ pet_status pet_plan_get_tuning(const pet_plan *plan, int32_t *h_fwd_chunks, int3
  * stacks have nothing to tune. */
 pet_status pet_plan_autotune(pet_plan *plan, int32_t *h_fwd_chunks, int32_t *h_back_run);
 
+/* Device bytes a plan holds, and the bytes pet_problem_create would
+ * allocate for a problem on it (with a background sinogram if has_bg): the
+ * admission figures of a serving loop, beside pet_state_create's query. */
+pet_status pet_plan_bytes(const pet_plan *plan, size_t *h_bytes);
+pet_status pet_problem_bytes(const pet_plan *plan, int32_t has_bg, size_t *h_bytes);
+/* The bytes pet_state_create would allocate for `algo` on any problem of plan. */
+pet_status pet_plan_state_bytes(const pet_plan *plan, int32_t algo, int32_t table_dtype, size_t *h_bytes);
+
 /* Copy sens_t (t >= 0) or sens (t = -1), nx*ny floats, into d_out. */
 pet_status pet_plan_sensitivity(const pet_plan *plan, int32_t t, float *d_out, void *stream);
 
@@ -275,6 +283,11 @@ pet_status pet_state_objective_async(pet_state *state, double *d_phi, void *stre
  * a state in a batch may still be used on its own between batch calls. */
 pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out);
 pet_status pet_batch_destroy(pet_batch *batch);
+
+/* Whether pet_batch_epoch captures and replays CUDA graphs (default on).
+ * A batch whose membership changes every few calls (a serving loop) is
+ * cheaper without: each new batch would otherwise pay one capture. */
+pet_status pet_batch_set_graphs(pet_batch *batch, int32_t on);
 
 /* n_iter updates of every member: h_subset_seqs is row-major [n][n_iter]
  * (member j's subset indices), h_alpha[j] and h_eta[j] its step size and

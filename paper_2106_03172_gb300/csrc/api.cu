@@ -205,6 +205,20 @@ pet_status read_status(const pet_problem *p, cudaStream_t s) {
     return PET_OK;
 }
 
+// Device bytes pet_state_create allocates for `algo` on plan pl.
+size_t state_bytes(const pet_plan *pl, int algo, int table_dtype) {
+    const size_t Nz = (size_t)pl->N * pl->nz, Mz = (size_t)pl->M * pl->nz;
+    const size_t n_part = (size_t)forward_blocks(pl->M, pl->nz, choose_group(pl)) + (Nz + 255) / 256;
+    const size_t table_bytes = (size_t)pl->ns * Nz * (table_dtype == PET_TABLE_BF16 ? 2 : 4);
+    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * pl->nz * 4 + n_part * 8;
+    if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + Mz * 4;
+    if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + Mz * 4;
+    if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
+    if (algo == PET_ALGO_SEM) bytes += Nz * 4 + Mz * 4;
+    if (algo == PET_ALGO_SAGAEM) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4;
+    return bytes;
+}
+
 // (Re)initialise an allocated state at its current image: update counter,
 // SVREM statistic flag, SAGA table/mean/preconditioner, SVRG preconditioner.
 pet_status state_init(pet_state *st, cudaStream_t s) {
@@ -466,6 +480,28 @@ pet_status pet_plan_nnz(const pet_plan *pl, int32_t t, int64_t *h_nnz) {
     return PET_OK;
 }
 
+pet_status pet_plan_bytes(const pet_plan *pl, size_t *h_bytes) {
+    if (!pl || !h_bytes) return set_error(PET_ERR_INVALID, "null argument");
+    *h_bytes = sizeof(ViewParams) * pl->na + sizeof(float2) * (size_t)pl->M + sizeof(int) * (2 * (size_t)pl->na + pl->ns + 3) +
+               sizeof(float) * ((size_t)pl->ns + 1) * pl->N;
+    return PET_OK;
+}
+
+pet_status pet_problem_bytes(const pet_plan *pl, int32_t has_bg, size_t *h_bytes) {
+    if (!pl || !h_bytes) return set_error(PET_ERR_INVALID, "null argument");
+    const size_t Mz = (size_t)pl->M * pl->nz, Nz = (size_t)pl->N * pl->nz;
+    const size_t n_part = (size_t)forward_blocks(pl->M, pl->nz, choose_group(pl)) + (Nz + 255) / 256;
+    *h_bytes = sizeof(float) * (Mz * (has_bg ? 3 : 2) + Nz) + sizeof(double) * (n_part + pl->nz + 8) + sizeof(int);
+    return PET_OK;
+}
+
+pet_status pet_plan_state_bytes(const pet_plan *pl, int32_t algo, int32_t table_dtype, size_t *h_bytes) {
+    if (!pl || !h_bytes) return set_error(PET_ERR_INVALID, "null argument");
+    if (algo < PET_ALGO_OSEM || algo > PET_ALGO_SAGAEM) return set_error(PET_ERR_INVALID, "unknown algorithm");
+    *h_bytes = state_bytes(pl, algo, table_dtype);
+    return PET_OK;
+}
+
 pet_status pet_plan_set_tuning(pet_plan *pl, int32_t fwd_chunks, int32_t back_run) {
     if (!pl) return set_error(PET_ERR_INVALID, "null plan");
     if (fwd_chunks != 0 && fwd_chunks != 8 && fwd_chunks != 16 && fwd_chunks != 32)
@@ -721,12 +757,7 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     const pet_plan *pl = p->plan;
     const size_t Nz = (size_t)pl->N * pl->nz;
     const size_t table_bytes = (size_t)pl->ns * Nz * (table_dtype == PET_TABLE_BF16 ? 2 : 4);
-    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * pl->nz * 4 + (size_t)p->n_part * 8;
-    if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
-    if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + (size_t)pl->M * pl->nz * 4;
-    if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
-    if (algo == PET_ALGO_SEM) bytes += Nz * 4 + (size_t)pl->M * pl->nz * 4;
-    if (algo == PET_ALGO_SAGAEM) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4;
+    const size_t bytes = state_bytes(pl, algo, table_dtype);
     if (bytes_needed) *bytes_needed = bytes;
     if (!out) return PET_OK;
     *out = nullptr;
@@ -1055,6 +1086,12 @@ pet_status pet_batch_destroy(pet_batch *b) {
     return PET_OK;
 }
 
+pet_status pet_batch_set_graphs(pet_batch *b, int32_t on) {
+    if (!b) return set_error(PET_ERR_INVALID, "null batch");
+    b->graphs_on = on != 0;
+    return PET_OK;
+}
+
 pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out) {
     if (!states || !out || n < 1) return set_error(PET_ERR_INVALID, "need at least one state");
     *out = nullptr;
@@ -1254,7 +1291,7 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
                                     s),
                     "batch member copy"));
     std::vector<std::vector<uint8_t>> anchors(n, std::vector<uint8_t>((size_t)n_iter, 0));
-    bool direct = !use_graphs() || profiling_enabled();
+    bool direct = !use_graphs() || profiling_enabled() || !b->graphs_on;
     std::vector<int64_t> key = {n_iter};
     for (int j = 0; j < n; ++j) {
         pet_state *st = b->states[j];

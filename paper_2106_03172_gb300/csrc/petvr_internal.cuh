@@ -336,6 +336,7 @@ struct pet_batch {
         int max_views;
     };
     std::vector<Group> fwd_groups, back_groups;
+    bool graphs_on = true;
     int *d_seqs = nullptr;          // [n][seq_cap] subset indices of the current call
     float *d_alphas = nullptr;      // [n][seq_cap] step sizes of the current call
     int seq_cap = 0;

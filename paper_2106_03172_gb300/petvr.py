@@ -74,6 +74,10 @@ _SIGS = {
     "pet_state_reset": (c_int32, [c_void_p, c_void_p]),
     "pet_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
     "pet_batch_destroy": (c_int32, [c_void_p]),
+    "pet_batch_set_graphs": (c_int32, [c_void_p, c_int32]),
+    "pet_plan_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
+    "pet_problem_bytes": (c_int32, [c_void_p, c_int32, POINTER(c_size_t)]),
+    "pet_plan_state_bytes": (c_int32, [c_void_p, c_int32, c_int32, POINTER(c_size_t)]),
     "pet_batch_epoch": (c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_float), POINTER(c_int32), c_void_p]),
     "pet_batch_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_osem_epoch": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
@@ -308,6 +312,28 @@ def pet_batch_create(states) -> c_void_p:
     return h
 
 
+def pet_batch_set_graphs(batch, on: bool):
+    _call("pet_batch_set_graphs", batch, 1 if on else 0)
+
+
+def pet_plan_bytes(plan) -> int:
+    n = c_size_t()
+    _call("pet_plan_bytes", plan, byref(n))
+    return n.value
+
+
+def pet_problem_bytes(plan, has_bg: bool = False) -> int:
+    n = c_size_t()
+    _call("pet_problem_bytes", plan, 1 if has_bg else 0, byref(n))
+    return n.value
+
+
+def pet_plan_state_bytes(plan, algo: str, table: str = "fp32") -> int:
+    n = c_size_t()
+    _call("pet_plan_state_bytes", plan, ALGO[algo], TABLE[table], byref(n))
+    return n.value
+
+
 def pet_batch_epoch(batch, seqs, alphas, etas, stream=None):
     """seqs: one equal-length subset sequence per member."""
     n = len(seqs)
@@ -360,9 +386,11 @@ class Problem:
 class Batch:
     """States whose updates run together (one launch per phase for all)."""
 
-    def __init__(self, states):
+    def __init__(self, states, graphs: bool = True):
         self.states = list(states)
         self.handle = pet_batch_create([st.handle for st in self.states])
+        if not graphs:
+            pet_batch_set_graphs(self.handle, False)
 
     def epoch(self, seqs, alphas, etas, stream=None):
         pet_batch_epoch(self.handle, seqs, alphas, etas, stream)

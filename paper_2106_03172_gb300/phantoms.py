@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "Geometry", "Workload", "WORKLOADS", "Ellipse", "random_ellipse_phantom",
     "ellipsoid_stack_phantom", "rasterise", "analytic_sinogram", "make_data",
-    "splitmix64", "subset_sequence", "batched_workloads",
+    "splitmix64", "subset_sequence", "batched_workloads", "serving_workloads",
 ]
 
 
@@ -282,6 +282,27 @@ def subset_sequence(seed: int, n_subsets: int, length: int) -> np.ndarray:
         raise ValueError("n_subsets must be positive and length nonnegative")
     vals = splitmix64(seed, length)
     return np.array([int(((v >> 11) * n_subsets) >> 53) for v in vals], dtype=np.int32)
+
+
+def serving_workloads(seed: int, count: int, sizes=(128, 256)) -> list:
+    """Request templates of the serving stream: image N uniform in ``sizes``,
+    views round(1.4 N) (720 for N = 512), bins the odd integer nearest 1.43 N,
+    counts log-uniform in [1e6, 1e8], subsets uniform in {6, 12, 21}, method
+    SVREM or SAGA.  The method is stored in ``methods[0]``."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(list(sizes)))
+        views = 720 if n == 512 else int(round(1.4 * n))
+        nb = int(round(1.43 * n))
+        if nb % 2 == 0:
+            nb += 1 if (1.43 * n) >= nb else -1
+        geom = Geometry(n, n, views, nb)
+        cnt = float(10.0 ** rng.uniform(6.0, 8.0))
+        algo = str(rng.choice(["svrem", "saga"]))
+        out.append(Workload(f"serve{i}", geom, n_subsets=int(rng.choice([6, 12, 21])), counts=cnt,
+                            bg_frac=0.10, beta=0.005, n_ellipses=12, n_lesions=2, methods=(algo,)))
+    return out
 
 
 def batched_workloads(seed: int, count: int) -> list:

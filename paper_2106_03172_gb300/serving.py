@@ -1,0 +1,200 @@
+"""Continuous-batching reconstruction server: a host scheduler over the C ABI.
+
+Requests (a geometry, counts, a method and a target objective Phi*) arrive
+over time.  The server admits a request as soon as it has arrived and both a
+slot and device memory are free: its budget counts the plan (shared by every
+request of the same geometry and subset count), the problem and the state
+bytes the library reports, SAGA's gradient table included.  All admitted
+requests advance together: every tick runs `tick` updates of every active
+state in one batched launch per phase (pet_batch_epoch), so requests that
+arrive while others run join the next tick and their work shares the
+kernels.  At the end of each of its epochs a request's objective is checked
+against its Phi*; once the relative gap is at most `gap` (or it has run
+`max_epochs` epochs) its image is copied back and its memory released.
+
+A request's result depends only on the request: its subset sequence is
+seeded by the request, ticks are counted from its own admission, and the
+batched kernels give each member exactly what its own epoch calls would.
+Served alone or in a mix, it returns the same image.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import petvr
+from .phantoms import Workload, subset_sequence
+
+STEP = {"svrem": (0.7, 1), "saga": (1.0, 1), "svrg": (2.0, 2), "osem": (1.0, 1)}
+
+
+@dataclass
+class Request:
+    rid: int
+    work: Workload
+    counts: np.ndarray          # float32 sinogram [view][bin]
+    w: float                    # uniform background per bin
+    phi_star: float             # target objective (from the FP64 oracle)
+    arrival: float              # seconds after the stream starts
+    seed: int = 0
+    algo: str = ""
+    # filled in by the server
+    admitted: float = float("nan")
+    done: float = float("nan")
+    epochs: int = 0
+    gap: float = float("nan")
+    reached: bool = False
+    image: np.ndarray | None = None
+    bytes: int = 0
+
+    def __post_init__(self):
+        if not self.algo:
+            self.algo = self.work.methods[0]
+
+
+@dataclass
+class _Slot:
+    req: Request
+    problem: petvr.Problem
+    state: petvr.State
+    img: torch.Tensor
+    seq: np.ndarray
+    pos: int = 0
+
+
+@dataclass
+class ServerStats:
+    ticks: int = 0
+    max_active: int = 0
+    active_sum: int = 0
+    admissions_deferred: int = 0
+    batches_built: int = 0
+    peak_bytes: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+class Server:
+    def __init__(self, budget_bytes: int, max_slots: int = 64, gap: float = 1e-4, max_epochs: int = 60,
+                 tick: int = 3):
+        if tick < 1 or max_slots < 1:
+            raise ValueError("tick and max_slots must be positive")
+        self.budget, self.max_slots = int(budget_bytes), int(max_slots)
+        self.gap, self.max_epochs, self.tick = gap, max_epochs, tick
+        self.plans = {}                 # (nx, ny, views, bins, subsets) -> (Plan, bytes, users)
+        self.used = 0
+        self.active: list[_Slot] = []
+        self.stats = ServerStats()
+        self._batch = None
+        self._phi = torch.zeros(max_slots, 3, dtype=torch.float64, device="cuda")
+        self._phi_host = torch.zeros(max_slots, 3, dtype=torch.float64).pin_memory()
+
+    # ---- memory accounting -------------------------------------------------
+    @staticmethod
+    def _key(work):
+        g = work.geometry
+        return (g.nx, g.ny, g.n_angles, g.n_bins, work.n_subsets)
+
+    def _plan(self, work):
+        key = self._key(work)
+        if key not in self.plans:
+            plan = petvr.Plan(work.geometry, work.n_subsets)
+            self.plans[key] = [plan, petvr.pet_plan_bytes(plan.handle), 0]
+        return self.plans[key]
+
+    def bytes_needed(self, req: Request) -> int:
+        """Device bytes admitting `req` adds (its plan only if no active request holds it)."""
+        plan, plan_bytes, users = self._plan(req.work)
+        table = "bf16" if req.algo == "saga" else "fp32"
+        return ((plan_bytes if users == 0 else 0) + petvr.pet_problem_bytes(plan.handle, False)
+                + petvr.pet_plan_state_bytes(plan.handle, req.algo, table))
+
+    # ---- admission and retirement -----------------------------------------
+    def _admit(self, req: Request, now: float):
+        entry = self._plan(req.work)
+        plan = entry[0]
+        need = self.bytes_needed(req)
+        counts = torch.from_numpy(np.ascontiguousarray(req.counts, dtype=np.float32).ravel()).cuda()
+        problem = petvr.Problem(plan, counts, None, req.w, req.work.beta)
+        img = torch.empty(req.work.geometry.n_pixels, device="cuda")
+        petvr.pet_warm_start(problem.handle, img)
+        table = "bf16" if req.algo == "saga" else "fp32"
+        state = petvr.State(problem, req.algo, img, table=table)
+        ns = req.work.n_subsets
+        if ns % self.tick:
+            raise ValueError(f"tick {self.tick} must divide the request's {ns} subsets")
+        seq = subset_sequence(req.seed, ns, self.max_epochs * ns)
+        entry[2] += 1
+        self.used += need
+        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
+        req.admitted, req.bytes = now, need
+        self.active.append(_Slot(req, problem, state, img, seq))
+        self._batch = None
+
+    def _retire(self, slot: _Slot, now: float):
+        slot.req.image = slot.img.cpu().numpy()
+        slot.req.done = now
+        self.used -= slot.req.bytes
+        entry = self.plans[self._key(slot.req.work)]
+        entry[2] -= 1
+        self.active.remove(slot)
+        self._batch = None
+
+    # ---- the loop ------------------------------------------------------------
+    def serve(self, requests, clock=time.perf_counter):
+        """Serve `requests` (arrival times in seconds from now); returns them
+        with admission/completion times, epochs, final gap and image."""
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        t0 = clock()
+        stream = torch.cuda.current_stream()
+        while pending or self.active:
+            now = clock() - t0
+            while pending and pending[0].arrival <= now and len(self.active) < self.max_slots:
+                if self.used + self.bytes_needed(pending[0]) > self.budget and self.active:
+                    self.stats.admissions_deferred += 1
+                    break
+                self._admit(pending.pop(0), clock() - t0)
+            if not self.active:
+                wait = pending[0].arrival - (clock() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.001))
+                continue
+            if self._batch is None:
+                self._batch = petvr.Batch([s.state for s in self.active], graphs=False)
+                self.stats.batches_built += 1
+            seqs = [s.seq[s.pos:s.pos + self.tick] for s in self.active]
+            self._batch.epoch(seqs, [STEP[s.req.algo][0] for s in self.active],
+                              [STEP[s.req.algo][1] for s in self.active], stream=stream)
+            checks = []
+            for j, s in enumerate(self.active):
+                s.pos += self.tick
+                if s.pos % s.req.work.n_subsets == 0:        # an epoch of this request just ended
+                    s.state.objective_async(self._phi[j], stream=stream)
+                    checks.append((j, s))
+            if checks:
+                self._phi_host.copy_(self._phi, non_blocking=True)
+            torch.cuda.synchronize()
+            now = clock() - t0
+            self.stats.ticks += 1
+            self.stats.active_sum += len(self.active)
+            self.stats.max_active = max(self.stats.max_active, len(self.active))
+            for j, s in checks:
+                r = s.req
+                r.epochs = s.pos // r.work.n_subsets
+                r.gap = (r.phi_star - float(self._phi_host[j, 0])) / abs(r.phi_star)
+                if r.gap <= self.gap or r.epochs >= self.max_epochs:
+                    r.reached = r.gap <= self.gap
+                    self._retire(s, now)
+        return requests
+
+
+def latency_summary(requests):
+    lat = np.array([r.done - r.arrival for r in requests if np.isfinite(r.done)])
+    wait = np.array([r.admitted - r.arrival for r in requests if np.isfinite(r.admitted)])
+    span = max(r.done for r in requests) - min(r.arrival for r in requests)
+    return {"completed": int(len(lat)), "reached_gap": int(sum(r.reached for r in requests)),
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_wait_ms": 1e3 * float(wait.mean()), "recon_per_s": len(lat) / span,
+            "epochs_mean": float(np.mean([r.epochs for r in requests]))}

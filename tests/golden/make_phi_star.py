@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle.em import build_problem, map_reference  # noqa: E402
-from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data  # noqa: E402
+from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data, serving_workloads  # noqa: E402
 
 OUT = os.path.join(HERE, "phi_star.json")
 
@@ -24,10 +24,13 @@ def counts_sha256(g) -> str:
     return hashlib.sha256(g.astype("<f4").tobytes()).hexdigest()
 
 
+SERVING_POOL = {w.name: w for w in serving_workloads(0, 8)}
+
+
 def main(names):
     table = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:
-        work = WORKLOADS[name]
+        work = WORKLOADS.get(name) or SERVING_POOL[name]
         data = make_data(work, 0)
         prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
         t = time.time()
@@ -42,4 +45,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["c64", "c256"])
+    main(sys.argv[1:] or ["c64", "c256"] + sorted(SERVING_POOL))

@@ -1,0 +1,70 @@
+"""Continuous-batching server through the C ABI: requests that arrive while
+others run share the batched kernels, each request's image is the same
+served alone or in the mix, every request reaches the objective gap against
+the FP64 oracle's Phi*, and admission respects the device-memory budget."""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.em import build_problem, map_reference
+from paper_2106_03172_gb300.phantoms import Geometry, Workload, make_data
+
+pytestmark = pytest.mark.gpu
+
+TEMPLATES = [
+    Workload("s0", Geometry(48, 48, 66, 69), n_subsets=6, counts=3e5, bg_frac=0.1, beta=0.005, n_ellipses=5,
+             methods=("svrem",)),
+    Workload("s1", Geometry(64, 64, 90, 91), n_subsets=12, counts=1e6, bg_frac=0.1, beta=0.005, n_ellipses=6,
+             methods=("saga",)),
+    Workload("s2", Geometry(48, 48, 66, 69), n_subsets=6, counts=2e6, bg_frac=0.1, beta=0.005, n_ellipses=5,
+             methods=("saga",)),
+    Workload("s3", Geometry(64, 64, 90, 91), n_subsets=12, counts=5e5, bg_frac=0.1, beta=0.005, n_ellipses=6,
+             methods=("svrem",)),
+]
+
+
+@functools.lru_cache(maxsize=None)
+def _template(i):
+    work = TEMPLATES[i]
+    data = make_data(work, 40 + i)
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    _, phi, _ = map_reference(prob)
+    return work, data, phi
+
+
+def _requests(arrivals):
+    from paper_2106_03172_gb300.serving import Request
+    out = []
+    for rid, t in enumerate(arrivals):
+        work, data, phi = _template(rid % len(TEMPLATES))
+        out.append(Request(rid, work, data["g"], data["w"], phi, arrival=t, seed=900 + rid))
+    return out
+
+
+def test_results_same_alone_and_in_the_mix():
+    from paper_2106_03172_gb300.serving import Server, latency_summary
+    arrivals = [0.0, 0.0005, 0.001, 0.0015, 0.002, 0.0025]
+    mixed = Server(budget_bytes=1 << 34, tick=3, max_epochs=40).serve(_requests(arrivals))
+    summary = latency_summary(mixed)
+    assert summary["completed"] == len(arrivals) and summary["reached_gap"] == len(arrivals)
+    for r in mixed:
+        alone = Server(budget_bytes=1 << 34, tick=3, max_epochs=40).serve(_requests(arrivals)[r.rid:r.rid + 1])[0]
+        assert alone.epochs == r.epochs
+        np.testing.assert_array_equal(alone.image, r.image)
+
+
+def test_admission_respects_the_memory_budget():
+    from paper_2106_03172_gb300.serving import Server
+    reqs = _requests([0.0] * 6)
+    probe = Server(budget_bytes=1 << 40)
+    need = max(probe.bytes_needed(r) for r in reqs)
+    budget = 2 * need + need // 2
+    srv = Server(budget_bytes=budget, tick=3, max_epochs=40)
+    done = srv.serve(reqs)
+    assert all(np.isfinite(r.done) for r in done)
+    assert srv.stats.peak_bytes <= budget and srv.stats.admissions_deferred > 0
+    assert srv.stats.max_active < len(reqs)
+    assert srv.used == 0
