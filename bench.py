@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", type=int, default=20, help="reconstructions per method for the gap metric")
     ap.add_argument("--tuning", default="", help="pin launch shapes 'chunks,run' instead of autotuning")
+    ap.add_argument("--requests", type=int, default=200, help="serve workload: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
+    ap.add_argument("--budget-gib", type=float, default=1.0, help="serve workload: device-memory budget")
     ap.add_argument("--batch", dest="batch", action="store_true",
                     help="run the four methods as one batch (one launch per phase) instead of four streams")
     return ap.parse_args()
@@ -670,12 +673,77 @@ def run_batch64(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: an open-loop Poisson stream of SVREM/SAGA requests drawn from
+    eight seeded request templates (128x128 and 256x256, 1e6-1e8 counts, 6/12/21
+    subsets), each stopped at a relative objective gap of 1e-4 against the
+    FP64 oracle's Phi* of its template; continuous batching with admission by
+    device-memory budget."""
+    import hashlib
+
+    import torch
+
+    from paper_2106_03172_gb300 import build as _build
+    from paper_2106_03172_gb300 import petvr
+    from paper_2106_03172_gb300.phantoms import make_data, serving_workloads
+    from paper_2106_03172_gb300.serving import Request, Server, latency_summary
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    _build.build()
+    petvr.lib()
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "phi_star.json")))
+    pool, skipped = [], []
+    for w in serving_workloads(0, 8):
+        data = make_data(w, 0)
+        ent = golden.get(w.name)
+        sha = hashlib.sha256(data["g"].astype("<f4").tobytes()).hexdigest()
+        if ent and ent["counts_sha256"] == sha:
+            pool.append((w, data, ent["phi_star"]))
+        else:
+            skipped.append(w.name)
+    rng = np.random.default_rng(77)
+    n_req = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    reqs = []
+    for i, t in enumerate(arrivals):
+        w, data, phi = pool[int(rng.integers(len(pool)))]
+        reqs.append(Request(i, w, data["g"], data["w"], phi, arrival=float(t), seed=5000 + i))
+    srv = Server(budget_bytes=int(args.budget_gib * (1 << 30)), max_slots=64, gap=GAP, max_epochs=60, tick=3)
+    srv.prepare([w for w, _, _ in pool])
+    clocks = ClockSampler(visible_index(torch))
+    launches0 = petvr.pet_kernel_launches()
+    clocks.start()
+    done = srv.serve(reqs)
+    clk = clocks.stop()
+    summ = latency_summary(done)
+    line = {
+        "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
+        "value": summ["recon_per_s"], "unit": "reconstructions/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
+        "ms_per_step": summ["p50_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (bf16 SAGA tables)", "data": "synthetic (seeded ellipse phantoms, Poisson counts)",
+        "config": {"workload": f"serve: {n_req} requests, Poisson arrivals at {args.rate:g}/s, templates "
+                               f"{', '.join(w.name for w, _, _ in pool)} (128^2 and 256^2, SVREM/SAGA), "
+                               f"stop at relative gap {GAP:g} against the oracle's Phi*",
+                   "budget_gib": args.budget_gib, "max_slots": 64, "tick_updates": 3,
+                   "templates_without_phi_star": skipped},
+        "latency": summ, "gpu_launches": int(petvr.pet_kernel_launches() - launches0), "clocks": clk,
+        "server": {"ticks": srv.stats.ticks, "max_active": srv.stats.max_active,
+                   "mean_active": srv.stats.active_sum / max(1, srv.stats.ticks),
+                   "admissions_deferred": srv.stats.admissions_deferred,
+                   "batches_built": srv.stats.batches_built, "peak_bytes": srv.stats.peak_bytes},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch64(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

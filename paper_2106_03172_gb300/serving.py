@@ -111,6 +111,13 @@ class Server:
         return ((plan_bytes if users == 0 else 0) + petvr.pet_problem_bytes(plan.handle, False)
                 + petvr.pet_plan_state_bytes(plan.handle, req.algo, table))
 
+    def prepare(self, works):
+        """Build the plans of these request shapes ahead of the stream (a
+        plan is computed once per geometry and subset count)."""
+        for w in works:
+            self._plan(w)
+        torch.cuda.synchronize()
+
     # ---- admission and retirement -----------------------------------------
     def _admit(self, req: Request, now: float):
         entry = self._plan(req.work)
