@@ -60,9 +60,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", type=int, default=20, help="reconstructions per method for the gap metric")
     ap.add_argument("--tuning", default="", help="pin launch shapes 'chunks,run' instead of autotuning")
-    ap.add_argument("--requests", type=int, default=200, help="serve workload: number of requests")
+    ap.add_argument("--requests", type=int, default=1000, help="serve workload: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
     ap.add_argument("--budget-gib", type=float, default=1.0, help="serve workload: device-memory budget")
+    ap.add_argument("--window", type=int, default=4, help="serve workload: ticks per host round trip")
     ap.add_argument("--batch", dest="batch", action="store_true",
                     help="run the four methods as one batch (one launch per phase) instead of four streams")
     return ap.parse_args()
@@ -674,26 +675,27 @@ def run_batch64(args):
 
 
 def run_serve(args):
-    """Serving: an open-loop Poisson stream of SVREM/SAGA requests drawn from
-    eight seeded request templates (128x128 and 256x256, 1e6-1e8 counts, 6/12/21
-    subsets), each stopped at a relative objective gap of 1e-4 against the
-    FP64 oracle's Phi* of its template; continuous batching with admission by
-    device-memory budget."""
+    """Serving: an open-loop Poisson stream of SVREM/SAGA requests, image size
+    uniform over the request templates' sizes (128^2 to 512^2, 1e6-1e8 counts,
+    6/12/21 subsets), each stopped at a relative objective gap of 1e-4 against
+    the FP64 oracle's Phi* of its template; continuous batching with admission
+    by device-memory budget, against the same stream served one request at a
+    time through the plain per-reconstruction path."""
     import hashlib
 
     import torch
 
     from paper_2106_03172_gb300 import build as _build
     from paper_2106_03172_gb300 import petvr
-    from paper_2106_03172_gb300.phantoms import make_data, serving_workloads
-    from paper_2106_03172_gb300.serving import Request, Server, latency_summary
+    from paper_2106_03172_gb300.phantoms import make_data, serving_pool
+    from paper_2106_03172_gb300.serving import Request, Server, latency_summary, serve_plain
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     _build.build()
     petvr.lib()
     golden = json.load(open(os.path.join(ROOT, "tests", "golden", "phi_star.json")))
     pool, skipped = [], []
-    for w in serving_workloads(0, 8):
+    for w in serving_pool():
         data = make_data(w, 0)
         ent = golden.get(w.name)
         sha = hashlib.sha256(data["g"].astype("<f4").tobytes()).hexdigest()
@@ -704,29 +706,51 @@ def run_serve(args):
     rng = np.random.default_rng(77)
     n_req = args.requests
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
-    reqs = []
-    for i, t in enumerate(arrivals):
-        w, data, phi = pool[int(rng.integers(len(pool)))]
-        reqs.append(Request(i, w, data["g"], data["w"], phi, arrival=float(t), seed=5000 + i))
-    srv = Server(budget_bytes=int(args.budget_gib * (1 << 30)), max_slots=64, gap=GAP, max_epochs=60, tick=3)
+    # image size uniform over the pool's sizes, then a template of that size
+    by_size = {}
+    for k, (w, _, _) in enumerate(pool):
+        by_size.setdefault(w.geometry.nx, []).append(k)
+    size_keys = sorted(by_size)
+    picks = []
+    for _ in range(n_req):
+        group = by_size[size_keys[int(rng.integers(len(size_keys)))]]
+        picks.append(group[int(rng.integers(len(group)))])
+
+    def requests():
+        return [Request(i, pool[k][0], pool[k][1]["g"], pool[k][1]["w"], pool[k][2], arrival=float(t),
+                        seed=5000 + i) for i, (t, k) in enumerate(zip(arrivals, picks))]
+
+    srv = Server(budget_bytes=int(args.budget_gib * (1 << 30)), max_slots=64, gap=GAP, max_epochs=60, tick=3,
+                 window=args.window)
     srv.prepare([w for w, _, _ in pool])
     clocks = ClockSampler(visible_index(torch))
     launches0 = petvr.pet_kernel_launches()
     clocks.start()
-    done = srv.serve(reqs)
+    done = srv.serve(requests())
     clk = clocks.stop()
+    launches = petvr.pet_kernel_launches() - launches0
     summ = latency_summary(done)
+    # the same stream through the plain per-reconstruction path, one request at a time
+    plain = serve_plain(requests(), gap=GAP, max_epochs=60)
+    plain_summ = latency_summary(plain)
+    same = all(a.epochs == b.epochs and np.array_equal(a.image, b.image) for a, b in zip(done, plain))
+    sizes = sorted({w.geometry.nx for w, _, _ in pool})
     line = {
         "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
         "value": summ["recon_per_s"], "unit": "reconstructions/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
         "ms_per_step": summ["p50_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (bf16 SAGA tables)", "data": "synthetic (seeded ellipse phantoms, Poisson counts)",
         "config": {"workload": f"serve: {n_req} requests, Poisson arrivals at {args.rate:g}/s, templates "
-                               f"{', '.join(w.name for w, _, _ in pool)} (128^2 and 256^2, SVREM/SAGA), "
+                               f"{', '.join(w.name for w, _, _ in pool)} "
+                               f"({'/'.join(f'{n}^2' for n in sizes)}, SVREM/SAGA), "
                                f"stop at relative gap {GAP:g} against the oracle's Phi*",
-                   "budget_gib": args.budget_gib, "max_slots": 64, "tick_updates": 3,
+                   "budget_gib": args.budget_gib, "max_slots": 64, "tick_updates": 3, "window_ticks": args.window,
                    "templates_without_phi_star": skipped},
-        "latency": summ, "gpu_launches": int(petvr.pet_kernel_launches() - launches0), "clocks": clk,
+        "latency": summ, "gpu_launches": int(launches), "clocks": clk,
+        "plain": {"latency": plain_summ, "how": "the same requests one at a time in arrival order, each "
+                  "through its own State epochs (captured graphs), objective after every epoch"},
+        "speedup_vs_plain": summ["recon_per_s"] / plain_summ["recon_per_s"],
+        "bit_identical_to_plain": bool(same),
         "server": {"ticks": srv.stats.ticks, "max_active": srv.stats.max_active,
                    "mean_active": srv.stats.active_sum / max(1, srv.stats.ticks),
                    "admissions_deferred": srv.stats.admissions_deferred,

@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "Geometry", "Workload", "WORKLOADS", "Ellipse", "random_ellipse_phantom",
     "ellipsoid_stack_phantom", "rasterise", "analytic_sinogram", "make_data",
-    "splitmix64", "subset_sequence", "batched_workloads", "serving_workloads",
+    "splitmix64", "subset_sequence", "batched_workloads", "serving_workloads", "serving_pool",
 ]
 
 
@@ -284,11 +284,12 @@ def subset_sequence(seed: int, n_subsets: int, length: int) -> np.ndarray:
     return np.array([int(((v >> 11) * n_subsets) >> 53) for v in vals], dtype=np.int32)
 
 
-def serving_workloads(seed: int, count: int, sizes=(128, 256)) -> list:
+def serving_workloads(seed: int, count: int, sizes=(128, 256), prefix: str = "serve") -> list:
     """Request templates of the serving stream: image N uniform in ``sizes``,
     views round(1.4 N) (720 for N = 512), bins the odd integer nearest 1.43 N,
     counts log-uniform in [1e6, 1e8], subsets uniform in {6, 12, 21}, method
-    SVREM or SAGA.  The method is stored in ``methods[0]``."""
+    SVREM or SAGA.  The method is stored in ``methods[0]``; template i is
+    named ``f"{prefix}{i}"``."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -300,9 +301,18 @@ def serving_workloads(seed: int, count: int, sizes=(128, 256)) -> list:
         geom = Geometry(n, n, views, nb)
         cnt = float(10.0 ** rng.uniform(6.0, 8.0))
         algo = str(rng.choice(["svrem", "saga"]))
-        out.append(Workload(f"serve{i}", geom, n_subsets=int(rng.choice([6, 12, 21])), counts=cnt,
+        out.append(Workload(f"{prefix}{i}", geom, n_subsets=int(rng.choice([6, 12, 21])), counts=cnt,
                             bg_frac=0.10, beta=0.005, n_ellipses=12, n_lesions=2, methods=(algo,)))
     return out
+
+
+def serving_pool() -> list:
+    """The request templates the serving stream draws from: eight at 128^2 and
+    256^2 (seed 0), two at 384^2 with 538 views x 549 bins (seed 5: SVREM
+    with 21 subsets, SAGA with 6) and two at 512^2 with 720 views x 733 bins
+    (seed 3: SVREM with 6 subsets, SAGA with 12)."""
+    return (serving_workloads(0, 8) + serving_workloads(5, 2, sizes=(384,), prefix="serve384_")
+            + serving_workloads(3, 2, sizes=(512,), prefix="serve512_"))
 
 
 def batched_workloads(seed: int, count: int) -> list:

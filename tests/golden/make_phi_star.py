@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle.em import build_problem, map_reference  # noqa: E402
-from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data, serving_workloads  # noqa: E402
+from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data, serving_pool  # noqa: E402
 
 OUT = os.path.join(HERE, "phi_star.json")
 
@@ -24,24 +24,33 @@ def counts_sha256(g) -> str:
     return hashlib.sha256(g.astype("<f4").tobytes()).hexdigest()
 
 
-SERVING_POOL = {w.name: w for w in serving_workloads(0, 8)}
+SERVING_POOL = {w.name: w for w in serving_pool()}
+
+
+def _store(name, entry):
+    """Merge one entry into the table (re-read just before writing, so that
+    solves run side by side keep each other's entries)."""
+    table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    table[name] = entry
+    tmp = f"{OUT}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, OUT)
 
 
 def main(names):
-    table = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:
         work = WORKLOADS.get(name) or SERVING_POOL[name]
         data = make_data(work, 0)
         prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
         t = time.time()
         _, phi, kkt = map_reference(prob)
-        table[name] = {"seed": 0, "phi_star": phi, "kkt_residual": kkt,
-                       "counts_sha256": counts_sha256(data["g"]),
-                       "solver": "scipy L-BFGS-B on the FP64 oracle objective",
-                       "seconds": round(time.time() - t, 1)}
-        print(name, table[name])
-    with open(OUT, "w") as f:
-        json.dump(table, f, indent=1, sort_keys=True)
+        entry = {"seed": 0, "phi_star": phi, "kkt_residual": kkt,
+                 "counts_sha256": counts_sha256(data["g"]),
+                 "solver": "scipy L-BFGS-B on the FP64 oracle objective",
+                 "seconds": round(time.time() - t, 1)}
+        print(name, entry, flush=True)
+        _store(name, entry)
 
 
 if __name__ == "__main__":

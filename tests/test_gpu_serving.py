@@ -44,16 +44,31 @@ def _requests(arrivals):
     return out
 
 
-def test_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("window", [1, 4])
+def test_results_same_alone_and_in_the_mix(window):
+    """A window of several ticks per host round trip changes when requests
+    are admitted and retired, not what they return."""
     from paper_2106_03172_gb300.serving import Server, latency_summary
     arrivals = [0.0, 0.0005, 0.001, 0.0015, 0.002, 0.0025]
-    mixed = Server(budget_bytes=1 << 34, tick=3, max_epochs=40).serve(_requests(arrivals))
+    mixed = Server(budget_bytes=1 << 34, tick=3, max_epochs=40, window=window).serve(_requests(arrivals))
     summary = latency_summary(mixed)
     assert summary["completed"] == len(arrivals) and summary["reached_gap"] == len(arrivals)
     for r in mixed:
         alone = Server(budget_bytes=1 << 34, tick=3, max_epochs=40).serve(_requests(arrivals)[r.rid:r.rid + 1])[0]
         assert alone.epochs == r.epochs
         np.testing.assert_array_equal(alone.image, r.image)
+
+
+def test_plain_path_gives_the_same_results():
+    """The one-at-a-time per-reconstruction path (State epochs, captured
+    graphs) and the continuous-batching server agree bit for bit."""
+    from paper_2106_03172_gb300.serving import Server, serve_plain
+    arrivals = [0.0, 0.0005, 0.001, 0.0015]
+    served = Server(budget_bytes=1 << 34, tick=3, max_epochs=40, window=3).serve(_requests(arrivals))
+    plain = serve_plain(_requests(arrivals), max_epochs=40)
+    for a, b in zip(served, plain):
+        assert a.epochs == b.epochs and a.reached and b.reached
+        np.testing.assert_array_equal(a.image, b.image)
 
 
 def test_admission_respects_the_memory_budget():
