@@ -58,6 +58,8 @@ enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG =
        PET_ALGO_SGA = 4, PET_ALGO_SEM = 5, PET_ALGO_SAGAEM = 6 };
 /* SAGA gradient-table storage (pet_state_create). */
 enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
+/* Preconditioner of SAGA and SVRG (pet_state_set_preconditioner). */
+enum { PET_PRECOND_CONSTANT = 0, PET_PRECOND_ITERATE = 1 };
 /* Potentials of the pairwise penalty (Table 1, t = f_n - f_j, delta > 0):
  * quadratic t^2/2; Huber t^2/2 for |t| <= delta else delta|t| - delta^2/2;
  * log cosh delta^2 log cosh(t/delta); hyperbola delta^2 (sqrt(1+(t/delta)^2) - 1)
@@ -237,6 +239,19 @@ pet_status pet_state_destroy(pet_state *state);
  * anchor), without allocating: a slot can serve a new reconstruction.
  * Enqueued on `stream`. */
 pet_status pet_state_reset(pet_state *state, void *stream);
+
+/* Preconditioner of a SAGA or SVRG state's updates (§4).
+ * PET_PRECOND_CONSTANT (the default): d = N_s f^(0) / A^T 1, frozen at the
+ *   state's starting image (§4: the remedy of freezing the preconditioner;
+ *   0 where A^T 1 = 0).
+ * PET_PRECOND_ITERATE: d_t(f^k) = f^k / A_t^T 1 of Eq. (preconditioners),
+ *   recomputed at every update from the current iterate and the subset's
+ *   sensitivity, as Eqs. (saga_update) and (svrg_update) print it (0 where
+ *   A_t^T 1 = 0).
+ * Takes effect from the next update; the SAGA table and the SVRG anchor are
+ * left as they are.  Returns PET_ERR_INVALID for another algorithm or kind.
+ * Host-side only (no stream work). */
+pet_status pet_state_set_preconditioner(pet_state *state, int32_t kind);
 
 /* n_iter updates (an epoch is n_iter = n_subsets) with subset indices
  * h_subset_seq[0..n_iter-1], each in [0, n_subsets).  The update counter k

@@ -307,6 +307,15 @@ def preconditioner(prob: Problem, f0):
     return np.where(pos, prob.Ns * f0 / np.where(pos, prob.sens, 1.0), 0.0)
 
 
+def subset_preconditioner(prob: Problem, f, t):
+    """Iteration- and subset-dependent d_t(f) = f / A_t^T 1 (0 where
+    A_t^T 1 = 0) (§4, Eq. (preconditioners)), the form Eqs. (saga_update) and
+    (svrg_update) print before the constant one is adopted."""
+    S = prob.sens_t[t]
+    pos = S > 0
+    return np.where(pos, f / np.where(pos, S, 1.0), 0.0)
+
+
 class SAGA:
     """Preconditioned proximal SAGA (§4, Eq. (saga_update), readings C6, C10):
 
@@ -315,10 +324,14 @@ class SAGA:
         q_t <- q_new
     The table starts at q_t = grad Phi_t(f^(0)) for every t.  With
     ``table="bf16"`` every stored table entry is rounded to bfloat16 (the mean
-    is taken over the rounded entries)."""
+    is taken over the rounded entries).  ``precond="constant"`` takes
+    d = d(f^(0)) (reading C13); ``precond="iterate"`` takes d_t(f^k) of
+    Eq. (preconditioners) at every update."""
 
-    def __init__(self, prob: Problem, f0, alpha: float, d=None, table="fp32"):
-        self.p, self.f, self.alpha = prob, f0.copy(), alpha
+    def __init__(self, prob: Problem, f0, alpha: float, d=None, table="fp32", precond="constant"):
+        if precond not in ("constant", "iterate"):
+            raise ValueError(precond)
+        self.p, self.f, self.alpha, self.precond = prob, f0.copy(), alpha, precond
         self.d = preconditioner(prob, f0) if d is None else d
         self.rnd = bf16_round if table == "bf16" else (lambda x: x)
         self.q = [self.rnd(prob.grad_Phi_t(self.f, t)) for t in range(prob.Ns)]
@@ -326,7 +339,8 @@ class SAGA:
     def step(self, t):
         q_new = self.rnd(self.p.grad_Phi_t(self.f, t))
         mean_old = sum(self.q) / self.p.Ns
-        self.f = np.maximum(self.f + self.alpha * self.d * (q_new - self.q[t] + mean_old), 0.0)
+        d = self.d if self.precond == "constant" else subset_preconditioner(self.p, self.f, t)
+        self.f = np.maximum(self.f + self.alpha * d * (q_new - self.q[t] + mean_old), 0.0)
         self.q[t] = q_new
         return self.f
 
@@ -336,10 +350,13 @@ class SVRG:
 
         if k mod eta*N_s == 0:  f_anc = f^k,  q_tilde = grad Phi(f_anc) / N_s
         f^{k+1} = P_{>=0}(f^k + alpha d . (grad Phi_t(f^k) - grad Phi_t(f_anc) + q_tilde))
-    """
+    ``precond`` as for SAGA: d(f^(0)) or d_t(f^k) at every update."""
 
-    def __init__(self, prob: Problem, f0, alpha: float, eta: int, d=None):
+    def __init__(self, prob: Problem, f0, alpha: float, eta: int, d=None, precond="constant"):
+        if precond not in ("constant", "iterate"):
+            raise ValueError(precond)
         self.p, self.f, self.alpha, self.eta, self.k = prob, f0.copy(), alpha, eta, 0
+        self.precond = precond
         self.d = preconditioner(prob, f0) if d is None else d
 
     def refresh_anchor(self):
@@ -351,7 +368,8 @@ class SVRG:
         if self.k % (self.eta * self.p.Ns) == 0:
             self.refresh_anchor()
         direction = self.p.grad_Phi_t(self.f, t) - self.g_anc[t] + self.q_tilde
-        self.f = np.maximum(self.f + self.alpha * self.d * direction, 0.0)
+        d = self.d if self.precond == "constant" else subset_preconditioner(self.p, self.f, t)
+        self.f = np.maximum(self.f + self.alpha * d * direction, 0.0)
         self.k += 1
         return self.f
 

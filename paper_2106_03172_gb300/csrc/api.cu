@@ -47,6 +47,14 @@ ProfileScope::~ProfileScope() {
     g_profile_records.push_back({kind, ev[0], ev[1]});
 }
 
+bool use_pdl() {
+    static const bool on = [] {
+        const char *e = std::getenv("PETVR_NO_PDL");
+        return !(e && e[0] && e[0] != '0');
+    }();
+    return on && !profiling_enabled();
+}
+
 pet_status check_launch(const char *what) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     const cudaError_t e = cudaGetLastError();
@@ -866,12 +874,12 @@ pet_status enqueue_update(pet_state *st, int algo, const int *t_dev, const float
         b.B = st->B;
     } else if (algo == PET_ALGO_SAGA) {
         epi = EPI_SAGA;
-        b.d = st->d;
+        b.d = st->precond == PET_PRECOND_ITERATE ? nullptr : st->d;
         b.table = st->table;
         b.qbar = st->qbar;
     } else if (algo == PET_ALGO_SVRG) {
         epi = EPI_SVRG;
-        b.d = st->d;
+        b.d = st->precond == PET_PRECOND_ITERATE ? nullptr : st->d;
         b.B = st->B;
         b.qtil = st->qtil;
     } else if (algo == PET_ALGO_SGA) {
@@ -1179,7 +1187,7 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.f_anc = st->f_anc;
     m.s_anc = st->s_anc;
     m.B = st->B;
-    m.d = st->d;
+    m.d = st->precond == PET_PRECOND_ITERATE ? nullptr : st->d;
     m.table = st->table;
     m.qbar = st->qbar;
     m.qtil = st->qtil;
@@ -1343,6 +1351,21 @@ pet_status pet_batch_objective_async(pet_batch *b, double *d_phi, void *stream) 
         PET_TRY(launch_batch_objective(b->d_members, b->d_idx + g.offset, g.count, g.value, blocks, 0, s));
     }
     return launch_batch_objective_finish(b->d_members, n, pen_blocks, s);
+}
+
+pet_status pet_state_set_preconditioner(pet_state *st, int32_t kind) {
+    if (!st) return set_error(PET_ERR_INVALID, "null state");
+    if (st->algo != PET_ALGO_SAGA && st->algo != PET_ALGO_SVRG)
+        return set_error(PET_ERR_INVALID, "the preconditioner choice applies to SAGA and SVRG states");
+    if (kind != PET_PRECOND_CONSTANT && kind != PET_PRECOND_ITERATE)
+        return set_error(PET_ERR_INVALID, "unknown preconditioner kind");
+    if (kind != st->precond) {
+        st->precond = kind;
+        // captured epochs hold the old preconditioner pointer
+        for (auto &g : st->graphs) cudaGraphExecDestroy(g.exec);
+        st->graphs.clear();
+    }
+    return PET_OK;
 }
 
 pet_status pet_state_reset(pet_state *st, void *stream) {

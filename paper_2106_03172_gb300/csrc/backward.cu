@@ -130,7 +130,8 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         } else {
             const float q_old = load_q<TQ>(a.table, qi);
             const float qb = a.qbar[i];
-            const float step = fmaf(alpha * a.d[i], q - q_old + qb, fk);
+            const float dn = a.d ? a.d[i] : (S > 0.0f ? fk / S : 0.0f);    // d(f^(0)) or d_t(f^k)
+            const float step = fmaf(alpha * dn, q - q_old + qb, fk);
             a.f_out[i] = fmaxf(step, 0.0f);
             a.qbar[i] = fmaf(q - q_old, inv_ns, qb);
             store_q<TQ>(a.table, qi, q);
@@ -141,7 +142,14 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float gradR = st.grad;
         const float Bt = a.B[(long long)t * plane + i];
         const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
-        a.f_out[i] = fmaxf(fmaf(alpha * a.d[i], dir, fk), 0.0f);
+        float dn;                                                   // d(f^(0)) or d_t(f^k)
+        if (a.d) {
+            dn = a.d[i];
+        } else {
+            const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+            dn = S > 0.0f ? fk / S : 0.0f;
+        }
+        a.f_out[i] = fmaxf(fmaf(alpha * dn, dir, fk), 0.0f);
     } else if (EPI == EPI_SGA) {
         const float fk = a.f[i];
         const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
@@ -293,6 +301,12 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
         }
         for (int e = threadIdx.x; e < nq * kTile * kTile; e += nthr) s_part[e] = 0.0f;
         __syncthreads();
+        if (q0 == 0) {
+            // the staging above read plan constants only; the ratios and the
+            // images below come from earlier kernels
+            pdl_wait();
+            pdl_trigger();
+        }
         for (int run = threadIdx.x; run < nq * kRunsPerView; run += nthr) {
             const int ql = run / kRunsPerView;
             const int rem = run - ql * kRunsPerView;
@@ -332,6 +346,7 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
             for (int ql = 0; ql < nq; ++ql) acc += s_part[ql * kTile * kTile + threadIdx.x];
         __syncthreads();
     }
+    pdl_wait();   // returns at once after the wait above; covers an empty subset
     if (threadIdx.x >= kTile * kTile) return;
     const int ix = x0 + (threadIdx.x % kTile);
     const int iy = y0 + (threadIdx.x / kTile);
@@ -417,10 +432,8 @@ pet_status go_impl(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views
         const int run = a.run == 4 ? 4 : 8;
         const int per_view = kTile * (kTile / run);
         const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
-        if (run == 4)
-            back_tile_kernel<EPI, TQ, 4, GENPOT><<<grid, threads, smem, s>>>(a);
-        else
-            back_tile_kernel<EPI, TQ, 8, GENPOT><<<grid, threads, smem, s>>>(a);
+        launch_dependent(run == 4 ? back_tile_kernel<EPI, TQ, 4, GENPOT> : back_tile_kernel<EPI, TQ, 8, GENPOT>,
+                         grid, dim3((unsigned)threads), smem, s, a);
         return check_launch("back_tile_kernel");
     }
     const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
@@ -447,17 +460,10 @@ pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int
     const int per_view = kTile * (kTile / run);
     const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
     const dim3 grid((unsigned)tiles, (unsigned)n_members);
-    if (general_potential) {
-        if (run == 4)
-            batch_back_kernel<4, true><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
-        else
-            batch_back_kernel<8, true><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
-    } else {
-        if (run == 4)
-            batch_back_kernel<4, false><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
-        else
-            batch_back_kernel<8, false><<<grid, threads, smem, s>>>(d_members, d_idx, iter, in_is_img);
-    }
+    void (*k)(const BatchMember *, const int *, int, int) =
+        general_potential ? (run == 4 ? batch_back_kernel<4, true> : batch_back_kernel<8, true>)
+                          : (run == 4 ? batch_back_kernel<4, false> : batch_back_kernel<8, false>);
+    launch_dependent(k, grid, dim3((unsigned)threads), smem, s, d_members, d_idx, iter, in_is_img);
     return check_launch("batch_back_kernel");
 }
 

@@ -156,43 +156,77 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
     const int ray_local = 8 * (warp / WPG) + r8;
     const long long ray = (long long)bx * RAYS + ray_local;
 
+    // the ray's geometry: plan constants only, so it may overlap the end of
+    // the kernel before this one
     float acc = 0.0f;
+    ViewParams vp{};
+    float2 u = make_float2(0.0f, 0.0f);
+    int kb = 0, ke = 0, n_minor = 0, ui = 0;
+    float hm = 0.0f;
     if (ray < n_rays) {
         const int p = rr.v_begin + (int)(ray / a.nb);
         const int j = (int)(ray % a.nb);
         const int v = __ldg(a.order + p);
-        const ViewParams vp = a.views[v];
-        const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
+        vp = a.views[v];
+        u = __ldg(a.uc + (long long)v * a.nb + j);
         const int n_major = vp.col ? a.nx : a.ny;
-        const int n_minor = vp.col ? a.ny : a.nx;
-        const int mo = n_minor >> 1;
-        const float hm = 0.5f * (float)n_major;
+        n_minor = vp.col ? a.ny : a.nx;
+        hm = 0.5f * (float)n_major;
+        ui = (int)u.x + (n_minor >> 1);
         int k_lo, k_hi;
         band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
         // chunks are aligned to the same bands for every ray of the view, so
         // neighbouring lanes read the same image rows
         const int per = (n_major + CHUNKS - 1) / CHUNKS;
-        const int kb = max(k_lo, chunk * per);
-        const int ke = min(k_hi, (chunk + 1) * per);
+        kb = max(k_lo, chunk * per);
+        ke = min(k_hi, (chunk + 1) * per);
+    }
+    pdl_wait();
+    pdl_trigger();
+    {
         if (kb < ke) {
             const int s_major = vp.col ? 1 : a.nx;
             const int s_minor = vp.col ? a.nx : 1;
-            const int ui = (int)u.x + mo;
-            const float *rowp = a.img + kb * s_major;
             float kc = (float)kb - hm;
             float va = band_point(vp, u.y, kc);
-#pragma unroll 2
-            for (int k = kb; k < ke; ++k) {
-                kc += 1.0f;
-                const float vb = band_point(vp, u.y, kc);
-                float fl, w0, w1;
-                band_split(vp, va, vb, fl, w0, w1);
-                const int m0 = (int)fl + ui;
-                if ((unsigned)m0 < (unsigned)n_minor) acc = fmaf(w0, __ldg(rowp + m0 * s_minor), acc);
-                if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor)
-                    acc = fmaf(w1, __ldg(rowp + (m0 + 1) * s_minor), acc);
-                va = vb;
-                rowp += s_major;
+            // kBatch bands at a time: all their pixel offsets and weights
+            // first, then the loads, then the FMAs in band order, so that the
+            // loads of a batch are in flight together.  A piece outside the
+            // image (or of a band past ke) is not loaded and adds 0 * 0,
+            // which leaves acc unchanged: the sum is the same as with the
+            // piece skipped.
+            constexpr int kBatch = 4;
+            for (int k = kb; k < ke; k += kBatch) {
+                int o0[kBatch], o1[kBatch];
+                float c0[kBatch], c1[kBatch];
+#pragma unroll
+                for (int b = 0; b < kBatch; ++b) {
+                    kc += 1.0f;
+                    const float vb = band_point(vp, u.y, kc);
+                    float fl, w0, w1;
+                    band_split(vp, va, vb, fl, w0, w1);
+                    const int m0 = (int)fl + ui;
+                    const bool live = k + b < ke;
+                    const bool ok0 = live && (unsigned)m0 < (unsigned)n_minor;
+                    const bool ok1 = live && w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor;
+                    const int row = (k + b) * s_major;
+                    o0[b] = ok0 ? row + m0 * s_minor : 0;
+                    o1[b] = ok1 ? row + (m0 + 1) * s_minor : 0;
+                    c0[b] = ok0 ? w0 : 0.0f;
+                    c1[b] = ok1 ? w1 : 0.0f;
+                    va = vb;
+                }
+                float x0[kBatch], x1[kBatch];
+#pragma unroll
+                for (int b = 0; b < kBatch; ++b) {
+                    x0[b] = c0[b] != 0.0f ? __ldg(a.img + o0[b]) : 0.0f;
+                    x1[b] = c1[b] != 0.0f ? __ldg(a.img + o1[b]) : 0.0f;
+                }
+#pragma unroll
+                for (int b = 0; b < kBatch; ++b) {
+                    acc = fmaf(c0[b], x0[b], acc);
+                    acc = fmaf(c1[b], x1[b], acc);
+                }
             }
         }
     }
@@ -326,16 +360,18 @@ pet_status dispatch_mode(const FwdArgs &a, int mode, bool ll, int blocks, cudaSt
 
 template <int CHUNKS>
 pet_status dispatch_tile(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    void (*k)(FwdArgs) = nullptr;
     if (mode == FWD_YHAT && !ll)
-        forward_tile_kernel<CHUNKS, FWD_YHAT, false><<<blocks, kBlock, 0, s>>>(a);
+        k = forward_tile_kernel<CHUNKS, FWD_YHAT, false>;
     else if (mode == FWD_RATIO && !ll)
-        forward_tile_kernel<CHUNKS, FWD_RATIO, false><<<blocks, kBlock, 0, s>>>(a);
+        k = forward_tile_kernel<CHUNKS, FWD_RATIO, false>;
     else if (mode == FWD_RATIO && ll)
-        forward_tile_kernel<CHUNKS, FWD_RATIO, true><<<blocks, kBlock, 0, s>>>(a);
+        k = forward_tile_kernel<CHUNKS, FWD_RATIO, true>;
     else if (mode == FWD_NONE && ll)
-        forward_tile_kernel<CHUNKS, FWD_NONE, true><<<blocks, kBlock, 0, s>>>(a);
+        k = forward_tile_kernel<CHUNKS, FWD_NONE, true>;
     else
         return set_error(PET_ERR_INVALID, "forward: unsupported mode");
+    launch_dependent(k, dim3((unsigned)blocks), dim3(kBlock), 0, s, a);
     return check_launch("forward_tile_kernel");
 }
 
@@ -352,12 +388,14 @@ pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, 
                                 int blocks, int iter, int in_is_img, cudaStream_t s) {
     if (n_members == 0 || blocks == 0) return PET_OK;
     const dim3 grid((unsigned)blocks, (unsigned)n_members);
+    void (*k)(const BatchMember *, const int *, int, int) = nullptr;
     switch (chunks) {
-        case 8: batch_forward_kernel<8><<<grid, kBlock, 0, s>>>(d_members, d_idx, iter, in_is_img); break;
-        case 16: batch_forward_kernel<16><<<grid, kBlock, 0, s>>>(d_members, d_idx, iter, in_is_img); break;
-        case 32: batch_forward_kernel<32><<<grid, kBlock, 0, s>>>(d_members, d_idx, iter, in_is_img); break;
+        case 8: k = batch_forward_kernel<8>; break;
+        case 16: k = batch_forward_kernel<16>; break;
+        case 32: k = batch_forward_kernel<32>; break;
         default: return set_error(PET_ERR_INVALID, "batch forward: unsupported chunk count");
     }
+    launch_dependent(k, grid, dim3(kBlock), 0, s, d_members, d_idx, iter, in_is_img);
     return check_launch("batch_forward_kernel");
 }
 

@@ -151,6 +151,38 @@ __device__ __forceinline__ float potential_rho(int pot, float delta, float t) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90 and later).  A projector launched
+// through launch_dependent() may start while the kernel before it on the
+// stream is still running: before pdl_wait() it reads only plan constants
+// (views, ray offsets, subset tables, the subset sequence), and pdl_wait()
+// blocks until that kernel has completed and its writes are visible.  Right
+// after its own wait it calls pdl_trigger(), so the next projector's blocks
+// can be scheduled and run their constant-only prologue; by then every
+// kernel before this one has completed, so whatever that prologue reads was
+// written before it started.  Launched the ordinary way, both are no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+bool use_pdl();   // false when PETVR_NO_PDL is set (or while per-launch profiling is on)
+
+template <typename... Params, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = use_pdl() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Kernel argument blocks.
 // ---------------------------------------------------------------------------
 enum FwdMode { FWD_NONE = 0, FWD_YHAT = 1, FWD_RATIO = 2 };
@@ -215,7 +247,7 @@ struct BackArgs {
     const float *f_anc;   // SVREM anchor image
     const float *s_anc;   // SVREM anchor statistic
     const float *B;       // SVREM/SVRG cached A_t^T r_t(f_anc), [ns][N*nz]
-    const float *d;       // SAGA/SVRG preconditioner
+    const float *d;       // SAGA/SVRG constant preconditioner; null: d_t(f^k) = f^k / sens_t
     void *table;          // SAGA table [ns][N*nz] (float or bf16)
     float *qbar;          // SAGA running mean of the table
     const float *qtil;    // SVRG full-gradient term
@@ -307,6 +339,7 @@ struct pet_state {
     float *B = nullptr, *d = nullptr, *qbar = nullptr, *qtil = nullptr;
     void *table = nullptr;
     long long k = 0;
+    int precond = PET_PRECOND_CONSTANT;   // SAGA / SVRG: d(f^(0)) or d_t(f^k)
     size_t bytes = 0;
     bool s_hat_ready = false;       // SVREM: s_hat initialised by the first anchor
     int *d_seq = nullptr;           // device copy of the current call's subset sequence

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libpetvr.so")
 
 ALGO = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3, "sga": 4, "sem": 5, "sagaem": 6}
 TABLE = {"fp32": 0, "bf16": 1}
+PRECOND = {"constant": 0, "iterate": 1}
 STATUS = {0: "PET_OK", 1: "PET_ERR_INVALID", 2: "PET_ERR_OOM", 3: "PET_ERR_CUDA",
           4: "PET_ERR_TIMEOUT", 5: "PET_ERR_NUMERIC", 6: "PET_ERR_STATE"}
 
@@ -72,6 +73,7 @@ _SIGS = {
                                    POINTER(c_void_p), c_void_p]),
     "pet_state_destroy": (c_int32, [c_void_p]),
     "pet_state_reset": (c_int32, [c_void_p, c_void_p]),
+    "pet_state_set_preconditioner": (c_int32, [c_void_p, c_int32]),
     "pet_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
     "pet_batch_destroy": (c_int32, [c_void_p]),
     "pet_batch_set_graphs": (c_int32, [c_void_p, c_int32]),
@@ -257,6 +259,11 @@ def pet_state_reset(state, stream=None):
     _call("pet_state_reset", state, _stream(stream))
 
 
+def pet_state_set_preconditioner(state, kind: str):
+    """``"constant"``: d = N_s f^(0) / A^T 1; ``"iterate"``: d_t(f^k) = f^k / A_t^T 1."""
+    _call("pet_state_set_preconditioner", state, PRECOND[kind])
+
+
 def pet_osem_epoch(state, seq, stream=None):
     arr, n = _seq(seq)
     _call("pet_osem_epoch", state, arr, n, _stream(stream))
@@ -429,6 +436,9 @@ class State:
 
     def reset(self, stream=None):
         pet_state_reset(self.handle, stream)
+
+    def set_preconditioner(self, kind: str):
+        pet_state_set_preconditioner(self.handle, kind)
 
     def objective_async(self, phi_out, stream=None):
         pet_state_objective_async(self.handle, phi_out, stream)

@@ -392,6 +392,38 @@ def test_non_vr_baseline_updates(case, method, alpha0, decay):
     assert _host(img).min() >= 0.0
 
 
+@pytest.mark.parametrize("method", ["saga", "svrg"])
+def test_iterate_preconditioner_updates(case, method):
+    """SAGA and SVRG with d_t(f^k) = f^k / A_t^T 1 recomputed at every update
+    (§4, Eq. (preconditioners)), against the oracle's same variant; then a
+    switch back to the constant d(f^(0)) at an epoch boundary."""
+    pv, prob, data, work, plan = case
+    gp = _gpu_problem(pv, plan, data, work)
+    f0 = prob.initial_image().astype(np.float32).astype(np.float64)
+    img = _cuda(f0)
+    state = pv.State(gp, method, img)
+    state.set_preconditioner("iterate")
+    alpha = 1.0
+    alg = (em.SAGA(prob, f0, alpha, precond="iterate") if method == "saga"
+           else em.SVRG(prob, f0, alpha, work.eta_svrg, precond="iterate"))
+    seq = subset_sequence(4200, work.n_subsets, 2 * work.n_subsets)
+    for k, t in enumerate(seq):
+        state.epoch([int(t)], alpha=alpha, eta=work.eta_svrg)
+        f = alg.step(int(t))
+        err = rel_l2(_host(img), f)
+        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+    # back to the constant preconditioner of the starting image for one epoch
+    state.set_preconditioner("constant")
+    alg.precond = "constant"
+    state.epoch(seq[:work.n_subsets], alpha=alpha, eta=work.eta_svrg)
+    for t in seq[:work.n_subsets]:
+        f = alg.step(int(t))
+    assert rel_l2(_host(img), f) <= 1e-4
+    assert _host(img).min() >= 0.0
+    with pytest.raises(pv.PetError):
+        pv.State(gp, "osem", _cuda(f0)).set_preconditioner("iterate")
+
+
 def test_sagaem_updates(case):
     """SAGA on the EM statistic (§2.3 remark) against the oracle."""
     pv, prob, data, work, plan = case

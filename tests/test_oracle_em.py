@@ -287,6 +287,9 @@ def test_kkt_point_is_fixed_point_of_vr_methods(prob_and_data, map_solution):
         assert np.linalg.norm(saga.step(t) - fs) / scale < 1e-6
         svrg = em.SVRG(prob, fs, alpha=2.0, eta=2, d=d)
         assert np.linalg.norm(svrg.step(t) - fs) / scale < 1e-6
+        for pre in (em.SAGA(prob, fs, alpha=1.0, precond="iterate"),
+                    em.SVRG(prob, fs, alpha=1.0, eta=2, precond="iterate")):
+            assert np.linalg.norm(pre.step(t) - fs) / scale < 1e-6
         svrem = em.SVREM(prob, fs, alpha=0.7, eta=1)
         assert np.linalg.norm(svrem.step(t) - fs) / scale < 1e-6
     assert np.linalg.norm(em.osem_step(prob, fs, 0) - fs) / scale > 1e-4
@@ -324,6 +327,28 @@ def test_sga_at_beta_zero_is_osem():
     for t in (0, 2, 1, 1):
         want = em.osem_step(p, alg.f, t)
         np.testing.assert_allclose(alg.step(t), want, rtol=1e-12, atol=1e-14)
+
+
+def test_iterate_preconditioned_vr_single_subset_is_mlem():
+    """§4, Eqs. (saga_update), (svrg_update) with d_t(f^k) of Eq.
+    (preconditioners): with one subset, beta = 0 and alpha = 1 the table
+    correction (SAGA) and the anchor correction (SVRG) cancel, and the step is
+    f + (f / A^T 1) grad L(f), which is MLEM (§2.2).  The constant
+    preconditioner d(f^(0)) gives a different step."""
+    geom = Geometry(12, 12, 18, 17)
+    p1, _ = tiny_problem(geom, seed=21, n_subsets=1, beta=0.0)
+    f = p1.uniform_image()
+    saga = em.SAGA(p1, f, alpha=1.0, precond="iterate")
+    svrg = em.SVRG(p1, f, alpha=1.0, eta=1, precond="iterate")
+    for _ in range(4):
+        want = em.mlem_step(p1, f)
+        np.testing.assert_allclose(saga.step(0), want, rtol=1e-11, atol=1e-13)
+        np.testing.assert_allclose(svrg.step(0), want, rtol=1e-11, atol=1e-13)
+        f = want
+    const = em.SAGA(p1, p1.uniform_image(), alpha=1.0)
+    const.step(0)
+    const.step(0)
+    assert np.abs(const.step(0) - saga.f).max() > 1e-6 * np.abs(saga.f).max()
 
 
 def test_sem_full_step_single_subset_is_map_em():
