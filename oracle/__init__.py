@@ -12,6 +12,8 @@ Layout of the oracle:
   geometry.py  view angles, bin centres (the parallel-beam geometry)
   siddon.py    explicit sparse system matrix by classical Siddon ray tracing,
                and a brute-force per-pixel line clipper used to pin it
+  siddon3d.py  the same for a multi-ring scanner's oblique lines of response
+               through a voxel volume, with a per-voxel 3-D clipper
   subsets.py   angle-interleaved ordered-subset partition (§2.1)
   penalty.py   pairwise penalty, potentials of Table 1, parabolic surrogate
                and the closed-form M-step root (§3)
@@ -21,7 +23,9 @@ Layout of the oracle:
 
 Every image is a float64 array of shape (N, nz) with N = nx*ny pixels in
 row-major [iy][ix] order and nz independent slices; every sinogram is
-(M, nz) with M = n_angles*n_bins rays in [view][bin] order.
+(M, nz) with M = n_angles*n_bins rays in [view][bin] order.  A multi-ring
+volume is one column (nx*ny*nz, 1) in [iy][ix][iz] order, its sinogram one
+column in [view][bin][ring pair] order.
 
 Parity status of each function is stated in its docstring; the conventions the
 paper leaves open (tie-break of rays lying on grid lines, subset sensitivity in

@@ -54,7 +54,7 @@ class Problem:
     Eq. (PET-MAP)) with its subset split (§2.1, Eq. (subobjective))."""
 
     def __init__(self, A: sp.csr_matrix, g, w, subsets, beta: float, nx: int, ny: int,
-                 nz: int = 1, potential="quadratic", delta=1.0):
+                 nz: int = 1, potential="quadratic", delta=1.0, axial: int = 1):
         self.A = A.tocsr()
         self.M, self.N = A.shape
         self.nz = nz
@@ -64,7 +64,7 @@ class Problem:
         self.subsets = [np.asarray(r) for r in subsets]
         self.Ns = len(self.subsets)
         self.beta = float(beta)
-        self.pen = Penalty(nx, ny, potential, delta)
+        self.pen = Penalty(nx, ny, potential, delta, axial)
         self.At = [self.A[r] for r in self.subsets]
         self.gt = [self.g[r] for r in self.subsets]
         self.wt = [self.w[r] for r in self.subsets]
@@ -391,12 +391,24 @@ def svrem_direction_appendix_b(prob: Problem, f, f_anc, t):
 
 def build_problem(geom, g, w, n_subsets, beta, potential="quadratic", delta=1.0, A=None):
     """Problem for a geometry object with fields nx, ny, nz, n_angles, n_bins,
-    pixel_mm and ds (A is built by Siddon unless given)."""
-    from .siddon import system_matrix
+    pixel_mm and ds (A is built by Siddon unless given).  A multi-ring
+    geometry (n_rings > 0) gives one volume problem: A from the 3-D Siddon
+    matrix, the image a column of nx ny nz voxels (axial index innermost),
+    the sinogram a column in [view][bin][ring pair] order, subsets by view
+    (every bin and ring pair of a view) and the 6-neighbourhood penalty."""
     from .subsets import subset_rows
+    rows = subset_rows(geom.n_angles, geom.n_bins, n_subsets)
+    if getattr(geom, "n_rings", 0) > 0:
+        from .siddon3d import system_matrix3d
+        if A is None:
+            A = system_matrix3d(geom)
+        npairs = geom.n_rings ** 2
+        rows = [(r[:, None] * npairs + np.arange(npairs)[None, :]).ravel() for r in rows]
+        return Problem(A, np.asarray(g).reshape(-1, 1), w, rows, beta, geom.nx, geom.ny, 1,
+                       potential, delta, axial=geom.nz)
+    from .siddon import system_matrix
     if A is None:
         A = system_matrix(geom)
-    rows = subset_rows(geom.n_angles, geom.n_bins, n_subsets)
     return Problem(A, np.asarray(g).reshape(geom.n_rays, geom.nz), w, rows, beta,
                    geom.nx, geom.ny, geom.nz, potential, delta)
 

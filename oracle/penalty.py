@@ -2,7 +2,9 @@
 
 R(f) = 1/2 sum_n sum_{j in N_n} w_nj rho(f_n - f_j)            (§3, penalty)
 with N_n the 4-neighbourhood of pixel n inside the image (out-of-image
-neighbours are dropped, slices are not coupled) and w_nj = 1.
+neighbours are dropped, slices of a stack are not coupled) and w_nj = 1; a
+multi-ring volume uses the 6-neighbourhood (its axial neighbours added, also
+with w_nj = 1).
 
 Potentials rho, rho' and the curvature gamma = rho'(t)/t follow Table 1
 (quadratic, Huber, log cosh, hyperbola); the hyperbola's printed rho lacks a
@@ -88,29 +90,37 @@ def gamma(t, potential="quadratic", delta=1.0):
     raise ValueError(potential)
 
 
-def neighbour_pairs(nx: int, ny: int):
-    """Ordered pairs (n, j), j in the in-image 4-neighbourhood of n."""
-    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
-    n = (iy * nx + ix).ravel()
-    iy, ix = iy.ravel(), ix.ravel()
+def neighbour_pairs(nx: int, ny: int, axial: int = 1):
+    """Ordered pairs (n, j), j in the in-image 4-neighbourhood of n; with
+    axial > 1 the image is a volume of `axial` layers (index
+    (iy nx + ix) axial + iz) and the neighbourhood its in-volume
+    6-neighbourhood (the two axial neighbours added, weight 1)."""
+    iy, ix, iz = np.meshgrid(np.arange(ny), np.arange(nx), np.arange(axial), indexing="ij")
+    n = ((iy * nx + ix) * axial + iz).ravel()
+    iy, ix, iz = iy.ravel(), ix.ravel(), iz.ravel()
+    steps = [(0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)]
+    if axial > 1:
+        steps += [(0, 0, -1), (0, 0, 1)]
     src, dst = [], []
-    for dy, dx in ((0, -1), (0, 1), (-1, 0), (1, 0)):
-        jy, jx = iy + dy, ix + dx
-        ok = (jy >= 0) & (jy < ny) & (jx >= 0) & (jx < nx)
+    for dy, dx, dz in steps:
+        jy, jx, jz = iy + dy, ix + dx, iz + dz
+        ok = (jy >= 0) & (jy < ny) & (jx >= 0) & (jx < nx) & (jz >= 0) & (jz < axial)
         src.append(n[ok])
-        dst.append((jy * nx + jx)[ok])
+        dst.append(((jy * nx + jx) * axial + jz)[ok])
     return np.concatenate(src), np.concatenate(dst)
 
 
 class Penalty:
-    """R, its gradient and surrogate weights on images of shape (N, nz)."""
+    """R, its gradient and surrogate weights on images of shape (N, nz)
+    (nz independent slices), or with axial > 1 on volumes of shape
+    (N * axial, 1) coupled along z as well."""
 
-    def __init__(self, nx: int, ny: int, potential="quadratic", delta=1.0):
+    def __init__(self, nx: int, ny: int, potential="quadratic", delta=1.0, axial: int = 1):
         if potential not in POTENTIALS:
             raise ValueError(potential)
-        self.nx, self.ny = nx, ny
+        self.nx, self.ny, self.axial = nx, ny, axial
         self.potential, self.delta = potential, delta
-        self.src, self.dst = neighbour_pairs(nx, ny)
+        self.src, self.dst = neighbour_pairs(nx, ny, axial)
 
     def value(self, f):
         """R(f) per slice, shape (nz,)."""

@@ -28,20 +28,27 @@ import numpy as np
 
 __all__ = [
     "Geometry", "Workload", "WORKLOADS", "Ellipse", "random_ellipse_phantom",
-    "ellipsoid_stack_phantom", "rasterise", "analytic_sinogram", "make_data",
+    "ellipsoid_stack_phantom", "ellipsoid_solids", "rasterise", "analytic_sinogram",
+    "analytic_lor_sinogram", "rasterise_volume", "make_data",
     "splitmix64", "subset_sequence", "batched_workloads", "serving_workloads", "serving_pool",
 ]
 
 
 @dataclass(frozen=True)
 class Geometry:
-    """2-D parallel-beam geometry, optionally with ``nz`` independent slices.
+    """2-D parallel-beam geometry, optionally with ``nz`` independent slices,
+    or (``n_rings`` > 0) a multi-ring scanner with fully 3-D lines of response.
 
     Image: ``nx`` x ``ny`` square pixels of side ``pixel_mm`` centred on the
-    origin, stored row-major ``[iy][ix]`` (slice index innermost when nz > 1).
-    Sinogram: ``n_angles`` views at ``theta_i = i*pi/n_angles`` and
+    origin, stored row-major ``[iy][ix]`` (slice / axial index innermost when
+    nz > 1).  Sinogram: ``n_angles`` views at ``theta_i = i*pi/n_angles`` and
     ``n_bins`` radial bins centred on the origin with spacing ``bin_mm``,
     stored ``[view][bin]`` (slice index innermost when nz > 1).
+
+    Multi-ring mode: the nz image layers are ``slice_mm`` thick and centred
+    on z = 0; ``n_rings`` rings ``ring_mm`` apart (centred on z = 0) sit on a
+    cylinder of radius ``radius_mm``; the sinogram is ``[view][bin][pair]``
+    with one line of response per ordered ring pair, pair = r1 n_rings + r2.
     """
 
     nx: int
@@ -51,6 +58,19 @@ class Geometry:
     pixel_mm: float = 2.0
     bin_mm: float | None = None
     nz: int = 1
+    n_rings: int = 0
+    ring_mm: float = 0.0
+    radius_mm: float = 0.0
+    slice_mm: float = 0.0
+
+    @property
+    def multiring(self) -> bool:
+        return self.n_rings > 0
+
+    @property
+    def n_pairs(self) -> int:
+        """Sinogram entries per (view, bin): ring pairs, or slices of a stack."""
+        return self.n_rings * self.n_rings if self.multiring else self.nz
 
     @property
     def ds(self) -> float:
@@ -167,15 +187,13 @@ def random_ellipse_phantom(geom: Geometry, seed: int, n_ellipses: int,
     return out
 
 
-def ellipsoid_stack_phantom(geom: Geometry, seed: int, n_ellipsoids: int) -> list:
-    """Per-slice ellipse lists of a random ellipsoid phantom sampled at the
-    ``nz`` slice centres (slice thickness = pixel size).  Each slice of an
-    ellipsoid with semi-axes (a, b, c) at height dz from its centre is the
-    ellipse with semi-axes scaled by sqrt(1 - (dz/c)^2)."""
+def ellipsoid_solids(geom: Geometry, seed: int, n_ellipsoids: int, zhalf: float, body_c: float = 1.05) -> list:
+    """Random ellipsoids (cx, cy, cz, a, b, c, phi, value), rotated by phi about
+    z: a body of activity 1 with axial semi-axis ``body_c * zhalf`` plus
+    ``n_ellipsoids`` inner ones adding U[0.5, 4]."""
     rng = np.random.default_rng(seed)
     half = 0.5 * min(geom.nx, geom.ny) * geom.pixel_mm
-    zhalf = 0.5 * geom.nz * geom.pixel_mm
-    solids = [(0.0, 0.0, 0.0, 0.85 * half, 0.66 * half, 1.05 * zhalf, 0.0, 1.0)]
+    solids = [(0.0, 0.0, 0.0, 0.85 * half, 0.66 * half, body_c * zhalf, 0.0, 1.0)]
     for _ in range(n_ellipsoids):
         r = math.sqrt(rng.uniform(0.0, 1.0)) * 0.55
         ang = rng.uniform(0.0, 2.0 * math.pi)
@@ -183,6 +201,15 @@ def ellipsoid_stack_phantom(geom: Geometry, seed: int, n_ellipsoids: int) -> lis
                        rng.uniform(-0.5, 0.5) * zhalf, half * rng.uniform(0.05, 0.2),
                        half * rng.uniform(0.05, 0.2), zhalf * rng.uniform(0.2, 0.6),
                        rng.uniform(0.0, math.pi), rng.uniform(0.5, 4.0)))
+    return solids
+
+
+def ellipsoid_stack_phantom(geom: Geometry, seed: int, n_ellipsoids: int) -> list:
+    """Per-slice ellipse lists of a random ellipsoid phantom sampled at the
+    ``nz`` slice centres (slice thickness = pixel size).  Each slice of an
+    ellipsoid with semi-axes (a, b, c) at height dz from its centre is the
+    ellipse with semi-axes scaled by sqrt(1 - (dz/c)^2)."""
+    solids = ellipsoid_solids(geom, seed, n_ellipsoids, 0.5 * geom.nz * geom.pixel_mm)
     slices = []
     for k in range(geom.nz):
         z = (k - 0.5 * (geom.nz - 1)) * geom.pixel_mm
@@ -231,17 +258,80 @@ def analytic_sinogram(ellipses, geom: Geometry) -> np.ndarray:
     return out
 
 
+def _ring_positions(geom: Geometry) -> np.ndarray:
+    return (np.arange(geom.n_rings) - 0.5 * (geom.n_rings - 1)) * geom.ring_mm
+
+
+def analytic_lor_sinogram(solids, geom: Geometry) -> np.ndarray:
+    """Closed-form line integrals of the continuous ellipsoid phantom along
+    the multi-ring lines of response, ``[view][bin][pair]`` float64.
+
+    Line (i, j, r1, r2): p(t) = (s_j cos th_i, s_j sin th_i, zm) + t (-sin th_i,
+    cos th_i, kappa), zm = (z_r1 + z_r2)/2, kappa = (z_r2 - z_r1) / (2T),
+    T = sqrt(R^2 - s_j^2) (ring r1 at t = -T, ring r2 at t = +T on the
+    cylinder of radius R).  For an ellipsoid x'^T D x' <= 1 (x' the point
+    relative to the centre, rotated by -phi about z) the chord in t solves
+    A t^2 + 2 B t + C = 0; its length is 2 sqrt(B^2 - A C) / A times
+    sqrt(1 + kappa^2)."""
+    th = np.arange(geom.n_angles) * (math.pi / geom.n_angles)
+    s = (np.arange(geom.n_bins) - 0.5 * (geom.n_bins - 1)) * geom.ds
+    zr = _ring_positions(geom)
+    T = np.sqrt(geom.radius_mm ** 2 - s ** 2)
+    out = np.zeros((geom.n_angles, geom.n_bins, geom.n_rings, geom.n_rings))
+    c, sn = np.cos(th)[:, None], np.sin(th)[:, None]
+    for r1 in range(geom.n_rings):
+        for r2 in range(geom.n_rings):
+            kappa = ((zr[r2] - zr[r1]) / (2.0 * T))[None, :]
+            zm = 0.5 * (zr[r1] + zr[r2])
+            stretch = np.sqrt(1.0 + kappa * kappa)
+            for (cx, cy, cz, a, b, cc, phi, val) in solids:
+                cp, sp = math.cos(phi), math.sin(phi)
+                px, py, pz = s[None, :] * c - cx, s[None, :] * sn - cy, zm - cz
+                ux, uy = -sn, c
+                # rotate into the ellipsoid's frame
+                qx, qy = px * cp + py * sp, -px * sp + py * cp
+                vx, vy = ux * cp + uy * sp, -ux * sp + uy * cp
+                A = (vx / a) ** 2 + (vy / b) ** 2 + (kappa / cc) ** 2
+                B = qx * vx / a ** 2 + qy * vy / b ** 2 + pz * kappa / cc ** 2
+                C = (qx / a) ** 2 + (qy / b) ** 2 + (pz / cc) ** 2 - 1.0
+                disc = B * B - A * C
+                chord = np.where(disc > 0.0, 2.0 * np.sqrt(np.maximum(disc, 0.0)) / A, 0.0)
+                out[:, :, r1, r2] += val * chord * stretch
+    return out.reshape(geom.n_angles, geom.n_bins, geom.n_rings * geom.n_rings)
+
+
+def rasterise_volume(solids, geom: Geometry) -> np.ndarray:
+    """Sample the ellipsoid phantom at voxel centres, ``[iy][ix][iz]`` float64."""
+    xs = (np.arange(geom.nx) - 0.5 * (geom.nx - 1)) * geom.pixel_mm
+    ys = (np.arange(geom.ny) - 0.5 * (geom.ny - 1)) * geom.pixel_mm
+    zs = (np.arange(geom.nz) - 0.5 * (geom.nz - 1)) * geom.slice_mm
+    Y, X, Z = np.meshgrid(ys, xs, zs, indexing="ij")
+    vol = np.zeros((geom.ny, geom.nx, geom.nz))
+    for (cx, cy, cz, a, b, cc, phi, val) in solids:
+        cp, sp = math.cos(phi), math.sin(phi)
+        xr = (X - cx) * cp + (Y - cy) * sp
+        yr = -(X - cx) * sp + (Y - cy) * cp
+        vol += val * (((xr / a) ** 2 + (yr / b) ** 2 + ((Z - cz) / cc) ** 2) <= 1.0)
+    return vol
+
+
 def make_data(work: Workload, seed: int):
     """Phantom ``seed`` and Poisson data with noise seed ``seed + 1000``.
 
     Returns a dict with
-      ``g``      float32 counts, ``[view][bin]`` (``[view][bin][z]`` for stacks);
+      ``g``      float32 counts, ``[view][bin]`` (``[view][bin][z]`` for stacks,
+                 ``[view][bin][ring pair]`` for multi-ring scanners);
       ``w``      float background per bin (uniform: ``bg_frac`` x mean trues);
       ``x_true`` float64 scaled reference image ``[iy][ix]`` (``[iy][ix][z]``);
       ``scale``  the activity scale that makes the expected trues sum to ``counts``.
     """
     geom = work.geometry
-    if work.stack:
+    if geom.multiring:
+        # the body stays inside the axial field of view (no activity the image cannot hold)
+        solids = ellipsoid_solids(geom, seed, work.n_ellipses, 0.5 * geom.nz * geom.slice_mm, body_c=0.9)
+        sino = analytic_lor_sinogram(solids, geom)
+        img = rasterise_volume(solids, geom)
+    elif work.stack:
         per_slice = ellipsoid_stack_phantom(geom, seed, work.n_ellipses)
         sino = np.stack([analytic_sinogram(e, geom) for e in per_slice], axis=-1)
         img = np.stack([rasterise(e, geom) for e in per_slice], axis=-1)
