@@ -63,7 +63,12 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=1000, help="serve workload: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
     ap.add_argument("--budget-gib", type=float, default=1.0, help="serve workload: device-memory budget")
-    ap.add_argument("--window", type=int, default=4, help="serve workload: ticks per host round trip")
+    ap.add_argument("--window", type=int, default=4, help="serve workload, batch server: ticks per host round trip")
+    ap.add_argument("--max-epochs", type=int, default=200,
+                    help="serve workload: epochs after which a request stops without reaching the gap")
+    ap.add_argument("--depth", type=int, default=2, help="serve workload, stream server: epochs in flight per request")
+    ap.add_argument("--server", choices=["streams", "batch"], default="streams",
+                    help="serve workload: the server the headline value is taken from (the other is reported too)")
     ap.add_argument("--batch", dest="batch", action="store_true",
                     help="run the four methods as one batch (one launch per phase) instead of four streams")
     return ap.parse_args()
@@ -674,6 +679,14 @@ def run_batch64(args):
     return 0
 
 
+def _server_stats(srv):
+    st = srv.stats
+    return {"max_active": st.max_active, "admissions_deferred": st.admissions_deferred,
+            "peak_bytes": st.peak_bytes, "slots_created": st.slots_created, "slots_reused": st.slots_reused,
+            "slots_released": st.slots_released, "ticks": st.ticks, "batches_built": st.batches_built,
+            "epochs_launched": st.epochs_launched}
+
+
 def run_serve(args):
     """Serving: an open-loop Poisson stream of SVREM/SAGA requests, image size
     uniform over the request templates' sizes (128^2 to 512^2, 1e6-1e8 counts,
@@ -688,7 +701,8 @@ def run_serve(args):
     from paper_2106_03172_gb300 import build as _build
     from paper_2106_03172_gb300 import petvr
     from paper_2106_03172_gb300.phantoms import make_data, serving_pool
-    from paper_2106_03172_gb300.serving import Request, Server, latency_summary, serve_plain
+    from paper_2106_03172_gb300.serving import (Request, Server, StreamServer, latency_summary, per_template,
+                                                serve_plain)
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     _build.build()
@@ -720,41 +734,55 @@ def run_serve(args):
         return [Request(i, pool[k][0], pool[k][1]["g"], pool[k][1]["w"], pool[k][2], arrival=float(t),
                         seed=5000 + i) for i, (t, k) in enumerate(zip(arrivals, picks))]
 
-    srv = Server(budget_bytes=int(args.budget_gib * (1 << 30)), max_slots=64, gap=GAP, max_epochs=60, tick=3,
-                 window=args.window)
-    srv.prepare([w for w, _, _ in pool])
-    clocks = ClockSampler(visible_index(torch))
-    launches0 = petvr.pet_kernel_launches()
-    clocks.start()
-    done = srv.serve(requests())
-    clk = clocks.stop()
-    launches = petvr.pet_kernel_launches() - launches0
+    budget = int(args.budget_gib * (1 << 30))
+    me = args.max_epochs
+    servers = {"streams": lambda: StreamServer(budget_bytes=budget, max_slots=64, gap=GAP, max_epochs=me,
+                                               depth=args.depth),
+               "batch": lambda: Server(budget_bytes=budget, max_slots=64, gap=GAP, max_epochs=me, tick=3,
+                                       window=args.window)}
+    order = [args.server] + [k for k in servers if k != args.server]
+    runs = {}
+    for kind in order:
+        srv = servers[kind]()
+        srv.prepare([w for w, _, _ in pool])
+        clocks = ClockSampler(visible_index(torch))
+        launches0 = petvr.pet_kernel_launches()
+        clocks.start()
+        done = srv.serve(requests())
+        clk = clocks.stop()
+        runs[kind] = (srv, done, clk, petvr.pet_kernel_launches() - launches0)
+        del srv
+    srv, done, clk, launches = runs[args.server]
     summ = latency_summary(done)
     # the same stream through the plain per-reconstruction path, one request at a time
-    plain = serve_plain(requests(), gap=GAP, max_epochs=60)
+    plain = serve_plain(requests(), gap=GAP, max_epochs=args.max_epochs)
     plain_summ = latency_summary(plain)
-    same = all(a.epochs == b.epochs and np.array_equal(a.image, b.image) for a, b in zip(done, plain))
+    same = all(a.epochs == b.epochs and np.array_equal(a.image, b.image)
+               for _, d, _, _ in runs.values() for a, b in zip(d, plain))
     sizes = sorted({w.geometry.nx for w, _, _ in pool})
+    other = [k for k in order if k != args.server][0]
+    o_srv, o_done, _, _ = runs[other]
     line = {
         "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
-        "value": summ["recon_per_s"], "unit": "reconstructions/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
+        "value": summ["reached_per_s"], "unit": "reconstructions/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
         "ms_per_step": summ["p50_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (bf16 SAGA tables)", "data": "synthetic (seeded ellipse phantoms, Poisson counts)",
         "config": {"workload": f"serve: {n_req} requests, Poisson arrivals at {args.rate:g}/s, templates "
                                f"{', '.join(w.name for w, _, _ in pool)} "
                                f"({'/'.join(f'{n}^2' for n in sizes)}, SVREM/SAGA), "
                                f"stop at relative gap {GAP:g} against the oracle's Phi*",
-                   "budget_gib": args.budget_gib, "max_slots": 64, "tick_updates": 3, "window_ticks": args.window,
+                   "server": args.server, "budget_gib": args.budget_gib, "max_slots": 64, "max_epochs": me,
+                   "streams_depth_epochs": args.depth, "batch_tick_updates": 3, "batch_window_ticks": args.window,
                    "templates_without_phi_star": skipped},
         "latency": summ, "gpu_launches": int(launches), "clocks": clk,
         "plain": {"latency": plain_summ, "how": "the same requests one at a time in arrival order, each "
                   "through its own State epochs (captured graphs), objective after every epoch"},
-        "speedup_vs_plain": summ["recon_per_s"] / plain_summ["recon_per_s"],
+        "per_template": per_template(done),
+        "speedup_vs_plain": summ["reached_per_s"] / plain_summ["reached_per_s"],
+        "p50_speedup_vs_plain": plain_summ["p50_ms"] / summ["p50_ms"],
         "bit_identical_to_plain": bool(same),
-        "server": {"ticks": srv.stats.ticks, "max_active": srv.stats.max_active,
-                   "mean_active": srv.stats.active_sum / max(1, srv.stats.ticks),
-                   "admissions_deferred": srv.stats.admissions_deferred,
-                   "batches_built": srv.stats.batches_built, "peak_bytes": srv.stats.peak_bytes},
+        "server_stats": _server_stats(srv),
+        "other_server": {"server": other, "latency": latency_summary(o_done), "stats": _server_stats(o_srv)},
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -175,7 +175,9 @@ void pet_problem_destroy(pet_problem *problem);
 /* Replace the counts (and background) of an existing problem in place, with
  * the same layouts and rules as pet_problem_create; nothing is allocated.
  * d_bg must be non-NULL exactly when the problem was created with a
- * background sinogram. */
+ * background sinogram.  States of this problem keep working: a new scalar
+ * background makes them re-capture their cached epoch graphs at their next
+ * call (new counts need no re-capture). */
 pet_status pet_problem_update(pet_problem *problem, const float *d_counts, const float *d_bg, float bg,
                               void *stream);
 

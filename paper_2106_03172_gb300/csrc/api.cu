@@ -698,7 +698,10 @@ pet_status pet_problem_update(pet_problem *p, const float *d_counts, const float
     if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
     const pet_plan *pl = p->plan;
     cudaStream_t s = (cudaStream_t)stream;
-    p->w_scalar = bg;
+    if (bg != p->w_scalar) {        // counts are read through pointers; the scalar is captured by value
+        p->w_scalar = bg;
+        ++p->version;
+    }
     PET_TRY(launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, pl->nz, s));
     if (d_bg) PET_TRY(launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, pl->nz, s));
     return PET_OK;
@@ -947,6 +950,13 @@ bool use_graphs() {
 // graph under `key`, and launch it on `s`.
 template <class Enqueue>
 pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_t s, Enqueue &&enqueue) {
+    if (st->prob && st->graph_version != st->prob->version) {
+        // the problem's data changed since these were captured (kernel
+        // arguments such as the scalar background are baked into a graph)
+        for (auto &g : st->graphs) cudaGraphExecDestroy(g.exec);
+        st->graphs.clear();
+        st->graph_version = st->prob->version;
+    }
     pet_state::Graph *hit = nullptr;
     for (auto &g : st->graphs)
         if (g.key == key) hit = &g;

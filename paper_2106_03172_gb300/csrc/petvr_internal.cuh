@@ -324,6 +324,7 @@ struct pet_problem {
     int n_part = 0;
     double *d_scalar = nullptr;     // [4 + nz] reduction results
     int *d_status = nullptr;        // device error latch
+    uint64_t version = 0;           // bumped by pet_problem_update (graphs hold w_scalar by value)
 };
 
 struct pet_batch;
@@ -354,6 +355,7 @@ struct pet_state {
         uint64_t kernels;           // kernel nodes, counted at capture
     };
     std::vector<Graph> graphs;      // captured epochs / objectives
+    uint64_t graph_version = 0;     // problem version the captured graphs were made with
 };
 
 struct pet_batch {

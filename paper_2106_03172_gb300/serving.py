@@ -1,33 +1,47 @@
-"""Continuous-batching reconstruction server: a host scheduler over the C ABI.
+"""Continuous-batching reconstruction servers: host schedulers over the C ABI.
 
 Requests (a geometry, counts, a method and a target objective Phi*) arrive
-over time.  The server admits a request as soon as it has arrived and both a
-slot and device memory are free: its budget counts the plan (shared by every
-request of the same geometry and subset count), the problem and the state
-bytes the library reports, SAGA's gradient table included.  All admitted
-requests advance together: every tick runs `tick` updates of every active
-state in one batched launch per phase (pet_batch_epoch), so requests that
-arrive while others run join the next tick and their work shares the
-kernels.  At the end of each of its epochs a request's objective is enqueued
-and its image copied aside; once the relative gap to its Phi* is at most
-`gap` (or it has run `max_epochs` epochs) the image of that epoch is its
-result and its memory is released.
+over time.  A server admits a request as soon as it has arrived and both a
+slot and device memory are free.  The budget counts every plan (built once
+per geometry and subset count and kept), and the problem and state bytes the
+library reports for each slot, SAGA's gradient table included.  A retired
+request's slot (problem, state, image buffer) is kept in a pool: a later
+request of the same shape, method and penalty reuses it through
+pet_problem_update, pet_warm_start and pet_state_reset, which allocate
+nothing; pooled slots are released, oldest first, when an admission needs
+their memory.
 
-The host meets the device once per `window` ticks: it enqueues the window's
-ticks back to back, then synchronises once, reads every epoch-end objective
-of the window in order, retires finished requests and admits new ones.  A
-request that finished early in a window runs the rest of it (updates past
-its stopping epoch, which do not change its result); the price of a longer
-window is that waste and a later admission, the gain is one host round trip
-per window instead of per tick.
+Two ways to let the work of concurrent requests overlap on the device:
 
-A request's result depends only on the request: its subset sequence is
-seeded by the request, ticks are counted from its own admission, and the
-batched kernels give each member exactly what its own epoch calls would.
-Served alone or in a mix, it returns the same image.
+* ``Server`` (one batch): all admitted requests advance together; every tick
+  runs `tick` updates of every active state in one batched launch per phase
+  (pet_batch_epoch), so requests that arrive while others run join the next
+  tick and share its kernels.  The host meets the device once per `window`
+  ticks: it enqueues the window's ticks back to back, synchronises once,
+  reads every epoch-end objective of the window in order, retires finished
+  requests and admits new ones.  A request that finished early in a window
+  runs the rest of it (updates past its stopping epoch, whose image is not
+  the result).
+
+* ``StreamServer`` (one stream per request): every active request runs whole
+  epochs through its own State (captured graphs) on its own CUDA stream, so
+  the kernels of different requests run concurrently on the device; the host
+  polls events and launches a request's next epoch as soon as its previous
+  one is checked, or (while fewer than `speculate_below` requests are active)
+  up to `depth` epochs ahead of the check.
+
+At the end of each of its epochs a request's objective is enqueued and its
+image copied aside; once the relative gap to its Phi* is at most `gap` (or it
+has run `max_epochs` epochs) the image of that epoch is its result.  A
+request's result depends only on the request: its subset sequence is seeded
+by the request and counted from its admission, and the batched kernels give
+each member exactly what its own epoch calls would.  Served alone, in a mix,
+by either server or by the plain one-at-a-time path (serve_plain), it
+returns the same image.
 """
 from __future__ import annotations
 
+import collections
 import time
 from dataclasses import dataclass, field
 
@@ -64,14 +78,26 @@ class Request:
             self.algo = self.work.methods[0]
 
 
+def _table(algo: str) -> str:
+    return "bf16" if algo == "saga" else "fp32"
+
+
 @dataclass
 class _Slot:
-    req: Request
+    key: tuple                  # (plan key, algo, table, beta): what a pooled slot can serve
     problem: petvr.Problem
     state: petvr.State
     img: torch.Tensor
-    seq: np.ndarray
-    pos: int = 0
+    bytes: int
+    stream: torch.cuda.Stream | None = None
+    req: Request | None = None
+    seq: np.ndarray | None = None
+    pos: int = 0                # Server: updates issued
+    launched: int = 0           # StreamServer: epochs issued
+    inflight: collections.deque = field(default_factory=collections.deque)
+    phi: torch.Tensor | None = None
+    phi_host: torch.Tensor | None = None
+    retiring: tuple | None = None
 
 
 @dataclass
@@ -82,99 +108,177 @@ class ServerStats:
     admissions_deferred: int = 0
     batches_built: int = 0
     peak_bytes: int = 0
+    slots_created: int = 0
+    slots_reused: int = 0
+    slots_released: int = 0
+    epochs_launched: int = 0
     extra: dict = field(default_factory=dict)
 
 
-class Server:
-    def __init__(self, budget_bytes: int, max_slots: int = 64, gap: float = 1e-4, max_epochs: int = 60,
-                 tick: int = 3, window: int = 1):
-        if tick < 1 or max_slots < 1 or window < 1:
-            raise ValueError("tick, window and max_slots must be positive")
-        self.budget, self.max_slots = int(budget_bytes), int(max_slots)
-        self.gap, self.max_epochs, self.tick, self.window = gap, max_epochs, tick, window
-        self.plans = {}                 # (nx, ny, views, bins, subsets) -> (Plan, bytes, users)
-        self.used = 0
-        self.active: list[_Slot] = []
-        self.stats = ServerStats()
-        self._batch = None
-        # one objective row per epoch end a window can hold
-        rows = max_slots * window
-        self._phi = torch.zeros(rows, 3, dtype=torch.float64, device="cuda")
-        self._phi_host = torch.zeros(rows, 3, dtype=torch.float64).pin_memory()
+class _Base:
+    """Plans, the slot pool and the device-memory budget."""
 
-    # ---- memory accounting -------------------------------------------------
+    def __init__(self, budget_bytes: int, max_slots: int, gap: float, max_epochs: int):
+        if max_slots < 1:
+            raise ValueError("max_slots must be positive")
+        self.budget, self.max_slots = int(budget_bytes), int(max_slots)
+        self.gap, self.max_epochs = gap, max_epochs
+        self.plans = {}                 # (nx, ny, views, bins, subsets) -> (Plan, bytes)
+        self.used = 0                   # plans + active slots + pooled slots
+        self.active: list[_Slot] = []
+        self.pool: collections.OrderedDict = collections.OrderedDict()   # id -> idle _Slot, oldest first
+        self.stats = ServerStats()
+
     @staticmethod
-    def _key(work):
+    def _plan_key(work):
         g = work.geometry
         return (g.nx, g.ny, g.n_angles, g.n_bins, work.n_subsets)
 
+    def _slot_key(self, req: Request):
+        return (self._plan_key(req.work), req.algo, _table(req.algo), float(req.work.beta))
+
     def _plan(self, work):
-        key = self._key(work)
+        key = self._plan_key(work)
         if key not in self.plans:
             plan = petvr.Plan(work.geometry, work.n_subsets)
-            self.plans[key] = [plan, petvr.pet_plan_bytes(plan.handle), 0]
-        return self.plans[key]
+            nbytes = petvr.pet_plan_bytes(plan.handle)
+            self.plans[key] = (plan, nbytes)
+            self._charge(nbytes)
+        return self.plans[key][0]
 
-    def bytes_needed(self, req: Request) -> int:
-        """Device bytes admitting `req` adds (its plan only if no active request holds it)."""
-        plan, plan_bytes, users = self._plan(req.work)
-        table = "bf16" if req.algo == "saga" else "fp32"
-        return ((plan_bytes if users == 0 else 0) + petvr.pet_problem_bytes(plan.handle, False)
-                + petvr.pet_plan_state_bytes(plan.handle, req.algo, table))
+    def _charge(self, nbytes: int):
+        self.used += nbytes
+        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
+
+    @property
+    def active_bytes(self) -> int:
+        return sum(s.bytes for s in self.active)
 
     def prepare(self, works):
-        """Build the plans of these request shapes ahead of the stream (a
-        plan is computed once per geometry and subset count)."""
+        """Build the plans of these request shapes ahead of the stream."""
         for w in works:
             self._plan(w)
         torch.cuda.synchronize()
 
-    # ---- admission and retirement -----------------------------------------
-    def _admit(self, req: Request, now: float):
-        entry = self._plan(req.work)
-        plan = entry[0]
+    def slot_bytes(self, req: Request) -> int:
+        plan = self._plan(req.work)
+        return (petvr.pet_problem_bytes(plan.handle, False)
+                + petvr.pet_plan_state_bytes(plan.handle, req.algo, _table(req.algo)))
+
+    def bytes_needed(self, req: Request) -> int:
+        """Device bytes admitting `req` adds: none if a pooled slot fits it,
+        else its problem and state (and its plan, if not built yet)."""
+        key = self._slot_key(req)
+        if any(s.key == key for s in self.pool.values()):
+            return 0
+        if self._plan_key(req.work) in self.plans:
+            return self.slot_bytes(req)
+        plan = petvr.Plan(req.work.geometry, req.work.n_subsets)
+        return (petvr.pet_plan_bytes(plan.handle) + petvr.pet_problem_bytes(plan.handle, False)
+                + petvr.pet_plan_state_bytes(plan.handle, req.algo, _table(req.algo)))
+
+    def _fits(self, req: Request) -> bool:
+        """Make room for `req` by releasing pooled slots (oldest first) that
+        it cannot use; True if it then fits the budget."""
         need = self.bytes_needed(req)
-        counts = torch.from_numpy(np.ascontiguousarray(req.counts, dtype=np.float32).ravel()).cuda()
-        problem = petvr.Problem(plan, counts, None, req.w, req.work.beta)
-        img = torch.empty(req.work.geometry.n_pixels, device="cuda")
-        petvr.pet_warm_start(problem.handle, img)
-        table = "bf16" if req.algo == "saga" else "fp32"
-        state = petvr.State(problem, req.algo, img, table=table)
-        ns = req.work.n_subsets
+        if need == 0:
+            return True
+        for sid in list(self.pool):
+            if self.used + need <= self.budget:
+                break
+            slot = self.pool.pop(sid)
+            self.used -= slot.bytes
+            self.stats.slots_released += 1
+            del slot
+        return self.used + need <= self.budget
+
+    def _take_slot(self, req: Request, stream) -> _Slot:
+        """A slot holding `req`'s data and a warm-started state, enqueued on
+        `stream`: a pooled one when its shape, method and penalty match."""
+        key = self._slot_key(req)
+        counts_host = np.ascontiguousarray(req.counts, dtype=np.float32).ravel()
+        with torch.cuda.stream(stream):
+            counts = torch.from_numpy(counts_host).to("cuda")
+        for sid, slot in self.pool.items():
+            if slot.key == key:
+                del self.pool[sid]
+                petvr.pet_problem_update(slot.problem.handle, counts, None, req.w, stream)
+                petvr.pet_warm_start(slot.problem.handle, slot.img, stream)
+                slot.state.reset(stream)
+                self.stats.slots_reused += 1
+                return slot
+        plan = self._plan(req.work)
+        nbytes = self.slot_bytes(req)
+        problem = petvr.Problem(plan, counts, None, req.w, req.work.beta, stream=stream)
+        with torch.cuda.stream(stream):
+            img = torch.empty(req.work.geometry.n_pixels, device="cuda")
+        petvr.pet_warm_start(problem.handle, img, stream)
+        state = petvr.State(problem, req.algo, img, table=_table(req.algo), stream=stream)
+        self._charge(nbytes)
+        self.stats.slots_created += 1
+        return _Slot(key, problem, state, img, nbytes)
+
+    def _release(self, slot: _Slot):
+        """Back to the pool (its memory stays charged until it is evicted)."""
+        self.active.remove(slot)
+        slot.req, slot.seq, slot.retiring = None, None, None
+        slot.inflight.clear()
+        self.pool[id(slot)] = slot
+
+    def _admit_arrivals(self, pending, t0, clock, stream_for):
+        """Admit every request that has arrived while a slot and memory are
+        free (a request that does not fit waits, and so do those behind it)."""
+        while pending and pending[0].arrival <= clock() - t0 and len(self.active) < self.max_slots:
+            req = pending[0]
+            if not self._fits(req) and self.active:
+                self.stats.admissions_deferred += 1
+                return
+            pending.pop(0)
+            stream = stream_for()
+            slot = self._take_slot(req, stream)
+            slot.req, slot.stream = req, stream
+            req.admitted, req.bytes = clock() - t0, slot.bytes
+            self._start(slot)
+            self.active.append(slot)
+            self.stats.max_active = max(self.stats.max_active, len(self.active))
+
+    def _start(self, slot: _Slot):
+        raise NotImplementedError
+
+
+class Server(_Base):
+    """One batch: every tick advances all active requests by `tick` updates
+    in one batched launch per phase; the host synchronises once per
+    `window` ticks."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, gap: float = 1e-4, max_epochs: int = 60,
+                 tick: int = 3, window: int = 1):
+        if tick < 1 or window < 1:
+            raise ValueError("tick and window must be positive")
+        super().__init__(budget_bytes, max_slots, gap, max_epochs)
+        self.tick, self.window = tick, window
+        self._batch = None
+        rows = max_slots * window       # one objective row per epoch end a window can hold
+        self._phi = torch.zeros(rows, 3, dtype=torch.float64, device="cuda")
+        self._phi_host = torch.zeros(rows, 3, dtype=torch.float64).pin_memory()
+
+    def _start(self, slot: _Slot):
+        ns = slot.req.work.n_subsets
         if ns % self.tick:
             raise ValueError(f"tick {self.tick} must divide the request's {ns} subsets")
         # updates past max_epochs (the rest of a window) read the tail
-        seq = subset_sequence(req.seed, ns, self.max_epochs * ns + self.window * self.tick)
-        entry[2] += 1
-        self.used += need
-        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
-        req.admitted, req.bytes = now, need
-        self.active.append(_Slot(req, problem, state, img, seq))
+        slot.seq = subset_sequence(slot.req.seed, ns, self.max_epochs * ns + self.window * self.tick)
+        slot.pos = 0
         self._batch = None
 
-    def _retire(self, slot: _Slot, now: float, image: torch.Tensor):
-        slot.req.image = image.cpu().numpy()
-        slot.req.done = now
-        self.used -= slot.req.bytes
-        entry = self.plans[self._key(slot.req.work)]
-        entry[2] -= 1
-        self.active.remove(slot)
-        self._batch = None
-
-    # ---- the loop ------------------------------------------------------------
     def serve(self, requests, clock=time.perf_counter):
         """Serve `requests` (arrival times in seconds from now); returns them
         with admission/completion times, epochs, final gap and image."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
-        t0 = clock()
         stream = torch.cuda.current_stream()
+        t0 = clock()
         while pending or self.active:
-            now = clock() - t0
-            while pending and pending[0].arrival <= now and len(self.active) < self.max_slots:
-                if self.used + self.bytes_needed(pending[0]) > self.budget and self.active:
-                    self.stats.admissions_deferred += 1
-                    break
-                self._admit(pending.pop(0), clock() - t0)
+            self._admit_arrivals(pending, t0, clock, lambda: stream)
             if not self.active:
                 wait = pending[0].arrival - (clock() - t0)
                 if wait > 0:
@@ -198,7 +302,6 @@ class Server:
                         checks.append((s, row, s.img.clone(), s.pos // ns))
                 self.stats.ticks += 1
                 self.stats.active_sum += len(self.active)
-            self.stats.max_active = max(self.stats.max_active, len(self.active))
             if checks:
                 self._phi_host[:len(checks)].copy_(self._phi[:len(checks)], non_blocking=True)
             torch.cuda.synchronize()
@@ -212,21 +315,132 @@ class Server:
                 r.gap = (r.phi_star - float(self._phi_host[row, 0])) / abs(r.phi_star)
                 if r.gap <= self.gap or r.epochs >= self.max_epochs:
                     r.reached = r.gap <= self.gap
-                    self._retire(s, now, image)
+                    r.image = image.cpu().numpy()
+                    r.done = now
                     retired.add(id(s))
+                    self._release(s)
+                    self._batch = None
+        return requests
+
+
+@dataclass
+class _Epoch:
+    event: torch.cuda.Event
+    epoch: int
+    row: int
+    image: torch.Tensor
+
+
+class StreamServer(_Base):
+    """One stream per request: whole epochs through each request's own State
+    (captured graphs) on its own stream, up to `depth` epochs ahead of the
+    host's gap checks."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, gap: float = 1e-4, max_epochs: int = 60,
+                 depth: int = 2, speculate_below: int = 16):
+        if depth < 1:
+            raise ValueError("depth must be positive")
+        super().__init__(budget_bytes, max_slots, gap, max_epochs)
+        self.depth = depth
+        # epochs beyond the one the host has not checked yet are speculative
+        # (wasted if the gap was reached): worth it only while few requests
+        # share the device and an idle gap between epochs would show
+        self.speculate_below = speculate_below
+        self._streams: list[torch.cuda.Stream] = []
+
+    def _stream(self):
+        return self._streams.pop() if self._streams else torch.cuda.Stream()
+
+    def _start(self, slot: _Slot):
+        ns = slot.req.work.n_subsets
+        slot.seq = subset_sequence(slot.req.seed, ns, self.max_epochs * ns)
+        slot.launched = 0
+        if slot.phi is None:
+            slot.phi = torch.zeros(self.depth, 3, dtype=torch.float64, device="cuda")
+            slot.phi_host = torch.zeros(self.depth, 3, dtype=torch.float64).pin_memory()
+
+    def _launch_epoch(self, slot: _Slot):
+        r = slot.req
+        ns = r.work.n_subsets
+        e = slot.launched
+        row = e % self.depth
+        alpha, eta = STEP[r.algo]
+        with torch.cuda.stream(slot.stream):
+            slot.state.epoch(slot.seq[e * ns:(e + 1) * ns], alpha=alpha, eta=eta, stream=slot.stream)
+            slot.state.objective_async(slot.phi[row], stream=slot.stream)
+            image = slot.img.clone()
+            slot.phi_host[row].copy_(slot.phi[row], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+        slot.inflight.append(_Epoch(ev, e + 1, row, image))
+        slot.launched += 1
+        self.stats.epochs_launched += 1
+
+    def _poll(self, slot: _Slot, now) -> bool:
+        """Advance one request; True if anything happened."""
+        if slot.retiring is not None:           # its result is on the way to the host
+            ev, host = slot.retiring
+            if not ev.query():
+                return False
+            slot.req.image = host.numpy().copy()
+            slot.req.done = now()
+            self._streams.append(slot.stream)
+            self._release(slot)
+            return True
+        progressed = False
+        ahead = self.depth if len(self.active) < self.speculate_below else 1
+        while len(slot.inflight) < ahead and slot.launched < self.max_epochs:
+            self._launch_epoch(slot)
+            progressed = True
+        head = slot.inflight[0]
+        if not head.event.query():
+            return progressed
+        slot.inflight.popleft()
+        r = slot.req
+        r.epochs = head.epoch
+        r.gap = (r.phi_star - float(slot.phi_host[head.row, 0])) / abs(r.phi_star)
+        if r.gap <= self.gap or r.epochs >= self.max_epochs:
+            r.reached = r.gap <= self.gap
+            with torch.cuda.stream(slot.stream):
+                host = torch.empty(head.image.shape, dtype=head.image.dtype).pin_memory()
+                host.copy_(head.image, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(slot.stream)
+            slot.retiring = (ev, host)
+        return True
+
+    def serve(self, requests, clock=time.perf_counter):
+        """Serve `requests` (arrival times in seconds from now); returns them
+        with admission/completion times, epochs, final gap and image."""
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        t0 = clock()
+        now = lambda: clock() - t0       # noqa: E731
+        while pending or self.active:
+            self._admit_arrivals(pending, t0, clock, self._stream)
+            progressed = False
+            for slot in list(self.active):
+                progressed |= self._poll(slot, now)
+            if not progressed:
+                if not self.active and pending:
+                    wait = pending[0].arrival - now()
+                    if wait > 0:
+                        time.sleep(min(wait, 0.001))
+                else:
+                    time.sleep(0)
         return requests
 
 
 def serve_plain(requests, gap: float = 1e-4, max_epochs: int = 60, clock=time.perf_counter):
-    """The plain per-reconstruction path, for comparison with Server: requests
-    are taken in arrival order, one at a time, each run epoch by epoch through
-    its own State (one captured graph per epoch shape) with the objective
-    checked after every epoch.  A request uses the same subset sequence, step
-    size and stopping rule as under Server, so it returns the same image."""
+    """The plain per-reconstruction path, for comparison with the servers:
+    requests are taken in arrival order, one at a time, each run epoch by
+    epoch through its own State (one captured graph per epoch shape) with
+    the objective checked after every epoch.  A request uses the same subset
+    sequence, step size and stopping rule as under the servers, so it
+    returns the same image."""
     pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
     plans = {}
     for r in pending:                       # plans ahead of the stream, as Server.prepare
-        key = Server._key(r.work)
+        key = _Base._plan_key(r.work)
         if key not in plans:
             plans[key] = petvr.Plan(r.work.geometry, r.work.n_subsets)
     stream = torch.cuda.current_stream()
@@ -240,10 +454,10 @@ def serve_plain(requests, gap: float = 1e-4, max_epochs: int = 60, clock=time.pe
             time.sleep(wait)
         r.admitted = clock() - t0
         counts = torch.from_numpy(np.ascontiguousarray(r.counts, dtype=np.float32).ravel()).cuda()
-        problem = petvr.Problem(plans[Server._key(r.work)], counts, None, r.w, r.work.beta)
+        problem = petvr.Problem(plans[_Base._plan_key(r.work)], counts, None, r.w, r.work.beta)
         img = torch.empty(r.work.geometry.n_pixels, device="cuda")
         petvr.pet_warm_start(problem.handle, img)
-        state = petvr.State(problem, r.algo, img, table="bf16" if r.algo == "saga" else "fp32")
+        state = petvr.State(problem, r.algo, img, table=_table(r.algo))
         ns = r.work.n_subsets
         seq = subset_sequence(r.seed, ns, max_epochs * ns)
         alpha, eta = STEP[r.algo]
@@ -264,10 +478,29 @@ def serve_plain(requests, gap: float = 1e-4, max_epochs: int = 60, clock=time.pe
 
 
 def latency_summary(requests):
+    """Completion latency (arrival to result on the host) percentiles, queueing
+    (arrival to admission), and rates over the span from the first arrival to
+    the last completion: all completed requests, and those that reached the
+    objective gap (the others stopped at max_epochs)."""
     lat = np.array([r.done - r.arrival for r in requests if np.isfinite(r.done)])
     wait = np.array([r.admitted - r.arrival for r in requests if np.isfinite(r.admitted)])
     span = max(r.done for r in requests) - min(r.arrival for r in requests)
-    return {"completed": int(len(lat)), "reached_gap": int(sum(r.reached for r in requests)),
+    reached = int(sum(r.reached for r in requests))
+    return {"completed": int(len(lat)), "reached_gap": reached,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "mean_wait_ms": 1e3 * float(wait.mean()), "recon_per_s": len(lat) / span,
-            "epochs_mean": float(np.mean([r.epochs for r in requests]))}
+            "reached_per_s": reached / span, "epochs_mean": float(np.mean([r.epochs for r in requests]))}
+
+
+def per_template(requests):
+    """Requests, gap reached and mean epochs per request template."""
+    out = {}
+    for r in requests:
+        e = out.setdefault(r.work.name, {"requests": 0, "reached": 0, "epochs": 0.0, "algo": r.algo,
+                                         "size": r.work.geometry.nx, "subsets": r.work.n_subsets})
+        e["requests"] += 1
+        e["reached"] += int(r.reached)
+        e["epochs"] += r.epochs
+    for e in out.values():
+        e["epochs"] /= max(1, e["requests"])
+    return out

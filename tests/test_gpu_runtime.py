@@ -81,6 +81,41 @@ def test_state_reset_equals_fresh_state():
         assert torch.equal(a, b), m
 
 
+def test_problem_update_reaches_captured_epochs():
+    """After pet_problem_update with new counts and a new scalar background,
+    a state whose epochs were captured before (and reset) gives what a state
+    of a fresh problem with that data gives: cached graphs do not keep the
+    old background."""
+    pv = _pv()
+    prob, data, work = oracle_problem("c64")
+    from paper_2106_03172_gb300.phantoms import make_data
+    other = dict(make_data(work, 77))
+    other["w"] = 1.5 * data["w"]                       # the generator's w depends only on the total counts
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    gp = pv.Problem(plan, torch.from_numpy(data["g"].ravel()).cuda(), None, data["w"], work.beta)
+    fresh = pv.Problem(plan, torch.from_numpy(other["g"].ravel()).cuda(), None, other["w"], work.beta)
+    f0 = torch.from_numpy(prob.initial_image().astype(np.float32).ravel()).cuda()
+    seq = subset_sequence(600, work.n_subsets, work.n_subsets)
+    for m, (alpha, eta) in ALPHA.items():
+        a, b = f0.clone(), f0.clone()
+        sa = pv.State(gp, m, a)
+        sa.epoch(seq, alpha=alpha, eta=eta)              # captures with the first data
+        pv.pet_problem_update(gp.handle, torch.from_numpy(other["g"].ravel()).cuda(), None, other["w"])
+        a.copy_(f0)
+        sa.reset()
+        sb = pv.State(fresh, m, b)
+        sa.epoch(seq, alpha=alpha, eta=eta)
+        sb.epoch(seq, alpha=alpha, eta=eta)
+        phi_a = torch.zeros(3, dtype=torch.float64, device="cuda")
+        phi_b = torch.zeros(3, dtype=torch.float64, device="cuda")
+        sa.objective_async(phi_a)
+        sb.objective_async(phi_b)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), m
+        assert torch.equal(phi_a, phi_b), m
+        pv.pet_problem_update(gp.handle, torch.from_numpy(data["g"].ravel()).cuda(), None, data["w"])
+
+
 def test_launch_accounting_includes_graph_replays():
     pv = _pv()
     prob, data, work = oracle_problem("c64")

@@ -44,13 +44,24 @@ def _requests(arrivals):
     return out
 
 
-@pytest.mark.parametrize("window", [1, 4])
-def test_results_same_alone_and_in_the_mix(window):
-    """A window of several ticks per host round trip changes when requests
-    are admitted and retired, not what they return."""
+SERVERS = {"batch": lambda **kw: _srv("Server", tick=3, **kw),
+           "batch-window4": lambda **kw: _srv("Server", tick=3, window=4, **kw),
+           "streams": lambda **kw: _srv("StreamServer", depth=2, **kw)}
+
+
+def _srv(kind, **kw):
+    from paper_2106_03172_gb300 import serving
+    return getattr(serving, kind)(**kw)
+
+
+@pytest.mark.parametrize("kind", list(SERVERS))
+def test_results_same_alone_and_in_the_mix(kind):
+    """Served in a mix (one batch, with one or four ticks per host round
+    trip, or one stream per request) a request returns what it returns
+    served alone."""
     from paper_2106_03172_gb300.serving import Server, latency_summary
     arrivals = [0.0, 0.0005, 0.001, 0.0015, 0.002, 0.0025]
-    mixed = Server(budget_bytes=1 << 34, tick=3, max_epochs=40, window=window).serve(_requests(arrivals))
+    mixed = SERVERS[kind](budget_bytes=1 << 34, max_epochs=40).serve(_requests(arrivals))
     summary = latency_summary(mixed)
     assert summary["completed"] == len(arrivals) and summary["reached_gap"] == len(arrivals)
     for r in mixed:
@@ -61,25 +72,51 @@ def test_results_same_alone_and_in_the_mix(window):
 
 def test_plain_path_gives_the_same_results():
     """The one-at-a-time per-reconstruction path (State epochs, captured
-    graphs) and the continuous-batching server agree bit for bit."""
-    from paper_2106_03172_gb300.serving import Server, serve_plain
+    graphs) and both servers agree bit for bit."""
+    from paper_2106_03172_gb300.serving import serve_plain
     arrivals = [0.0, 0.0005, 0.001, 0.0015]
-    served = Server(budget_bytes=1 << 34, tick=3, max_epochs=40, window=3).serve(_requests(arrivals))
     plain = serve_plain(_requests(arrivals), max_epochs=40)
-    for a, b in zip(served, plain):
-        assert a.epochs == b.epochs and a.reached and b.reached
-        np.testing.assert_array_equal(a.image, b.image)
+    for kind in ("batch-window4", "streams"):
+        served = SERVERS[kind](budget_bytes=1 << 34, max_epochs=40).serve(_requests(arrivals))
+        for a, b in zip(served, plain):
+            assert a.epochs == b.epochs and a.reached and b.reached
+            np.testing.assert_array_equal(a.image, b.image)
 
 
-def test_admission_respects_the_memory_budget():
+def test_pooled_slots_are_reused_without_changing_results():
+    """Requests of one shape arriving one after another reuse the first
+    one's slot (problem update, warm start, state reset: no allocation) and
+    return what fresh slots return."""
+    from paper_2106_03172_gb300.phantoms import make_data
+    from paper_2106_03172_gb300.serving import Request, Server
+    work, _, phi = _template(0)
+    # one shape and method, different counts and backgrounds (noise seeds)
+    datas = [make_data(work, 40 + k) for k in range(3)]
+
+    def reqs():
+        return [Request(k, work, d["g"], d["w"], phi, 0.0, seed=950 + k) for k, d in enumerate(datas)]
+
+    for kind in ("batch", "streams"):
+        srv = SERVERS[kind](budget_bytes=1 << 34, max_epochs=40)
+        rs = reqs()
+        done = srv.serve(rs[:1]) + srv.serve(rs[1:2]) + srv.serve(rs[2:])
+        assert srv.stats.slots_reused == 2 and srv.stats.slots_created == 1
+        for r, fresh_req in zip(done, reqs()):
+            fresh = Server(budget_bytes=1 << 34, tick=3, max_epochs=40).serve([fresh_req])[0]
+            assert fresh.epochs == r.epochs
+            np.testing.assert_array_equal(fresh.image, r.image)
+
+
+@pytest.mark.parametrize("kind", ["batch", "streams"])
+def test_admission_respects_the_memory_budget(kind):
     from paper_2106_03172_gb300.serving import Server
     reqs = _requests([0.0] * 6)
     probe = Server(budget_bytes=1 << 40)
     need = max(probe.bytes_needed(r) for r in reqs)
     budget = 2 * need + need // 2
-    srv = Server(budget_bytes=budget, tick=3, max_epochs=40)
+    srv = SERVERS[kind](budget_bytes=budget, max_epochs=40)
     done = srv.serve(reqs)
     assert all(np.isfinite(r.done) for r in done)
     assert srv.stats.peak_bytes <= budget and srv.stats.admissions_deferred > 0
     assert srv.stats.max_active < len(reqs)
-    assert srv.used == 0
+    assert srv.active_bytes == 0 and not srv.active
