@@ -75,12 +75,29 @@ enum { PET_POT_QUADRATIC = 0, PET_POT_HUBER = 1, PET_POT_LOGCOSH = 2, PET_POT_HY
  * pixel n: the exact Siddon intersection length (the paper's forward model is
  * a Radon transform, §5.1; A is any nonnegative system matrix, §2.1).
  * Limits: nx, ny <= 16384, n_angles <= 1024, nx*ny*nz and n_angles*n_bins*nz
- * below 2^31. */
+ * below 2^31.
+ *
+ * n_rings = 0: nz independent slices (a stack of 2-D problems), sinograms
+ * [view][bin][z].  n_rings >= 1: a multi-ring scanner with fully 3-D lines
+ * of response (the torso data of §5.3 come from 2 rings).  The image is a
+ * volume of nz layers, each slice_mm thick, centred on z = 0; voxel
+ * (ix, iy, iz) is half-open in z as in x and y, stored [iy][ix][iz].  Ring r
+ * sits at z_r = (r - (n_rings-1)/2) ring_mm on a detector cylinder of radius
+ * radius_mm, which must exceed every |s_j|.  Line (i, j, r1, r2) is ray
+ * (i, j) in the transaxial plane, meeting the cylinder at t = -T on ring r1
+ * and t = +T on ring r2 (t the transaxial arc length, T = sqrt(R^2 - s_j^2)),
+ * so z(t) = (z_r1 + z_r2)/2 + t (z_r2 - z_r1) / (2T); a_mn is its 3-D length
+ * inside voxel n.  Sinograms are [view][bin][pair], pair = r1 n_rings + r2
+ * (every ordered pair), and the penalty couples the two axial neighbours
+ * too (6-neighbourhood).  n_rings <= 4.  Fields after bin_mm are ignored when
+ * n_rings = 0, so a zero-initialised tail selects the stacked 2-D mode. */
 typedef struct {
     int32_t nx, ny, nz;
     double pixel_mm;
     int32_t n_angles, n_bins;
     double bin_mm;
+    int32_t n_rings;
+    double ring_mm, radius_mm, slice_mm;
 } pet_geometry;
 
 /* Ordered subsets (§2.1): scheme 0 = angle-interleaved, view i belongs to

@@ -106,6 +106,9 @@ double snap(double v) {
 
 int max_sub_rays(const pet_plan *pl) { return pl->max_sub_views * pl->nb; }
 
+// Sinogram entries per (view, bin): slices of a stack, or ring pairs.
+int sino_inner(const pet_plan *pl) { return pl->ring ? pl->pairs : pl->nz; }
+
 FwdArgs fwd_args(const pet_plan *pl, const float *img, int subset, bool natural) {
     FwdArgs a{};
     a.views = pl->d_views;
@@ -120,8 +123,10 @@ FwdArgs fwd_args(const pet_plan *pl, const float *img, int subset, bool natural)
     }
     a.nx = pl->nx;
     a.ny = pl->ny;
-    a.nz = pl->nz;
+    a.nz = sino_inner(pl);
     a.nb = pl->nb;
+    a.layers = pl->layers;
+    a.lz = pl->d_lz;
     a.img = img;
     return a;
 }
@@ -136,9 +141,12 @@ BackArgs back_args(const pet_plan *pl, const float *r, int subset, bool natural)
     a.r_view0 = subset < 0 ? 0 : pl->sub_off[subset];
     a.nx = pl->nx;
     a.ny = pl->ny;
-    a.nz = pl->nz;
+    a.nz = pl->ring ? pl->layers : pl->nz;
     a.nb = pl->nb;
     a.ns = pl->ns;
+    a.axial = pl->ring;
+    a.pairs = pl->pairs;
+    a.lz = pl->d_lz;
     a.r = r;
     a.sens_t = pl->d_sens_t;
     a.sens = pl->d_sens;
@@ -152,7 +160,7 @@ long long plane_of(const pet_plan *pl) { return (long long)pl->N * pl->nz; }
 pet_status ratio_subset(const pet_problem *p, const float *f, int t, float *ratio, cudaStream_t s) {
     const pet_plan *pl = p->plan;
     FwdArgs a = fwd_args(pl, f, t, false);
-    const long long off = (long long)pl->sub_off[t] * pl->nb * pl->nz;
+    const long long off = (long long)pl->sub_off[t] * pl->nb * sino_inner(pl);
     a.g = p->d_g + off;
     a.w = p->d_w ? p->d_w + off : nullptr;
     a.w_scalar = p->w_scalar;
@@ -218,7 +226,7 @@ size_t state_bytes(const pet_plan *pl, int algo, int table_dtype) {
     const size_t Nz = (size_t)pl->N * pl->nz, Mz = (size_t)pl->M * pl->nz;
     const size_t n_part = (size_t)forward_blocks(pl->M, pl->nz, choose_group(pl)) + (Nz + 255) / 256;
     const size_t table_bytes = (size_t)pl->ns * Nz * (table_dtype == PET_TABLE_BF16 ? 2 : 4);
-    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * pl->nz * 4 + n_part * 8;
+    size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * sino_inner(pl) * 4 + n_part * 8;
     if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + Mz * 4;
     if (algo == PET_ALGO_SVRG) bytes += 2 * Nz * 4 + (size_t)pl->ns * Nz * 4 + Mz * 4;
     if (algo == PET_ALGO_SAGA) bytes += 2 * Nz * 4 + table_bytes;
@@ -334,6 +342,7 @@ void pet_plan_destroy(pet_plan *pl) {
     dfree(pl->d_all_off);
     dfree(pl->d_sens_t);
     dfree(pl->d_sens);
+    dfree(pl->d_lz);
     delete pl;
 }
 
@@ -349,8 +358,20 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     if (sub->scheme != 0) return set_error(PET_ERR_INVALID, "only the interleaved subset scheme (0) exists");
     if (sub->n_subsets < 1 || sub->n_subsets > g->n_angles)
         return set_error(PET_ERR_INVALID, "need 1 <= n_subsets <= n_angles");
-    const long long N = (long long)g->nx * g->ny, M = (long long)g->n_angles * g->n_bins;
-    if (N * g->nz > kMaxElems || M * g->nz > kMaxElems)
+    const bool ring = g->n_rings > 0;
+    const double ds_chk = g->bin_mm > 0.0 ? g->bin_mm : g->pixel_mm;
+    if (ring) {
+        if (g->n_rings > 4) return set_error(PET_ERR_INVALID, "n_rings must be <= 4");
+        if (!(g->slice_mm > 0.0) || !std::isfinite(g->slice_mm) || !(g->ring_mm >= 0.0) ||
+            !std::isfinite(g->ring_mm) || !std::isfinite(g->radius_mm))
+            return set_error(PET_ERR_INVALID, "multi-ring geometry needs slice_mm > 0 and finite ring_mm >= 0");
+        if (!(g->radius_mm > 0.5 * (g->n_bins - 1) * ds_chk))
+            return set_error(PET_ERR_INVALID, "radius_mm must exceed every bin offset |s_j|");
+    }
+    const int pairs = ring ? g->n_rings * g->n_rings : 1;
+    const long long N = (long long)g->nx * g->ny * (ring ? g->nz : 1);
+    const long long M = (long long)g->n_angles * g->n_bins * pairs;
+    if (N * (ring ? 1 : g->nz) > kMaxElems || M * (ring ? 1 : g->nz) > kMaxElems)
         return set_error(PET_ERR_INVALID, "image or sinogram larger than 2^31 - 1 elements");
 
     pet_plan *pl = new (std::nothrow) pet_plan();
@@ -358,7 +379,10 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     pl->geom = *g;
     pl->nx = g->nx;
     pl->ny = g->ny;
-    pl->nz = g->nz;
+    pl->nz = ring ? 1 : g->nz;
+    pl->ring = ring ? 1 : 0;
+    pl->layers = ring ? g->nz : 1;
+    pl->pairs = pairs;
     pl->na = g->n_angles;
     pl->nb = g->n_bins;
     pl->ns = sub->n_subsets;
@@ -370,7 +394,11 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
 
     // per-view parameters and per-ray centred minor offsets (FP64 -> FP32)
     std::vector<ViewParams> views(pl->na);
-    std::vector<float2> uc((size_t)M);
+    const long long R = (long long)pl->na * pl->nb;        // rays of the transaxial geometry
+    std::vector<float2> uc((size_t)R);
+    // multi-ring: per line, zeta(kc) = zc + zs kc in layer units and sqrt(1 + kappa^2)
+    std::vector<float4> lz(ring ? (size_t)M : 0);
+    const double z_min = -0.5 * g->nz * g->slice_mm;
     for (int i = 0; i < pl->na; ++i) {
         const double th = (double)i * M_PI / (double)pl->na;
         const double c = snap(std::cos(th)), s = snap(std::sin(th));
@@ -394,6 +422,21 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
             const double ui = std::nearbyint(u);
             uc[(size_t)i * pl->nb + j] = make_float2((float)ui, (float)(u - ui));
             if (j == 0) vp.uc0 = (float)u;
+            if (!ring) continue;
+            // transaxial arc length t(kc) = t0 + t1 kc along (-sin, cos) at centred major coordinate kc
+            const double t0 = vp.col ? sj * c / s : -sj * s / c;
+            const double t1 = vp.col ? -d / s : d / c;
+            const double T = std::sqrt(g->radius_mm * g->radius_mm - sj * sj);
+            for (int r1 = 0; r1 < g->n_rings; ++r1)
+                for (int r2 = 0; r2 < g->n_rings; ++r2) {
+                    const double z1 = (r1 - 0.5 * (g->n_rings - 1)) * g->ring_mm;
+                    const double z2 = (r2 - 0.5 * (g->n_rings - 1)) * g->ring_mm;
+                    const double kappa = (z2 - z1) / (2.0 * T);
+                    const double zm = 0.5 * (z1 + z2);
+                    lz[((size_t)i * pl->nb + j) * pairs + r1 * g->n_rings + r2] =
+                        make_float4((float)((zm + kappa * t0 - z_min) / g->slice_mm),
+                                    (float)(kappa * t1 / g->slice_mm), (float)std::sqrt(1.0 + kappa * kappa), 0.0f);
+                }
         }
         views[i] = vp;
     }
@@ -416,7 +459,8 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
         return e;
     };
     if ((st = dalloc(&pl->d_views, pl->na, "views")) != PET_OK) return fail(st);
-    if ((st = dalloc(&pl->d_uc, (size_t)M, "uc")) != PET_OK) return fail(st);
+    if ((st = dalloc(&pl->d_uc, (size_t)R, "uc")) != PET_OK) return fail(st);
+    if (ring && (st = dalloc(&pl->d_lz, (size_t)M, "lz")) != PET_OK) return fail(st);
     if ((st = dalloc(&pl->d_order, pl->na, "order")) != PET_OK) return fail(st);
     if ((st = dalloc(&pl->d_natural, pl->na, "natural")) != PET_OK) return fail(st);
     if ((st = dalloc(&pl->d_sub_off, pl->ns + 1, "sub_off")) != PET_OK) return fail(st);
@@ -426,7 +470,8 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
     if ((st = dalloc(&ones, (size_t)M, "ones")) != PET_OK) return fail(st);
     cudaError_t e = cudaSuccess;
     e = cudaMemcpy(pl->d_views, views.data(), sizeof(ViewParams) * pl->na, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(pl->d_uc, uc.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_uc, uc.data(), sizeof(float2) * R, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ring) e = cudaMemcpy(pl->d_lz, lz.data(), sizeof(float4) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_order, pl->order.data(), sizeof(int) * pl->na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_natural, natural.data(), sizeof(int) * pl->na, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -438,9 +483,10 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
         e = cudaMemcpy(ones, h1.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_ok(e, "ones upload"));
     }
-    // sens_t = A_t^T 1 for every subset (one slice: the geometry is shared by all slices)
+    // sens_t = A_t^T 1 for every subset (one slice of a stack: the geometry is shared
+    // by all slices; every voxel of a multi-ring volume)
     BackArgs b = back_args(pl, ones, -1, false);
-    b.nz = 1;
+    if (!ring) b.nz = 1;
     b.t0 = 0;
     b.r_view0 = 0;
     b.out = pl->d_sens_t;
@@ -453,7 +499,7 @@ pet_status pet_plan_create(const pet_geometry *g, const pet_subsets *sub, pet_pl
         e = cudaMemset(d_cnt, 0, sizeof(unsigned long long) * pl->ns);
         for (int t = 0; t < pl->ns && e == cudaSuccess && st == PET_OK; ++t) {
             FwdArgs a = fwd_args(pl, nullptr, t, false);
-            a.nz = 1;
+            if (!ring) a.nz = 1;
             st = launch_count_nnz(a, d_cnt + t, 0);
         }
         std::vector<unsigned long long> h((size_t)pl->ns, 0);
@@ -522,14 +568,14 @@ pet_status pet_plan_set_tuning(pet_plan *pl, int32_t fwd_chunks, int32_t back_ru
 
 pet_status pet_plan_get_tuning(const pet_plan *pl, int32_t *h_fwd_chunks, int32_t *h_back_run) {
     if (!pl || !h_fwd_chunks || !h_back_run) return set_error(PET_ERR_INVALID, "null argument");
-    *h_fwd_chunks = pl->nz > 1 ? 1 : choose_group(pl);
+    *h_fwd_chunks = choose_group(pl);
     *h_back_run = pl->back_run;
     return PET_OK;
 }
 
 pet_status pet_plan_autotune(pet_plan *pl, int32_t *h_fwd_chunks, int32_t *h_back_run) {
     if (!pl) return set_error(PET_ERR_INVALID, "null plan");
-    if (pl->nz == 1) {
+    if (pl->nz == 1 && !pl->ring) {
         const size_t N = (size_t)pl->N, R = (size_t)max_sub_rays(pl);
         float *img = nullptr, *sino = nullptr, *out = nullptr;
         cudaStream_t s = nullptr;
@@ -604,7 +650,7 @@ pet_status pet_plan_autotune(pet_plan *pl, int32_t *h_fwd_chunks, int32_t *h_bac
         cleanup();
         if (st != PET_OK) return st;
     }
-    if (h_fwd_chunks) *h_fwd_chunks = pl->nz > 1 ? 1 : choose_group(pl);
+    if (h_fwd_chunks) *h_fwd_chunks = choose_group(pl);
     if (h_back_run) *h_back_run = pl->back_run;
     return PET_OK;
 }
@@ -683,9 +729,9 @@ pet_status pet_problem_create(const pet_plan *pl, const float *d_counts, const f
     if ((st = dalloc(&p->d_scalar, (size_t)pl->nz + 8, "scalars")) != PET_OK) return fail(st);
     if ((st = dalloc(&p->d_status, 1, "status")) != PET_OK) return fail(st);
     if ((st = cuda_ok(cudaMemsetAsync(p->d_status, 0, sizeof(int), s), "memset")) != PET_OK) return fail(st);
-    if ((st = launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, pl->nz, s)) != PET_OK)
+    if ((st = launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, sino_inner(pl), s)) != PET_OK)
         return fail(st);
-    if (d_bg && (st = launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, pl->nz, s)) != PET_OK)
+    if (d_bg && (st = launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, sino_inner(pl), s)) != PET_OK)
         return fail(st);
     *out = p;
     return PET_OK;
@@ -702,8 +748,8 @@ pet_status pet_problem_update(pet_problem *p, const float *d_counts, const float
         p->w_scalar = bg;
         ++p->version;
     }
-    PET_TRY(launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, pl->nz, s));
-    if (d_bg) PET_TRY(launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, pl->nz, s));
+    PET_TRY(launch_permute_sino(d_counts, p->d_g, pl->d_order, pl->na, pl->nb, sino_inner(pl), s));
+    if (d_bg) PET_TRY(launch_permute_sino(d_bg, p->d_w, pl->d_order, pl->na, pl->nb, sino_inner(pl), s));
     return PET_OK;
 }
 
@@ -790,7 +836,7 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
     if ((e = dalloc(&st->alt, Nz, "alt")) != PET_OK) return fail(e);
     st->n_part = p->n_part;
     if ((e = dalloc(&st->d_part, (size_t)st->n_part, "objective partials")) != PET_OK) return fail(e);
-    if ((e = dalloc(&st->ratio, (size_t)max_sub_rays(pl) * pl->nz, "ratio")) != PET_OK) return fail(e);
+    if ((e = dalloc(&st->ratio, (size_t)max_sub_rays(pl) * sino_inner(pl), "ratio")) != PET_OK) return fail(e);
     if (algo == PET_ALGO_SVREM) {
         if ((e = dalloc(&st->s_hat, Nz, "s_hat")) != PET_OK) return fail(e);
         if ((e = dalloc(&st->f_anc, Nz, "f_anc")) != PET_OK) return fail(e);
@@ -1115,7 +1161,8 @@ pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out
     *out = nullptr;
     for (int j = 0; j < n; ++j) {
         if (!states[j]) return set_error(PET_ERR_INVALID, "null state in batch");
-        if (states[j]->prob->plan->nz != 1) return set_error(PET_ERR_INVALID, "batches take single-slice images");
+        if (states[j]->prob->plan->nz != 1 || states[j]->prob->plan->ring)
+            return set_error(PET_ERR_INVALID, "batches take single-slice images");
         for (int i = 0; i < j; ++i)
             if (states[i] == states[j]) return set_error(PET_ERR_INVALID, "a state appears twice in the batch");
     }

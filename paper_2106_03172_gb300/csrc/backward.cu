@@ -47,17 +47,21 @@ struct Stencil {
 // selects the edge-preserving potentials (runtime pot); otherwise quadratic.
 template <bool GENPOT>
 __device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int nx, int ny, int nz, int z,
-                                            float fk, int pot, float delta) {
+                                            float fk, int pot, float delta, int axial = 0) {
     const bool hl = ix > 0, hr = ix + 1 < nx, hd = iy > 0, hu = iy + 1 < ny;
-    const float fl = hl ? __ldg(f + ((long long)iy * nx + ix - 1) * nz + z) : 0.0f;
-    const float fr = hr ? __ldg(f + ((long long)iy * nx + ix + 1) * nz + z) : 0.0f;
-    const float fd = hd ? __ldg(f + ((long long)(iy - 1) * nx + ix) * nz + z) : 0.0f;
-    const float fu = hu ? __ldg(f + ((long long)(iy + 1) * nx + ix) * nz + z) : 0.0f;
+    const bool hb = axial && z > 0, ht = axial && z + 1 < nz;        // axial neighbours of a volume
+    const long long c = ((long long)iy * nx + ix) * nz + z;
+    const float fl = hl ? __ldg(f + c - nz) : 0.0f;
+    const float fr = hr ? __ldg(f + c + nz) : 0.0f;
+    const float fd = hd ? __ldg(f + c - (long long)nx * nz) : 0.0f;
+    const float fu = hu ? __ldg(f + c + (long long)nx * nz) : 0.0f;
+    const float fb = hb ? __ldg(f + c - 1) : 0.0f;
+    const float ft = ht ? __ldg(f + c + 1) : 0.0f;
     Stencil s{0.0f, 0.0f, 0.0f};
     if (!GENPOT) {
         // missing neighbours add exact zeros
-        s.cnt = (float)((int)hl + (int)hr + (int)hd + (int)hu);
-        s.sum = ((fl + fr) + fd) + fu;
+        s.cnt = (float)((int)hl + (int)hr + (int)hd + (int)hu + (int)hb + (int)ht);
+        s.sum = ((((fl + fr) + fd) + fu) + fb) + ft;
         s.grad = fk * s.cnt - s.sum;
         return s;
     }
@@ -66,6 +70,8 @@ __device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int 
     if (hr) { potential_dg(pot, delta, fk - fr, dr, g); s.cnt += g; s.sum += g * fr; s.grad += dr; }
     if (hd) { potential_dg(pot, delta, fk - fd, dr, g); s.cnt += g; s.sum += g * fd; s.grad += dr; }
     if (hu) { potential_dg(pot, delta, fk - fu, dr, g); s.cnt += g; s.sum += g * fu; s.grad += dr; }
+    if (hb) { potential_dg(pot, delta, fk - fb, dr, g); s.cnt += g; s.sum += g * fb; s.grad += dr; }
+    if (ht) { potential_dg(pot, delta, fk - ft, dr, g); s.cnt += g; s.sum += g * ft; s.grad += dr; }
     return s;
 }
 
@@ -94,6 +100,9 @@ template <int EPI, typename TQ, bool GENPOT>
 __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long long i, int n, int ix, int iy,
                                                int z, float acc) {
     const long long plane = (long long)a.nx * a.ny * a.nz;
+    // sensitivities: per pixel (shared by the slices of a stack) or per voxel
+    const long long splane = a.axial ? plane : (long long)a.nx * a.ny;
+    const long long sidx = a.axial ? i : (long long)n;
     const float inv_ns = 1.0f / (float)a.ns;
     const float alpha = a.alpha_dev ? __ldg(a.alpha_dev) : a.alpha;
     if (EPI == EPI_PLAIN) {
@@ -102,9 +111,9 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         a.out[(long long)t * plane + i] = acc;
     } else if (EPI == EPI_OSEM) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float bp = a.beta * inv_ns;
-        const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+        const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
         const float c = bp * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(fk * acc, S, bp * st.cnt, c);
     } else if (EPI == EPI_SVREM) {
@@ -114,15 +123,15 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float tau = ns * fk * acc - ns * a.f_anc[i] * Bt + a.s_anc[i];
         const float s = fmaf(alpha, tau, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
-        const float S = __ldg(a.sens + n);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const float S = __ldg(a.sens + sidx);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
     } else if (EPI == EPI_SAGA || EPI == EPI_SAGA_INIT) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float gradR = st.grad;
-        const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+        const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
         const float q = round_q<TQ>(acc - S - a.beta * inv_ns * gradR);
         const long long qi = (long long)t * plane + i;
         if (EPI == EPI_SAGA_INIT) {
@@ -138,7 +147,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         }
     } else if (EPI == EPI_SVRG) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float gradR = st.grad;
         const float Bt = a.B[(long long)t * plane + i];
         const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
@@ -146,14 +155,14 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         if (a.d) {
             dn = a.d[i];
         } else {
-            const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+            const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
             dn = S > 0.0f ? fk / S : 0.0f;
         }
         a.f_out[i] = fmaxf(fmaf(alpha * dn, dir, fk), 0.0f);
     } else if (EPI == EPI_SGA) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
-        const float S = __ldg(a.sens_t + (long long)t * a.nx * a.ny + n);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
         const float dir = acc - S - a.beta * inv_ns * st.grad;      // grad Phi_t
         const float dt = S > 0.0f ? fk / S : 0.0f;                  // d_t(f) = f / A_t^T 1
         a.f_out[i] = fmaxf(fmaf(alpha * dt, dir, fk), 0.0f);
@@ -161,8 +170,8 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float fk = a.f[i];
         const float s = fmaf(alpha, (float)a.ns * fk * acc, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
-        const float S = __ldg(a.sens + n);
+        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const float S = __ldg(a.sens + sidx);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
     } else if (EPI == EPI_SEM_INIT) {
@@ -179,8 +188,8 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
             const float Tb = a.qbar[i];
             const float s = fmaf(alpha, tau - T_old + Tb, (1.0f - alpha) * a.s_hat[i]);
             a.s_hat[i] = s;
-            const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta);
-            const float S = __ldg(a.sens + n);
+            const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+            const float S = __ldg(a.sens + sidx);
             const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
             a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
             a.qbar[i] = fmaf(tau - T_old, inv_ns, Tb);
@@ -263,6 +272,74 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
     for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (!live || lane != 0) return;
     apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, z, acc);
+}
+
+// Multi-ring path: kLanes lanes per voxel share the subset's views (lane l
+// takes views l, l+4, ...).  For each candidate bin the band piece of the
+// voxel's pixel is found as in the slice-stack path; each ring pair then adds
+// the part of that piece inside the voxel's layer (piece_fraction /
+// piece_zeta / layer_fraction, the forward projector's own expressions).
+template <int EPI, typename TQ, bool GENPOT>
+__global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    stage_views(a, vb, nv, s_views, s_vid);
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    const int L = a.nz, P = a.pairs;
+    const long long plane = (long long)a.nx * a.ny * L;
+    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const long long i = gid / kLanes;                    // voxel
+    const int lane = (int)(gid % kLanes);
+    const bool live = i < plane;
+    const int iz = (int)(i % L);
+    const int n = (int)(i / L);
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+
+    float acc = 0.0f;
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
+            const float2 *ucv = a.uc + (long long)v * a.nb;
+            const float4 *lzv = a.lz + (long long)v * a.nb * P;
+            const float *rv = a.r + (long long)(vb + q - r_view0) * a.nb * P;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const int side = (c0 == mrel) ? 0 : ((c0 + 1 == mrel && w1 > 0.0f) ? 1 : -1);
+                if (side < 0) continue;
+                const float w = side ? w1 : w0;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                for (int pr = 0; pr < P; ++pr) {
+                    const float4 lz = __ldg(lzv + (long long)j * P + pr);
+                    const float fr = layer_fraction(piece_zeta(lz, kc, f_lo), piece_zeta(lz, kc, f_hi), iz);
+                    if (fr > 0.0f) acc = fmaf((w * lz.z) * fr, __ldg(rv + (long long)j * P + pr), acc);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!live || lane != 0) return;
+    apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, iz, acc);
 }
 
 // Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
@@ -424,6 +501,13 @@ constexpr bool uses_stencil(int epi) {
 
 template <int EPI, typename TQ, bool GENPOT>
 pet_status go_impl(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
+    if (a.axial) {
+        const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
+        const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
+        const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
+        ring_back_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
+        return check_launch("ring_back_kernel");
+    }
     if (a.nz == 1) {
         const int tiles = ((a.nx + kTile - 1) / kTile) * ((a.ny + kTile - 1) / kTile);
         const dim3 grid((unsigned)tiles, (unsigned)ny_grid);

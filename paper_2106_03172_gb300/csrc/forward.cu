@@ -343,6 +343,157 @@ __global__ void __launch_bounds__(kBlock) count_nnz_kernel(const FwdArgs a, unsi
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// Multi-ring forward: one thread per line of response (ray, ring pair), the
+// pairs of one ray on consecutive threads (they read the same voxel columns).
+// Each thread walks its ray's bands; every band piece is spread over the
+// layers its axial range crosses (piece_fraction / piece_zeta /
+// layer_fraction, shared with the back projection).  Epilogue as above.
+template <int MODE, bool LL>
+__global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
+    const RayRange rr = ray_range(a);
+    const int P = a.nz;
+    const long long n_lor = (long long)(rr.v_end - rr.v_begin) * a.nb * P;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const bool live = tid < n_lor;
+    float acc = 0.0f;
+    if (live) {
+        const int pr = (int)(tid % P);
+        const long long ray = tid / P;
+        const int q = rr.v_begin + (int)(ray / a.nb);
+        const int j = (int)(ray % a.nb);
+        const int v = __ldg(a.order + q);
+        const ViewParams vp = a.views[v];
+        const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
+        const float4 lz = __ldg(a.lz + ((long long)v * a.nb + j) * P + pr);
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const float hm = 0.5f * (float)n_major;
+        const int ui = (int)u.x + (n_minor >> 1);
+        const long long s_major = vp.col ? 1 : a.nx;     // pixel strides
+        const long long s_minor = vp.col ? a.nx : 1;
+        const int L = a.layers;
+        int k_lo, k_hi;
+        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
+        float kc = (float)k_lo - hm;
+        float va = band_point(vp, u.y, kc);
+        for (int k = k_lo; k < k_hi; ++k) {
+            const float vb = band_point(vp, u.y, kc + 1.0f);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int m = m0 + side;
+                const float w = side ? w1 : w0;
+                if (!(w > 0.0f) || (unsigned)m >= (unsigned)n_minor) continue;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                const float wl = w * lz.z;
+                const int il = max(0, (int)floorf(fminf(za, zb)));
+                const int ih = min(L - 1, (int)floorf(fmaxf(za, zb)));
+                const float *colp = a.img + (k * s_major + m * s_minor) * L;
+                for (int iz = il; iz <= ih; ++iz) {
+                    const float fr = layer_fraction(za, zb, iz);
+                    if (fr > 0.0f) acc = fmaf(wl * fr, __ldg(colp + iz), acc);
+                }
+            }
+            va = vb;
+            kc += 1.0f;
+        }
+    }
+    double ll = 0.0;
+    if (live) {
+        const long long gi = rr.off + tid;
+        const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        if (MODE == FWD_YHAT) a.out[tid] = yhat;
+        if (MODE == FWD_RATIO || LL) {
+            const float g = __ldg(a.g + gi);
+            if (MODE == FWD_RATIO) a.out[tid] = (yhat != 0.0f) ? g / yhat : 0.0f;
+            if (LL) {
+                if (yhat > 0.0f) {
+                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
+                } else if (g > 0.0f) {
+                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
+                } else {
+                    ll = -(double)yhat;
+                }
+            }
+        }
+    }
+    if (LL) {
+        __shared__ double red[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int i = 0; i < kBlock / 32; ++i) sum += red[i];
+            a.ll_partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+// Nonzeros of the multi-ring lines of a view range: (piece, layer) pairs of
+// positive weight, with the projector's own geometry (one thread per line).
+__global__ void __launch_bounds__(kBlock) ring_count_nnz_kernel(const FwdArgs a, unsigned long long *count) {
+    const int P = a.nz;
+    const long long n_lor = (long long)(a.v_end - a.v_begin) * a.nb * P;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    unsigned long long c = 0;
+    if (tid < n_lor) {
+        const int pr = (int)(tid % P);
+        const long long ray = tid / P;
+        const int v = a.order[a.v_begin + (int)(ray / a.nb)];
+        const int j = (int)(ray % a.nb);
+        const ViewParams vp = a.views[v];
+        const float2 u = a.uc[(long long)v * a.nb + j];
+        const float4 lz = a.lz[((long long)v * a.nb + j) * P + pr];
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const int ui = (int)u.x + (n_minor >> 1);
+        float kc = -0.5f * (float)n_major;
+        float va = band_point(vp, u.y, kc);
+        for (int k = 0; k < n_major; ++k) {
+            const float vb = band_point(vp, u.y, kc + 1.0f);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
+            for (int side = 0; side < 2; ++side) {
+                const float w = side ? w1 : w0;
+                if (!(w > 0.0f) || (unsigned)(m0 + side) >= (unsigned)n_minor) continue;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                const int il = max(0, (int)floorf(fminf(za, zb)));
+                const int ih = min(a.layers - 1, (int)floorf(fmaxf(za, zb)));
+                for (int iz = il; iz <= ih; ++iz) c += layer_fraction(za, zb, iz) > 0.0f ? 1 : 0;
+            }
+            va = vb;
+            kc += 1.0f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    if (mode == FWD_YHAT && !ll)
+        ring_forward_kernel<FWD_YHAT, false><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && !ll)
+        ring_forward_kernel<FWD_RATIO, false><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && ll)
+        ring_forward_kernel<FWD_RATIO, true><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_NONE && ll)
+        ring_forward_kernel<FWD_NONE, true><<<blocks, kBlock, 0, s>>>(a);
+    else
+        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
+    return check_launch("ring_forward_kernel");
+}
+
 template <int GROUP>
 pet_status dispatch_mode(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
     if (mode == FWD_YHAT && !ll)
@@ -380,6 +531,11 @@ pet_status dispatch_tile(const FwdArgs &a, int mode, bool ll, int blocks, cudaSt
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s) {
     const int n_rays = (a.v_end - a.v_begin) * a.nb;
     if (n_rays == 0) return PET_OK;
+    if (a.lz) {
+        const long long n_lor = (long long)n_rays * a.nz;
+        ring_count_nnz_kernel<<<(unsigned)((n_lor + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, d_count);
+        return check_launch("ring_count_nnz_kernel");
+    }
     count_nnz_kernel<<<(n_rays + kBlock - 1) / kBlock, kBlock, 0, s>>>(a, d_count);
     return check_launch("count_nnz_kernel");
 }
@@ -453,7 +609,7 @@ int default_chunks(int nx, int ny) {
 }
 
 int choose_group(const pet_plan *plan) {
-    if (plan->nz > 1) return 1;
+    if (plan->nz > 1 || plan->ring) return 1;
     return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
 }
 
@@ -464,6 +620,10 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
     ProfileScope prof(a.t_dev ? 0 : 3, s);     // 0: subset update forward, 3: full-data / API forward
+    if (a.lz) {
+        if (group != 1) return set_error(PET_ERR_INVALID, "forward: multi-ring lines use group 1");
+        return dispatch_ring(a, mode, ll, blocks, s);
+    }
     if (a.nz == 1) {
         switch (group) {
             case 8: return dispatch_tile<8>(a, mode, ll, blocks, s);

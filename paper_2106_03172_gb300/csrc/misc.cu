@@ -69,15 +69,20 @@ __global__ void uniform_fill_kernel(float *img, long long plane, int nz, const d
     img[i] = den > 0.0 ? (float)(sums[i % nz] / den) : 0.0f;
 }
 
-// Per-block partial of R(f) = 1/2 sum_n sum_{j in N4(n)} rho(f_n - f_j): each
-// pixel adds half its four potential terms (rho in FP32, sums in FP64).
-__global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, int pot, float delta, double *part) {
+// Per-block partial of R(f) = 1/2 sum_n sum_{j in N(n)} rho(f_n - f_j): each
+// pixel adds half its potential terms (rho in FP32, sums in FP64).  N(n) is
+// the in-plane 4-neighbourhood, plus the two axial neighbours when `axial`
+// (a multi-ring volume; the slices of a stack are not coupled).
+__global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, int axial, int pot, float delta,
+                                       double *part) {
     const long long plane = (long long)nx * ny * nz;
     const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
     double r = 0.0;
     if (i < plane) {
         const int n = (int)(i / nz);
+        const int z = (int)(i % nz);
         const int ix = n % nx, iy = n / nx;
+        const bool hb = axial && z > 0, ht = axial && z + 1 < nz;
         const float fn = f[i];
         if (pot == PET_POT_QUADRATIC) {
             const double fd = fn;
@@ -86,6 +91,8 @@ __global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, i
             if (ix + 1 < nx) { const double d = fd - f[i + nz]; acc += d * d; }
             if (iy > 0) { const double d = fd - f[i - (long long)nx * nz]; acc += d * d; }
             if (iy + 1 < ny) { const double d = fd - f[i + (long long)nx * nz]; acc += d * d; }
+            if (hb) { const double d = fd - f[i - 1]; acc += d * d; }
+            if (ht) { const double d = fd - f[i + 1]; acc += d * d; }
             r = 0.25 * acc;
         } else {
             double acc = 0.0;
@@ -93,6 +100,8 @@ __global__ void penalty_partial_kernel(const float *f, int nx, int ny, int nz, i
             if (ix + 1 < nx) acc += potential_rho(pot, delta, fn - f[i + nz]);
             if (iy > 0) acc += potential_rho(pot, delta, fn - f[i - (long long)nx * nz]);
             if (iy + 1 < ny) acc += potential_rho(pot, delta, fn - f[i + (long long)nx * nz]);
+            if (hb) acc += potential_rho(pot, delta, fn - f[i - 1]);
+            if (ht) acc += potential_rho(pot, delta, fn - f[i + 1]);
             r = 0.5 * acc;
         }
     }
@@ -251,8 +260,9 @@ pet_status launch_objective_finish(const pet_problem *p, const float *img, int n
     const long long plane = (long long)pl->N * pl->nz;
     const int n_pen = (int)blocks_for(plane);
     double *pen_part = part + n_ll_blocks;
-    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, pl->nx, pl->ny, pl->nz, p->pen.potential, p->pen.delta,
-                                                    pen_part);
+    const int inner = pl->ring ? pl->layers : pl->nz;       // image entries per pixel
+    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, pl->nx, pl->ny, inner, pl->ring, p->pen.potential,
+                                                    p->pen.delta, pen_part);
     pet_status st = check_launch("penalty_partial_kernel");
     if (st != PET_OK) return st;
     objective_final_kernel<<<1, kBlock, 0, s>>>(part, n_ll_blocks, pen_part, n_pen, (double)p->pen.beta,
@@ -265,7 +275,7 @@ pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const
     const long long plane = (long long)nx * ny * nz;
     const int n_pen = (int)blocks_for(plane);
     double *pen_part = part + n_ll_blocks;
-    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, nx, ny, nz, PET_POT_QUADRATIC, 1.0f, pen_part);
+    penalty_partial_kernel<<<n_pen, kBlock, 0, s>>>(img, nx, ny, nz, 0, PET_POT_QUADRATIC, 1.0f, pen_part);
     pet_status st = check_launch("penalty_partial_kernel");
     if (st != PET_OK) return st;
     objective_final_kernel<<<1, kBlock, 0, s>>>(part, n_ll_blocks, pen_part, n_pen, (double)beta, d_out);

@@ -101,6 +101,42 @@ __device__ __forceinline__ void band_split(const ViewParams &vp, float va, float
     }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-ring lines of response.  A line's transaxial part is a 2-D ray, walked
+// band by band as above; along it z is linear in the centred major
+// coordinate kc, and in layer units (zeta = (z - z_min) / slice) each line
+// carries zeta(kc) = lz.x + lz.y * kc and the 3-D length per transaxial mm
+// lz.z = sqrt(1 + kappa^2) (FP64 on the host).  Inside band [kc, kc + 1] the
+// piece in minor pixel fl occupies the band fraction [f_lo, f_hi] below
+// (pixel fl + 1 the rest); a piece is shared between the layers its zeta
+// range crosses in proportion to the overlap.  Both projectors evaluate
+// exactly these expressions, so the 3-D A^T is the exact transpose of A.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void piece_fraction(const ViewParams &vp, float w0, float w1, bool upper, float &f_lo,
+                                               float &f_hi) {
+    if (w1 == 0.0f) {                       // the band lies in one pixel
+        f_lo = 0.0f;
+        f_hi = 1.0f;
+        return;
+    }
+    const float f0 = w0 / vp.L;             // share of pixel fl
+    // du > 0: the minor coordinate grows with kc, pixel fl comes first
+    const bool first = (vp.du > 0.0f) != upper;
+    f_lo = first ? 0.0f : (upper ? f0 : 1.0f - f0);
+    f_hi = first ? (upper ? 1.0f - f0 : f0) : 1.0f;
+}
+
+__device__ __forceinline__ float piece_zeta(const float4 &lz, float kc, float f) { return fmaf(lz.y, kc + f, lz.x); }
+
+// Share of the axial range between za and zb (layer units) inside layer iz;
+// a flat piece lies wholly in layer floor(za) (half-open layers).
+__device__ __forceinline__ float layer_fraction(float za, float zb, int iz) {
+    const float lo = fminf(za, zb), hi = fmaxf(za, zb);
+    if (!(hi > lo)) return floorf(lo) == (float)iz ? 1.0f : 0.0f;
+    const float ov = fminf(hi, (float)(iz + 1)) - fmaxf(lo, (float)iz);
+    return ov > 0.0f ? ov / (hi - lo) : 0.0f;
+}
+
 // Nonnegative root of a/f - 2 b f + c = 0 (the surrogate M-step of §3,
 // Eq. (svrsurder)); cancellation-free in both signs of c, b = 0 allowed;
 // 0 when S <= 0 or a <= 0 (zero-denominator remedy of §2.3).
@@ -195,8 +231,10 @@ struct FwdArgs {
     const int *t_dev;         // if set: subset index on the device; the range is
     const int *sub_off;       //   [sub_off[t], sub_off[t+1]) and g / w are the full
                               //   subset-major arrays (offset applied on the device)
-    int nx, ny, nz, nb;
-    const float *img;         // [ny][nx][nz]
+    int nx, ny, nz, nb;       // nz: entries per (view, bin): slices, or ring pairs (lz set)
+    int layers;               // multi-ring: image layers (voxel index = pixel * layers + iz)
+    const float4 *lz;         // multi-ring: axial table per line, [view][bin][pair]; else null
+    const float *img;         // [ny][nx][nz] ([ny][nx][layers] multi-ring)
     const float *g;           // counts of these rays (compact), FWD_RATIO / LL only
     const float *w;           // background of these rays (compact) or null
     float w_scalar;
@@ -230,8 +268,12 @@ struct BackArgs {
     int run;              // single-slice tile kernel: pixels per run (4 or 8)
     int r_view0;          // view position of r[0] (ignored when t_dev is set: r is
                           //   then the compact ratio of subset *t_dev)
-    int nx, ny, nz, nb, ns;
-    const float *r;       // ratio / sinogram, [view pos - r_view0][bin][z]
+    int nx, ny, nz, nb, ns;  // nz: image entries per pixel (slices, or layers when axial)
+    int axial;            // multi-ring: layers are coupled (6-neighbourhood penalty) and the
+                          //   sensitivities are per voxel ([ns][nx*ny*nz]); else per pixel
+    int pairs;            // multi-ring: sinogram entries per (view, bin)
+    const float4 *lz;     // multi-ring: axial table per line, [view][bin][pair]
+    const float *r;       // ratio / sinogram, [view pos - r_view0][bin][z] ([..][bin][pair])
     float *out;           // EPI_PLAIN: image; EPI_ANCHOR: B [ns][N*nz]
     // update inputs
     const float *f;       // current iterate f^k
@@ -293,8 +335,11 @@ struct BatchMember {
 
 struct pet_plan {
     pet_geometry geom;
-    int nx, ny, nz, na, nb, ns;
-    int N, M;                       // pixels and rays of one slice
+    int nx, ny, nz, na, nb, ns;     // nz: independent slices (1 for a multi-ring volume)
+    int N, M;                       // pixels and rays of one slice; multi-ring: voxels and lines
+    int ring = 0;                   // multi-ring scanner (fully 3-D lines of response)
+    int layers = 1;                 // multi-ring: image layers
+    int pairs = 1;                  // multi-ring: ring pairs (lines per ray)
     int max_sub_views;
     int device;
     int fwd_chunks = 0;             // single-slice forward: band chunks per ray (8, 16 or 32)
@@ -310,6 +355,7 @@ struct pet_plan {
     int *d_all_off = nullptr;       // {0, na}
     float *d_sens_t = nullptr;      // [ns][N]
     float *d_sens = nullptr;        // [N]
+    float4 *d_lz = nullptr;         // multi-ring: axial table per line [view][bin][pair]
 };
 
 struct pet_problem {

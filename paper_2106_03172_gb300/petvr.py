@@ -35,7 +35,8 @@ class PetError(RuntimeError):
 
 class pet_geometry(ctypes.Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("pixel_mm", c_double),
-                ("n_angles", c_int32), ("n_bins", c_int32), ("bin_mm", c_double)]
+                ("n_angles", c_int32), ("n_bins", c_int32), ("bin_mm", c_double),
+                ("n_rings", c_int32), ("ring_mm", c_double), ("radius_mm", c_double), ("slice_mm", c_double)]
 
 
 class pet_subsets(ctypes.Structure):
@@ -141,7 +142,9 @@ def _seq(seq):
 
 def pet_plan_create(geom, n_subsets: int) -> c_void_p:
     g = pet_geometry(geom.nx, geom.ny, geom.nz, geom.pixel_mm, geom.n_angles, geom.n_bins,
-                     geom.bin_mm if geom.bin_mm is not None else 0.0)
+                     geom.bin_mm if geom.bin_mm is not None else 0.0,
+                     getattr(geom, "n_rings", 0), getattr(geom, "ring_mm", 0.0),
+                     getattr(geom, "radius_mm", 0.0), getattr(geom, "slice_mm", 0.0))
     h = c_void_p()
     _call("pet_plan_create", byref(g), byref(pet_subsets(n_subsets, 0)), byref(h))
     return h
@@ -369,6 +372,11 @@ class Plan:
 
     def subset_rays(self, t: int) -> int:
         return self.subset_views[t] * self.geom.n_bins
+
+    def subset_lines(self, t: int) -> int:
+        """Sinogram entries of subset t per slice: rays, times ring pairs on a multi-ring scanner."""
+        rings = getattr(self.geom, "n_rings", 0)
+        return self.subset_rays(t) * (rings * rings if rings else 1)
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

@@ -20,6 +20,22 @@ CASES = {
                      geometry=Geometry(24, 24, 18, 35, bin_mm=1.4, nz=5), n_subsets=3, counts=2e5),
 }
 
+# multi-ring volumes (fully 3-D lines of response)
+RING_CASES = {
+    # two rings on a clinical-size cylinder (kappa <= ~0.007), rings at layer centres
+    "ring2": Workload("ring2", Geometry(32, 32, 30, 47, nz=3, n_rings=2, ring_mm=4.0, radius_mm=300.0,
+                                       slice_mm=2.0), n_subsets=5, counts=3e5, bg_frac=0.1, beta=0.02, n_ellipses=5),
+    # three rings on a narrow cylinder: steep lines whose pieces cross layer faces
+    "ring3steep": Workload("ring3steep", Geometry(24, 20, 18, 33, bin_mm=1.6, nz=6, n_rings=3, ring_mm=7.0,
+                                                  radius_mm=36.0, slice_mm=3.0),
+                           n_subsets=3, counts=2e5, bg_frac=0.1, beta=0.02, n_ellipses=4),
+    # rings on layer faces (z = -4, 0, +4): half-open layers decide the direct planes
+    "ringfaces": Workload("ringfaces", Geometry(16, 16, 12, 23, nz=2, n_rings=3, ring_mm=4.0, radius_mm=40.0,
+                                                slice_mm=4.0), n_subsets=4, counts=1e5, bg_frac=0.1, beta=0.02,
+                          n_ellipses=3),
+}
+CASES.update(RING_CASES)
+
 
 @functools.lru_cache(maxsize=None)
 def oracle_problem(name: str, seed: int = 0):

@@ -74,3 +74,7 @@ def test_batch_rejects_bad_input():
     batch = pv.Batch([st])
     with pytest.raises(pv.PetError):
         batch.epoch([[0, work.n_subsets]], [1.0], [1])
+    # batches take single-slice images: a multi-ring volume is refused
+    plan3, gp3, f3, _ = _setup(pv, "ring2")
+    with pytest.raises(pv.PetError):
+        pv.Batch([pv.State(gp3, "saga", f3.clone())])

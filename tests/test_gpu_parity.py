@@ -60,15 +60,15 @@ def test_forward_parity(case):
     geom = work.geometry
     f = np.random.default_rng(1).uniform(0.5, 3.0, (prob.N, prob.nz))
     fd = _cuda(f)
-    out = torch.empty(geom.n_rays * geom.nz, device="cuda")
+    out = torch.empty(prob.M * prob.nz, device="cuda")
     pv.pet_forward(plan.handle, fd, None, 0.25, -1, out)
-    _assert_proj(_host(out).reshape(-1, geom.nz), prob.A @ f + 0.25)
+    _assert_proj(_host(out).reshape(-1, prob.nz), prob.A @ f + 0.25)
     bg = np.random.default_rng(2).uniform(0.0, 1.0, (prob.M, prob.nz))
     for t in range(work.n_subsets):
         rows = prob.subsets[t]
-        sub = torch.empty(len(rows) * geom.nz, device="cuda")
+        sub = torch.empty(len(rows) * prob.nz, device="cuda")
         pv.pet_forward(plan.handle, fd, _cuda(bg[rows]), 0.0, t, sub)
-        _assert_proj(_host(sub).reshape(-1, geom.nz), prob.At[t] @ f + bg[rows])
+        _assert_proj(_host(sub).reshape(-1, prob.nz), prob.At[t] @ f + bg[rows])
 
 
 def test_back_parity_and_adjoint(case):
@@ -77,11 +77,11 @@ def test_back_parity_and_adjoint(case):
     y = np.random.default_rng(3).uniform(0.0, 2.0, (prob.M, prob.nz))
     img = torch.empty(prob.N * prob.nz, device="cuda")
     pv.pet_back(plan.handle, _cuda(y), -1, img)
-    _assert_proj(_host(img).reshape(-1, geom.nz), prob.A.T @ y)
+    _assert_proj(_host(img).reshape(-1, prob.nz), prob.A.T @ y)
     for t in range(work.n_subsets):
         rows = prob.subsets[t]
         pv.pet_back(plan.handle, _cuda(y[rows]), t, img)
-        _assert_proj(_host(img).reshape(-1, geom.nz), prob.At[t].T @ y[rows])
+        _assert_proj(_host(img).reshape(-1, prob.nz), prob.At[t].T @ y[rows])
     # adjoint identity <A x, y> = <x, A^T y>, both sides on the GPU
     x = np.random.default_rng(4).uniform(0.0, 1.0, (prob.N, prob.nz))
     ax = torch.empty(prob.M * prob.nz, device="cuda")
