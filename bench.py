@@ -77,9 +77,13 @@ def parse_args():
 def workload_config(work):
     g = work.geometry
     return {
-        "workload": f"{work.name}: {g.nx}x{g.ny} image ({g.pixel_mm:g} mm pixels), {g.n_angles} views x "
+        "workload": f"{work.name}: {g.nx}x{g.ny}" + (f"x{g.nz} volume ({g.n_rings} rings {g.ring_mm:g} mm apart, "
+                                                      f"cylinder radius {g.radius_mm:g} mm, {g.slice_mm:g} mm layers, "
+                                                      f"{g.n_pairs} lines per ray)" if g.multiring else " image")
+                    + f" ({g.pixel_mm:g} mm pixels), {g.n_angles} views x "
                     f"{g.n_bins} bins, {work.n_subsets} angle-interleaved subsets, {work.counts:.0e} counts, "
-                    f"{int(round(work.bg_frac * 100))}% background, quadratic beta={work.beta}",
+                    f"{int(round(work.bg_frac * 100))}% background, {work.potential}"
+                    + (f" (delta={work.delta:g})" if work.potential != "quadratic" else "") + f" beta={work.beta}",
         "step": f"one epoch each of OSEM, SVREM(alpha={work.alpha_svrem}, eta={work.eta_svrem}), "
                 f"SAGA(alpha={work.alpha_saga}, fp32 table), SVRG(alpha={work.alpha_svrg}, eta={work.eta_svrg}), "
                 "each followed by its FP64 objective",
@@ -206,7 +210,7 @@ def oracle_steps(work, data, n_steps: int, warmup: int = 0):
     from oracle import em
     from oracle.em import build_problem
     t0 = time.perf_counter()
-    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta, work.potential, work.delta)
     f0 = prob.initial_image()
     setup = time.perf_counter() - t0
     a = alphas(work)
@@ -272,10 +276,11 @@ def kernel_source_digest() -> str:
     return h.hexdigest()
 
 
-def dram_traffic_record(kind: int):
+def dram_traffic_record(kind: int, workload: str = "c256"):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary (profiles/roofline_traffic.txt), or None when that summary was
-    taken on other kernel sources or does not cover this kernel kind."""
+    taken on other kernel sources, another workload, or does not cover this
+    kernel kind."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -285,6 +290,8 @@ def dram_traffic_record(kind: int):
             key, val = line.split(":", 1)
             rec[key.strip()] = val.strip()
     key = f"kind{kind}_dram_bytes_per_launch"
+    if rec.get("workload", "c256") != workload:
+        return None
     if rec.get("source_sha256") != kernel_source_digest() or key not in rec:
         return None
     return float(rec[key])
@@ -307,7 +314,7 @@ def phi_star_for(work, data):
         if ent and ent["counts_sha256"] == sha:
             return ent["phi_star"], "tests/golden/phi_star.json (FP64 oracle, L-BFGS-B)"
     from oracle.em import build_problem, map_reference
-    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta, work.potential, work.delta)
     _, phi, _ = map_reference(prob)
     return phi, "FP64 oracle L-BFGS-B computed at run time (counts differ from the stored checksum)"
 
@@ -386,7 +393,7 @@ def run_ours(args):
     else:
         tuning = petvr.pet_plan_autotune(plan.handle)   # launch shapes timed on this geometry
         tune_src = "pet_plan_autotune"
-    prob = petvr.Problem(plan, g_dev, None, data["w"], work.beta)
+    prob = petvr.Problem(plan, g_dev, None, data["w"], work.beta, potential=work.potential, delta=work.delta)
     f0 = torch.empty(geom.n_pixels * geom.nz, device="cuda")
     petvr.pet_warm_start(prob.handle, f0)
     imgs = {m: f0.clone() for m in METHODS}
@@ -459,11 +466,13 @@ def run_ours(args):
 
     # ---- profiled pass: per-kernel durations for the roofline
     n_prof = min(args.steps, 8)
-    kinds_named = {0: "forward_tile_kernel (subset update, ratio)", 1: "back_tile_kernel (update epilogue)",
-                   2: "back_tile_kernel (anchor, all subsets)", 3: "forward_tile_kernel (all rays: anchor/objective)"}
+    fk, bk = (("ring_forward_kernel", "ring_back_kernel") if geom.multiring else
+              ("forward_kernel", "back_pixel_kernel") if geom.nz > 1 else ("forward_tile_kernel", "back_tile_kernel"))
+    kinds_named = {0: f"{fk} (subset update, ratio)", 1: f"{bk} (update epilogue)",
+                   2: f"{bk} (anchor, all subsets)", 3: f"{fk} (all rays: anchor/objective)"}
     alg_flops = {k: 0.0 for k in kinds_named}
     alg_bytes = {k: 0.0 for k in kinds_named}
-    N, M = geom.n_pixels, geom.n_rays
+    N, M = geom.n_pixels * geom.nz, geom.n_rays * geom.n_pairs      # image and sinogram floats
     upd_bytes = {"osem": 12, "svrem": 32, "saga": 32, "svrg": 20}   # per pixel, see DESIGN
     petvr.pet_profile_reset()
     petvr.pet_profile_enable(True)
@@ -473,7 +482,7 @@ def run_ours(args):
         seqs = one_step(args.warmup + args.steps + k, concurrent=False)
         for i, m in enumerate(METHODS):
             for t in seqs[i]:
-                rays = plan.subset_rays(int(t))
+                rays = plan.subset_lines(int(t)) * (1 if geom.multiring else geom.nz)
                 alg_flops[0] += 2.0 * nnz_t[int(t)]
                 alg_bytes[0] += 4.0 * N + 8.0 * rays
                 alg_flops[1] += 2.0 * nnz_t[int(t)]
@@ -499,7 +508,7 @@ def run_ours(args):
     dom = max(kinds, key=lambda k: kinds[k]["total_ms"])
     peak_alu = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
     achieved = alg_flops[dom] / (kinds[dom]["total_ms"] / 1e3) / 1e12
-    traffic = dram_traffic_record(dom)
+    traffic = dram_traffic_record(dom, work.name)
     roofline = {"bound": "alu", "kernel": kinds[dom]["name"], "achieved": achieved, "peak": peak_alu,
                 "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)",
@@ -530,7 +539,7 @@ def run_ours(args):
         e2e_ms.append(s_ev.elapsed_time(e_ev))
         rep.advance()
     e2e_value, _, _ = combine_ranks(float(sum(e2e_ms)), float(e2e_pairs), device="cuda")
-    h2d = 4 * geom.n_rays * geom.nz
+    h2d = 4 * geom.n_rays * geom.n_pairs
     d2h = 4 * 4 * geom.n_pixels * geom.nz + 4 * 3 * 8
 
     # ---- reconstructions to a 1e-4 relative objective gap (Phi* from the oracle)

@@ -105,6 +105,8 @@ class Workload:
     alpha_saga: float = 1.0
     alpha_svrg: float = 2.0
     stack: bool = False
+    potential: str = "quadratic"
+    delta: float = 1.0
     extra: dict = field(default_factory=dict)
 
 
@@ -125,6 +127,13 @@ WORKLOADS = {
         "c128x47", Geometry(128, 128, 252, 344, bin_mm=math.sqrt(2.0) * 128 * 2.0 / 344, nz=47),
         n_subsets=14, counts=5e8, bg_frac=0.15, beta=0.002, n_ellipses=10, epochs=10,
         methods=("svrg",), eta_svrg=2, stack=True),
+    # fully 3-D data of a 2-ring scanner, shaped after the torso experiment of §5.3 (280 views,
+    # 20 subsets of 14 views, log-cosh penalty with delta = 1, SVRG anchor every 5 epochs and
+    # SVREM every 3): 128 x 128 x 3 volume (direct and cross planes, slice = ring/2)
+    "ring2_128": Workload(
+        "ring2_128", Geometry(128, 128, 280, 183, nz=3, n_rings=2, ring_mm=4.0, radius_mm=400.0, slice_mm=2.0),
+        n_subsets=20, counts=1e7, bg_frac=0.10, beta=0.005, n_ellipses=12, epochs=10,
+        methods=("osem", "svrem", "saga", "svrg"), eta_svrg=5, eta_svrem=3, potential="logcosh", delta=1.0),
 }
 
 

@@ -43,7 +43,7 @@ def oracle_problem(name: str, seed: int = 0):
     from oracle.em import build_problem
     work = CASES.get(name) or WORKLOADS[name]
     data = make_data(work, seed)
-    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta, work.potential, work.delta)
     return prob, data, work
 
 

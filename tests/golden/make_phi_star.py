@@ -42,7 +42,7 @@ def main(names):
     for name in names:
         work = WORKLOADS.get(name) or SERVING_POOL[name]
         data = make_data(work, 0)
-        prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+        prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta, work.potential, work.delta)
         t = time.time()
         _, phi, kkt = map_reference(prob)
         entry = {"seed": 0, "phi_star": phi, "kkt_residual": kkt,
