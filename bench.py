@@ -204,9 +204,10 @@ def visible_index(torch):
 
 # --------------------------------------------------------------------------- oracle timing
 
-def oracle_steps(work, data, n_steps: int, warmup: int = 0):
-    """Time ``n_steps`` oracle steps (the bench step in FP64 on the host);
-    returns (per-step seconds, per-step pairs, setup seconds)."""
+def oracle_steps(work, data, n_steps: int, warmup: int = 0, min_seconds: float = 0.0, max_steps: int = 64):
+    """Time ``n_steps`` oracle steps (the bench step in FP64 on the host),
+    continuing up to ``max_steps`` while fewer than ``min_seconds`` have been
+    timed; returns (per-step seconds, per-step pairs, setup seconds)."""
     from oracle import em
     from oracle.em import build_problem
     t0 = time.perf_counter()
@@ -219,7 +220,8 @@ def oracle_steps(work, data, n_steps: int, warmup: int = 0):
     f_osem = f0.copy()
     rep = Replica(work)
     times, pairs = [], []
-    for step in range(warmup + n_steps):
+    step = 0
+    while step < warmup + n_steps or (sum(times) < min_seconds and len(times) < max_steps):
         seqs = seqs_for_step(step, work.n_subsets)
         p, _ = rep.step_pairs()
         t = time.perf_counter()
@@ -234,6 +236,7 @@ def oracle_steps(work, data, n_steps: int, warmup: int = 0):
         if step >= warmup:
             times.append(dt)
             pairs.append(p)
+        step += 1
     return times, pairs, setup
 
 
@@ -569,10 +572,10 @@ def run_ours(args):
         "objective_last_step": [float(x) for x in phi_host[:, 0]],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, cpairs, setup = oracle_steps(work, data, 8)
+        times, cpairs, setup = oracle_steps(work, data, 8, min_seconds=12.0)
         line["cpu_baseline"] = {
             "value": sum(cpairs) / sum(times), "unit": unit, "cores": 1, "kind": "oracle",
-            "sample": f"8 bench steps of the FP64 oracle (about {sum(times):.0f} s; system matrix build "
+            "sample": f"{len(times)} bench steps of the FP64 oracle (about {sum(times):.0f} s; system matrix build "
                       f"and warm start, {setup:.1f} s, untimed)"}
     if world > 1:
         dist.barrier()

@@ -233,13 +233,15 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
     __syncthreads();
     const int r_view0 = a.t_dev ? vb : a.r_view0;
 
+    // 32-bit index arithmetic: images are below 2^31 elements (checked at plan time)
     const long long plane = (long long)a.nx * a.ny * a.nz;
     const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
     const long long i = gid / kLanes;                    // (pixel, slice)
     const int lane = (int)(gid % kLanes);
     const bool live = i < plane;
-    const int z = (int)(i % a.nz);
-    const int n = (int)(i / a.nz);
+    const int iv = (int)min(i, plane);
+    const int z = iv % a.nz;
+    const int n = iv / a.nz;
     const int ix = n % a.nx;
     const int iy = n / a.nx;
 
@@ -291,14 +293,16 @@ __global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
     __syncthreads();
     const int r_view0 = a.t_dev ? vb : a.r_view0;
 
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
     const int L = a.nz, P = a.pairs;
-    const long long plane = (long long)a.nx * a.ny * L;
+    const int plane = a.nx * a.ny * L;
     const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
     const long long i = gid / kLanes;                    // voxel
     const int lane = (int)(gid % kLanes);
     const bool live = i < plane;
-    const int iz = (int)(i % L);
-    const int n = (int)(i / L);
+    const int iv = (int)i;
+    const int iz = iv % L;
+    const int n = iv / L;
     const int ix = n % a.nx;
     const int iy = n / a.nx;
 
@@ -315,9 +319,9 @@ __global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
             const float kc = (float)k - 0.5f * (float)n_major;
             int jlo, jhi;
             candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
-            const float2 *ucv = a.uc + (long long)v * a.nb;
-            const float4 *lzv = a.lz + (long long)v * a.nb * P;
-            const float *rv = a.r + (long long)(vb + q - r_view0) * a.nb * P;
+            const float2 *ucv = a.uc + v * a.nb;
+            const float4 *lzv = a.lz + v * a.nb * P;
+            const float *rv = a.r + (vb + q - r_view0) * a.nb * P;
             for (int j = jlo; j <= jhi; ++j) {
                 const float2 u = __ldg(ucv + j);
                 float fl, w0, w1;
@@ -329,9 +333,9 @@ __global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
                 float f_lo, f_hi;
                 piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
                 for (int pr = 0; pr < P; ++pr) {
-                    const float4 lz = __ldg(lzv + (long long)j * P + pr);
+                    const float4 lz = __ldg(lzv + j * P + pr);
                     const float fr = layer_fraction(piece_zeta(lz, kc, f_lo), piece_zeta(lz, kc, f_hi), iz);
-                    if (fr > 0.0f) acc = fmaf((w * lz.z) * fr, __ldg(rv + (long long)j * P + pr), acc);
+                    if (fr > 0.0f) acc = fmaf((w * lz.z) * fr, __ldg(rv + j * P + pr), acc);
                 }
             }
         }

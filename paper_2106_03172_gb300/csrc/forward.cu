@@ -49,17 +49,19 @@ template <int GROUP, int MODE, bool LL>
 __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
     const RayRange rr = ray_range(a);
     const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
-    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const int z = (int)(tid % a.nz);
-    const long long rest = tid / a.nz;
-    const int lane_g = (int)(rest % GROUP);
-    const long long ray = rest / GROUP;
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const int tid = (int)min(gtid, (long long)n_rays * a.nz * GROUP);
+    const int z = tid % a.nz;
+    const int rest = tid / a.nz;
+    const int lane_g = rest % GROUP;
+    const int ray = rest / GROUP;
     const bool live = ray < n_rays;
 
     float acc = 0.0f;
     if (live) {
-        const int p = rr.v_begin + (int)(ray / a.nb);
-        const int j = (int)(ray % a.nb);
+        const int p = rr.v_begin + ray / a.nb;
+        const int j = ray % a.nb;
         const int v = __ldg(a.order + p);
         const ViewParams vp = a.views[v];
         const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
@@ -343,40 +345,49 @@ __global__ void __launch_bounds__(kBlock) count_nnz_kernel(const FwdArgs a, unsi
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-// Multi-ring forward: one thread per line of response (ray, ring pair), the
-// pairs of one ray on consecutive threads (they read the same voxel columns).
-// Each thread walks its ray's bands; every band piece is spread over the
-// layers its axial range crosses (piece_fraction / piece_zeta /
-// layer_fraction, shared with the back projection).  Epilogue as above.
-template <int MODE, bool LL>
+// Multi-ring forward: CH consecutive lanes per line of response (ray, ring
+// pair), each walking one chunk of the ray's bands (chunks aligned to the
+// same bands for every line, so neighbouring lines read the same image rows),
+// then an xor-shuffle sum over the CH lanes in a fixed order.  Every band
+// piece is spread over the layers its axial range crosses (piece_fraction /
+// piece_zeta / layer_fraction, shared with the back projection).  Epilogue
+// as above, on the chunk-0 lane.
+template <int MODE, bool LL, int CH>
 __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
     const RayRange rr = ray_range(a);
     const int P = a.nz;
     const long long n_lor = (long long)(rr.v_end - rr.v_begin) * a.nb * P;
-    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const int chunk = (int)(gtid % CH);
+    const long long tid = gtid / CH;                     // line index in the range
     const bool live = tid < n_lor;
     float acc = 0.0f;
     if (live) {
-        const int pr = (int)(tid % P);
-        const long long ray = tid / P;
-        const int q = rr.v_begin + (int)(ray / a.nb);
-        const int j = (int)(ray % a.nb);
+        // 32-bit index arithmetic: sinograms and images are below 2^31 elements (checked at plan time)
+        const int lt = (int)tid;
+        const int pr = lt % P;
+        const int ray = lt / P;
+        const int q = rr.v_begin + ray / a.nb;
+        const int j = ray % a.nb;
         const int v = __ldg(a.order + q);
         const ViewParams vp = a.views[v];
-        const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
-        const float4 lz = __ldg(a.lz + ((long long)v * a.nb + j) * P + pr);
+        const float2 u = __ldg(a.uc + v * a.nb + j);
+        const float4 lz = __ldg(a.lz + (v * a.nb + j) * P + pr);
         const int n_major = vp.col ? a.nx : a.ny;
         const int n_minor = vp.col ? a.ny : a.nx;
         const float hm = 0.5f * (float)n_major;
         const int ui = (int)u.x + (n_minor >> 1);
-        const long long s_major = vp.col ? 1 : a.nx;     // pixel strides
-        const long long s_minor = vp.col ? a.nx : 1;
+        const int s_major = vp.col ? 1 : a.nx;           // pixel strides
+        const int s_minor = vp.col ? a.nx : 1;
         const int L = a.layers;
         int k_lo, k_hi;
         band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
-        float kc = (float)k_lo - hm;
+        const int per = (n_major + CH - 1) / CH;
+        const int kb = max(k_lo, chunk * per);
+        const int ke = min(k_hi, (chunk + 1) * per);
+        float kc = (float)kb - hm;
         float va = band_point(vp, u.y, kc);
-        for (int k = k_lo; k < k_hi; ++k) {
+        for (int k = kb; k < ke; ++k) {
             const float vb = band_point(vp, u.y, kc + 1.0f);
             float fl, w0, w1;
             band_split(vp, va, vb, fl, w0, w1);
@@ -392,7 +403,7 @@ __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
                 const float wl = w * lz.z;
                 const int il = max(0, (int)floorf(fminf(za, zb)));
                 const int ih = min(L - 1, (int)floorf(fmaxf(za, zb)));
-                const float *colp = a.img + (k * s_major + m * s_minor) * L;
+                const float *colp = a.img + (k * s_major + m * s_minor) * L;     // < 2^31 (plan check)
                 for (int iz = il; iz <= ih; ++iz) {
                     const float fr = layer_fraction(za, zb, iz);
                     if (fr > 0.0f) acc = fmaf(wl * fr, __ldg(colp + iz), acc);
@@ -402,8 +413,10 @@ __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
             kc += 1.0f;
         }
     }
+#pragma unroll
+    for (int o = CH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     double ll = 0.0;
-    if (live) {
+    if (live && chunk == 0) {
         const long long gi = rr.off + tid;
         const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
         if (MODE == FWD_YHAT) a.out[tid] = yhat;
@@ -480,15 +493,16 @@ __global__ void __launch_bounds__(kBlock) ring_count_nnz_kernel(const FwdArgs a,
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+template <int CH>
 pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
     if (mode == FWD_YHAT && !ll)
-        ring_forward_kernel<FWD_YHAT, false><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_YHAT, false, CH><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && !ll)
-        ring_forward_kernel<FWD_RATIO, false><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_RATIO, false, CH><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && ll)
-        ring_forward_kernel<FWD_RATIO, true><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_RATIO, true, CH><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_NONE && ll)
-        ring_forward_kernel<FWD_NONE, true><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_NONE, true, CH><<<blocks, kBlock, 0, s>>>(a);
     else
         return set_error(PET_ERR_INVALID, "forward: unsupported mode");
     return check_launch("ring_forward_kernel");
@@ -609,7 +623,9 @@ int default_chunks(int nx, int ny) {
 }
 
 int choose_group(const pet_plan *plan) {
-    if (plan->nz > 1 || plan->ring) return 1;
+    if (plan->ring)                                                  // band chunks per line
+        return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
+    if (plan->nz > 1) return 1;
     return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
 }
 
@@ -621,8 +637,12 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
     if (blocks == 0) return PET_OK;
     ProfileScope prof(a.t_dev ? 0 : 3, s);     // 0: subset update forward, 3: full-data / API forward
     if (a.lz) {
-        if (group != 1) return set_error(PET_ERR_INVALID, "forward: multi-ring lines use group 1");
-        return dispatch_ring(a, mode, ll, blocks, s);
+        switch (group) {
+            case 8: return dispatch_ring<8>(a, mode, ll, blocks, s);
+            case 16: return dispatch_ring<16>(a, mode, ll, blocks, s);
+            case 32: return dispatch_ring<32>(a, mode, ll, blocks, s);
+            default: return set_error(PET_ERR_INVALID, "forward: unsupported band chunk count");
+        }
     }
     if (a.nz == 1) {
         switch (group) {

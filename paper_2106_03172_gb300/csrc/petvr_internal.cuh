@@ -119,7 +119,9 @@ __device__ __forceinline__ void piece_fraction(const ViewParams &vp, float w0, f
         f_hi = 1.0f;
         return;
     }
-    const float f0 = w0 / vp.L;             // share of pixel fl
+    // share of pixel fl (fast division: no slow-path call; both projectors
+    // evaluate this same expression, so the transpose stays exact)
+    const float f0 = __fdividef(w0, vp.L);
     // du > 0: the minor coordinate grows with kc, pixel fl comes first
     const bool first = (vp.du > 0.0f) != upper;
     f_lo = first ? 0.0f : (upper ? f0 : 1.0f - f0);
@@ -134,7 +136,7 @@ __device__ __forceinline__ float layer_fraction(float za, float zb, int iz) {
     const float lo = fminf(za, zb), hi = fmaxf(za, zb);
     if (!(hi > lo)) return floorf(lo) == (float)iz ? 1.0f : 0.0f;
     const float ov = fminf(hi, (float)(iz + 1)) - fmaxf(lo, (float)iz);
-    return ov > 0.0f ? ov / (hi - lo) : 0.0f;
+    return ov > 0.0f ? __fdividef(ov, hi - lo) : 0.0f;
 }
 
 // Nonnegative root of a/f - 2 b f + c = 0 (the surrogate M-step of §3,
