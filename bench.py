@@ -470,7 +470,7 @@ def run_ours(args):
     # ---- profiled pass: per-kernel durations for the roofline
     n_prof = min(args.steps, 8)
     fk, bk = (("ring_forward_kernel", "ring_back_kernel") if geom.multiring else
-              ("forward_kernel", "back_pixel_kernel") if geom.nz > 1 else ("forward_tile_kernel", "back_tile_kernel"))
+              ("forward_stack_kernel", "back_stack_kernel") if geom.nz > 1 else ("forward_tile_kernel", "back_tile_kernel"))
     kinds_named = {0: f"{fk} (subset update, ratio)", 1: f"{bk} (update epilogue)",
                    2: f"{bk} (anchor, all subsets)", 3: f"{fk} (all rays: anchor/objective)"}
     alg_flops = {k: 0.0 for k in kinds_named}

@@ -1,17 +1,19 @@
 // Back projection as a pixel-driven gather (K2), fused with the per-pixel
 // update of each method (K3).
 //
-// b_n = sum_{m in S_t} a_mn r_m: four lanes per (pixel, slice) share the
-// views of the subset (lane l takes views l, l+4, ...) and combine with an
-// xor-shuffle in a fixed order.  In each view only the bins whose ray can
-// cross the pixel's major band at the pixel are candidates (usually 2-3),
-// found from the bin spacing K, and each candidate's weight comes from
-// band_point() / band_split(), the functions the forward kernel uses, so A^T
-// here is the exact transpose of A there.  A gather (not atomics) keeps the
-// result deterministic.
+// b_n = sum_{m in S_t} a_mn r_m as a gather per pixel (no atomics, so the
+// result is deterministic).  Single slices use tiles with runs of pixels
+// that share each ray's band split (back_tile_kernel); slice stacks carry a
+// block of 8 slices per thread; multi-ring volumes split each band piece over
+// the layers its axial range crosses.  In each view only the bins whose ray
+// can cross the pixel's major band at the pixel are candidates (usually
+// 2-3), found from the bin spacing K, and each candidate's weight comes from
+// band_point() / band_split(), the functions the forward kernels use, so A^T
+// here is the exact transpose of A there.
 //
-// The epilogue then applies, with b_n still in a register (§8 of the method's
-// update rules; the quadratic 4-neighbour penalty of §3 is read from f^k):
+// The epilogue then applies the method's update with b_n still in a
+// register (the penalty's neighbours, 4 in a plane and 2 more along z in a
+// volume, are read from f^k, §3):
 //   OSEM   f' = root(a = f b, S = sens_t, beta / N_s)                (§2.2, §3)
 //   SVREM  s' = (1-alpha) s + alpha (N_s f b - N_s f_anc B_t + s_anc),
 //          f' = root(a = s', S = sens, beta)                        (§2.3, §3)
@@ -219,10 +221,16 @@ __device__ __forceinline__ void stage_views(const BackArgs &a, int vb, int nv, V
     }
 }
 
-// General path (slice stacks): kLanes lanes per (pixel, slice) share the
-// subset's views and combine with an xor-shuffle in a fixed order.
+// Slice-stack path: the geometry is shared by every slice, so a thread takes
+// a block of kSliceBlock consecutive slices of one pixel (sums in registers)
+// and kLanes lanes share the subset's views (lane l takes views l, l+4, ...).
+// Each candidate bin's band piece is found once per slice block; the ratios
+// of its slices are contiguous ([view][bin][z]).  After the lane sum, lane l
+// applies the update to slices l, l + kLanes, ... of the block.
+constexpr int kSliceBlock = 8;
+
 template <int EPI, typename TQ, bool GENPOT>
-__global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
+__global__ void __launch_bounds__(kBlock) back_stack_kernel(const BackArgs a) {
     extern __shared__ unsigned char smem_raw[];
     ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
     const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
@@ -233,19 +241,21 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
     __syncthreads();
     const int r_view0 = a.t_dev ? vb : a.r_view0;
 
-    // 32-bit index arithmetic: images are below 2^31 elements (checked at plan time)
-    const long long plane = (long long)a.nx * a.ny * a.nz;
-    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const long long i = gid / kLanes;                    // (pixel, slice)
-    const int lane = (int)(gid % kLanes);
-    const bool live = i < plane;
-    const int iv = (int)min(i, plane);
-    const int z = iv % a.nz;
-    const int n = iv / a.nz;
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
+    const int gid = blockIdx.x * kBlock + threadIdx.x;
+    const int lane = gid % kLanes;
+    const int rest = gid / kLanes;
+    const int z0 = (rest % nzb) * kSliceBlock;
+    const int n = rest / nzb;                            // pixel
+    const bool live = n < a.nx * a.ny;
     const int ix = n % a.nx;
     const int iy = n / a.nx;
+    const int zc = min(kSliceBlock, a.nz - z0);          // slices in this block
 
-    float acc = 0.0f;
+    float acc[kSliceBlock];
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
     if (live) {
         for (int q = lane; q < nv; q += kLanes) {
             const ViewParams vp = s_views[q];
@@ -258,22 +268,31 @@ __global__ void __launch_bounds__(kBlock) back_pixel_kernel(const BackArgs a) {
             const float kc = (float)k - 0.5f * (float)n_major;
             int jlo, jhi;
             candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
-            const float2 *ucv = a.uc + (long long)v * a.nb;
-            const float *rv = a.r + ((long long)(vb + q - r_view0) * a.nb) * a.nz + z;
+            const float2 *ucv = a.uc + v * a.nb;
+            const float *rv = a.r + (vb + q - r_view0) * a.nb * a.nz + z0;
             for (int j = jlo; j <= jhi; ++j) {
                 const float2 u = __ldg(ucv + j);
                 float fl, w0, w1;
                 band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
                 const int c0 = (int)fl + (int)u.x;
                 const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
-                if (w != 0.0f) acc = fmaf(w, __ldg(rv + (long long)j * a.nz), acc);
+                if (w == 0.0f) continue;
+                const float *rj = rv + j * a.nz;
+#pragma unroll
+                for (int zz = 0; zz < kSliceBlock; ++zz)
+                    if (zz < zc) acc[zz] = fmaf(w, __ldg(rj + zz), acc[zz]);
             }
         }
     }
 #pragma unroll
-    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (!live || lane != 0) return;
-    apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, z, acc);
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+#pragma unroll
+        for (int o = kLanes / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
+    if (!live) return;
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+        if (zz % kLanes == lane && zz < zc)
+            apply_epilogue<EPI, TQ, GENPOT>(a, t, (long long)n * a.nz + z0 + zz, n, ix, iy, z0 + zz, acc[zz]);
 }
 
 // Multi-ring path: kLanes lanes per voxel share the subset's views (lane l
@@ -344,6 +363,87 @@ __global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
     for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (!live || lane != 0) return;
     apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, iz, acc);
+}
+
+// Multi-ring path for volumes of at most LMAX layers: kLanes lanes per pixel
+// column share the subset's views; every candidate bin's band piece is found
+// once per pixel and each ring pair's share is added to the layers its axial
+// range crosses (per-layer sums in registers).  After the lane sum, lane l
+// applies the update to layers l, l + kLanes, ...
+template <int EPI, typename TQ, bool GENPOT, int LMAX>
+__global__ void __launch_bounds__(kBlock) ring_back_column_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    stage_views(a, vb, nv, s_views, s_vid);
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const int L = a.nz, P = a.pairs;
+    const int npix = a.nx * a.ny;
+    const int gid = blockIdx.x * kBlock + threadIdx.x;
+    const int n = gid / kLanes;                          // pixel
+    const int lane = gid % kLanes;
+    const bool live = n < npix;
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+
+    float acc[LMAX];
+#pragma unroll
+    for (int iz = 0; iz < LMAX; ++iz) acc[iz] = 0.0f;
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
+            const float2 *ucv = a.uc + v * a.nb;
+            const float4 *lzv = a.lz + v * a.nb * P;
+            const float *rv = a.r + (vb + q - r_view0) * a.nb * P;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const int side = (c0 == mrel) ? 0 : ((c0 + 1 == mrel && w1 > 0.0f) ? 1 : -1);
+                if (side < 0) continue;
+                const float w = side ? w1 : w0;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                for (int pr = 0; pr < P; ++pr) {
+                    const float4 lz = __ldg(lzv + j * P + pr);
+                    const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                    const int il = (int)floorf(fminf(za, zb)), ih = (int)floorf(fmaxf(za, zb));
+                    if (ih < 0 || il >= L) continue;
+                    const float wr = __ldg(rv + j * P + pr);
+#pragma unroll
+                    for (int iz = 0; iz < LMAX; ++iz) {
+                        if (iz < il || iz > ih || iz >= L) continue;
+                        const float fr = layer_fraction(za, zb, iz);
+                        if (fr > 0.0f) acc[iz] = fmaf((w * lz.z) * fr, wr, acc[iz]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int iz = 0; iz < LMAX; ++iz)
+#pragma unroll
+        for (int o = kLanes / 2; o > 0; o >>= 1) acc[iz] += __shfl_xor_sync(0xffffffffu, acc[iz], o);
+    if (!live) return;
+#pragma unroll
+    for (int iz = 0; iz < LMAX; ++iz)
+        if (iz % kLanes == lane && iz < L) apply_epilogue<EPI, TQ, GENPOT>(a, t, n * L + iz, n, ix, iy, iz, acc[iz]);
 }
 
 // Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
@@ -505,6 +605,16 @@ constexpr bool uses_stencil(int epi) {
 
 template <int EPI, typename TQ, bool GENPOT>
 pet_status go_impl(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views) {
+    if (a.axial && a.nz <= 8) {
+        const int threads = a.nx * a.ny * kLanes;
+        const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
+        const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
+        if (a.nz <= 4)
+            ring_back_column_kernel<EPI, TQ, GENPOT, 4><<<grid, kBlock, smem, s>>>(a);
+        else
+            ring_back_column_kernel<EPI, TQ, GENPOT, 8><<<grid, kBlock, smem, s>>>(a);
+        return check_launch("ring_back_column_kernel");
+    }
     if (a.axial) {
         const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
         const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
@@ -524,11 +634,11 @@ pet_status go_impl(const BackArgs &a, int ny_grid, cudaStream_t s, int max_views
                          grid, dim3((unsigned)threads), smem, s, a);
         return check_launch("back_tile_kernel");
     }
-    const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
+    const long long threads = (long long)a.nx * a.ny * ((a.nz + kSliceBlock - 1) / kSliceBlock) * kLanes;
     const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
     const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
-    back_pixel_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
-    return check_launch("back_pixel_kernel");
+    back_stack_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
+    return check_launch("back_stack_kernel");
 }
 
 template <int EPI, typename TQ>

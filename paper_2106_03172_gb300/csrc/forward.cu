@@ -7,11 +7,12 @@
 // optionally reduces the log-likelihood sum_m g_m log yhat_m - yhat_m (§2.1,
 // Eq. (log_likelihood)) in FP64 to one partial per block.
 //
-// Thread layout: GROUP consecutive lanes share one ray (single-slice images),
-// each walking a contiguous chunk of the ray's major bands, then an xor-
-// shuffle all-reduce combines the chunks in a fixed order (deterministic).
-// For slice stacks (nz > 1) lanes run along the slice index instead
-// (GROUP = 1): consecutive lanes read consecutive floats of one pixel column.
+// Thread layout: consecutive lanes share one ray, each walking a contiguous
+// chunk of the ray's major bands, then an xor-shuffle all-reduce combines
+// the chunks in a fixed order (deterministic).  For slice stacks (nz > 1) a
+// thread carries a block of 8 slices of its ray (the geometry is shared by
+// all slices; a pixel's slices are contiguous); multi-ring lines get their
+// own kernel (the axial split of each piece).
 //
 // The view range is either given on the host (v_begin/v_end) or, when
 // a.t_dev is set, read on the device from the subset offsets, so that one
@@ -45,66 +46,88 @@ __device__ __forceinline__ RayRange ray_range(const FwdArgs &a) {
     return r;
 }
 
-template <int GROUP, int MODE, bool LL>
-__global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
+// Slice-stack forward: the geometry is shared by every slice, so a thread
+// takes a block of kSliceBlock consecutive slices of one ray (sums in
+// registers; the slices of a pixel are contiguous, [iy][ix][z]) and one of
+// CH aligned chunks of its bands; the CH chunk lanes are consecutive and
+// summed by xor-shuffles in a fixed order, then lane c writes slice c of the
+// block.
+constexpr int kSliceBlock = 8;
+
+template <int MODE, bool LL, int CH>
+__global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) {
+    static_assert(CH == kSliceBlock, "one chunk lane per slice of the block writes the epilogue");
     const RayRange rr = ray_range(a);
     const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
+    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
     // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
     const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const int tid = (int)min(gtid, (long long)n_rays * a.nz * GROUP);
-    const int z = tid % a.nz;
-    const int rest = tid / a.nz;
-    const int lane_g = rest % GROUP;
-    const int ray = rest / GROUP;
+    const int tid = (int)min(gtid, (long long)n_rays * nzb * CH);
+    const int chunk = tid % CH;
+    const int rest = tid / CH;
+    const int z0 = (rest % nzb) * kSliceBlock;
+    const int ray = rest / nzb;
     const bool live = ray < n_rays;
+    const int zc = min(kSliceBlock, a.nz - z0);
 
-    float acc = 0.0f;
+    float acc[kSliceBlock];
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
     if (live) {
         const int p = rr.v_begin + ray / a.nb;
         const int j = ray % a.nb;
         const int v = __ldg(a.order + p);
         const ViewParams vp = a.views[v];
-        const float2 u = __ldg(a.uc + (long long)v * a.nb + j);
+        const float2 u = __ldg(a.uc + v * a.nb + j);
         const int n_major = vp.col ? a.nx : a.ny;
         const int n_minor = vp.col ? a.ny : a.nx;
-        const int mo = n_minor >> 1;
         const float hm = 0.5f * (float)n_major;
         int k_lo, k_hi;
         band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
-        const int cnt = max(0, k_hi - k_lo);
-        const int per = (cnt + GROUP - 1) / GROUP;
-        const int kb = k_lo + lane_g * per;
-        const int ke = min(k_hi, kb + per);
-        if (kb < ke) {
-            // 32-bit strides: images are below 2^31 elements (checked at plan time)
-            const int s_major = (vp.col ? 1 : a.nx) * a.nz;
-            const int s_minor = (vp.col ? a.nx : 1) * a.nz;
-            const int ui = (int)u.x + mo;              // pixel index of fractional position 0
-            const float *rowp = a.img + z + kb * s_major;
-            float kc = (float)kb - hm;
-            float va = band_point(vp, u.y, kc);
-            for (int k = kb; k < ke; ++k) {
-                kc += 1.0f;
-                const float vb = band_point(vp, u.y, kc);
-                float fl, w0, w1;
-                band_split(vp, va, vb, fl, w0, w1);
-                const int m0 = (int)fl + ui;
-                if ((unsigned)m0 < (unsigned)n_minor) acc = fmaf(w0, __ldg(rowp + m0 * s_minor), acc);
-                if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor)
-                    acc = fmaf(w1, __ldg(rowp + (m0 + 1) * s_minor), acc);
-                va = vb;
-                rowp += s_major;
+        const int per = (n_major + CH - 1) / CH;
+        const int kb = max(k_lo, chunk * per);
+        const int ke = min(k_hi, (chunk + 1) * per);
+        const int s_major = (vp.col ? 1 : a.nx) * a.nz;
+        const int s_minor = (vp.col ? a.nx : 1) * a.nz;
+        const int ui = (int)u.x + (n_minor >> 1);        // pixel index of fractional position 0
+        float kc = (float)kb - hm;
+        float va = band_point(vp, u.y, kc);
+        for (int k = kb; k < ke; ++k) {
+            const float vb = band_point(vp, u.y, kc + 1.0f);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
+            const float *rowp = a.img + k * s_major + z0;
+            if ((unsigned)m0 < (unsigned)n_minor) {
+                const float *px = rowp + m0 * s_minor;
+#pragma unroll
+                for (int zz = 0; zz < kSliceBlock; ++zz)
+                    if (zz < zc) acc[zz] = fmaf(w0, __ldg(px + zz), acc[zz]);
             }
+            if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor) {
+                const float *px = rowp + (m0 + 1) * s_minor;
+#pragma unroll
+                for (int zz = 0; zz < kSliceBlock; ++zz)
+                    if (zz < zc) acc[zz] = fmaf(w1, __ldg(px + zz), acc[zz]);
+            }
+            va = vb;
+            kc += 1.0f;
         }
     }
 #pragma unroll
-    for (int o = GROUP / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+#pragma unroll
+        for (int o = CH / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
+    float mine = 0.0f;                                   // this lane's slice of the block
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+        if (zz == chunk) mine = acc[zz];
 
     double ll = 0.0;
-    if (live && lane_g == 0) {
-        const long long idx = ray * a.nz + z;
+    if (live && chunk < zc) {
+        const int idx = ray * a.nz + z0 + chunk;
         const long long gi = rr.off + idx;
-        const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        const float yhat = mine + (a.w ? __ldg(a.w + gi) : a.w_scalar);
         if (MODE == FWD_YHAT) a.out[idx] = yhat;
         if (MODE == FWD_RATIO || LL) {
             const float g = __ldg(a.g + gi);
@@ -130,10 +153,10 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(const FwdArgs a) {
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double s = 0.0;
+            double sum = 0.0;
 #pragma unroll
-            for (int i = 0; i < kBlock / 32; ++i) s += red[i];
-            a.ll_partials[blockIdx.x] = s;
+            for (int i = 0; i < kBlock / 32; ++i) sum += red[i];
+            a.ll_partials[blockIdx.x] = sum;
         }
     }
 }
@@ -508,19 +531,18 @@ pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaSt
     return check_launch("ring_forward_kernel");
 }
 
-template <int GROUP>
-pet_status dispatch_mode(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
     if (mode == FWD_YHAT && !ll)
-        forward_kernel<GROUP, FWD_YHAT, false><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_YHAT, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && !ll)
-        forward_kernel<GROUP, FWD_RATIO, false><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_RATIO, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && ll)
-        forward_kernel<GROUP, FWD_RATIO, true><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_RATIO, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_NONE && ll)
-        forward_kernel<GROUP, FWD_NONE, true><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_NONE, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
     else
         return set_error(PET_ERR_INVALID, "forward: unsupported mode");
-    return check_launch("forward_kernel");
+    return check_launch("forward_stack_kernel");
 }
 
 template <int CHUNKS>
@@ -608,13 +630,17 @@ pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx
     return check_launch("batch_objective_kernel");
 }
 
+// Blocks of a forward launch over n_rays rays: single slices (nz == 1) run
+// `group` band-chunk lanes per ray, slice stacks `group` lanes per block of
+// kSliceBlock slices.  (Multi-ring launches pass n_rays * pairs and nz = 1.)
 int forward_blocks(int n_rays, int nz, int group) {
-    const long long threads = (long long)n_rays * nz * group;
+    const long long per_ray = nz > 1 ? (long long)((nz + kSliceBlock - 1) / kSliceBlock) * group : group;
+    const long long threads = (long long)n_rays * per_ray;
     return (int)((threads + kBlock - 1) / kBlock);
 }
 
-// Lanes per ray: slice stacks put lanes along z (1 per ray); single slices
-// split each ray into chunks of about 8 bands, as many as the image needs.
+// Band chunks per ray for single slices and multi-ring lines: chunks of about
+// 8 bands, as many as the image needs (slice stacks always use 8).
 int default_chunks(int nx, int ny) {
     const int n = nx > ny ? nx : ny;
     if (n >= 160) return 32;
@@ -625,14 +651,14 @@ int default_chunks(int nx, int ny) {
 int choose_group(const pet_plan *plan) {
     if (plan->ring)                                                  // band chunks per line
         return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
-    if (plan->nz > 1) return 1;
+    if (plan->nz > 1) return kSliceBlock;                          // band chunks per slice block
     return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
 }
 
 pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s, int *n_blocks_out,
                           int rays_for_grid) {
     const int n_rays = rays_for_grid >= 0 ? rays_for_grid : (a.v_end - a.v_begin) * a.nb;
-    const int blocks = forward_blocks(n_rays, a.nz, group);
+    const int blocks = a.lz ? forward_blocks(n_rays * a.nz, 1, group) : forward_blocks(n_rays, a.nz, group);
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
     ProfileScope prof(a.t_dev ? 0 : 3, s);     // 0: subset update forward, 3: full-data / API forward
@@ -652,8 +678,8 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
             default: return set_error(PET_ERR_INVALID, "forward: unsupported lane group");
         }
     }
-    if (group != 1) return set_error(PET_ERR_INVALID, "forward: slice stacks use group 1");
-    return dispatch_mode<1>(a, mode, ll, blocks, s);
+    if (group != kSliceBlock) return set_error(PET_ERR_INVALID, "forward: slice stacks use 8 band chunks");
+    return dispatch_stack(a, mode, ll, blocks, s);
 }
 
 }  // namespace petvr
