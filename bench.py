@@ -273,7 +273,7 @@ def kernel_source_digest() -> str:
     measurement still describes the kernels being run."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("forward.cu", "backward.cu", "petvr_internal.cuh"):
+    for name in ("forward.cu", "backward.cu", "epilogue.cuh", "petvr_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2106_03172_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -469,7 +469,8 @@ def run_ours(args):
 
     # ---- profiled pass: per-kernel durations for the roofline
     n_prof = min(args.steps, 8)
-    fk, bk = (("ring_forward_kernel", "ring_back_kernel") if geom.multiring else
+    fk, bk = (("ring_forward_kernel", "ring_back_column_kernel" if geom.nz <= 8 else "ring_back_kernel")
+              if geom.multiring else
               ("forward_stack_kernel", "back_stack_kernel") if geom.nz > 1 else ("forward_tile_kernel", "back_tile_kernel"))
     kinds_named = {0: f"{fk} (subset update, ratio)", 1: f"{bk} (update epilogue)",
                    2: f"{bk} (anchor, all subsets)", 3: f"{fk} (all rays: anchor/objective)"}

@@ -26,140 +26,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-struct RayRange {
-    int v_begin, v_end;
-    long long off;   // element offset of the range's first ray in g / w (compact layouts)
-};
-
-__device__ __forceinline__ RayRange ray_range(const FwdArgs &a) {
-    RayRange r;
-    if (a.t_dev) {
-        const int t = __ldg(a.t_dev);
-        r.v_begin = __ldg(a.sub_off + t);
-        r.v_end = __ldg(a.sub_off + t + 1);
-        r.off = (long long)r.v_begin * a.nb * a.nz;
-    } else {
-        r.v_begin = a.v_begin;
-        r.v_end = a.v_end;
-        r.off = 0;
-    }
-    return r;
-}
-
-// Slice-stack forward: the geometry is shared by every slice, so a thread
-// takes a block of kSliceBlock consecutive slices of one ray (sums in
-// registers; the slices of a pixel are contiguous, [iy][ix][z]) and one of
-// CH aligned chunks of its bands; the CH chunk lanes are consecutive and
-// summed by xor-shuffles in a fixed order, then lane c writes slice c of the
-// block.
-constexpr int kSliceBlock = 8;
-
-template <int MODE, bool LL, int CH>
-__global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) {
-    static_assert(CH == kSliceBlock, "one chunk lane per slice of the block writes the epilogue");
-    const RayRange rr = ray_range(a);
-    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
-    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
-    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
-    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const int tid = (int)min(gtid, (long long)n_rays * nzb * CH);
-    const int chunk = tid % CH;
-    const int rest = tid / CH;
-    const int z0 = (rest % nzb) * kSliceBlock;
-    const int ray = rest / nzb;
-    const bool live = ray < n_rays;
-    const int zc = min(kSliceBlock, a.nz - z0);
-
-    float acc[kSliceBlock];
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
-    if (live) {
-        const int p = rr.v_begin + ray / a.nb;
-        const int j = ray % a.nb;
-        const int v = __ldg(a.order + p);
-        const ViewParams vp = a.views[v];
-        const float2 u = __ldg(a.uc + v * a.nb + j);
-        const int n_major = vp.col ? a.nx : a.ny;
-        const int n_minor = vp.col ? a.ny : a.nx;
-        const float hm = 0.5f * (float)n_major;
-        int k_lo, k_hi;
-        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
-        const int per = (n_major + CH - 1) / CH;
-        const int kb = max(k_lo, chunk * per);
-        const int ke = min(k_hi, (chunk + 1) * per);
-        const int s_major = (vp.col ? 1 : a.nx) * a.nz;
-        const int s_minor = (vp.col ? a.nx : 1) * a.nz;
-        const int ui = (int)u.x + (n_minor >> 1);        // pixel index of fractional position 0
-        float kc = (float)kb - hm;
-        float va = band_point(vp, u.y, kc);
-        for (int k = kb; k < ke; ++k) {
-            const float vb = band_point(vp, u.y, kc + 1.0f);
-            float fl, w0, w1;
-            band_split(vp, va, vb, fl, w0, w1);
-            const int m0 = (int)fl + ui;
-            const float *rowp = a.img + k * s_major + z0;
-            if ((unsigned)m0 < (unsigned)n_minor) {
-                const float *px = rowp + m0 * s_minor;
-#pragma unroll
-                for (int zz = 0; zz < kSliceBlock; ++zz)
-                    if (zz < zc) acc[zz] = fmaf(w0, __ldg(px + zz), acc[zz]);
-            }
-            if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor) {
-                const float *px = rowp + (m0 + 1) * s_minor;
-#pragma unroll
-                for (int zz = 0; zz < kSliceBlock; ++zz)
-                    if (zz < zc) acc[zz] = fmaf(w1, __ldg(px + zz), acc[zz]);
-            }
-            va = vb;
-            kc += 1.0f;
-        }
-    }
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz)
-#pragma unroll
-        for (int o = CH / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
-    float mine = 0.0f;                                   // this lane's slice of the block
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz)
-        if (zz == chunk) mine = acc[zz];
-
-    double ll = 0.0;
-    if (live && chunk < zc) {
-        const int idx = ray * a.nz + z0 + chunk;
-        const long long gi = rr.off + idx;
-        const float yhat = mine + (a.w ? __ldg(a.w + gi) : a.w_scalar);
-        if (MODE == FWD_YHAT) a.out[idx] = yhat;
-        if (MODE == FWD_RATIO || LL) {
-            const float g = __ldg(a.g + gi);
-            if (MODE == FWD_RATIO) a.out[idx] = (yhat != 0.0f) ? g / yhat : 0.0f;
-            if (LL) {
-                if (yhat > 0.0f) {
-                    // per-ray term with an FP32 log (GB300's FP64 pipe is too slow for a
-                    // log per ray; the term's error, ~g ulp(log yhat), is far below the
-                    // FP32 rounding of yhat itself), reduced in FP64
-                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
-                } else if (g > 0.0f) {
-                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
-                } else {
-                    ll = -(double)yhat;
-                }
-            }
-        }
-    }
-    if (LL) {
-        __shared__ double red[kBlock / 32];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sum = 0.0;
-#pragma unroll
-            for (int i = 0; i < kBlock / 32; ++i) sum += red[i];
-            a.ll_partials[blockIdx.x] = sum;
-        }
-    }
-}
 
 // Single-slice forward: a block takes RAYS adjacent rays of the view range
 // and splits each ray's bands into CHUNKS contiguous chunks (RAYS * CHUNKS =
@@ -368,183 +234,6 @@ __global__ void __launch_bounds__(kBlock) count_nnz_kernel(const FwdArgs a, unsi
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-// Multi-ring forward: CH consecutive lanes per line of response (ray, ring
-// pair), each walking one chunk of the ray's bands (chunks aligned to the
-// same bands for every line, so neighbouring lines read the same image rows),
-// then an xor-shuffle sum over the CH lanes in a fixed order.  Every band
-// piece is spread over the layers its axial range crosses (piece_fraction /
-// piece_zeta / layer_fraction, shared with the back projection).  Epilogue
-// as above, on the chunk-0 lane.
-template <int MODE, bool LL, int CH>
-__global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
-    const RayRange rr = ray_range(a);
-    const int P = a.nz;
-    const long long n_lor = (long long)(rr.v_end - rr.v_begin) * a.nb * P;
-    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const int chunk = (int)(gtid % CH);
-    const long long tid = gtid / CH;                     // line index in the range
-    const bool live = tid < n_lor;
-    float acc = 0.0f;
-    if (live) {
-        // 32-bit index arithmetic: sinograms and images are below 2^31 elements (checked at plan time)
-        const int lt = (int)tid;
-        const int pr = lt % P;
-        const int ray = lt / P;
-        const int q = rr.v_begin + ray / a.nb;
-        const int j = ray % a.nb;
-        const int v = __ldg(a.order + q);
-        const ViewParams vp = a.views[v];
-        const float2 u = __ldg(a.uc + v * a.nb + j);
-        const float4 lz = __ldg(a.lz + (v * a.nb + j) * P + pr);
-        const int n_major = vp.col ? a.nx : a.ny;
-        const int n_minor = vp.col ? a.ny : a.nx;
-        const float hm = 0.5f * (float)n_major;
-        const int ui = (int)u.x + (n_minor >> 1);
-        const int s_major = vp.col ? 1 : a.nx;           // pixel strides
-        const int s_minor = vp.col ? a.nx : 1;
-        const int L = a.layers;
-        int k_lo, k_hi;
-        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
-        const int per = (n_major + CH - 1) / CH;
-        const int kb = max(k_lo, chunk * per);
-        const int ke = min(k_hi, (chunk + 1) * per);
-        float kc = (float)kb - hm;
-        float va = band_point(vp, u.y, kc);
-        for (int k = kb; k < ke; ++k) {
-            const float vb = band_point(vp, u.y, kc + 1.0f);
-            float fl, w0, w1;
-            band_split(vp, va, vb, fl, w0, w1);
-            const int m0 = (int)fl + ui;
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const int m = m0 + side;
-                const float w = side ? w1 : w0;
-                if (!(w > 0.0f) || (unsigned)m >= (unsigned)n_minor) continue;
-                float f_lo, f_hi;
-                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
-                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
-                const float wl = w * lz.z;
-                const int il = max(0, (int)floorf(fminf(za, zb)));
-                const int ih = min(L - 1, (int)floorf(fmaxf(za, zb)));
-                const float *colp = a.img + (k * s_major + m * s_minor) * L;     // < 2^31 (plan check)
-                for (int iz = il; iz <= ih; ++iz) {
-                    const float fr = layer_fraction(za, zb, iz);
-                    if (fr > 0.0f) acc = fmaf(wl * fr, __ldg(colp + iz), acc);
-                }
-            }
-            va = vb;
-            kc += 1.0f;
-        }
-    }
-#pragma unroll
-    for (int o = CH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    double ll = 0.0;
-    if (live && chunk == 0) {
-        const long long gi = rr.off + tid;
-        const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
-        if (MODE == FWD_YHAT) a.out[tid] = yhat;
-        if (MODE == FWD_RATIO || LL) {
-            const float g = __ldg(a.g + gi);
-            if (MODE == FWD_RATIO) a.out[tid] = (yhat != 0.0f) ? g / yhat : 0.0f;
-            if (LL) {
-                if (yhat > 0.0f) {
-                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
-                } else if (g > 0.0f) {
-                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
-                } else {
-                    ll = -(double)yhat;
-                }
-            }
-        }
-    }
-    if (LL) {
-        __shared__ double red[kBlock / 32];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sum = 0.0;
-#pragma unroll
-            for (int i = 0; i < kBlock / 32; ++i) sum += red[i];
-            a.ll_partials[blockIdx.x] = sum;
-        }
-    }
-}
-
-// Nonzeros of the multi-ring lines of a view range: (piece, layer) pairs of
-// positive weight, with the projector's own geometry (one thread per line).
-__global__ void __launch_bounds__(kBlock) ring_count_nnz_kernel(const FwdArgs a, unsigned long long *count) {
-    const int P = a.nz;
-    const long long n_lor = (long long)(a.v_end - a.v_begin) * a.nb * P;
-    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    unsigned long long c = 0;
-    if (tid < n_lor) {
-        const int pr = (int)(tid % P);
-        const long long ray = tid / P;
-        const int v = a.order[a.v_begin + (int)(ray / a.nb)];
-        const int j = (int)(ray % a.nb);
-        const ViewParams vp = a.views[v];
-        const float2 u = a.uc[(long long)v * a.nb + j];
-        const float4 lz = a.lz[((long long)v * a.nb + j) * P + pr];
-        const int n_major = vp.col ? a.nx : a.ny;
-        const int n_minor = vp.col ? a.ny : a.nx;
-        const int ui = (int)u.x + (n_minor >> 1);
-        float kc = -0.5f * (float)n_major;
-        float va = band_point(vp, u.y, kc);
-        for (int k = 0; k < n_major; ++k) {
-            const float vb = band_point(vp, u.y, kc + 1.0f);
-            float fl, w0, w1;
-            band_split(vp, va, vb, fl, w0, w1);
-            const int m0 = (int)fl + ui;
-            for (int side = 0; side < 2; ++side) {
-                const float w = side ? w1 : w0;
-                if (!(w > 0.0f) || (unsigned)(m0 + side) >= (unsigned)n_minor) continue;
-                float f_lo, f_hi;
-                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
-                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
-                const int il = max(0, (int)floorf(fminf(za, zb)));
-                const int ih = min(a.layers - 1, (int)floorf(fmaxf(za, zb)));
-                for (int iz = il; iz <= ih; ++iz) c += layer_fraction(za, zb, iz) > 0.0f ? 1 : 0;
-            }
-            va = vb;
-            kc += 1.0f;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
-}
-
-template <int CH>
-pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
-    if (mode == FWD_YHAT && !ll)
-        ring_forward_kernel<FWD_YHAT, false, CH><<<blocks, kBlock, 0, s>>>(a);
-    else if (mode == FWD_RATIO && !ll)
-        ring_forward_kernel<FWD_RATIO, false, CH><<<blocks, kBlock, 0, s>>>(a);
-    else if (mode == FWD_RATIO && ll)
-        ring_forward_kernel<FWD_RATIO, true, CH><<<blocks, kBlock, 0, s>>>(a);
-    else if (mode == FWD_NONE && ll)
-        ring_forward_kernel<FWD_NONE, true, CH><<<blocks, kBlock, 0, s>>>(a);
-    else
-        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
-    return check_launch("ring_forward_kernel");
-}
-
-pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
-    if (mode == FWD_YHAT && !ll)
-        forward_stack_kernel<FWD_YHAT, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
-    else if (mode == FWD_RATIO && !ll)
-        forward_stack_kernel<FWD_RATIO, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
-    else if (mode == FWD_RATIO && ll)
-        forward_stack_kernel<FWD_RATIO, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
-    else if (mode == FWD_NONE && ll)
-        forward_stack_kernel<FWD_NONE, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
-    else
-        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
-    return check_launch("forward_stack_kernel");
-}
-
 template <int CHUNKS>
 pet_status dispatch_tile(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
     void (*k)(FwdArgs) = nullptr;
@@ -567,11 +256,7 @@ pet_status dispatch_tile(const FwdArgs &a, int mode, bool ll, int blocks, cudaSt
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s) {
     const int n_rays = (a.v_end - a.v_begin) * a.nb;
     if (n_rays == 0) return PET_OK;
-    if (a.lz) {
-        const long long n_lor = (long long)n_rays * a.nz;
-        ring_count_nnz_kernel<<<(unsigned)((n_lor + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, d_count);
-        return check_launch("ring_count_nnz_kernel");
-    }
+    if (a.lz) return launch_count_nnz_ring(a, d_count, s);
     count_nnz_kernel<<<(n_rays + kBlock - 1) / kBlock, kBlock, 0, s>>>(a, d_count);
     return check_launch("count_nnz_kernel");
 }
@@ -662,14 +347,7 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
     ProfileScope prof(a.t_dev ? 0 : 3, s);     // 0: subset update forward, 3: full-data / API forward
-    if (a.lz) {
-        switch (group) {
-            case 8: return dispatch_ring<8>(a, mode, ll, blocks, s);
-            case 16: return dispatch_ring<16>(a, mode, ll, blocks, s);
-            case 32: return dispatch_ring<32>(a, mode, ll, blocks, s);
-            default: return set_error(PET_ERR_INVALID, "forward: unsupported band chunk count");
-        }
-    }
+    if (a.lz || a.nz > 1) return launch_forward_volume(a, mode, ll, group, blocks, s);
     if (a.nz == 1) {
         switch (group) {
             case 8: return dispatch_tile<8>(a, mode, ll, blocks, s);
@@ -678,8 +356,7 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
             default: return set_error(PET_ERR_INVALID, "forward: unsupported lane group");
         }
     }
-    if (group != kSliceBlock) return set_error(PET_ERR_INVALID, "forward: slice stacks use 8 band chunks");
-    return dispatch_stack(a, mode, ll, blocks, s);
+    return set_error(PET_ERR_INVALID, "forward: unsupported lane group");
 }
 
 }  // namespace petvr

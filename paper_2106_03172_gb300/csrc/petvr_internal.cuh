@@ -188,6 +188,7 @@ __device__ __forceinline__ float potential_rho(int pot, float delta, float t) {
     return 0.5f * t * t;
 }
 
+
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch (sm_90 and later).  A projector launched
 // through launch_dependent() may start while the kernel before it on the
@@ -244,6 +245,33 @@ struct FwdArgs {
     double *ll_partials;      // per-block partial log-likelihood (LL only)
     int *status;              // device error latch (may be null)
 };
+
+// View range of a forward launch: given on the host, or (t_dev set) read on
+// the device from the subset offsets, with the element offset of the range's
+// first ray into the subset-major counts / background.
+struct RayRange {
+    int v_begin, v_end;
+    long long off;   // element offset of the range's first ray in g / w (compact layouts)
+};
+
+__device__ __forceinline__ RayRange ray_range(const FwdArgs &a) {
+    RayRange r;
+    if (a.t_dev) {
+        const int t = __ldg(a.t_dev);
+        r.v_begin = __ldg(a.sub_off + t);
+        r.v_end = __ldg(a.sub_off + t + 1);
+        r.off = (long long)r.v_begin * a.nb * a.nz;
+    } else {
+        r.v_begin = a.v_begin;
+        r.v_end = a.v_end;
+        r.off = 0;
+    }
+    return r;
+}
+
+// Slices a thread of the slice-stack kernels carries (the geometry is shared
+// by every slice of a stack).
+constexpr int kSliceBlock = 8;
 
 enum BackEpi {
     EPI_PLAIN = 0,       // out = A_t^T r
@@ -444,6 +472,11 @@ pet_status check_launch(const char *what);
 bool profiling_enabled();
 
 // Kernel launchers (forward.cu / backward.cu / misc.cu).
+// Volumes (volume.cu): slice stacks and multi-ring scanners.
+pet_status launch_forward_volume(const FwdArgs &a, int mode, bool ll, int group, int blocks, cudaStream_t s);
+pet_status launch_back_volume(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid, cudaStream_t s,
+                              int max_views);
+pet_status launch_count_nnz_ring(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
 pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s,
                           int *n_blocks_out, int rays_for_grid = -1);
 int forward_blocks(int n_rays, int nz, int group);

@@ -1,0 +1,584 @@
+// Projectors for volumes (K1, K2, K3): slice stacks (nz independent slices
+// sharing one 2-D geometry) and multi-ring scanners (fully 3-D lines of
+// response through a voxel volume).  Their forward kernels write the same
+// ratio / log-likelihood outputs as the single-slice ones (forward.cu), and
+// their back projections end in the same per-pixel update (epilogue.cuh).
+#include "epilogue.cuh"
+
+namespace petvr {
+
+namespace {
+
+// Slice-stack forward: the geometry is shared by every slice, so a thread
+// takes a block of kSliceBlock consecutive slices of one ray (sums in
+// registers; the slices of a pixel are contiguous, [iy][ix][z]) and one of
+// CH aligned chunks of its bands; the CH chunk lanes are consecutive and
+// summed by xor-shuffles in a fixed order, then lane c writes slice c of the
+// block.
+template <int MODE, bool LL, int CH>
+__global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) {
+    static_assert(CH == kSliceBlock, "one chunk lane per slice of the block writes the epilogue");
+    const RayRange rr = ray_range(a);
+    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
+    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const int tid = (int)min(gtid, (long long)n_rays * nzb * CH);
+    const int chunk = tid % CH;
+    const int rest = tid / CH;
+    const int z0 = (rest % nzb) * kSliceBlock;
+    const int ray = rest / nzb;
+    const bool live = ray < n_rays;
+    const int zc = min(kSliceBlock, a.nz - z0);
+
+    float acc[kSliceBlock];
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
+    if (live) {
+        const int p = rr.v_begin + ray / a.nb;
+        const int j = ray % a.nb;
+        const int v = __ldg(a.order + p);
+        const ViewParams vp = a.views[v];
+        const float2 u = __ldg(a.uc + v * a.nb + j);
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const float hm = 0.5f * (float)n_major;
+        int k_lo, k_hi;
+        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
+        const int per = (n_major + CH - 1) / CH;
+        const int kb = max(k_lo, chunk * per);
+        const int ke = min(k_hi, (chunk + 1) * per);
+        const int s_major = (vp.col ? 1 : a.nx) * a.nz;
+        const int s_minor = (vp.col ? a.nx : 1) * a.nz;
+        const int ui = (int)u.x + (n_minor >> 1);        // pixel index of fractional position 0
+        float kc = (float)kb - hm;
+        float va = band_point(vp, u.y, kc);
+        for (int k = kb; k < ke; ++k) {
+            const float vb = band_point(vp, u.y, kc + 1.0f);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
+            const float *rowp = a.img + k * s_major + z0;
+            if ((unsigned)m0 < (unsigned)n_minor) {
+                const float *px = rowp + m0 * s_minor;
+#pragma unroll
+                for (int zz = 0; zz < kSliceBlock; ++zz)
+                    if (zz < zc) acc[zz] = fmaf(w0, __ldg(px + zz), acc[zz]);
+            }
+            if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor) {
+                const float *px = rowp + (m0 + 1) * s_minor;
+#pragma unroll
+                for (int zz = 0; zz < kSliceBlock; ++zz)
+                    if (zz < zc) acc[zz] = fmaf(w1, __ldg(px + zz), acc[zz]);
+            }
+            va = vb;
+            kc += 1.0f;
+        }
+    }
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+#pragma unroll
+        for (int o = CH / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
+    float mine = 0.0f;                                   // this lane's slice of the block
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+        if (zz == chunk) mine = acc[zz];
+
+    double ll = 0.0;
+    if (live && chunk < zc) {
+        const int idx = ray * a.nz + z0 + chunk;
+        const long long gi = rr.off + idx;
+        const float yhat = mine + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        if (MODE == FWD_YHAT) a.out[idx] = yhat;
+        if (MODE == FWD_RATIO || LL) {
+            const float g = __ldg(a.g + gi);
+            if (MODE == FWD_RATIO) a.out[idx] = (yhat != 0.0f) ? g / yhat : 0.0f;
+            if (LL) {
+                if (yhat > 0.0f) {
+                    // per-ray term with an FP32 log (GB300's FP64 pipe is too slow for a
+                    // log per ray; the term's error, ~g ulp(log yhat), is far below the
+                    // FP32 rounding of yhat itself), reduced in FP64
+                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
+                } else if (g > 0.0f) {
+                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
+                } else {
+                    ll = -(double)yhat;
+                }
+            }
+        }
+    }
+    if (LL) {
+        __shared__ double red[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int i = 0; i < kBlock / 32; ++i) sum += red[i];
+            a.ll_partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+// Multi-ring forward: CH consecutive lanes per line of response (ray, ring
+// pair), each walking one chunk of the ray's bands (chunks aligned to the
+// same bands for every line, so neighbouring lines read the same image rows),
+// then an xor-shuffle sum over the CH lanes in a fixed order.  Every band
+// piece is spread over the layers its axial range crosses (piece_fraction /
+// piece_zeta / layer_fraction, shared with the back projection).  Epilogue
+// as above, on the chunk-0 lane.
+template <int MODE, bool LL, int CH>
+__global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
+    const RayRange rr = ray_range(a);
+    const int P = a.nz;
+    const long long n_lor = (long long)(rr.v_end - rr.v_begin) * a.nb * P;
+    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const int chunk = (int)(gtid % CH);
+    const long long tid = gtid / CH;                     // line index in the range
+    const bool live = tid < n_lor;
+    float acc = 0.0f;
+    if (live) {
+        // 32-bit index arithmetic: sinograms and images are below 2^31 elements (checked at plan time)
+        const int lt = (int)tid;
+        const int pr = lt % P;
+        const int ray = lt / P;
+        const int q = rr.v_begin + ray / a.nb;
+        const int j = ray % a.nb;
+        const int v = __ldg(a.order + q);
+        const ViewParams vp = a.views[v];
+        const float2 u = __ldg(a.uc + v * a.nb + j);
+        const float4 lz = __ldg(a.lz + (v * a.nb + j) * P + pr);
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const float hm = 0.5f * (float)n_major;
+        const int ui = (int)u.x + (n_minor >> 1);
+        const int s_major = vp.col ? 1 : a.nx;           // pixel strides
+        const int s_minor = vp.col ? a.nx : 1;
+        const int L = a.layers;
+        int k_lo, k_hi;
+        band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
+        const int per = (n_major + CH - 1) / CH;
+        const int kb = max(k_lo, chunk * per);
+        const int ke = min(k_hi, (chunk + 1) * per);
+        float kc = (float)kb - hm;
+        float va = band_point(vp, u.y, kc);
+        for (int k = kb; k < ke; ++k) {
+            const float vb = band_point(vp, u.y, kc + 1.0f);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int m = m0 + side;
+                const float w = side ? w1 : w0;
+                if (!(w > 0.0f) || (unsigned)m >= (unsigned)n_minor) continue;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                const float wl = w * lz.z;
+                const int il = max(0, (int)floorf(fminf(za, zb)));
+                const int ih = min(L - 1, (int)floorf(fmaxf(za, zb)));
+                const float *colp = a.img + (k * s_major + m * s_minor) * L;     // < 2^31 (plan check)
+                for (int iz = il; iz <= ih; ++iz) {
+                    const float fr = layer_fraction(za, zb, iz);
+                    if (fr > 0.0f) acc = fmaf(wl * fr, __ldg(colp + iz), acc);
+                }
+            }
+            va = vb;
+            kc += 1.0f;
+        }
+    }
+#pragma unroll
+    for (int o = CH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    double ll = 0.0;
+    if (live && chunk == 0) {
+        const long long gi = rr.off + tid;
+        const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        if (MODE == FWD_YHAT) a.out[tid] = yhat;
+        if (MODE == FWD_RATIO || LL) {
+            const float g = __ldg(a.g + gi);
+            if (MODE == FWD_RATIO) a.out[tid] = (yhat != 0.0f) ? g / yhat : 0.0f;
+            if (LL) {
+                if (yhat > 0.0f) {
+                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
+                } else if (g > 0.0f) {
+                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
+                } else {
+                    ll = -(double)yhat;
+                }
+            }
+        }
+    }
+    if (LL) {
+        __shared__ double red[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ll;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int i = 0; i < kBlock / 32; ++i) sum += red[i];
+            a.ll_partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+// Nonzeros of the multi-ring lines of a view range: (piece, layer) pairs of
+// positive weight, with the projector's own geometry (one thread per line).
+__global__ void __launch_bounds__(kBlock) ring_count_nnz_kernel(const FwdArgs a, unsigned long long *count) {
+    const int P = a.nz;
+    const long long n_lor = (long long)(a.v_end - a.v_begin) * a.nb * P;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    unsigned long long c = 0;
+    if (tid < n_lor) {
+        const int pr = (int)(tid % P);
+        const long long ray = tid / P;
+        const int v = a.order[a.v_begin + (int)(ray / a.nb)];
+        const int j = (int)(ray % a.nb);
+        const ViewParams vp = a.views[v];
+        const float2 u = a.uc[(long long)v * a.nb + j];
+        const float4 lz = a.lz[((long long)v * a.nb + j) * P + pr];
+        const int n_major = vp.col ? a.nx : a.ny;
+        const int n_minor = vp.col ? a.ny : a.nx;
+        const int ui = (int)u.x + (n_minor >> 1);
+        float kc = -0.5f * (float)n_major;
+        float va = band_point(vp, u.y, kc);
+        for (int k = 0; k < n_major; ++k) {
+            const float vb = band_point(vp, u.y, kc + 1.0f);
+            float fl, w0, w1;
+            band_split(vp, va, vb, fl, w0, w1);
+            const int m0 = (int)fl + ui;
+            for (int side = 0; side < 2; ++side) {
+                const float w = side ? w1 : w0;
+                if (!(w > 0.0f) || (unsigned)(m0 + side) >= (unsigned)n_minor) continue;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                const int il = max(0, (int)floorf(fminf(za, zb)));
+                const int ih = min(a.layers - 1, (int)floorf(fmaxf(za, zb)));
+                for (int iz = il; iz <= ih; ++iz) c += layer_fraction(za, zb, iz) > 0.0f ? 1 : 0;
+            }
+            va = vb;
+            kc += 1.0f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+template <int CH>
+pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    if (mode == FWD_YHAT && !ll)
+        ring_forward_kernel<FWD_YHAT, false, CH><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && !ll)
+        ring_forward_kernel<FWD_RATIO, false, CH><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && ll)
+        ring_forward_kernel<FWD_RATIO, true, CH><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_NONE && ll)
+        ring_forward_kernel<FWD_NONE, true, CH><<<blocks, kBlock, 0, s>>>(a);
+    else
+        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
+    return check_launch("ring_forward_kernel");
+}
+
+pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    if (mode == FWD_YHAT && !ll)
+        forward_stack_kernel<FWD_YHAT, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && !ll)
+        forward_stack_kernel<FWD_RATIO, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_RATIO && ll)
+        forward_stack_kernel<FWD_RATIO, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+    else if (mode == FWD_NONE && ll)
+        forward_stack_kernel<FWD_NONE, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+    else
+        return set_error(PET_ERR_INVALID, "forward: unsupported mode");
+    return check_launch("forward_stack_kernel");
+}
+
+// Slice-stack path: the geometry is shared by every slice, so a thread takes
+// a block of kSliceBlock consecutive slices of one pixel (sums in registers)
+// and kLanes lanes share the subset's views (lane l takes views l, l+4, ...).
+// Each candidate bin's band piece is found once per slice block; the ratios
+// of its slices are contiguous ([view][bin][z]).  After the lane sum, lane l
+// applies the update to slices l, l + kLanes, ... of the block.
+template <int EPI, typename TQ, bool GENPOT>
+__global__ void __launch_bounds__(kBlock) back_stack_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    stage_views(a, vb, nv, s_views, s_vid);
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
+    const int gid = blockIdx.x * kBlock + threadIdx.x;
+    const int lane = gid % kLanes;
+    const int rest = gid / kLanes;
+    const int z0 = (rest % nzb) * kSliceBlock;
+    const int n = rest / nzb;                            // pixel
+    const bool live = n < a.nx * a.ny;
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+    const int zc = min(kSliceBlock, a.nz - z0);          // slices in this block
+
+    float acc[kSliceBlock];
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
+            const float2 *ucv = a.uc + v * a.nb;
+            const float *rv = a.r + (vb + q - r_view0) * a.nb * a.nz + z0;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
+                if (w == 0.0f) continue;
+                const float *rj = rv + j * a.nz;
+#pragma unroll
+                for (int zz = 0; zz < kSliceBlock; ++zz)
+                    if (zz < zc) acc[zz] = fmaf(w, __ldg(rj + zz), acc[zz]);
+            }
+        }
+    }
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+#pragma unroll
+        for (int o = kLanes / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
+    if (!live) return;
+#pragma unroll
+    for (int zz = 0; zz < kSliceBlock; ++zz)
+        if (zz % kLanes == lane && zz < zc)
+            apply_epilogue<EPI, TQ, GENPOT>(a, t, (long long)n * a.nz + z0 + zz, n, ix, iy, z0 + zz, acc[zz]);
+}
+
+// Multi-ring path: kLanes lanes per voxel share the subset's views (lane l
+// takes views l, l+4, ...).  For each candidate bin the band piece of the
+// voxel's pixel is found as in the slice-stack path; each ring pair then adds
+// the part of that piece inside the voxel's layer (piece_fraction /
+// piece_zeta / layer_fraction, the forward projector's own expressions).
+template <int EPI, typename TQ, bool GENPOT>
+__global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    stage_views(a, vb, nv, s_views, s_vid);
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const int L = a.nz, P = a.pairs;
+    const int plane = a.nx * a.ny * L;
+    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const long long i = gid / kLanes;                    // voxel
+    const int lane = (int)(gid % kLanes);
+    const bool live = i < plane;
+    const int iv = (int)i;
+    const int iz = iv % L;
+    const int n = iv / L;
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+
+    float acc = 0.0f;
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
+            const float2 *ucv = a.uc + v * a.nb;
+            const float4 *lzv = a.lz + v * a.nb * P;
+            const float *rv = a.r + (vb + q - r_view0) * a.nb * P;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const int side = (c0 == mrel) ? 0 : ((c0 + 1 == mrel && w1 > 0.0f) ? 1 : -1);
+                if (side < 0) continue;
+                const float w = side ? w1 : w0;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                for (int pr = 0; pr < P; ++pr) {
+                    const float4 lz = __ldg(lzv + j * P + pr);
+                    const float fr = layer_fraction(piece_zeta(lz, kc, f_lo), piece_zeta(lz, kc, f_hi), iz);
+                    if (fr > 0.0f) acc = fmaf((w * lz.z) * fr, __ldg(rv + j * P + pr), acc);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!live || lane != 0) return;
+    apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, iz, acc);
+}
+
+// Multi-ring path for volumes of at most LMAX layers: kLanes lanes per pixel
+// column share the subset's views; every candidate bin's band piece is found
+// once per pixel and each ring pair's share is added to the layers its axial
+// range crosses (per-layer sums in registers).  After the lane sum, lane l
+// applies the update to layers l, l + kLanes, ...
+template <int EPI, typename TQ, bool GENPOT, int LMAX>
+__global__ void __launch_bounds__(kBlock) ring_back_column_kernel(const BackArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    const int vb = __ldg(a.sub_off + t);
+    const int nv = __ldg(a.sub_off + t + 1) - vb;
+    int *s_vid = reinterpret_cast<int *>(s_views + nv);
+    stage_views(a, vb, nv, s_views, s_vid);
+    __syncthreads();
+    const int r_view0 = a.t_dev ? vb : a.r_view0;
+
+    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
+    const int L = a.nz, P = a.pairs;
+    const int npix = a.nx * a.ny;
+    const int gid = blockIdx.x * kBlock + threadIdx.x;
+    const int n = gid / kLanes;                          // pixel
+    const int lane = gid % kLanes;
+    const bool live = n < npix;
+    const int ix = n % a.nx;
+    const int iy = n / a.nx;
+
+    float acc[LMAX];
+#pragma unroll
+    for (int iz = 0; iz < LMAX; ++iz) acc[iz] = 0.0f;
+    if (live) {
+        for (int q = lane; q < nv; q += kLanes) {
+            const ViewParams vp = s_views[q];
+            const int v = s_vid[q];
+            const int k = vp.col ? ix : iy;              // major index
+            const int minor = vp.col ? iy : ix;
+            const int n_major = vp.col ? a.nx : a.ny;
+            const int n_minor = vp.col ? a.ny : a.nx;
+            const int mrel = minor - (n_minor >> 1);
+            const float kc = (float)k - 0.5f * (float)n_major;
+            int jlo, jhi;
+            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
+            const float2 *ucv = a.uc + v * a.nb;
+            const float4 *lzv = a.lz + v * a.nb * P;
+            const float *rv = a.r + (vb + q - r_view0) * a.nb * P;
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c0 = (int)fl + (int)u.x;
+                const int side = (c0 == mrel) ? 0 : ((c0 + 1 == mrel && w1 > 0.0f) ? 1 : -1);
+                if (side < 0) continue;
+                const float w = side ? w1 : w0;
+                float f_lo, f_hi;
+                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
+                for (int pr = 0; pr < P; ++pr) {
+                    const float4 lz = __ldg(lzv + j * P + pr);
+                    const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                    const int il = (int)floorf(fminf(za, zb)), ih = (int)floorf(fmaxf(za, zb));
+                    if (ih < 0 || il >= L) continue;
+                    const float wr = __ldg(rv + j * P + pr);
+#pragma unroll
+                    for (int iz = 0; iz < LMAX; ++iz) {
+                        if (iz < il || iz > ih || iz >= L) continue;
+                        const float fr = layer_fraction(za, zb, iz);
+                        if (fr > 0.0f) acc[iz] = fmaf((w * lz.z) * fr, wr, acc[iz]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int iz = 0; iz < LMAX; ++iz)
+#pragma unroll
+        for (int o = kLanes / 2; o > 0; o >>= 1) acc[iz] += __shfl_xor_sync(0xffffffffu, acc[iz], o);
+    if (!live) return;
+#pragma unroll
+    for (int iz = 0; iz < LMAX; ++iz)
+        if (iz % kLanes == lane && iz < L) apply_epilogue<EPI, TQ, GENPOT>(a, t, n * L + iz, n, ix, iy, iz, acc[iz]);
+}
+
+// Back-projection launches of one epilogue / table type / potential.
+struct VolumeBack {
+    const BackArgs &a;
+    int ny_grid;
+    cudaStream_t s;
+    int max_views;
+
+    template <int EPI, typename TQ, bool GENPOT>
+    pet_status run() const {
+        const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
+        if (a.axial && a.nz <= 8) {                     // multi-ring, layers in registers
+            const int threads = a.nx * a.ny * kLanes;
+            const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
+            if (a.nz <= 4)
+                ring_back_column_kernel<EPI, TQ, GENPOT, 4><<<grid, kBlock, smem, s>>>(a);
+            else
+                ring_back_column_kernel<EPI, TQ, GENPOT, 8><<<grid, kBlock, smem, s>>>(a);
+            return check_launch("ring_back_column_kernel");
+        }
+        if (a.axial) {                                  // multi-ring, one voxel per lane group
+            const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
+            const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
+            ring_back_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
+            return check_launch("ring_back_kernel");
+        }
+        const long long threads = (long long)a.nx * a.ny * ((a.nz + kSliceBlock - 1) / kSliceBlock) * kLanes;
+        const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
+        back_stack_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
+        return check_launch("back_stack_kernel");
+    }
+};
+
+}  // namespace
+
+pet_status launch_forward_volume(const FwdArgs &a, int mode, bool ll, int group, int blocks, cudaStream_t s) {
+    if (a.lz) {
+        switch (group) {
+            case 8: return dispatch_ring<8>(a, mode, ll, blocks, s);
+            case 16: return dispatch_ring<16>(a, mode, ll, blocks, s);
+            case 32: return dispatch_ring<32>(a, mode, ll, blocks, s);
+            default: return set_error(PET_ERR_INVALID, "forward: unsupported band chunk count");
+        }
+    }
+    if (group != kSliceBlock) return set_error(PET_ERR_INVALID, "forward: slice stacks use 8 band chunks");
+    return dispatch_stack(a, mode, ll, blocks, s);
+}
+
+pet_status launch_back_volume(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid, cudaStream_t s,
+                              int max_views) {
+    return with_epilogue(epi, table_dtype, a.pot, VolumeBack{a, n_subsets_grid, s, max_views});
+}
+
+pet_status launch_count_nnz_ring(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s) {
+    const long long n_lor = (long long)(a.v_end - a.v_begin) * a.nb * a.nz;
+    if (n_lor == 0) return PET_OK;
+    ring_count_nnz_kernel<<<(unsigned)((n_lor + kBlock - 1) / kBlock), kBlock, 0, s>>>(a, d_count);
+    return check_launch("ring_count_nnz_kernel");
+}
+
+}  // namespace petvr
