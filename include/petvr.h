@@ -234,7 +234,8 @@ pet_status pet_objective_async(const pet_problem *problem, const float *d_img, d
  * that overlap on the GPU (different streams, or different threads) race:
  * order them on one stream.  Nonpositive expected counts with positive data
  * are not latched by this entry point (pet_objective reports them).
- * Enqueued only. */
+ * Multi-ring plans are rejected with PET_ERR_INVALID (their penalty couples
+ * layers; use pet_objective_async).  Enqueued only. */
 pet_status pet_objective_noalloc(const pet_plan *plan, const float *d_img, const float *d_counts,
                                  const float *d_bg, float bg, float beta, double *d_phi, void *stream);
 

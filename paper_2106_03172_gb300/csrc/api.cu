@@ -109,6 +109,14 @@ int max_sub_rays(const pet_plan *pl) { return pl->max_sub_views * pl->nb; }
 // Sinogram entries per (view, bin): slices of a stack, or ring pairs.
 int sino_inner(const pet_plan *pl) { return pl->ring ? pl->pairs : pl->nz; }
 
+// Blocks (log-likelihood partials) of a full-data forward pass, an upper
+// bound over the launch shapes launch_forward may pick (multi-ring launches
+// widen their band chunks up to 32 when the grid would be small).
+int full_forward_blocks(const pet_plan *pl) {
+    if (pl->ring) return forward_blocks(pl->na * pl->nb, 1, 32);
+    return forward_blocks(pl->M, pl->nz, choose_group(pl));
+}
+
 FwdArgs fwd_args(const pet_plan *pl, const float *img, int subset, bool natural) {
     FwdArgs a{};
     a.views = pl->d_views;
@@ -224,7 +232,7 @@ pet_status read_status(const pet_problem *p, cudaStream_t s) {
 // Device bytes pet_state_create allocates for `algo` on plan pl.
 size_t state_bytes(const pet_plan *pl, int algo, int table_dtype) {
     const size_t Nz = (size_t)pl->N * pl->nz, Mz = (size_t)pl->M * pl->nz;
-    const size_t n_part = (size_t)forward_blocks(pl->M, pl->nz, choose_group(pl)) + (Nz + 255) / 256;
+    const size_t n_part = (size_t)full_forward_blocks(pl) + (Nz + 255) / 256;
     const size_t table_bytes = (size_t)pl->ns * Nz * (table_dtype == PET_TABLE_BF16 ? 2 : 4);
     size_t bytes = Nz * 4 + (size_t)max_sub_rays(pl) * sino_inner(pl) * 4 + n_part * 8;
     if (algo == PET_ALGO_SVREM) bytes += 3 * Nz * 4 + (size_t)pl->ns * Nz * 4 + Mz * 4;
@@ -544,7 +552,7 @@ pet_status pet_plan_bytes(const pet_plan *pl, size_t *h_bytes) {
 pet_status pet_problem_bytes(const pet_plan *pl, int32_t has_bg, size_t *h_bytes) {
     if (!pl || !h_bytes) return set_error(PET_ERR_INVALID, "null argument");
     const size_t Mz = (size_t)pl->M * pl->nz, Nz = (size_t)pl->N * pl->nz;
-    const size_t n_part = (size_t)forward_blocks(pl->M, pl->nz, choose_group(pl)) + (Nz + 255) / 256;
+    const size_t n_part = (size_t)full_forward_blocks(pl) + (Nz + 255) / 256;
     *h_bytes = sizeof(float) * (Mz * (has_bg ? 3 : 2) + Nz) + sizeof(double) * (n_part + pl->nz + 8) + sizeof(int);
     return PET_OK;
 }
@@ -714,8 +722,7 @@ pet_status pet_problem_create(const pet_plan *pl, const float *d_counts, const f
     p->pen = *pen;
     p->w_scalar = bg;
     const size_t Mz = (size_t)pl->M * pl->nz, Nz = (size_t)pl->N * pl->nz;
-    const int group = choose_group(pl);
-    p->n_part = forward_blocks(pl->M, pl->nz, group) + (int)((Nz + 255) / 256);
+    p->n_part = full_forward_blocks(pl) + (int)((Nz + 255) / 256);
     pet_status st;
     auto fail = [&](pet_status e) {
         pet_problem_destroy(p);

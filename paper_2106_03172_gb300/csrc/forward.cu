@@ -315,35 +315,19 @@ pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx
     return check_launch("batch_objective_kernel");
 }
 
-// Blocks of a forward launch over n_rays rays: single slices (nz == 1) run
-// `group` band-chunk lanes per ray, slice stacks `group` lanes per block of
-// kSliceBlock slices.  (Multi-ring launches pass n_rays * pairs and nz = 1.)
-int forward_blocks(int n_rays, int nz, int group) {
-    const long long per_ray = nz > 1 ? (long long)((nz + kSliceBlock - 1) / kSliceBlock) * group : group;
-    const long long threads = (long long)n_rays * per_ray;
-    return (int)((threads + kBlock - 1) / kBlock);
-}
-
-// Band chunks per ray for single slices and multi-ring lines: chunks of about
-// 8 bands, as many as the image needs (slice stacks always use 8).
-int default_chunks(int nx, int ny) {
-    const int n = nx > ny ? nx : ny;
-    if (n >= 160) return 32;
-    if (n >= 80) return 16;
-    return 8;
-}
-
-int choose_group(const pet_plan *plan) {
-    if (plan->ring)                                                  // band chunks per line
-        return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
-    if (plan->nz > 1) return kSliceBlock;                          // band chunks per slice block
-    return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
-}
+// Below this many blocks a multi-ring forward launch is too small to fill a
+// 152-SM GB300 twice over with one block per SM.
+constexpr int kSmallGrid = 2 * 152;
 
 pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaStream_t s, int *n_blocks_out,
                           int rays_for_grid) {
     const int n_rays = rays_for_grid >= 0 ? rays_for_grid : (a.v_end - a.v_begin) * a.nb;
-    const int blocks = a.lz ? forward_blocks(n_rays * a.nz, 1, group) : forward_blocks(n_rays, a.nz, group);
+    // multi-ring threads carry all ring pairs of their ray; a small multi-ring
+    // grid (a subset update) widens its band chunks up to 32 per ray to cut
+    // each thread's chain, while full passes keep the plan's chunk count
+    if (a.lz)
+        while (group < 32 && forward_blocks(n_rays, 1, group) < kSmallGrid) group *= 2;
+    const int blocks = a.lz ? forward_blocks(n_rays, 1, group) : forward_blocks(n_rays, a.nz, group);
     if (n_blocks_out) *n_blocks_out = blocks;
     if (blocks == 0) return PET_OK;
     ProfileScope prof(a.t_dev ? 0 : 3, s);     // 0: subset update forward, 3: full-data / API forward

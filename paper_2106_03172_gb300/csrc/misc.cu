@@ -220,6 +220,34 @@ __global__ void batch_objective_final_kernel(const BatchMember *ms) {
 
 }  // namespace
 
+// ---- launch shapes of the forward projectors (host) --------------------------
+
+// Blocks of a forward launch over n_rays rays: single slices (nz == 1) run
+// `group` band-chunk lanes per ray, slice stacks `group` lanes per block of
+// kSliceBlock slices.  (Multi-ring launches pass nz = 1: a thread carries all
+// ring pairs of its ray.)
+int forward_blocks(int n_rays, int nz, int group) {
+    const long long per_ray = nz > 1 ? (long long)((nz + kSliceBlock - 1) / kSliceBlock) * group : group;
+    const long long threads = (long long)n_rays * per_ray;
+    return (int)((threads + kBlock - 1) / kBlock);
+}
+
+// Band chunks per ray for single slices and multi-ring lines: chunks of about
+// 8 bands, as many as the image needs (slice stacks always use 8).
+int default_chunks(int nx, int ny) {
+    const int n = nx > ny ? nx : ny;
+    if (n >= 160) return 32;
+    if (n >= 80) return 16;
+    return 8;
+}
+
+int choose_group(const pet_plan *plan) {
+    if (plan->ring)                                                  // band chunks per line
+        return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
+    if (plan->nz > 1) return kSliceBlock;                          // band chunks per slice block
+    return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
+}
+
 pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_members, int pen_blocks,
                                          cudaStream_t s) {
     if (n_members == 0) return PET_OK;

@@ -56,6 +56,7 @@ extern "C" pet_status pet_objective_noalloc(const pet_plan *plan, const float *d
     if (!plan || !d_img || !d_counts || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
     if (!(beta >= 0.0f) || !std::isfinite(beta)) return set_error(PET_ERR_INVALID, "beta must be >= 0");
     if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
+    if (plan->ring) return set_error(PET_ERR_INVALID, "pet_objective_noalloc: multi-ring plans are not supported");
     const int group = choose_group(plan);
     const int n_ll = forward_blocks(plan->M, plan->nz, group);
     const long long plane = (long long)plan->N * plan->nz;

@@ -122,34 +122,33 @@ __global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) 
     }
 }
 
-// Multi-ring forward: CH consecutive lanes per line of response (ray, ring
-// pair), each walking one chunk of the ray's bands (chunks aligned to the
-// same bands for every line, so neighbouring lines read the same image rows),
-// then an xor-shuffle sum over the CH lanes in a fixed order.  Every band
-// piece is spread over the layers its axial range crosses (piece_fraction /
-// piece_zeta / layer_fraction, shared with the back projection).  Epilogue
-// as above, on the chunk-0 lane.
-template <int MODE, bool LL, int CH>
+// Multi-ring forward: CH consecutive lanes per ray, each walking one chunk of
+// the ray's bands (chunks aligned to the same bands for every ray, so
+// neighbouring rays read the same image rows) and carrying the sums of all
+// P ring pairs of the ray in registers: the transaxial work of a band is done
+// once for its P lines.  Every band piece is spread over the layers each
+// line's axial range crosses (piece_fraction / piece_zeta / layer_fraction,
+// shared with the back projection).  The chunk sums are combined by
+// xor-shuffles in a fixed order; lane c writes the lines c, c + CH, ...
+template <int MODE, bool LL, int CH, int P>
 __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
     const RayRange rr = ray_range(a);
-    const int P = a.nz;
-    const long long n_lor = (long long)(rr.v_end - rr.v_begin) * a.nb * P;
+    // 32-bit index arithmetic: sinograms and images are below 2^31 elements (checked at plan time)
+    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
     const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
     const int chunk = (int)(gtid % CH);
-    const long long tid = gtid / CH;                     // line index in the range
-    const bool live = tid < n_lor;
-    float acc = 0.0f;
+    const int ray = (int)min(gtid / CH, (long long)n_rays);
+    const bool live = ray < n_rays;
+    float acc[P];
+#pragma unroll
+    for (int pr = 0; pr < P; ++pr) acc[pr] = 0.0f;
     if (live) {
-        // 32-bit index arithmetic: sinograms and images are below 2^31 elements (checked at plan time)
-        const int lt = (int)tid;
-        const int pr = lt % P;
-        const int ray = lt / P;
         const int q = rr.v_begin + ray / a.nb;
         const int j = ray % a.nb;
         const int v = __ldg(a.order + q);
         const ViewParams vp = a.views[v];
         const float2 u = __ldg(a.uc + v * a.nb + j);
-        const float4 lz = __ldg(a.lz + (v * a.nb + j) * P + pr);
+        const float4 *lzr = a.lz + (v * a.nb + j) * P;
         const int n_major = vp.col ? a.nx : a.ny;
         const int n_minor = vp.col ? a.ny : a.nx;
         const float hm = 0.5f * (float)n_major;
@@ -176,14 +175,18 @@ __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
                 if (!(w > 0.0f) || (unsigned)m >= (unsigned)n_minor) continue;
                 float f_lo, f_hi;
                 piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
-                const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
-                const float wl = w * lz.z;
-                const int il = max(0, (int)floorf(fminf(za, zb)));
-                const int ih = min(L - 1, (int)floorf(fmaxf(za, zb)));
                 const float *colp = a.img + (k * s_major + m * s_minor) * L;     // < 2^31 (plan check)
-                for (int iz = il; iz <= ih; ++iz) {
-                    const float fr = layer_fraction(za, zb, iz);
-                    if (fr > 0.0f) acc = fmaf(wl * fr, __ldg(colp + iz), acc);
+#pragma unroll
+                for (int pr = 0; pr < P; ++pr) {
+                    const float4 lz = __ldg(lzr + pr);
+                    const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
+                    const float wl = w * lz.z;
+                    const int il = max(0, (int)floorf(fminf(za, zb)));
+                    const int ih = min(L - 1, (int)floorf(fmaxf(za, zb)));
+                    for (int iz = il; iz <= ih; ++iz) {
+                        const float fr = layer_fraction(za, zb, iz);
+                        if (fr > 0.0f) acc[pr] = fmaf(wl * fr, __ldg(colp + iz), acc[pr]);
+                    }
                 }
             }
             va = vb;
@@ -191,22 +194,29 @@ __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
         }
     }
 #pragma unroll
-    for (int o = CH / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int pr = 0; pr < P; ++pr)
+#pragma unroll
+        for (int o = CH / 2; o > 0; o >>= 1) acc[pr] += __shfl_xor_sync(0xffffffffu, acc[pr], o);
     double ll = 0.0;
-    if (live && chunk == 0) {
-        const long long gi = rr.off + tid;
-        const float yhat = acc + (a.w ? __ldg(a.w + gi) : a.w_scalar);
-        if (MODE == FWD_YHAT) a.out[tid] = yhat;
-        if (MODE == FWD_RATIO || LL) {
-            const float g = __ldg(a.g + gi);
-            if (MODE == FWD_RATIO) a.out[tid] = (yhat != 0.0f) ? g / yhat : 0.0f;
-            if (LL) {
-                if (yhat > 0.0f) {
-                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
-                } else if (g > 0.0f) {
-                    if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
-                } else {
-                    ll = -(double)yhat;
+    if (live) {
+#pragma unroll
+        for (int pr = 0; pr < P; ++pr) {
+            if (pr % CH != chunk) continue;
+            const int idx = ray * P + pr;
+            const long long gi = rr.off + idx;
+            const float yhat = acc[pr] + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+            if (MODE == FWD_YHAT) a.out[idx] = yhat;
+            if (MODE == FWD_RATIO || LL) {
+                const float g = __ldg(a.g + gi);
+                if (MODE == FWD_RATIO) a.out[idx] = (yhat != 0.0f) ? g / yhat : 0.0f;
+                if (LL) {
+                    if (yhat > 0.0f) {
+                        ll += (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
+                    } else if (g > 0.0f) {
+                        if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
+                    } else {
+                        ll += -(double)yhat;
+                    }
                 }
             }
         }
@@ -270,19 +280,30 @@ __global__ void __launch_bounds__(kBlock) ring_count_nnz_kernel(const FwdArgs a,
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-template <int CH>
-pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+template <int CH, int P>
+pet_status dispatch_ring_p(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
     if (mode == FWD_YHAT && !ll)
-        ring_forward_kernel<FWD_YHAT, false, CH><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_YHAT, false, CH, P><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && !ll)
-        ring_forward_kernel<FWD_RATIO, false, CH><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_RATIO, false, CH, P><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && ll)
-        ring_forward_kernel<FWD_RATIO, true, CH><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_RATIO, true, CH, P><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_NONE && ll)
-        ring_forward_kernel<FWD_NONE, true, CH><<<blocks, kBlock, 0, s>>>(a);
+        ring_forward_kernel<FWD_NONE, true, CH, P><<<blocks, kBlock, 0, s>>>(a);
     else
         return set_error(PET_ERR_INVALID, "forward: unsupported mode");
     return check_launch("ring_forward_kernel");
+}
+
+template <int CH>
+pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    switch (a.nz) {                                      // ring pairs: n_rings^2, n_rings <= 4
+        case 1: return dispatch_ring_p<CH, 1>(a, mode, ll, blocks, s);
+        case 4: return dispatch_ring_p<CH, 4>(a, mode, ll, blocks, s);
+        case 9: return dispatch_ring_p<CH, 9>(a, mode, ll, blocks, s);
+        case 16: return dispatch_ring_p<CH, 16>(a, mode, ll, blocks, s);
+        default: return set_error(PET_ERR_INVALID, "forward: unsupported number of ring pairs");
+    }
 }
 
 pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {

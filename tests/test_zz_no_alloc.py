@@ -63,3 +63,14 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert e.value.status == 1
     torch.cuda.synchronize()
     assert torch.count_nonzero(out).item() == 0
+
+
+def test_noalloc_rejects_multi_ring_plans():
+    pv = _pv()
+    prob, data, work = oracle_problem("ring2")
+    plan = pv.Plan(work.geometry, work.n_subsets)
+    img = torch.ones(prob.N, device="cuda")
+    counts = torch.ones(prob.M, device="cuda")
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(pv.PetError, match="multi-ring"):
+        pv.pet_objective_noalloc(plan.handle, img, counts, None, 0.1, 0.01, out)
