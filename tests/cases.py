@@ -29,6 +29,10 @@ RING_CASES = {
     "ring3steep": Workload("ring3steep", Geometry(24, 20, 18, 33, bin_mm=1.6, nz=6, n_rings=3, ring_mm=7.0,
                                                   radius_mm=36.0, slice_mm=3.0),
                            n_subsets=3, counts=2e5, bg_frac=0.1, beta=0.02, n_ellipses=4),
+    # four rings (16 lines per ray) through a 10-layer volume: the per-voxel back projection for tall volumes
+    "ring4tall": Workload("ring4tall", Geometry(12, 12, 8, 17, nz=10, n_rings=4, ring_mm=3.0, radius_mm=30.0,
+                                                slice_mm=1.5), n_subsets=2, counts=1e5, bg_frac=0.1, beta=0.02,
+                          n_ellipses=3),
     # rings on layer faces (z = -4, 0, +4): half-open layers decide the direct planes
     "ringfaces": Workload("ringfaces", Geometry(16, 16, 12, 23, nz=2, n_rings=3, ring_mm=4.0, radius_mm=40.0,
                                                 slice_mm=4.0), n_subsets=4, counts=1e5, bg_frac=0.1, beta=0.02,
