@@ -186,7 +186,7 @@ pet_status ratio_all(const pet_problem *p, const float *f, float *ratio, cudaStr
     a.w_scalar = p->w_scalar;
     a.out = ratio;
     a.status = p->d_status;
-    return launch_forward(a, FWD_RATIO, false, choose_group(pl), s, nullptr);
+    return launch_forward(a, FWD_RATIO, false, full_group(pl), s, nullptr);
 }
 
 // n_iter updates with the iterate ping-ponging between the caller's image and
@@ -292,7 +292,7 @@ pet_status objective_enqueue(const pet_problem *p, const float *d_img, double *d
     a.ll_partials = part;
     a.status = p->d_status;
     int n_ll = 0;
-    PET_TRY(launch_forward(a, FWD_NONE, true, choose_group(pl), s, &n_ll));
+    PET_TRY(launch_forward(a, FWD_NONE, true, full_group(pl), s, &n_ll));
     return launch_objective_finish(p, d_img, n_ll, part, d_phi, s);
 }
 
@@ -681,7 +681,8 @@ pet_status pet_forward(const pet_plan *pl, const float *d_img, const float *d_bg
     a.w = d_bg;
     a.w_scalar = bg;
     a.out = d_sino;
-    return launch_forward(a, FWD_YHAT, false, choose_group(pl), (cudaStream_t)stream, nullptr);
+    return launch_forward(a, FWD_YHAT, false, subset < 0 ? full_group(pl) : choose_group(pl), (cudaStream_t)stream,
+                          nullptr);
 }
 
 pet_status pet_back(const pet_plan *pl, const float *d_sino, int32_t subset, float *d_img, void *stream) {
@@ -1179,29 +1180,36 @@ pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out
     b->members.resize(n);
     // group members by launch shape
     std::vector<int> idx;
-    auto add_groups = [&](bool fwd) {
+    // kind 0: subset forwards (band chunks), 1: back projections (run length),
+    // 2: full-data objective forwards (their band chunks)
+    auto value_of = [](int kind, const pet_plan *pl) {
+        return kind == 0 ? choose_group(pl) : kind == 1 ? pl->back_run : full_group(pl);
+    };
+    auto add_groups = [&](int kind) {
         std::vector<int> values;
         for (pet_state *st : b->states) {
-            const int v = fwd ? choose_group(st->prob->plan) : st->prob->plan->back_run;
+            const int v = value_of(kind, st->prob->plan);
             if (std::find(values.begin(), values.end(), v) == values.end()) values.push_back(v);
         }
         for (int v : values) {
             pet_batch::Group g{v, (int)idx.size(), 0, 0, 0};
             for (int j = 0; j < n; ++j) {
                 const pet_plan *pl = b->states[j]->prob->plan;
-                if ((fwd ? choose_group(pl) : pl->back_run) != v) continue;
+                if (value_of(kind, pl) != v) continue;
                 idx.push_back(j);
                 ++g.count;
-                const int gx = fwd ? forward_blocks(max_sub_rays(pl), 1, v)
-                                   : ((pl->nx + 15) / 16) * ((pl->ny + 15) / 16);
+                const int gx = kind == 0 ? forward_blocks(max_sub_rays(pl), 1, v)
+                               : kind == 1 ? ((pl->nx + 15) / 16) * ((pl->ny + 15) / 16)
+                                           : forward_blocks(pl->M, 1, v);
                 g.grid_x = std::max(g.grid_x, gx);
                 g.max_views = std::max(g.max_views, pl->max_sub_views);
             }
-            (fwd ? b->fwd_groups : b->back_groups).push_back(g);
+            (kind == 0 ? b->fwd_groups : kind == 1 ? b->back_groups : b->obj_groups).push_back(g);
         }
     };
-    add_groups(true);
-    add_groups(false);
+    add_groups(0);
+    add_groups(1);
+    add_groups(2);
     pet_status e;
     if ((e = dalloc(&b->d_members, (size_t)n, "batch members")) != PET_OK ||
         (e = dalloc(&b->d_idx, idx.size(), "batch index")) != PET_OK) {
@@ -1259,7 +1267,7 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.seq = seq;
     m.alphas = nullptr;
     m.na = pl->na;
-    m.n_ll = forward_blocks(pl->M, 1, choose_group(pl));
+    m.n_ll = forward_blocks(pl->M, 1, full_group(pl));
     m.part = st->d_part;
 }
 
@@ -1409,11 +1417,8 @@ pet_status pet_batch_objective_async(pet_batch *b, double *d_phi, void *stream) 
     PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_members, b->members.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice,
                                     s),
                     "batch member copy"));
-    for (const auto &g : b->fwd_groups) {
-        int blocks = 0;
-        for (int q = 0; q < g.count; ++q) blocks = std::max(blocks, b->members[b->h_idx[g.offset + q]].n_ll);
-        PET_TRY(launch_batch_objective(b->d_members, b->d_idx + g.offset, g.count, g.value, blocks, 0, s));
-    }
+    for (const auto &g : b->obj_groups)
+        PET_TRY(launch_batch_objective(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, 0, s));
     return launch_batch_objective_finish(b->d_members, n, pen_blocks, s);
 }
 

@@ -45,7 +45,7 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
     const int r8 = lane & 7;
     const int chunk = 4 * (warp % WPG) + (lane >> 3);
     const int ray_local = 8 * (warp / WPG) + r8;
-    const long long ray = (long long)bx * RAYS + ray_local;
+    const int ray = bx * RAYS + ray_local;     // 32-bit: a plan has fewer than 2^31 rays
 
     // the ray's geometry: plan constants only, so it may overlap the end of
     // the kernel before this one
@@ -55,9 +55,9 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
     int kb = 0, ke = 0, n_minor = 0, ui = 0;
     float hm = 0.0f;
     if (ray < n_rays) {
-        const int p = rr.v_begin + (int)(ray / a.nb);
-        const int j = (int)(ray % a.nb);
-        const int v = __ldg(a.order + p);
+        const int q = ray / a.nb;
+        const int j = ray - q * a.nb;
+        const int v = __ldg(a.order + rr.v_begin + q);
         vp = a.views[v];
         u = __ldg(a.uc + (long long)v * a.nb + j);
         const int n_major = vp.col ? a.nx : a.ny;
@@ -74,6 +74,17 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
     }
     pdl_wait();
     pdl_trigger();
+    // counts and background of the ray this thread finishes below: issued now
+    // (they may come from the kernel before, hence after the wait) so that
+    // their latency hides behind the band walk
+    const int ray_f = bx * RAYS + (int)threadIdx.x;
+    const bool fin = threadIdx.x < RAYS && ray_f < n_rays;
+    const long long gi = rr.off + ray_f;
+    float g_f = 0.0f, w_f = a.w_scalar;
+    if (fin) {
+        if (MODE == FWD_RATIO || LL) g_f = __ldg(a.g + gi);
+        if (a.w) w_f = __ldg(a.w + gi);
+    }
     {
         if (kb < ke) {
             const int s_major = vp.col ? 1 : a.nx;
@@ -134,13 +145,11 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
         float sum = 0.0f;
 #pragma unroll
         for (int w = 0; w < WPG; ++w) sum += red[g * WPG + w][threadIdx.x & 7];
-        const long long ray_f = (long long)bx * RAYS + threadIdx.x;
-        if (ray_f < n_rays) {
-            const long long gi = rr.off + ray_f;
-            const float yhat = sum + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        if (fin) {
+            const float yhat = sum + w_f;
             if (MODE == FWD_YHAT) a.out[ray_f] = yhat;
             if (MODE == FWD_RATIO || LL) {
-                const float g = __ldg(a.g + gi);
+                const float g = g_f;
                 if (MODE == FWD_RATIO) a.out[ray_f] = (yhat != 0.0f) ? g / yhat : 0.0f;
                 if (LL) {
                     if (yhat > 0.0f) {

@@ -248,6 +248,23 @@ int choose_group(const pet_plan *plan) {
     return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
 }
 
+// Band chunks per ray of a full-data forward pass (anchor ratios, objectives,
+// all-view projections) of a single-slice plan.  Such a grid is large, so the
+// kernel is bound by instruction issue rather than latency, and each thread's
+// fixed work (ray set-up, chunk reduction, epilogue) is better spread over
+// more bands: the chunk count is halved from the plan's, down to 16, while the
+// grid keeps at least kLargeGrid blocks (8 chunks measured slower again on a
+// 256^2 image: too few warps left to hide the load latency).  Stacks and
+// multi-ring plans keep theirs.
+constexpr int kLargeGrid = 8 * 152;
+
+int full_group(const pet_plan *plan) {
+    int g = choose_group(plan);
+    if (plan->nz != 1 || plan->ring) return g;
+    while (g > 16 && forward_blocks(plan->M, 1, g / 2) >= kLargeGrid) g /= 2;
+    return g;
+}
+
 pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_members, int pen_blocks,
                                          cudaStream_t s) {
     if (n_members == 0) return PET_OK;

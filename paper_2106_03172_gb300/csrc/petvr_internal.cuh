@@ -438,15 +438,15 @@ struct pet_batch {
     std::vector<pet_state *> states;
     std::vector<petvr::BatchMember> members;   // host copy; uploaded before every call
     petvr::BatchMember *d_members = nullptr;
-    int *d_idx = nullptr;           // member indices: forward groups, then back groups
+    int *d_idx = nullptr;           // member indices: forward, back, then objective groups
     std::vector<int> h_idx;
     struct Group {
-        int value;                  // forward: band chunks; back: run length
+        int value;                  // forward / objective: band chunks; back: run length
         int offset, count;          // slice of d_idx
         int grid_x;                 // forward blocks / back tiles to cover every member
         int max_views;
     };
-    std::vector<Group> fwd_groups, back_groups;
+    std::vector<Group> fwd_groups, back_groups, obj_groups;
     bool graphs_on = true;
     int *d_seqs = nullptr;          // [n][seq_cap] subset indices of the current call
     float *d_alphas = nullptr;      // [n][seq_cap] step sizes of the current call
@@ -481,6 +481,7 @@ pet_status launch_forward(const FwdArgs &a, int mode, bool ll, int group, cudaSt
                           int *n_blocks_out, int rays_for_grid = -1);
 int forward_blocks(int n_rays, int nz, int group);
 int choose_group(const pet_plan *plan);
+int full_group(const pet_plan *plan);     // band chunks of a full-data single-slice pass
 int default_chunks(int nx, int ny);
 pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,
                        cudaStream_t s, int max_views);
