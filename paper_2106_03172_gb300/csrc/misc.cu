@@ -223,17 +223,17 @@ __global__ void batch_objective_final_kernel(const BatchMember *ms) {
 // ---- launch shapes of the forward projectors (host) --------------------------
 
 // Blocks of a forward launch over n_rays rays: single slices (nz == 1) run
-// `group` band-chunk lanes per ray, slice stacks `group` lanes per block of
-// kSliceBlock slices.  (Multi-ring launches pass nz = 1: a thread carries all
-// ring pairs of its ray.)
+// `group` band-chunk lanes per ray, slice stacks one warp (`group` chunks x 8
+// z-lanes) per ray and slice window.  (Multi-ring launches pass nz = 1: a
+// thread carries all ring pairs of its ray.)
 int forward_blocks(int n_rays, int nz, int group) {
-    const long long per_ray = nz > 1 ? (long long)((nz + kSliceBlock - 1) / kSliceBlock) * group : group;
+    const long long per_ray = nz > 1 ? (long long)stack_windows(nz) * 8 * group : group;
     const long long threads = (long long)n_rays * per_ray;
     return (int)((threads + kBlock - 1) / kBlock);
 }
 
 // Band chunks per ray for single slices and multi-ring lines: chunks of about
-// 8 bands, as many as the image needs (slice stacks always use 8).
+// 8 bands, as many as the image needs (slice stacks always use kStackChunks).
 int default_chunks(int nx, int ny) {
     const int n = nx > ny ? nx : ny;
     if (n >= 160) return 32;
@@ -244,7 +244,7 @@ int default_chunks(int nx, int ny) {
 int choose_group(const pet_plan *plan) {
     if (plan->ring)                                                  // band chunks per line
         return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
-    if (plan->nz > 1) return kSliceBlock;                          // band chunks per slice block
+    if (plan->nz > 1) return kStackChunks;                         // band chunks per ray and window
     return plan->fwd_chunks > 0 ? plan->fwd_chunks : default_chunks(plan->nx, plan->ny);
 }
 

@@ -269,9 +269,16 @@ __device__ __forceinline__ RayRange ray_range(const FwdArgs &a) {
     return r;
 }
 
-// Slices a thread of the slice-stack kernels carries (the geometry is shared
-// by every slice of a stack).
+// Slices a thread of the slice-stack back projection carries (the geometry is
+// shared by every slice of a stack).
 constexpr int kSliceBlock = 8;
+
+// Slice-stack forward: a warp is kStackChunks band chunks x 8 z-lanes, and a
+// z-lane carries stack_lane_slices(nz) slices (a window of 8 times that many
+// per warp; deeper stacks take several windows).
+constexpr int kStackChunks = 4;
+inline int stack_lane_slices(int nz) { return nz <= 16 ? 2 : nz <= 32 ? 4 : nz <= 48 ? 6 : 8; }
+inline int stack_windows(int nz) { return (nz + 8 * stack_lane_slices(nz) - 1) / (8 * stack_lane_slices(nz)); }
 
 enum BackEpi {
     EPI_PLAIN = 0,       // out = A_t^T r

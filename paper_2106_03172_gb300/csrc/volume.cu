@@ -9,31 +9,36 @@ namespace petvr {
 
 namespace {
 
-// Slice-stack forward: the geometry is shared by every slice, so a thread
-// takes a block of kSliceBlock consecutive slices of one ray (sums in
-// registers; the slices of a pixel are contiguous, [iy][ix][z]) and one of
-// CH aligned chunks of its bands; the CH chunk lanes are consecutive and
-// summed by xor-shuffles in a fixed order, then lane c writes slice c of the
-// block.
-template <int MODE, bool LL, int CH>
+// Slice-stack forward: the geometry is shared by every slice.  A warp takes
+// one ray and a window of 8 ZW consecutive slices; its lanes are kStackChunks
+// band chunks x 8 z-lanes, and z-lane l carries slices l, l + 8, ... of the
+// window, so each load instruction reads 8 consecutive floats of a pixel's
+// slice column per chunk ([iy][ix][z] layout: coalesced).  The band geometry
+// is evaluated once per band: in each batch of 8 bands of a chunk, z-lane l
+// evaluates band kbase + l and the chunk's other lanes take its pixel offset
+// and weights by shuffles.  Bands are added in order within a chunk (w0 piece,
+// then w1 piece) and the chunk sums are combined by xor-shuffles in a fixed
+// order, so the result is deterministic.
+template <int MODE, bool LL, int ZW>
 __global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) {
-    static_assert(CH == kSliceBlock, "one chunk lane per slice of the block writes the epilogue");
     const RayRange rr = ray_range(a);
-    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
-    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
     // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
-    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const int tid = (int)min(gtid, (long long)n_rays * nzb * CH);
-    const int chunk = tid % CH;
-    const int rest = tid / CH;
-    const int z0 = (rest % nzb) * kSliceBlock;
-    const int ray = rest / nzb;
-    const bool live = ray < n_rays;
-    const int zc = min(kSliceBlock, a.nz - z0);
+    const int n_rays = (rr.v_end - rr.v_begin) * a.nb;
+    const int n_win = (a.nz + 8 * ZW - 1) / (8 * ZW);
+    const int lane = threadIdx.x & 31;
+    const int zl = lane & 7;                              // z-lane
+    const int chunk = lane >> 3;                          // band chunk (kStackChunks = 4 per warp)
+    const unsigned gmask = 0xffu << (8 * chunk);          // the chunk's 8 lanes
+    const long long wid = (long long)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    const int ray = (int)min(wid / n_win, (long long)n_rays);
+    const int win = (int)(wid % n_win);
+    const bool live = ray < n_rays;                       // the same for the whole warp
+    const int z0 = win * 8 * ZW + zl;                     // this lane's first slice
+    const int n_zi = live ? min(ZW, max(0, (a.nz - z0 + 7) / 8)) : 0;   // slices this lane carries
 
-    float acc[kSliceBlock];
+    float acc[ZW];
 #pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
+    for (int i = 0; i < ZW; ++i) acc[i] = 0.0f;
     if (live) {
         const int p = rr.v_begin + ray / a.nb;
         const int j = ray % a.nb;
@@ -45,50 +50,60 @@ __global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) 
         const float hm = 0.5f * (float)n_major;
         int k_lo, k_hi;
         band_range(vp, u.x + u.y, n_major, n_minor, k_lo, k_hi);
-        const int per = (n_major + CH - 1) / CH;
+        const int per = (n_major + kStackChunks - 1) / kStackChunks;
         const int kb = max(k_lo, chunk * per);
         const int ke = min(k_hi, (chunk + 1) * per);
-        const int s_major = (vp.col ? 1 : a.nx) * a.nz;
-        const int s_minor = (vp.col ? a.nx : 1) * a.nz;
-        const int ui = (int)u.x + (n_minor >> 1);        // pixel index of fractional position 0
-        float kc = (float)kb - hm;
-        float va = band_point(vp, u.y, kc);
-        for (int k = kb; k < ke; ++k) {
-            const float vb = band_point(vp, u.y, kc + 1.0f);
-            float fl, w0, w1;
-            band_split(vp, va, vb, fl, w0, w1);
-            const int m0 = (int)fl + ui;
-            const float *rowp = a.img + k * s_major + z0;
-            if ((unsigned)m0 < (unsigned)n_minor) {
-                const float *px = rowp + m0 * s_minor;
-#pragma unroll
-                for (int zz = 0; zz < kSliceBlock; ++zz)
-                    if (zz < zc) acc[zz] = fmaf(w0, __ldg(px + zz), acc[zz]);
+        const int s_major = vp.col ? 1 : a.nx;            // pixel strides
+        const int s_minor = vp.col ? a.nx : 1;
+        const int ui = (int)u.x + (n_minor >> 1);         // pixel index of fractional position 0
+        const float *img = a.img + z0;
+        for (int kbase = kb; kbase < ke; kbase += 8) {    // the same trip count for the chunk's 8 lanes
+            const int k = kbase + zl;
+            int n0 = 0;
+            float c0 = 0.0f, c1 = 0.0f;
+            if (k < ke) {
+                const float kc = (float)k - hm;
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int m0 = (int)fl + ui;
+                n0 = k * s_major + m0 * s_minor;
+                c0 = (unsigned)m0 < (unsigned)n_minor ? w0 : 0.0f;
+                c1 = w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor ? w1 : 0.0f;
             }
-            if (w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor) {
-                const float *px = rowp + (m0 + 1) * s_minor;
+            const int nbands = min(8, ke - kbase);
+            for (int b = 0; b < nbands; ++b) {
+                const int nb0 = __shfl_sync(gmask, n0, b, 8);
+                const float w0b = __shfl_sync(gmask, c0, b, 8);
+                const float w1b = __shfl_sync(gmask, c1, b, 8);
+                if (w0b != 0.0f) {
+                    const float *px = img + nb0 * a.nz;
 #pragma unroll
-                for (int zz = 0; zz < kSliceBlock; ++zz)
-                    if (zz < zc) acc[zz] = fmaf(w1, __ldg(px + zz), acc[zz]);
+                    for (int i = 0; i < ZW; ++i)
+                        if (i < n_zi) acc[i] = fmaf(w0b, __ldg(px + 8 * i), acc[i]);
+                }
+                if (w1b != 0.0f) {
+                    const float *px = img + (nb0 + s_minor) * a.nz;
+#pragma unroll
+                    for (int i = 0; i < ZW; ++i)
+                        if (i < n_zi) acc[i] = fmaf(w1b, __ldg(px + 8 * i), acc[i]);
+                }
             }
-            va = vb;
-            kc += 1.0f;
         }
     }
 #pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz)
-#pragma unroll
-        for (int o = CH / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
-    float mine = 0.0f;                                   // this lane's slice of the block
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz)
-        if (zz == chunk) mine = acc[zz];
+    for (int i = 0; i < ZW; ++i) {
+        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 8);
+        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
+    }
 
+    // every chunk holds the totals now; chunk c finishes slices i = c, c + 4, ...
     double ll = 0.0;
-    if (live && chunk < zc) {
-        const int idx = ray * a.nz + z0 + chunk;
+#pragma unroll
+    for (int i = 0; i < ZW; ++i) {
+        if (i % kStackChunks != chunk || i >= n_zi) continue;
+        const int idx = ray * a.nz + z0 + 8 * i;
         const long long gi = rr.off + idx;
-        const float yhat = mine + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        const float yhat = acc[i] + (a.w ? __ldg(a.w + gi) : a.w_scalar);
         if (MODE == FWD_YHAT) a.out[idx] = yhat;
         if (MODE == FWD_RATIO || LL) {
             const float g = __ldg(a.g + gi);
@@ -98,11 +113,11 @@ __global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) 
                     // per-ray term with an FP32 log (GB300's FP64 pipe is too slow for a
                     // log per ray; the term's error, ~g ulp(log yhat), is far below the
                     // FP32 rounding of yhat itself), reduced in FP64
-                    ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
+                    ll += (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
                 } else if (g > 0.0f) {
                     if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
                 } else {
-                    ll = -(double)yhat;
+                    ll += -(double)yhat;
                 }
             }
         }
@@ -306,18 +321,28 @@ pet_status dispatch_ring(const FwdArgs &a, int mode, bool ll, int blocks, cudaSt
     }
 }
 
-pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+template <int ZW>
+pet_status dispatch_stack_zw(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
     if (mode == FWD_YHAT && !ll)
-        forward_stack_kernel<FWD_YHAT, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_YHAT, false, ZW><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && !ll)
-        forward_stack_kernel<FWD_RATIO, false, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_RATIO, false, ZW><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_RATIO && ll)
-        forward_stack_kernel<FWD_RATIO, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_RATIO, true, ZW><<<blocks, kBlock, 0, s>>>(a);
     else if (mode == FWD_NONE && ll)
-        forward_stack_kernel<FWD_NONE, true, kSliceBlock><<<blocks, kBlock, 0, s>>>(a);
+        forward_stack_kernel<FWD_NONE, true, ZW><<<blocks, kBlock, 0, s>>>(a);
     else
         return set_error(PET_ERR_INVALID, "forward: unsupported mode");
     return check_launch("forward_stack_kernel");
+}
+
+pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaStream_t s) {
+    switch (stack_lane_slices(a.nz)) {
+        case 2: return dispatch_stack_zw<2>(a, mode, ll, blocks, s);
+        case 4: return dispatch_stack_zw<4>(a, mode, ll, blocks, s);
+        case 6: return dispatch_stack_zw<6>(a, mode, ll, blocks, s);
+        default: return dispatch_stack_zw<8>(a, mode, ll, blocks, s);
+    }
 }
 
 // Slice-stack path: the geometry is shared by every slice, so a thread takes
@@ -586,7 +611,7 @@ pet_status launch_forward_volume(const FwdArgs &a, int mode, bool ll, int group,
             default: return set_error(PET_ERR_INVALID, "forward: unsupported band chunk count");
         }
     }
-    if (group != kSliceBlock) return set_error(PET_ERR_INVALID, "forward: slice stacks use 8 band chunks");
+    if (group != kStackChunks) return set_error(PET_ERR_INVALID, "forward: slice stacks use 4 band chunks");
     return dispatch_stack(a, mode, ll, blocks, s);
 }
 
