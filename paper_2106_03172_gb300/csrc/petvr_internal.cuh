@@ -269,14 +269,13 @@ __device__ __forceinline__ RayRange ray_range(const FwdArgs &a) {
     return r;
 }
 
-// Slices a thread of the slice-stack back projection carries (the geometry is
-// shared by every slice of a stack).
-constexpr int kSliceBlock = 8;
-
-// Slice-stack forward: a warp is kStackChunks band chunks x 8 z-lanes, and a
-// z-lane carries stack_lane_slices(nz) slices (a window of 8 times that many
-// per warp; deeper stacks take several windows).
+// Slice stacks (the geometry is shared by every slice): a warp of the forward
+// is kStackChunks band chunks x 8 z-lanes, one of the back projection
+// kStackPixels pixels x 8 z-lanes, and a z-lane carries stack_lane_slices(nz)
+// slices (a window of 8 times that many per warp; deeper stacks take several
+// windows).
 constexpr int kStackChunks = 4;
+constexpr int kStackPixels = 4;
 inline int stack_lane_slices(int nz) { return nz <= 16 ? 2 : nz <= 32 ? 4 : nz <= 48 ? 6 : 8; }
 inline int stack_windows(int nz) { return (nz + 8 * stack_lane_slices(nz) - 1) / (8 * stack_lane_slices(nz)); }
 

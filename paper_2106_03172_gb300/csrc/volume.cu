@@ -1,8 +1,8 @@
-// Projectors for volumes (K1, K2, K3): slice stacks (nz independent slices
+// Forward projectors for volumes (K1): slice stacks (nz independent slices
 // sharing one 2-D geometry) and multi-ring scanners (fully 3-D lines of
-// response through a voxel volume).  Their forward kernels write the same
-// ratio / log-likelihood outputs as the single-slice ones (forward.cu), and
-// their back projections end in the same per-pixel update (epilogue.cuh).
+// response through a voxel volume).  They write the same ratio /
+// log-likelihood outputs as the single-slice kernels (forward.cu); their back
+// projections are in volume_back.cu.
 #include "epilogue.cuh"
 
 namespace petvr {
@@ -96,14 +96,20 @@ __global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) 
         acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
     }
 
-    // every chunk holds the totals now; chunk c finishes slices i = c, c + 4, ...
+    // every chunk holds the totals now; in round e chunk c finishes slice
+    // i = kStackChunks e + c, so the warp runs each round's epilogue once
     double ll = 0.0;
 #pragma unroll
-    for (int i = 0; i < ZW; ++i) {
-        if (i % kStackChunks != chunk || i >= n_zi) continue;
+    for (int e = 0; e < (ZW + kStackChunks - 1) / kStackChunks; ++e) {
+        float val = acc[e * kStackChunks];
+#pragma unroll
+        for (int c = 1; c < kStackChunks; ++c)
+            if (e * kStackChunks + c < ZW && chunk == c) val = acc[e * kStackChunks + c];
+        const int i = e * kStackChunks + chunk;
+        if (i >= ZW || i >= n_zi) continue;
         const int idx = ray * a.nz + z0 + 8 * i;
         const long long gi = rr.off + idx;
-        const float yhat = acc[i] + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+        const float yhat = val + (a.w ? __ldg(a.w + gi) : a.w_scalar);
         if (MODE == FWD_YHAT) a.out[idx] = yhat;
         if (MODE == FWD_RATIO || LL) {
             const float g = __ldg(a.g + gi);
@@ -345,261 +351,6 @@ pet_status dispatch_stack(const FwdArgs &a, int mode, bool ll, int blocks, cudaS
     }
 }
 
-// Slice-stack path: the geometry is shared by every slice, so a thread takes
-// a block of kSliceBlock consecutive slices of one pixel (sums in registers)
-// and kLanes lanes share the subset's views (lane l takes views l, l+4, ...).
-// Each candidate bin's band piece is found once per slice block; the ratios
-// of its slices are contiguous ([view][bin][z]).  After the lane sum, lane l
-// applies the update to slices l, l + kLanes, ... of the block.
-template <int EPI, typename TQ, bool GENPOT>
-__global__ void __launch_bounds__(kBlock) back_stack_kernel(const BackArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
-    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
-    const int vb = __ldg(a.sub_off + t);
-    const int nv = __ldg(a.sub_off + t + 1) - vb;
-    int *s_vid = reinterpret_cast<int *>(s_views + nv);
-    stage_views(a, vb, nv, s_views, s_vid);
-    __syncthreads();
-    const int r_view0 = a.t_dev ? vb : a.r_view0;
-
-    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
-    const int nzb = (a.nz + kSliceBlock - 1) / kSliceBlock;
-    const int gid = blockIdx.x * kBlock + threadIdx.x;
-    const int lane = gid % kLanes;
-    const int rest = gid / kLanes;
-    const int z0 = (rest % nzb) * kSliceBlock;
-    const int n = rest / nzb;                            // pixel
-    const bool live = n < a.nx * a.ny;
-    const int ix = n % a.nx;
-    const int iy = n / a.nx;
-    const int zc = min(kSliceBlock, a.nz - z0);          // slices in this block
-
-    float acc[kSliceBlock];
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz) acc[zz] = 0.0f;
-    if (live) {
-        for (int q = lane; q < nv; q += kLanes) {
-            const ViewParams vp = s_views[q];
-            const int v = s_vid[q];
-            const int k = vp.col ? ix : iy;              // major index
-            const int minor = vp.col ? iy : ix;
-            const int n_major = vp.col ? a.nx : a.ny;
-            const int n_minor = vp.col ? a.ny : a.nx;
-            const int mrel = minor - (n_minor >> 1);
-            const float kc = (float)k - 0.5f * (float)n_major;
-            int jlo, jhi;
-            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
-            const float2 *ucv = a.uc + v * a.nb;
-            const float *rv = a.r + (vb + q - r_view0) * a.nb * a.nz + z0;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float2 u = __ldg(ucv + j);
-                float fl, w0, w1;
-                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
-                const int c0 = (int)fl + (int)u.x;
-                const float w = (c0 == mrel) ? w0 : ((c0 + 1 == mrel) ? w1 : 0.0f);
-                if (w == 0.0f) continue;
-                const float *rj = rv + j * a.nz;
-#pragma unroll
-                for (int zz = 0; zz < kSliceBlock; ++zz)
-                    if (zz < zc) acc[zz] = fmaf(w, __ldg(rj + zz), acc[zz]);
-            }
-        }
-    }
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz)
-#pragma unroll
-        for (int o = kLanes / 2; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
-    if (!live) return;
-#pragma unroll
-    for (int zz = 0; zz < kSliceBlock; ++zz)
-        if (zz % kLanes == lane && zz < zc)
-            apply_epilogue<EPI, TQ, GENPOT>(a, t, (long long)n * a.nz + z0 + zz, n, ix, iy, z0 + zz, acc[zz]);
-}
-
-// Multi-ring path: kLanes lanes per voxel share the subset's views (lane l
-// takes views l, l+4, ...).  For each candidate bin the band piece of the
-// voxel's pixel is found as in the slice-stack path; each ring pair then adds
-// the part of that piece inside the voxel's layer (piece_fraction /
-// piece_zeta / layer_fraction, the forward projector's own expressions).
-template <int EPI, typename TQ, bool GENPOT>
-__global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
-    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
-    const int vb = __ldg(a.sub_off + t);
-    const int nv = __ldg(a.sub_off + t + 1) - vb;
-    int *s_vid = reinterpret_cast<int *>(s_views + nv);
-    stage_views(a, vb, nv, s_views, s_vid);
-    __syncthreads();
-    const int r_view0 = a.t_dev ? vb : a.r_view0;
-
-    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
-    const int L = a.nz, P = a.pairs;
-    const int plane = a.nx * a.ny * L;
-    const long long gid = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const long long i = gid / kLanes;                    // voxel
-    const int lane = (int)(gid % kLanes);
-    const bool live = i < plane;
-    const int iv = (int)i;
-    const int iz = iv % L;
-    const int n = iv / L;
-    const int ix = n % a.nx;
-    const int iy = n / a.nx;
-
-    float acc = 0.0f;
-    if (live) {
-        for (int q = lane; q < nv; q += kLanes) {
-            const ViewParams vp = s_views[q];
-            const int v = s_vid[q];
-            const int k = vp.col ? ix : iy;              // major index
-            const int minor = vp.col ? iy : ix;
-            const int n_major = vp.col ? a.nx : a.ny;
-            const int n_minor = vp.col ? a.ny : a.nx;
-            const int mrel = minor - (n_minor >> 1);
-            const float kc = (float)k - 0.5f * (float)n_major;
-            int jlo, jhi;
-            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
-            const float2 *ucv = a.uc + v * a.nb;
-            const float4 *lzv = a.lz + v * a.nb * P;
-            const float *rv = a.r + (vb + q - r_view0) * a.nb * P;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float2 u = __ldg(ucv + j);
-                float fl, w0, w1;
-                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
-                const int c0 = (int)fl + (int)u.x;
-                const int side = (c0 == mrel) ? 0 : ((c0 + 1 == mrel && w1 > 0.0f) ? 1 : -1);
-                if (side < 0) continue;
-                const float w = side ? w1 : w0;
-                float f_lo, f_hi;
-                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
-                for (int pr = 0; pr < P; ++pr) {
-                    const float4 lz = __ldg(lzv + j * P + pr);
-                    const float fr = layer_fraction(piece_zeta(lz, kc, f_lo), piece_zeta(lz, kc, f_hi), iz);
-                    if (fr > 0.0f) acc = fmaf((w * lz.z) * fr, __ldg(rv + j * P + pr), acc);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (!live || lane != 0) return;
-    apply_epilogue<EPI, TQ, GENPOT>(a, t, i, n, ix, iy, iz, acc);
-}
-
-// Multi-ring path for volumes of at most LMAX layers: kLanes lanes per pixel
-// column share the subset's views; every candidate bin's band piece is found
-// once per pixel and each ring pair's share is added to the layers its axial
-// range crosses (per-layer sums in registers).  After the lane sum, lane l
-// applies the update to layers l, l + kLanes, ...
-template <int EPI, typename TQ, bool GENPOT, int LMAX>
-__global__ void __launch_bounds__(kBlock) ring_back_column_kernel(const BackArgs a) {
-    extern __shared__ unsigned char smem_raw[];
-    ViewParams *s_views = reinterpret_cast<ViewParams *>(smem_raw);
-    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
-    const int vb = __ldg(a.sub_off + t);
-    const int nv = __ldg(a.sub_off + t + 1) - vb;
-    int *s_vid = reinterpret_cast<int *>(s_views + nv);
-    stage_views(a, vb, nv, s_views, s_vid);
-    __syncthreads();
-    const int r_view0 = a.t_dev ? vb : a.r_view0;
-
-    // 32-bit index arithmetic: images and sinograms are below 2^31 elements (checked at plan time)
-    const int L = a.nz, P = a.pairs;
-    const int npix = a.nx * a.ny;
-    const int gid = blockIdx.x * kBlock + threadIdx.x;
-    const int n = gid / kLanes;                          // pixel
-    const int lane = gid % kLanes;
-    const bool live = n < npix;
-    const int ix = n % a.nx;
-    const int iy = n / a.nx;
-
-    float acc[LMAX];
-#pragma unroll
-    for (int iz = 0; iz < LMAX; ++iz) acc[iz] = 0.0f;
-    if (live) {
-        for (int q = lane; q < nv; q += kLanes) {
-            const ViewParams vp = s_views[q];
-            const int v = s_vid[q];
-            const int k = vp.col ? ix : iy;              // major index
-            const int minor = vp.col ? iy : ix;
-            const int n_major = vp.col ? a.nx : a.ny;
-            const int n_minor = vp.col ? a.ny : a.nx;
-            const int mrel = minor - (n_minor >> 1);
-            const float kc = (float)k - 0.5f * (float)n_major;
-            int jlo, jhi;
-            candidate_bins(vp, kc, (float)mrel, (float)mrel + 1.0f, a.nb, jlo, jhi);
-            const float2 *ucv = a.uc + v * a.nb;
-            const float4 *lzv = a.lz + v * a.nb * P;
-            const float *rv = a.r + (vb + q - r_view0) * a.nb * P;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float2 u = __ldg(ucv + j);
-                float fl, w0, w1;
-                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
-                const int c0 = (int)fl + (int)u.x;
-                const int side = (c0 == mrel) ? 0 : ((c0 + 1 == mrel && w1 > 0.0f) ? 1 : -1);
-                if (side < 0) continue;
-                const float w = side ? w1 : w0;
-                float f_lo, f_hi;
-                piece_fraction(vp, w0, w1, side == 1, f_lo, f_hi);
-                for (int pr = 0; pr < P; ++pr) {
-                    const float4 lz = __ldg(lzv + j * P + pr);
-                    const float za = piece_zeta(lz, kc, f_lo), zb = piece_zeta(lz, kc, f_hi);
-                    const int il = (int)floorf(fminf(za, zb)), ih = (int)floorf(fmaxf(za, zb));
-                    if (ih < 0 || il >= L) continue;
-                    const float wr = __ldg(rv + j * P + pr);
-#pragma unroll
-                    for (int iz = 0; iz < LMAX; ++iz) {
-                        if (iz < il || iz > ih || iz >= L) continue;
-                        const float fr = layer_fraction(za, zb, iz);
-                        if (fr > 0.0f) acc[iz] = fmaf((w * lz.z) * fr, wr, acc[iz]);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int iz = 0; iz < LMAX; ++iz)
-#pragma unroll
-        for (int o = kLanes / 2; o > 0; o >>= 1) acc[iz] += __shfl_xor_sync(0xffffffffu, acc[iz], o);
-    if (!live) return;
-#pragma unroll
-    for (int iz = 0; iz < LMAX; ++iz)
-        if (iz % kLanes == lane && iz < L) apply_epilogue<EPI, TQ, GENPOT>(a, t, n * L + iz, n, ix, iy, iz, acc[iz]);
-}
-
-// Back-projection launches of one epilogue / table type / potential.
-struct VolumeBack {
-    const BackArgs &a;
-    int ny_grid;
-    cudaStream_t s;
-    int max_views;
-
-    template <int EPI, typename TQ, bool GENPOT>
-    pet_status run() const {
-        const size_t smem = (size_t)max_views * (sizeof(ViewParams) + sizeof(int));
-        if (a.axial && a.nz <= 8) {                     // multi-ring, layers in registers
-            const int threads = a.nx * a.ny * kLanes;
-            const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
-            if (a.nz <= 4)
-                ring_back_column_kernel<EPI, TQ, GENPOT, 4><<<grid, kBlock, smem, s>>>(a);
-            else
-                ring_back_column_kernel<EPI, TQ, GENPOT, 8><<<grid, kBlock, smem, s>>>(a);
-            return check_launch("ring_back_column_kernel");
-        }
-        if (a.axial) {                                  // multi-ring, one voxel per lane group
-            const long long threads = (long long)a.nx * a.ny * a.nz * kLanes;
-            const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
-            ring_back_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
-            return check_launch("ring_back_kernel");
-        }
-        const long long threads = (long long)a.nx * a.ny * ((a.nz + kSliceBlock - 1) / kSliceBlock) * kLanes;
-        const dim3 grid((unsigned)((threads + kBlock - 1) / kBlock), (unsigned)ny_grid);
-        back_stack_kernel<EPI, TQ, GENPOT><<<grid, kBlock, smem, s>>>(a);
-        return check_launch("back_stack_kernel");
-    }
-};
-
 }  // namespace
 
 pet_status launch_forward_volume(const FwdArgs &a, int mode, bool ll, int group, int blocks, cudaStream_t s) {
@@ -613,11 +364,6 @@ pet_status launch_forward_volume(const FwdArgs &a, int mode, bool ll, int group,
     }
     if (group != kStackChunks) return set_error(PET_ERR_INVALID, "forward: slice stacks use 4 band chunks");
     return dispatch_stack(a, mode, ll, blocks, s);
-}
-
-pet_status launch_back_volume(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid, cudaStream_t s,
-                              int max_views) {
-    return with_epilogue(epi, table_dtype, a.pot, VolumeBack{a, n_subsets_grid, s, max_views});
 }
 
 pet_status launch_count_nnz_ring(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s) {

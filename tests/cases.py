@@ -18,6 +18,11 @@ CASES = {
     # slice stack, slice index innermost
     "stack": replace(WORKLOADS["c128x47"], name="stack",
                      geometry=Geometry(24, 24, 18, 35, bin_mm=1.4, nz=5), n_subsets=3, counts=2e5),
+    # deeper stacks: 20 slices (4 per z-lane), 70 slices (two slice windows of a warp, the second ragged)
+    "stack20": replace(WORKLOADS["c128x47"], name="stack20",
+                       geometry=Geometry(20, 16, 14, 27, bin_mm=1.5, nz=20), n_subsets=3, counts=2e5),
+    "stack70": replace(WORKLOADS["c128x47"], name="stack70",
+                       geometry=Geometry(12, 10, 11, 19, bin_mm=1.3, nz=70), n_subsets=4, counts=3e5),
 }
 
 # multi-ring volumes (fully 3-D lines of response)
