@@ -220,12 +220,19 @@ __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
         for (int o = CH / 2; o > 0; o >>= 1) acc[pr] += __shfl_xor_sync(0xffffffffu, acc[pr], o);
     double ll = 0.0;
     if (live) {
+        // round e: chunk lane c finishes line pr = CH e + c, so the warp runs
+        // each round's epilogue once
 #pragma unroll
-        for (int pr = 0; pr < P; ++pr) {
-            if (pr % CH != chunk) continue;
+        for (int e = 0; e < (P + CH - 1) / CH; ++e) {
+            float val = acc[e * CH];
+#pragma unroll
+            for (int c = 1; c < CH && e * CH + c < P; ++c)
+                if (chunk == c) val = acc[e * CH + c];
+            const int pr = e * CH + chunk;
+            if (pr >= P) continue;
             const int idx = ray * P + pr;
             const long long gi = rr.off + idx;
-            const float yhat = acc[pr] + (a.w ? __ldg(a.w + gi) : a.w_scalar);
+            const float yhat = val + (a.w ? __ldg(a.w + gi) : a.w_scalar);
             if (MODE == FWD_YHAT) a.out[idx] = yhat;
             if (MODE == FWD_RATIO || LL) {
                 const float g = __ldg(a.g + gi);

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) ring_back_kernel(const BackArgs a) {
 // column share the subset's views; every candidate bin's band piece is found
 // once per pixel and each ring pair's share is added to the layers its axial
 // range crosses (per-layer sums in registers).  After the lane sum, lane l
-// applies the update to layers l, l + kLanes, ...
+// applies the update to layers l, l + kLanes, ..., one round at a time.
 template <int EPI, typename TQ, bool GENPOT, int LMAX>
 __global__ void __launch_bounds__(kBlock) ring_back_column_kernel(const BackArgs a) {
     extern __shared__ unsigned char smem_raw[];
@@ -241,9 +241,18 @@ __global__ void __launch_bounds__(kBlock) ring_back_column_kernel(const BackArgs
 #pragma unroll
         for (int o = kLanes / 2; o > 0; o >>= 1) acc[iz] += __shfl_xor_sync(0xffffffffu, acc[iz], o);
     if (!live) return;
+    // round e: lane l updates layer kLanes e + l, so the warp runs each
+    // round's epilogue once
+    static_assert(LMAX % kLanes == 0, "whole rounds of lanes");
 #pragma unroll
-    for (int iz = 0; iz < LMAX; ++iz)
-        if (iz % kLanes == lane && iz < L) apply_epilogue<EPI, TQ, GENPOT>(a, t, n * L + iz, n, ix, iy, iz, acc[iz]);
+    for (int e = 0; e < LMAX / kLanes; ++e) {
+        float val = acc[e * kLanes];
+#pragma unroll
+        for (int l = 1; l < kLanes; ++l)
+            if (lane == l) val = acc[e * kLanes + l];
+        const int iz = e * kLanes + lane;
+        if (iz < L) apply_epilogue<EPI, TQ, GENPOT>(a, t, n * L + iz, n, ix, iy, iz, val);
+    }
 }
 
 // Back-projection launches of one epilogue / table type / potential.
