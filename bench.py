@@ -573,7 +573,7 @@ def run_ours(args):
         "objective_last_step": [float(x) for x in phi_host[:, 0]],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, cpairs, setup = oracle_steps(work, data, 8, min_seconds=12.0)
+        times, cpairs, setup = oracle_steps(work, data, 2, min_seconds=12.0)
         line["cpu_baseline"] = {
             "value": sum(cpairs) / sum(times), "unit": unit, "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} bench steps of the FP64 oracle (about {sum(times):.0f} s; system matrix build "
