@@ -12,7 +12,7 @@ namespace petvr {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kLanes = 4;           // volumes: lanes per pixel column, each takes every 4th view
+constexpr int kLanes = 4;           // multi-ring volumes: lanes per pixel column or voxel
 constexpr float kCandEps = 1e-3f;   // candidate-bin margin (pixels)
 
 struct Stencil {
