@@ -34,7 +34,7 @@ constexpr int kBlock = 256;
 // 8 neighbouring pixels each.  Chunk sums are reduced by xor-shuffles
 // (within the warp) and then over warps through shared memory, always in the
 // same order, so the result is deterministic.
-template <int CHUNKS, int MODE, bool LL>
+template <int CHUNKS, int MODE, bool LL, bool INTERIOR = true>
 __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx) {
     constexpr int RAYS = kBlock / CHUNKS;        // rays per block
     constexpr int WPG = CHUNKS / 4;              // warps per group of 8 rays
@@ -101,22 +101,52 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
             for (int k = kb; k < ke; k += kBatch) {
                 int o0[kBatch], o1[kBatch];
                 float c0[kBatch], c1[kBatch];
+                // Interior batch: the ray's minor position is linear in kc, so
+                // every band's pieces lie between the pixels of the batch's two
+                // end points, up to rounding that moves a floor by at most one.
+                // With one pixel of margin on each side both pieces of every
+                // band are inside the image, and the offsets need no checks
+                // (they equal the checked ones).
+                // (The batched kernels leave it out: they keep 40 registers,
+                // and both branches give the same sums.)
+                bool interior = false;
+                if (INTERIOR) {
+                    const float vend = band_point(vp, u.y, kc + (float)kBatch);
+                    const int e_lo = (int)floorf(fminf(va, vend)) + ui;
+                    const int e_hi = (int)floorf(fmaxf(va, vend)) + ui;
+                    interior = k + kBatch <= ke && e_lo >= 1 && e_hi <= n_minor - 3;
+                }
+                if (interior) {
 #pragma unroll
-                for (int b = 0; b < kBatch; ++b) {
-                    kc += 1.0f;
-                    const float vb = band_point(vp, u.y, kc);
-                    float fl, w0, w1;
-                    band_split(vp, va, vb, fl, w0, w1);
-                    const int m0 = (int)fl + ui;
-                    const bool live = k + b < ke;
-                    const bool ok0 = live && (unsigned)m0 < (unsigned)n_minor;
-                    const bool ok1 = live && w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor;
-                    const int row = (k + b) * s_major;
-                    o0[b] = ok0 ? row + m0 * s_minor : 0;
-                    o1[b] = ok1 ? row + (m0 + 1) * s_minor : 0;
-                    c0[b] = ok0 ? w0 : 0.0f;
-                    c1[b] = ok1 ? w1 : 0.0f;
-                    va = vb;
+                    for (int b = 0; b < kBatch; ++b) {
+                        kc += 1.0f;
+                        const float vb = band_point(vp, u.y, kc);
+                        float fl, w0, w1;
+                        band_split(vp, va, vb, fl, w0, w1);
+                        o0[b] = (k + b) * s_major + ((int)fl + ui) * s_minor;
+                        o1[b] = o0[b] + s_minor;
+                        c0[b] = w0;
+                        c1[b] = w1;
+                        va = vb;
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < kBatch; ++b) {
+                        kc += 1.0f;
+                        const float vb = band_point(vp, u.y, kc);
+                        float fl, w0, w1;
+                        band_split(vp, va, vb, fl, w0, w1);
+                        const int m0 = (int)fl + ui;
+                        const bool live = k + b < ke;
+                        const bool ok0 = live && (unsigned)m0 < (unsigned)n_minor;
+                        const bool ok1 = live && w1 > 0.0f && (unsigned)(m0 + 1) < (unsigned)n_minor;
+                        const int row = (k + b) * s_major;
+                        o0[b] = ok0 ? row + m0 * s_minor : 0;
+                        o1[b] = ok1 ? row + (m0 + 1) * s_minor : 0;
+                        c0[b] = ok0 ? w0 : 0.0f;
+                        c1[b] = ok1 ? w1 : 0.0f;
+                        va = vb;
+                    }
                 }
                 float x0[kBatch], x1[kBatch];
 #pragma unroll
@@ -178,8 +208,13 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
     }
 }
 
+// The kernels run beside the other streams' kernels: at 40 registers six
+// blocks fit on an SM (five for the full-data ratio pass, which spills at 40).
+template <int CHUNKS, bool LL>
+constexpr int fwd_min_blocks() { return CHUNKS >= 32 || LL ? 6 : 5; }
+
 template <int CHUNKS, int MODE, bool LL>
-__global__ void __launch_bounds__(kBlock) forward_tile_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(kBlock, fwd_min_blocks<CHUNKS, LL>()) forward_tile_kernel(const FwdArgs a) {
     forward_tile_body<CHUNKS, MODE, LL>(a, blockIdx.x);
 }
 
@@ -206,7 +241,7 @@ __global__ void __launch_bounds__(kBlock) batch_forward_kernel(const BatchMember
     a.w_scalar = m.w_scalar;
     a.out = m.ratio;
     a.status = m.status;
-    forward_tile_body<CHUNKS, FWD_RATIO, false>(a, blockIdx.x);
+    forward_tile_body<CHUNKS, FWD_RATIO, false, false>(a, blockIdx.x);
 }
 
 // Nonzeros of the rays of a view range: band pieces of positive length that
@@ -307,7 +342,7 @@ __global__ void __launch_bounds__(kBlock) batch_objective_kernel(const BatchMemb
     a.w_scalar = m.w_scalar;
     a.ll_partials = m.part;
     a.status = m.status;
-    forward_tile_body<CHUNKS, FWD_NONE, true>(a, blockIdx.x);
+    forward_tile_body<CHUNKS, FWD_NONE, true, false>(a, blockIdx.x);
 }
 
 pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
