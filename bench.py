@@ -270,13 +270,18 @@ def run_reference(args):
 
 
 def kernel_source_digest() -> str:
-    """SHA-256 of the projector sources, to tell whether a recorded ncu
-    measurement still describes the kernels being run."""
+    """SHA-256 of the projector sources with comments and whitespace removed,
+    to tell whether a recorded ncu measurement still describes the kernels
+    being run (a comment edit does not change them)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("forward.cu", "backward.cu", "epilogue.cuh", "petvr_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2106_03172_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2106_03172_gb300", "csrc", name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

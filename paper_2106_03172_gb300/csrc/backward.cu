@@ -3,9 +3,10 @@
 //
 // b_n = sum_{m in S_t} a_mn r_m as a gather per pixel (no atomics, so the
 // result is deterministic).  Single slices use tiles with runs of pixels
-// that share each ray's band split (back_tile_kernel); slice stacks carry a
-// block of 8 slices per thread; multi-ring volumes split each band piece over
-// the layers its axial range crosses.  In each view only the bins whose ray
+// that share each ray's band split (back_tile_kernel, here); slice stacks
+// and multi-ring volumes have their own kernels in volume_back.cu (z-lanes
+// over a pixel's slices; each band piece split over the layers its axial
+// range crosses).  In each view only the bins whose ray
 // can cross the pixel's major band at the pixel are candidates (usually
 // 2-3), found from the bin spacing K, and each candidate's weight comes from
 // band_point() / band_split(), the functions the forward kernels use, so A^T

@@ -9,10 +9,9 @@
 //
 // Thread layout: consecutive lanes share one ray, each walking a contiguous
 // chunk of the ray's major bands, then an xor-shuffle all-reduce combines
-// the chunks in a fixed order (deterministic).  For slice stacks (nz > 1) a
-// thread carries a block of 8 slices of its ray (the geometry is shared by
-// all slices; a pixel's slices are contiguous); multi-ring lines get their
-// own kernel (the axial split of each piece).
+// the chunks in a fixed order (deterministic).  Slice stacks (nz > 1) and
+// multi-ring lines have their own kernels in volume.cu (a warp of band chunks
+// x z-lanes per ray; the axial split of each piece).
 //
 // The view range is either given on the host (v_begin/v_end) or, when
 // a.t_dev is set, read on the device from the subset offsets, so that one
