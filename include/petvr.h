@@ -140,9 +140,12 @@ pet_status pet_plan_nnz(const pet_plan *plan, int32_t t, int64_t *h_nnz);
 
 /* Launch shapes of the single-slice kernels: band chunks per ray in the
  * forward projector (8, 16 or 32; 0 = size-based default) and pixels per run
- * in the tiled back projector (4 or 8).  Results are identical up to the
- * FP32 summation order.  Set them before creating states: captured epochs
- * keep the shapes they were captured with. */
+ * in the tiled back projector (4 or 8).  The chunk count is the one of subset
+ * projections; full-data forward passes (objectives, anchor ratios, all-view
+ * projections) of images large enough to fill the GPU several times over use
+ * half as many, but not fewer than 16.  Results are identical up to the FP32
+ * summation order.  Set them before creating states: captured epochs keep the
+ * shapes they were captured with. */
 pet_status pet_plan_set_tuning(pet_plan *plan, int32_t fwd_chunks, int32_t back_run);
 pet_status pet_plan_get_tuning(const pet_plan *plan, int32_t *h_fwd_chunks, int32_t *h_back_run);
 
