@@ -9,7 +9,8 @@ request's slot (problem, state, image buffer) is kept in a pool: a later
 request of the same shape, method and penalty reuses it through
 pet_problem_update, pet_warm_start and pet_state_reset, which allocate
 nothing; pooled slots are released, oldest first, when an admission needs
-their memory.
+their memory.  Plans get their launch shapes from the library's autotuner,
+timed once per request shape (tuned_plan) and shared by every path.
 
 Two ways to let the work of concurrent requests overlap on the device:
 
@@ -52,6 +53,23 @@ from . import petvr
 from .phantoms import Workload, subset_sequence
 
 STEP = {"svrem": (0.7, 1), "saga": (1.0, 1), "svrg": (2.0, 2), "osem": (1.0, 1)}
+
+# Launch shapes per request shape: timed once per process by the library's
+# autotuner on the first plan of that shape and set on every later one, so
+# that every path (either server, the plain path) runs a shape with the same
+# kernels and returns the same image.
+_TUNING: dict = {}
+
+
+def tuned_plan(work: Workload):
+    """A plan of this request shape with its process-wide launch shapes."""
+    plan = petvr.Plan(work.geometry, work.n_subsets)
+    key = _Base._plan_key(work)
+    if key not in _TUNING:
+        _TUNING[key] = petvr.pet_plan_autotune(plan.handle)
+    else:
+        petvr.pet_plan_set_tuning(plan.handle, *_TUNING[key])
+    return plan
 
 
 @dataclass
@@ -140,7 +158,7 @@ class _Base:
     def _plan(self, work):
         key = self._plan_key(work)
         if key not in self.plans:
-            plan = petvr.Plan(work.geometry, work.n_subsets)
+            plan = tuned_plan(work)
             nbytes = petvr.pet_plan_bytes(plan.handle)
             self.plans[key] = (plan, nbytes)
             self._charge(nbytes)
@@ -442,7 +460,7 @@ def serve_plain(requests, gap: float = 1e-4, max_epochs: int = 60, clock=time.pe
     for r in pending:                       # plans ahead of the stream, as Server.prepare
         key = _Base._plan_key(r.work)
         if key not in plans:
-            plans[key] = petvr.Plan(r.work.geometry, r.work.n_subsets)
+            plans[key] = tuned_plan(r.work)
     stream = torch.cuda.current_stream()
     phi = torch.zeros(3, dtype=torch.float64, device="cuda")
     phi_host = torch.zeros(3, dtype=torch.float64).pin_memory()
