@@ -331,6 +331,60 @@ def test_full_size_stack_projection():
     _assert_proj(_host(img).reshape(-1, geom.nz), A.T @ y)
 
 
+def test_max_size_projection_samples():
+    """512x512, 720 views x 733 bins (the largest serving size), 6 subsets:
+    sampled rays of the all-view forward projection and sampled pixels of the
+    all-view back projection against the oracle's Siddon rays computed one by
+    one, and the adjoint identity <A x, y> = <x, A^T y> over the whole image."""
+    pv = _pv()
+    from oracle.geometry import bin_offsets, view_trig
+    from oracle.siddon import siddon_ray
+    from paper_2106_03172_gb300.phantoms import Geometry
+    geom = Geometry(512, 512, 720, 733)
+    nx, ny, na, nb, d = geom.nx, geom.ny, geom.n_angles, geom.n_bins, geom.pixel_mm
+    plan = pv.Plan(geom, 6)
+    rng = np.random.default_rng(11)
+    f = rng.uniform(0.0, 2.0, nx * ny)
+    y = rng.uniform(0.0, 2.0, na * nb)
+    out = torch.empty(na * nb, device="cuda")
+    pv.pet_forward(plan.handle, _cuda(f), None, 0.0, -1, out)
+    img = torch.empty(nx * ny, device="cuda")
+    pv.pet_back(plan.handle, _cuda(y), -1, img)
+    fwd, back = _host(out), _host(img)
+    c, s = view_trig(na)
+    sj = bin_offsets(nb, geom.ds)
+
+    # sampled rays, one by one
+    rays = rng.choice(na * nb, 300, replace=False)
+    want = []
+    for m in rays:
+        idx, ln = siddon_ray(c[m // nb], s[m // nb], sj[m % nb], nx, ny, d)
+        want.append(float(np.dot(ln, f[idx])))
+    want = np.asarray(want)
+    _assert_proj(fwd[rays].reshape(-1, 1), want.reshape(-1, 1))
+
+    # sampled pixels: every ray passing within two pixels of the pixel centre
+    pix = rng.choice(nx * ny, 24, replace=False)
+    got, want = back[pix], []
+    for n in pix:
+        ix, iy = n % nx, n // nx
+        xc, yc = (ix - 0.5 * (nx - 1)) * d, (iy - 0.5 * (ny - 1)) * d
+        total = 0.0
+        for i in range(na):
+            sc = xc * c[i] + yc * s[i]                     # the pixel centre's radial coordinate
+            for j in np.nonzero(np.abs(sj - sc) <= 2.0 * d)[0]:
+                idx, ln = siddon_ray(c[i], s[i], sj[j], nx, ny, d)
+                hit = ln[idx == n]
+                if hit.size:
+                    total += float(hit.sum()) * y[i * nb + j]
+        want.append(total)
+    _assert_proj(got.reshape(-1, 1), np.asarray(want).reshape(-1, 1))
+
+    # adjoint over the whole image (FP64 dot products of the FP32 outputs)
+    lhs, rhs = float(np.dot(fwd, y)), float(np.dot(f, back))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
 @pytest.fixture(scope="module", params=[("huber", 0.05), ("logcosh", 0.05), ("hyperbola", 0.05)])
 def potential_case(request):
     """64x64 workload with an edge-preserving potential of Table 1 (the paper's
