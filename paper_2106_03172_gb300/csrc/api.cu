@@ -974,10 +974,8 @@ pet_status enqueue_epoch(pet_state *st, int algo, int32_t n_iter, const std::vec
     const long long plane = plane_of(pl);
     return pingpong(st->img, st->alt, plane, n_iter, s, [&](int i, const float *in, float *outp) {
         if (anchors[i] && algo == PET_ALGO_SVREM) {
-            PET_TRY(cuda_ok(cudaMemcpyAsync(st->f_anc, in, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
-                            "anchor copy"));
             PET_TRY(anchor_pass(st, in, st->ratio_full, s));
-            PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, st->f_anc, st->s_anc, st->s_hat,
+            PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, in, st->f_anc, st->s_anc, st->s_hat,
                                                !st->s_hat_ready, s));
             st->s_hat_ready = true;
         } else if (anchors[i] && algo == PET_ALGO_SVRG) {
@@ -1295,11 +1293,9 @@ pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<s
             const long long plane = plane_of(pl);
             const float *in = in_is_img ? st->img : st->alt;
             if (st->algo == PET_ALGO_SVREM) {
-                PET_TRY(cuda_ok(cudaMemcpyAsync(st->f_anc, in, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
-                                "anchor copy"));
                 PET_TRY(anchor_pass(st, in, st->ratio_full, s));
-                PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, st->f_anc, st->s_anc, st->s_hat,
-                                                   !st->s_hat_ready, s));
+                PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, in, st->f_anc, st->s_anc,
+                                                   st->s_hat, !st->s_hat_ready, s));
                 st->s_hat_ready = true;
             } else {
                 PET_TRY(anchor_pass(st, in, st->ratio_full, s));

@@ -124,13 +124,18 @@ __global__ void objective_final_kernel(const double *ll, int n_ll, const double 
     }
 }
 
-__global__ void svrem_finish_kernel(const float *B, int ns, long long plane, const float *f_anc,
+// SVREM anchor statistic s_anc = f_anc . sum_t B_t (the sum in FP64), with
+// the anchor image f_anc taken from the current iterate f here (the anchor
+// pass before this kernel reads f itself).
+__global__ void svrem_finish_kernel(const float *B, int ns, long long plane, const float *f, float *f_anc,
                                     float *s_anc, float *s_hat, int init) {
     const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
     if (i >= plane) return;
     double s = 0.0;
     for (int t = 0; t < ns; ++t) s += B[(long long)t * plane + i];
-    const float sa = (float)((double)f_anc[i] * s);
+    const float fa = f[i];
+    f_anc[i] = fa;
+    const float sa = (float)((double)fa * s);
     s_anc[i] = sa;
     if (init) s_hat[i] = sa;
 }
@@ -327,10 +332,10 @@ pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const
     return check_launch("objective_final_kernel");
 }
 
-pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz, const float *f_anc,
-                                      float *s_anc, float *s_hat, bool init, cudaStream_t s) {
+pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz, const float *f,
+                                      float *f_anc, float *s_anc, float *s_hat, bool init, cudaStream_t s) {
     (void)nz;
-    svrem_finish_kernel<<<blocks_for(plane), kBlock, 0, s>>>(B, ns, plane, f_anc, s_anc, s_hat, init ? 1 : 0);
+    svrem_finish_kernel<<<blocks_for(plane), kBlock, 0, s>>>(B, ns, plane, f, f_anc, s_anc, s_hat, init ? 1 : 0);
     return check_launch("svrem_finish_kernel");
 }
 

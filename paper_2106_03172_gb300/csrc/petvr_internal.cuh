@@ -508,9 +508,8 @@ pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_mem
                                          cudaStream_t s);
 pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
                              int max_views, int iter, int in_is_img, bool general_potential, cudaStream_t s);
-pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz,
-                                      const float *f_anc, float *s_anc, float *s_hat, bool init,
-                                      cudaStream_t s);
+pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz, const float *f,
+                                      float *f_anc, float *s_anc, float *s_hat, bool init, cudaStream_t s);
 pet_status launch_svrg_anchor_finish(const float *B, int ns, long long plane, int nz,
                                      const float *sens, float *qtil, cudaStream_t s);
 pet_status launch_saga_finish(const void *table, int table_dtype, int ns, long long plane, int nz,
