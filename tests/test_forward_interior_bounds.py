@@ -101,8 +101,18 @@ def _admitted_out_of_bounds(nx, ny, na, nb, pixel_mm=2.0, bin_mm=None, chunk_cou
     (37, 29, 23, 41, 1.7, 1.3),           # odd, non-square, bins != pixels
     (128, 128, 90, 183),
     (96, 80, 37, 131, 2.0, 1.6),          # odd view count, no axis-aligned views but 0
+    (256, 256, 180, 367),                 # the benchmark image
 ])
 def test_interior_batches_stay_inside_the_image(geom):
     bad, admitted = _admitted_out_of_bounds(*geom)
+    assert admitted > 0
+    assert bad == 0
+
+
+@pytest.mark.slow
+def test_interior_batches_stay_inside_the_largest_image():
+    """512x512, 720 views x 733 bins (the largest serving size), at the chunk
+    counts its launches use."""
+    bad, admitted = _admitted_out_of_bounds(512, 512, 720, 733, chunk_counts=(16, 32))
     assert admitted > 0
     assert bad == 0
