@@ -287,6 +287,16 @@ def kernel_source_digest() -> str:
     return h.hexdigest()
 
 
+def measured_hbm_peak():
+    """Copy bandwidth (GB/s) measured on the GB300s (MEASURED_PEAKS.json),
+    else the fallback figure, with which one it is."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
 def dram_traffic_record(kind: int, workload: str = "c256"):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary (profiles/roofline_traffic.txt), or None when that summary was
@@ -526,6 +536,10 @@ def run_ours(args):
                 "hbm_achieved_gbs": alg_bytes[dom] / (kinds[dom]["total_ms"] / 1e3) / 1e9,
                 "kernels": {v["name"]: {k2: v[k2] for k2 in ("launches", "avg_us", "share")}
                             for v in kinds.values()}}
+    hbm_peak, hbm_src = measured_hbm_peak()
+    roofline["hbm_peak_gbs"] = hbm_peak
+    roofline["hbm_frac"] = roofline["hbm_achieved_gbs"] / hbm_peak
+    roofline["hbm_peak_source"] = hbm_src
 
     # ---- end to end through the public API with host buffers
     img_host = torch.empty(4, geom.n_pixels * geom.nz, dtype=torch.float32).pin_memory()
