@@ -1,0 +1,66 @@
+"""Argument checks of the C ABI that return before any CUDA call, exercised on
+the CPU: each bad input is refused with PET_ERR_INVALID and a message from
+pet_last_error, and nothing is created."""
+import ctypes
+from ctypes import byref, c_void_p
+
+import pytest
+
+from paper_2106_03172_gb300 import build, petvr
+from paper_2106_03172_gb300.phantoms import Geometry
+
+PET_ERR_INVALID = 1
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    petvr._lib = None
+    return petvr.lib()
+
+
+def _create(lib, geom, n_subsets=1, scheme=0):
+    g = petvr.pet_geometry(geom.nx, geom.ny, geom.nz, geom.pixel_mm, geom.n_angles, geom.n_bins,
+                           geom.bin_mm if geom.bin_mm is not None else 0.0, geom.n_rings, geom.ring_mm,
+                           geom.radius_mm, geom.slice_mm)
+    h = c_void_p(12345)
+    st = lib.pet_plan_create(byref(g), byref(petvr.pet_subsets(n_subsets, scheme)), byref(h))
+    return st, h.value, lib.pet_last_error().decode()
+
+
+@pytest.mark.parametrize("geom,n_subsets,scheme,needle", [
+    (Geometry(0, 8, 4, 9), 1, 0, "sizes must be >= 1"),
+    (Geometry(8, 8, 4, 9, nz=0), 1, 0, "sizes must be >= 1"),
+    (Geometry(20000, 8, 4, 9), 1, 0, "<= 16384"),
+    (Geometry(8, 8, 2000, 9), 1, 0, "n_angles must be <= 1024"),
+    (Geometry(8, 8, 4, 9, pixel_mm=0.0), 1, 0, "pixel_mm"),
+    (Geometry(8, 8, 4, 9, pixel_mm=float("nan")), 1, 0, "pixel_mm"),
+    (Geometry(8, 8, 4, 9), 5, 0, "n_subsets <= n_angles"),
+    (Geometry(8, 8, 4, 9), 0, 0, "n_subsets <= n_angles"),
+    (Geometry(8, 8, 4, 9), 2, 1, "subset scheme"),
+    (Geometry(8, 8, 4, 9, nz=2, n_rings=5, ring_mm=4.0, radius_mm=40.0, slice_mm=2.0), 1, 0, "n_rings"),
+    (Geometry(8, 8, 4, 9, nz=2, n_rings=2, ring_mm=4.0, radius_mm=40.0, slice_mm=0.0), 1, 0, "slice_mm"),
+    (Geometry(8, 8, 4, 9, nz=2, n_rings=2, ring_mm=-1.0, radius_mm=40.0, slice_mm=2.0), 1, 0, "ring_mm"),
+    (Geometry(8, 8, 4, 9, nz=2, n_rings=2, ring_mm=4.0, radius_mm=5.0, slice_mm=2.0), 1, 0, "radius_mm"),
+    (Geometry(16384, 16384, 4, 9, nz=16), 1, 0, "2^31"),
+    (Geometry(8, 8, 1024, 16384, nz=256), 1, 0, "2^31"),
+])
+def test_plan_create_refuses_bad_geometry(lib, geom, n_subsets, scheme, needle):
+    st, handle, msg = _create(lib, geom, n_subsets, scheme)
+    assert st == PET_ERR_INVALID
+    assert handle is None                       # *out is cleared before any check that can fail
+    assert needle in msg, msg
+
+
+def test_null_arguments_are_refused(lib):
+    assert lib.pet_plan_create(None, None, None) == PET_ERR_INVALID
+    assert "null" in lib.pet_last_error().decode()
+    g = petvr.pet_geometry(8, 8, 1, 2.0, 4, 9, 0.0, 0, 0.0, 0.0, 0.0)
+    assert lib.pet_plan_create(byref(g), None, byref(c_void_p())) == PET_ERR_INVALID
+
+
+def test_destroy_accepts_null(lib):
+    """Destroying nothing is a no-op (the create calls above left no object)."""
+    for name in ("pet_plan_destroy", "pet_problem_destroy", "pet_state_destroy", "pet_batch_destroy"):
+        fn = getattr(lib, name)
+        fn(None)
