@@ -64,3 +64,21 @@ def test_destroy_accepts_null(lib):
     for name in ("pet_plan_destroy", "pet_problem_destroy", "pet_state_destroy", "pet_batch_destroy"):
         fn = getattr(lib, name)
         fn(None)
+
+
+def test_every_entry_point_refuses_null_handles(lib):
+    """Every status-returning call given null handles and pointers (zeros for
+    the scalars) returns PET_ERR_INVALID instead of touching memory."""
+    from ctypes import c_double, c_float, c_int32, c_int64, c_size_t
+    skip = {"pet_state_destroy", "pet_batch_destroy",      # null is a no-op by contract
+            "pet_profile_enable", "pet_profile_reset"}     # no handle to check
+    zero = {c_int32: 0, c_int64: 0, c_size_t: 0, c_float: 0.0, c_double: 0.0}
+    checked = 0
+    for name, (res, args) in petvr._SIGS.items():
+        if res is not c_int32 or not args or name in skip:
+            continue
+        vals = [zero.get(t, None) for t in args]
+        st = getattr(lib, name)(*vals)
+        assert st == PET_ERR_INVALID, f"{name} -> {st}: {lib.pet_last_error().decode()}"
+        checked += 1
+    assert checked >= 35
