@@ -89,3 +89,26 @@ def test_oracle_and_product_share_no_code():
         if f.endswith(".py"):
             mods = _imports(os.path.join(ROOT, "oracle", f))
             assert not any(m.startswith("paper_2106_03172_gb300") for m in mods), f
+
+
+def test_batched_and_served_shapes():
+    """Batched and served request shapes follow the stated rules: views
+    round(1.4 N) (720 at 512^2), bins the odd integer nearest 1.43 N, counts
+    and subsets in their ranges (64^2 -> 90 x 91, 128^2 -> 179 x 183, 192^2 ->
+    269 x 275, 256^2 -> 358 x 367, 384^2 -> 538 x 549, 512^2 -> 720 x 733)."""
+    from paper_2106_03172_gb300.phantoms import batched_workloads, serving_pool, serving_workloads
+    want = {64: (90, 91), 128: (179, 183), 192: (269, 275), 256: (358, 367), 384: (538, 549), 512: (720, 733)}
+    batch = batched_workloads(7, 64)
+    assert {w.geometry.nx for w in batch} == {64, 128, 192, 256}
+    served = serving_workloads(0, 40) + serving_workloads(1, 4, sizes=(384, 512))
+    for w in batch + served:
+        g = w.geometry
+        assert g.nx == g.ny and (g.n_angles, g.n_bins) == want[g.nx]
+        assert w.n_subsets in (6, 12, 21)
+        assert w.methods[0] in (("saga",) if w in batch else ("svrem", "saga"))
+    assert all(1e5 <= w.counts <= 1e7 for w in batch)
+    assert all(1e6 <= w.counts <= 1e8 for w in served)
+    pool = serving_pool()
+    assert [w.name for w in pool][-4:] == ["serve384_0", "serve384_1", "serve512_0", "serve512_1"]
+    assert {(w.geometry.nx, w.methods[0], w.n_subsets) for w in pool[-4:]} == {
+        (384, "svrem", 21), (384, "saga", 6), (512, "svrem", 6), (512, "saga", 12)}
