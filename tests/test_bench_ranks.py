@@ -64,3 +64,25 @@ def test_missing_rank_fails_on_the_host():
     p.start()
     p.join(60)
     assert not p.is_alive() and p.exitcode != 0
+
+
+def test_step_pairs_count_anchor_passes():
+    """The metric's units per step: 4 N_s subset pairs, plus N_s for each
+    anchor pass due (SVREM every eta_svrem epochs, SVRG every eta_svrg), the
+    anchors due at the epoch's first update."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2106_03172_gb300.phantoms import WORKLOADS
+    for name in ("c256", "c64", "ring2_128"):
+        work = WORKLOADS[name]
+        ns, e_svrem, e_svrg = work.n_subsets, work.eta_svrem, work.eta_svrg
+        rep = bench.Replica(work)
+        total = 0
+        for step in range(12):
+            p, anchors = rep.step_pairs()
+            want = ["svrem"] * (step % e_svrem == 0) + ["svrg"] * (step % e_svrg == 0)
+            assert anchors == want
+            assert p == 4 * ns + ns * len(want)
+            total += p
+            rep.advance()
+        assert total == 12 * 4 * ns + ns * (len(range(0, 12, e_svrem)) + len(range(0, 12, e_svrg)))
