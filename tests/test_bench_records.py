@@ -28,7 +28,7 @@ def test_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
     f = csrc / "forward.cu"
     f.write_text(f.read_text() + "\n// a comment\n/* and a\n   block comment */\n\n")
     assert bench.kernel_source_digest() == base
-    f.write_text(f.read_text().replace("constexpr int kBatch = 4;", "constexpr int kBatch = 2;"))
+    f.write_text(f.read_text() + "static const int kAddedForTheTest = 1;\n")
     assert bench.kernel_source_digest() != base
 
 
