@@ -419,8 +419,10 @@ def run_ours(args):
     states = {m: petvr.State(prob, m, imgs[m]) for m in METHODS}
     phi = torch.zeros(4, 3, dtype=torch.float64, device="cuda")
     a = alphas(work)
-    nnz_t = [petvr.pet_plan_nnz(plan.handle, t) for t in range(ns)]
-    nnz_all = petvr.pet_plan_nnz(plan.handle, -1)
+    # nonzeros of one slice's A_t (a stack repeats them on every slice)
+    slices = 1 if geom.multiring else geom.nz
+    nnz_t = [slices * petvr.pet_plan_nnz(plan.handle, t) for t in range(ns)]
+    nnz_all = slices * petvr.pet_plan_nnz(plan.handle, -1)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     stream = torch.cuda.current_stream()
     rep = Replica(work)
@@ -492,7 +494,7 @@ def run_ours(args):
                    2: f"{bk} (anchor, all subsets)", 3: f"{fk} (all rays: anchor/objective)"}
     alg_flops = {k: 0.0 for k in kinds_named}
     alg_bytes = {k: 0.0 for k in kinds_named}
-    N, M = geom.n_pixels * geom.nz, geom.n_rays * geom.n_pairs      # image and sinogram floats
+    N, M = geom.n_pixels * geom.nz, geom.n_rays * geom.n_pairs * slices   # image and sinogram floats
     upd_bytes = {"osem": 12, "svrem": 32, "saga": 32, "svrg": 20}   # per pixel, see DESIGN
     petvr.pet_profile_reset()
     petvr.pet_profile_enable(True)
@@ -568,8 +570,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = [s_ev.elapsed_time(e_ev) for s_ev, e_ev in e2e_events]
     e2e_value, _, _ = combine_ranks(float(sum(e2e_ms)), float(e2e_pairs), device="cuda")
-    h2d = 4 * geom.n_rays * geom.n_pairs
-    d2h = 4 * 4 * geom.n_pixels * geom.nz + 4 * 3 * 8
+    h2d = g_host.numel() * g_host.element_size()                     # the counts copied in every step
+    d2h = img_host.numel() * img_host.element_size() + phi_host_buf.numel() * phi_host_buf.element_size()
 
     # ---- reconstructions to a 1e-4 relative objective gap (Phi* from the oracle)
     phi_star, phi_src = phi_star_for(work, data)
