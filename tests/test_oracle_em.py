@@ -383,3 +383,170 @@ def test_sagaem_statistic_starts_at_full_statistic(prob_and_data):
     f = _rand_image(prob, 16)
     alg = em.SAGAEM(prob, f, alpha=0.5)
     np.testing.assert_allclose(alg.s_hat, prob.statistic(f), rtol=1e-12)
+
+
+# ---- unbiasedness of the stochastic directions (§2.3, §4) -------------------
+#
+# The variance-reduced estimators are unbiased: averaged over a uniformly drawn
+# subset t, the SAGA and SVRG directions equal grad Phi(f) / N_s (§4,
+# Eqs. (saga_update) and (svrg_update)) and the SAGA-EM statistic equals the
+# full statistic s(f) (§2.3, the remark after Eq. (tempsvrem)), for ANY table
+# or anchor, not only at a fixed point.  The identities hold only when the
+# table mean is taken before the current entry is overwritten (reading C6), so
+# they pin the table bookkeeping of the oracle.  grad Phi and s(f) themselves
+# are pinned by finite differences and the Poisson pmf above.
+
+def _unclipped_steps(alg, prob, f, t_list, make_state):
+    """Run one step of `alg` from the same state for every t and return the
+    direction of each step: the update is f + alpha d . dir with d = eps f,
+    alpha = 1 and eps small enough that P_{>=0} never clips, so that
+    dir = (f' - f) / (eps f) exactly up to rounding."""
+    dirs = []
+    for t in t_list:
+        make_state(alg)
+        f_new = alg.step(t)
+        dirs.append((f_new - f) / alg.d)
+    return dirs
+
+
+@pytest.mark.parametrize("table", ["fp32", "bf16"])
+def test_saga_direction_is_unbiased_for_any_table(prob_and_data, table):
+    """mean_t (q_new,t - q_t + mean_t' q_t') = mean_t q_new,t = grad Phi(f) / N_s
+    (FP32 table), with a random table far from f; the post-write mean would
+    add (mean_t q_new,t - mean q) / N_s."""
+    prob, _ = prob_and_data
+    rng = np.random.default_rng(31)
+    f = _rand_image(prob, 30)
+    grads = [prob.grad_Phi_t(f, t) for t in range(prob.Ns)]
+    scale = max(np.abs(g).max() for g in grads)
+    table0 = [rng.standard_normal(f.shape) * scale for _ in range(prob.Ns)]
+    rnd = em.bf16_round if table == "bf16" else (lambda x: x)
+    eps = 1e-3 / (5.0 * scale)
+    alg = em.SAGA(prob, f, alpha=1.0, d=eps * f, table=table)
+
+    def reset(a):
+        a.f = f.copy()
+        a.q = [rnd(q) for q in table0]
+
+    dirs = _unclipped_steps(alg, prob, f, range(prob.Ns), reset)
+    mean_dir = sum(dirs) / prob.Ns
+    want = sum(rnd(g) for g in grads) / prob.Ns          # = grad Phi(f) / N_s for the FP32 table
+    np.testing.assert_allclose(mean_dir, want, rtol=0, atol=1e-9 * scale)
+    if table == "fp32":
+        np.testing.assert_allclose(mean_dir, prob.grad_Phi(f) / prob.Ns, rtol=0, atol=1e-9 * scale)
+    # the table is far from f, so the pre- and post-write means differ by far more than the tolerance
+    assert np.abs(sum(grads) / prob.Ns - sum(table0) / prob.Ns).max() > 1e3 * 1e-9 * scale * prob.Ns
+
+
+def test_svrg_direction_is_unbiased_for_any_anchor(prob_and_data):
+    """mean_t (grad Phi_t(f) - grad Phi_t(f_anc) + grad Phi(f_anc) / N_s) = grad Phi(f) / N_s
+    with the anchor away from f (§4, Eq. (svrg_update))."""
+    prob, _ = prob_and_data
+    f = _rand_image(prob, 32)
+    f_anc = _rand_image(prob, 33)
+    scale = max(np.abs(prob.grad_Phi_t(x, t)).max() for x in (f, f_anc) for t in range(prob.Ns))
+    eps = 1e-3 / (5.0 * scale)
+    alg = em.SVRG(prob, f_anc, alpha=1.0, eta=3, d=eps * f)
+    alg.refresh_anchor()
+
+    def reset(a):
+        a.f, a.k = f.copy(), 1                             # inside the epoch: no anchor refresh
+
+    dirs = _unclipped_steps(alg, prob, f, range(prob.Ns), reset)
+    np.testing.assert_allclose(sum(dirs) / prob.Ns, prob.grad_Phi(f) / prob.Ns, rtol=0, atol=1e-9 * scale)
+    # each single direction is not the full gradient (the anchor correction is live)
+    assert max(np.abs(d - prob.grad_Phi(f) / prob.Ns).max() for d in dirs) > 1e-3 * scale
+
+
+def test_sagaem_statistic_is_unbiased_for_any_table():
+    """With alpha = 1 the SAGA-EM statistic is tau_t(f) - T_t + mean T; its mean
+    over t is mean_t tau_t(f) = s(f) = f . A^T(g / (A f + w)) for any table T
+    (§2.3), N_s = 4 and a table not built at f."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=34, n_subsets=4, beta=0.05)
+    rng = np.random.default_rng(35)
+    f = rng.uniform(0.5, 3.0, (p.N, 1))
+    s_full = f * (p.A.T @ (p.g / (p.A @ f + p.w)))       # the statistic from its definition
+    table0 = [rng.uniform(0.0, 2.0, f.shape) * s_full.max() for _ in range(p.Ns)]
+    alg = em.SAGAEM(p, f, alpha=1.0)
+    stats = []
+    for t in range(p.Ns):
+        alg.f, alg.T = f.copy(), [x.copy() for x in table0]
+        alg.step(t)
+        stats.append(alg.s_hat.copy())
+    np.testing.assert_allclose(sum(stats) / p.Ns, s_full, rtol=1e-12, atol=1e-12 * s_full.max())
+    assert np.abs(sum(table0) / p.Ns - s_full).max() > 1e-2 * s_full.max()
+
+
+def test_saga_three_steps_by_hand():
+    """Three SAGA steps (N_s = 3, subsets 1, 1, 2) written out from §4,
+    Eq. (saga_update) with the table mean taken before each write (C6):
+      f1 = P(f0 + a d (g1(f0) - g1(f0) + (g0(f0) + g1(f0) + g2(f0)) / 3))
+      f2 = P(f1 + a d (g1(f1) - g1(f0) + (g0(f0) + g1(f0) + g2(f0)) / 3))
+      f3 = P(f2 + a d (g2(f2) - g2(f0) + (g0(f0) + g1(f1) + g2(f0)) / 3))
+    with g_t = grad Phi_t and d = d(f0).  The post-write mean would change
+    the second and third steps."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=36, n_subsets=3, beta=0.05)
+    f0 = p.initial_image()
+    a = 0.8
+    d = em.preconditioner(p, f0)
+    g = p.grad_Phi_t
+    P = lambda x: np.maximum(x, 0.0)
+    f1 = P(f0 + a * d * (g(f0, 0) + g(f0, 1) + g(f0, 2)) / 3)
+    f2 = P(f1 + a * d * (g(f1, 1) - g(f0, 1) + (g(f0, 0) + g(f0, 1) + g(f0, 2)) / 3))
+    f3 = P(f2 + a * d * (g(f2, 2) - g(f0, 2) + (g(f0, 0) + g(f1, 1) + g(f0, 2)) / 3))
+    alg = em.SAGA(p, f0, alpha=a)
+    for t, want in zip((1, 1, 2), (f1, f2, f3)):
+        np.testing.assert_allclose(alg.step(t), want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+    # the readings differ here: the post-write mean moves f2 by a d (g1(f1) - g1(f0)) / 3
+    assert np.abs(a * d * (g(f1, 1) - g(f0, 1)) / 3).max() > 1e-6 * np.abs(f2).max()
+
+
+def test_sagaem_three_steps_by_hand():
+    """Three SAGA-EM steps (N_s = 3, subsets 0, 2, 0, alpha = 0.6) written out
+    from §2.3 (the remark after Eq. (tempsvrem)) with the M-step of §3:
+      s1 = (1-a) s0 + a (tau0(f0) - tau0(f0) + Tbar0),           Tbar0 = mean_t tau_t(f0)
+      s2 = (1-a) s1 + a (tau2(f1) - tau2(f0) + Tbar0)
+      s3 = (1-a) s2 + a (tau0(f2) - tau0(f0) + (tau0(f0) + tau1(f0) + tau2(f1)) / 3)
+    where f_{k+1} is the M-step root with s_{k+1}, s0 = Tbar0 = s(f0)."""
+    from oracle.penalty import m_step_root as root
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=37, n_subsets=3, beta=0.05)
+    f0 = p.initial_image()
+    a = 0.6
+    tau = p.tau_t
+    M = lambda s, fk: root(s, fk, p.sens, p.beta, p.pen)
+    Tbar0 = (tau(f0, 0) + tau(f0, 1) + tau(f0, 2)) / 3
+    s1 = (1 - a) * Tbar0 + a * Tbar0
+    f1 = M(s1, f0)
+    s2 = (1 - a) * s1 + a * (tau(f1, 2) - tau(f0, 2) + Tbar0)
+    f2 = M(s2, f1)
+    s3 = (1 - a) * s2 + a * (tau(f2, 0) - tau(f0, 0) + (tau(f0, 0) + tau(f0, 1) + tau(f1, 2)) / 3)
+    f3 = M(s3, f2)
+    alg = em.SAGAEM(p, f0, alpha=a)
+    for t, want in zip((0, 2, 0), (f1, f2, f3)):
+        np.testing.assert_allclose(alg.step(t), want, rtol=1e-11, atol=1e-13 * np.abs(want).max())
+
+
+def test_svrg_three_steps_by_hand():
+    """Three SVRG steps (N_s = 3, eta = 1, subsets 2, 0, 2) from §4,
+    Eq. (svrg_update): the anchor is f0 for the whole epoch,
+      f_{k+1} = P(f_k + a d (g_t(f_k) - g_t(f0) + grad Phi(f0) / 3))."""
+    geom = Geometry(12, 12, 18, 17)
+    p, _ = tiny_problem(geom, seed=38, n_subsets=3, beta=0.05)
+    f0 = p.initial_image()
+    a = 1.3
+    d = em.preconditioner(p, f0)
+    g = p.grad_Phi_t
+    P = lambda x: np.maximum(x, 0.0)
+    G0 = p.grad_Phi(f0) / 3
+    f1 = P(f0 + a * d * (g(f0, 2) - g(f0, 2) + G0))
+    f2 = P(f1 + a * d * (g(f1, 0) - g(f0, 0) + G0))
+    f3 = P(f2 + a * d * (g(f2, 2) - g(f0, 2) + G0))
+    alg = em.SVRG(p, f0, alpha=a, eta=1)
+    for t, want in zip((2, 0, 2), (f1, f2, f3)):
+        np.testing.assert_allclose(alg.step(t), want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+    # the fourth step (k = N_s) takes a new anchor: the direction is grad Phi(f3) / 3
+    want = P(f3 + a * d * p.grad_Phi(f3) / 3)
+    np.testing.assert_allclose(alg.step(1), want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
