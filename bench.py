@@ -495,7 +495,10 @@ def run_ours(args):
     alg_flops = {k: 0.0 for k in kinds_named}
     alg_bytes = {k: 0.0 for k in kinds_named}
     N, M = geom.n_pixels * geom.nz, geom.n_rays * geom.n_pairs * slices   # image and sinogram floats
-    upd_bytes = {"osem": 12, "svrem": 32, "saga": 32, "svrg": 20}   # per pixel, see DESIGN
+    # algorithmic bytes per pixel of the fused update epilogue (4 B per float read or written):
+    # OSEM f, sens_t, f_out; SVREM f, s_hat r+w, f_anc, B_t, s_anc, sens, f_out;
+    # SAGA (FP32 table) f, sens_t, q_t r+w, qbar r+w, d, f_out; SVRG f, B_t, q~, d, f_out
+    upd_bytes = {"osem": 12, "svrem": 32, "saga": 32, "svrg": 20}
     petvr.pet_profile_reset()
     petvr.pet_profile_enable(True)
     for k in range(n_prof):

@@ -209,7 +209,8 @@ pet_status pet_warm_start(const pet_problem *problem, float *d_img, void *stream
 /* Objective Phi(f) = sum_m (g_m log yhat_m - yhat_m) - beta R(f), with
  * yhat = A f + w, reduced in FP64 (§2.1, Eq. (log_likelihood); §3,
  * Eq. (PET-MAP)).  Synchronising: returns after *h_phi is written.  Returns
- * PET_ERR_NUMERIC if some yhat_m <= 0 with g_m > 0. */
+ * PET_ERR_NUMERIC if some yhat_m <= 0 with g_m > 0; *h_phi is then -inf (the
+ * log-likelihood of a nonpositive mean with positive data). */
 pet_status pet_objective(const pet_problem *problem, const float *d_img, double *h_phi, void *stream);
 
 /* The same objective, enqueued only: d_phi (device, 3 doubles) receives
@@ -235,10 +236,14 @@ pet_status pet_objective_async(const pet_problem *problem, const float *d_img, d
  * current), so make that first call before any stream capture.  All calls
  * share the array and every call overwrites the partials it uses, so calls
  * that overlap on the GPU (different streams, or different threads) race:
- * order them on one stream.  Nonpositive expected counts with positive data
- * are not latched by this entry point (pet_objective reports them).
- * Multi-ring plans are rejected with PET_ERR_INVALID (their penalty couples
- * layers; use pet_objective_async).  Enqueued only. */
+ * order them on one stream.  A ray with a nonpositive expected count and
+ * positive data makes Phi and L come out -inf (their true value); this entry
+ * point has no status word to latch it in (pet_objective also returns
+ * PET_ERR_NUMERIC for it).  The current device must be the plan's device
+ * (else PET_ERR_INVALID).  Every ray's expected count is the one
+ * pet_objective computes; only the FP64 summation order of the per-ray terms
+ * differs.  Multi-ring plans are rejected with PET_ERR_INVALID (their penalty
+ * couples layers; use pet_objective_async).  Enqueued only. */
 pet_status pet_objective_noalloc(const pet_plan *plan, const float *d_img, const float *d_counts,
                                  const float *d_bg, float bg, float beta, double *d_phi, void *stream);
 

@@ -184,6 +184,9 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
                     if (yhat > 0.0f) {
                         ll = (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
                     } else if (g > 0.0f) {
+                        // g log(yhat) with yhat <= 0 and g > 0: the objective is -inf there
+                        // (latched as well when the caller gave a status word)
+                        ll = -(double)INFINITY;
                         if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
                     } else {
                         ll = -(double)yhat;

@@ -28,10 +28,16 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 double *g_setup_ptr[kMaxDevices] = {};
 
-pet_status scratch_for_current_device(double **out) {
+// The plan's tables live on plan->device, so the call must run there: the
+// current device has to be the plan's (else PET_ERR_INVALID), and the scratch
+// address is that device's.
+pet_status scratch_for_plan_device(const pet_plan *plan, double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(PET_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev != plan->device)
+        return set_error(PET_ERR_INVALID, "pet_objective_noalloc: the current device (" + std::to_string(dev) +
+                                              ") is not the plan's device (" + std::to_string(plan->device) + ")");
     if (dev < 0 || dev >= kMaxDevices) return set_error(PET_ERR_INVALID, "device index beyond the supported range");
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!g_setup_ptr[dev]) {
@@ -57,7 +63,9 @@ extern "C" pet_status pet_objective_noalloc(const pet_plan *plan, const float *d
     if (!(beta >= 0.0f) || !std::isfinite(beta)) return set_error(PET_ERR_INVALID, "beta must be >= 0");
     if (!std::isfinite(bg)) return set_error(PET_ERR_INVALID, "background must be finite");
     if (plan->ring) return set_error(PET_ERR_INVALID, "pet_objective_noalloc: multi-ring plans are not supported");
-    const int group = choose_group(plan);
+    // the band-chunk count of pet_objective's full-data pass, so that every
+    // ray's expected count is the one pet_objective computes
+    const int group = full_group(plan);
     const int n_ll = forward_blocks(plan->M, plan->nz, group);
     const long long plane = (long long)plan->N * plan->nz;
     const long long n_pen = (plane + 255) / 256;
@@ -66,7 +74,7 @@ extern "C" pet_status pet_objective_noalloc(const pet_plan *plan, const float *d
                                               std::to_string((long long)n_ll + n_pen) + " block partials needed, " +
                                               std::to_string(kNoallocPartials) + " available)");
     double *scratch = nullptr;
-    const pet_status st = scratch_for_current_device(&scratch);
+    const pet_status st = scratch_for_plan_device(plan, &scratch);
     if (st != PET_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // every block writes its own partial, so nothing has to be cleared first

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kBlock) forward_stack_kernel(const FwdArgs a) 
                     // FP32 rounding of yhat itself), reduced in FP64
                     ll += (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
                 } else if (g > 0.0f) {
+                    ll = -(double)INFINITY;            // log of a nonpositive mean: Phi = -inf
                     if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
                 } else {
                     ll += -(double)yhat;
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(kBlock) ring_forward_kernel(const FwdArgs a) {
                     if (yhat > 0.0f) {
                         ll += (g > 0.0f ? (double)g * (double)logf(yhat) : 0.0) - (double)yhat;
                     } else if (g > 0.0f) {
+                        ll = -(double)INFINITY;        // log of a nonpositive mean: Phi = -inf
                         if (a.status) atomicExch(a.status, (int)PET_ERR_NUMERIC);
                     } else {
                         ll += -(double)yhat;

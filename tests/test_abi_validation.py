@@ -82,3 +82,29 @@ def test_every_entry_point_refuses_null_handles(lib):
         assert st == PET_ERR_INVALID, f"{name} -> {st}: {lib.pet_last_error().decode()}"
         checked += 1
     assert checked >= 35
+
+
+def test_noalloc_objective_refuses_bad_arguments(lib):
+    """pet_objective_noalloc checks its pointers, beta and background before it
+    reads the plan or makes any CUDA call; the stand-in handles below are never
+    dereferenced."""
+    import math
+    from ctypes import c_float
+    fake = [c_void_p(0x1000), c_void_p(0x2000), c_void_p(0x3000), c_void_p(0x4000)]   # plan, img, counts, phi
+    fn = lib.pet_objective_noalloc
+
+    def call(plan, img, counts, phi, bg=0.1, beta=0.01):
+        st = fn(plan, img, counts, None, c_float(bg), c_float(beta), phi, None)
+        return st, lib.pet_last_error().decode()
+
+    for k in range(4):                       # each pointer null in turn
+        args = list(fake)
+        args[k] = None
+        st, msg = call(*args)
+        assert st == PET_ERR_INVALID and "null" in msg, (k, msg)
+    for beta in (-1.0, math.nan, math.inf):
+        st, msg = call(*fake, beta=beta)
+        assert st == PET_ERR_INVALID and "beta" in msg, (beta, msg)
+    for bg in (math.nan, math.inf, -math.inf):
+        st, msg = call(*fake, bg=bg)
+        assert st == PET_ERR_INVALID and "background" in msg, (bg, msg)
