@@ -25,6 +25,21 @@ CASES = {
                        geometry=Geometry(12, 10, 11, 19, bin_mm=1.3, nz=70), n_subsets=4, counts=3e5),
 }
 
+# edge cases of the method
+EDGE_CASES = {
+    # no background (w = 0) and bins wider than the image: 324 of 1704 rays miss
+    # the image, so yhat = 0 there (ratio 0, §2.3 remedy) and their counts are 0;
+    # low counts leave most rays with g = 0
+    "nobg": Workload("nobg", Geometry(40, 28, 24, 71, pixel_mm=2.0, bin_mm=1.5), n_subsets=4, counts=4e3,
+                     bg_frac=0.0, beta=0.02, n_ellipses=4),
+    # four views and nine narrow bins: 4 pixels no ray reaches (sens_n = 0) and
+    # 225 / 120 pixels outside one subset's rays (sens_t,n = 0), so the M-step's
+    # S_n = 0 branch (f_n = 0) and zero preconditioner entries are taken
+    "sparse": Workload("sparse", Geometry(24, 24, 4, 9, pixel_mm=2.0, bin_mm=2.0), n_subsets=2, counts=2e4,
+                       bg_frac=0.1, beta=0.02, n_ellipses=4),
+}
+CASES.update(EDGE_CASES)
+
 # multi-ring volumes (fully 3-D lines of response)
 RING_CASES = {
     # two rings on a clinical-size cylinder (kappa <= ~0.007), rings at layer centres

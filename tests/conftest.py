@@ -1,3 +1,4 @@
+import json
 import os
 import sys
 
@@ -48,3 +49,25 @@ def tiny_problem(geom, seed=0, n_subsets=4, beta=0.05, counts=2e4, bg_frac=0.1,
     data = make_data(work, seed)
     w = 0.0 if w_zero else data["w"]
     return build_problem(geom, data["g"], w, n_subsets, beta, potential, delta), data
+
+
+# Measured errors of the GPU results against the FP64 oracle, one record per
+# result (test, case, method, table type, quantity, value).  Written at the end
+# of the session to the file named by PETVR_ERROR_RECORD, when it is set.
+_ERROR_RECORDS = []
+
+
+@pytest.fixture(scope="session")
+def record_error():
+    def record(**fields):
+        _ERROR_RECORDS.append({k: (float(v) if isinstance(v, (np.floating, float)) else v)
+                               for k, v in fields.items()})
+    return record
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("PETVR_ERROR_RECORD")
+    if path and _ERROR_RECORDS:
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(_ERROR_RECORDS, f, indent=0)

@@ -3,12 +3,12 @@
 Tolerances (float32 kernels against float64 oracle):
   * projections: per element |gpu - oracle| <= 2e-5 |oracle| + 2e-6 max|oracle|
     (FP32 accumulation along rays of up to ~2n pixels and FP32 ray geometry);
-  * one update from the same iterate: relative L2 <= 1e-5 (the stated
-    per-iterate tolerance);
-  * trajectories of several epochs: relative L2 <= 1e-4 and objective
-    |dPhi|/|Phi| <= 1e-7 (FP32 iterates, errors compound slowly);
+  * every iterate of a trajectory (the first update from the same iterate and
+    every later one, up to three epochs): relative L2 <= 1e-5, the stated
+    per-iterate tolerance; objective |dPhi|/|Phi| <= 1e-7;
   * FP64 objective of a given image: relative 1e-7;
-  * BF16 SAGA table against the oracle's BF16 emulation: relative L2 <= 1e-4.
+  * BF16 SAGA table against the oracle's BF16 emulation: one update within
+    1e-5, three epochs within 1e-4.
 """
 import numpy as np
 import pytest
@@ -22,6 +22,15 @@ from paper_2106_03172_gb300.phantoms import subset_sequence
 pytestmark = pytest.mark.gpu
 
 PROJ_RTOL, PROJ_ATOL = 2e-5, 2e-6
+# FP32 iterates against the FP64 oracle, relative L2, at EVERY step of a
+# trajectory (the stated per-iterate tolerance).  Measured: one update from
+# the same iterate 4e-8 to 1.3e-7; after two epochs of the small cases at most
+# 5.4e-7; after three epochs at 256^2 at most 2.2e-6 (SVRG).
+ITERATE_RTOL = 1e-5
+# BF16 SAGA table against the oracle's BF16 rounding: a rounding decision can
+# flip where the FP32 inputs differ by an ulp, and such flips accumulate
+# (measured up to 6e-5 after three epochs); one update stays within ITERATE_RTOL.
+BF16_TRAJ_RTOL = 1e-4
 METHOD_SEED = {"osem": 0, "svrem": 1, "saga": 2, "svrg": 3}
 
 
@@ -151,16 +160,19 @@ def _gpu_problem(pv, plan, data, work):
     return pv.Problem(plan, _cuda(data["g"]), None, data["w"], work.beta)
 
 
-def test_objective_and_warm_start(case):
+def test_objective_and_warm_start(case, record_error):
     pv, prob, data, work, plan = case
     gp = _gpu_problem(pv, plan, data, work)
     img = torch.empty(prob.N * prob.nz, device="cuda")
     pv.pet_warm_start(gp.handle, img)
     f0 = prob.initial_image()
-    assert rel_l2(_host(img), f0) <= 1e-5
+    err = rel_l2(_host(img), f0)
+    assert err <= ITERATE_RTOL
     f = f0.astype(np.float32).astype(np.float64)
-    phi_gpu = pv.pet_objective(gp.handle, _cuda(f))
-    assert phi_gpu == pytest.approx(prob.objective(f), rel=1e-7)
+    phi_gpu, phi_ora = pv.pet_objective(gp.handle, _cuda(f)), prob.objective(f)
+    record_error(test="objective_and_warm_start", case=work.name, method="warm start", table="-", epochs=1,
+                 one_step=err, phi_rel=abs(phi_gpu - phi_ora) / abs(phi_ora))
+    assert phi_gpu == pytest.approx(phi_ora, rel=1e-7)
 
 
 def _oracle_alg(prob, method, f0, work, table="fp32"):
@@ -180,9 +192,10 @@ def _gpu_step(state, method, t, work):
 
 
 @pytest.mark.parametrize("method", ["osem", "svrem", "saga", "svrg"])
-def test_update_parity(case, method):
-    """One update from the same iterate within 1e-5; then two epochs step by
-    step within 1e-4 and the objective within 1e-7."""
+def test_update_parity(case, method, record_error):
+    """Two epochs step by step, every iterate within the per-iterate
+    tolerance (the first one is an update from the same iterate), and the
+    objective within 1e-7."""
     pv, prob, data, work, plan = case
     gp = _gpu_problem(pv, plan, data, work)
     f0 = prob.initial_image().astype(np.float32).astype(np.float64)
@@ -191,29 +204,44 @@ def test_update_parity(case, method):
     alg = _oracle_alg(prob, method, f0, work)
     seq = subset_sequence(2000 + METHOD_SEED[method], work.n_subsets, 2 * work.n_subsets)
     f = f0
+    errs = []
     for k, t in enumerate(seq):
         _gpu_step(state, method, int(t), work)
         f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
         err = rel_l2(_host(img), f)
-        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+        errs.append(err)
+        assert err <= ITERATE_RTOL, f"step {k}: {err:.3e}"
     phi_gpu = pv.pet_objective(gp.handle, img)
-    assert phi_gpu == pytest.approx(prob.objective(f), rel=1e-7)
+    phi_ora = prob.objective(f)
+    record_error(test="update_parity", case=work.name, method=method, table="fp32", epochs=2,
+                 one_step=errs[0], trajectory=errs[-1], trajectory_max=max(errs),
+                 phi_rel=abs(phi_gpu - phi_ora) / abs(phi_ora))
+    assert phi_gpu == pytest.approx(phi_ora, rel=1e-7)
     assert _host(img).min() >= 0.0
 
 
-def test_saga_bf16_table():
+@pytest.mark.parametrize("name", ["c64", "ragged", "stack", "ring2"])
+def test_saga_bf16_table(name, record_error):
+    """SAGA with the BF16 table (FP32 running mean) against the oracle's BF16
+    rounding of every stored entry, three epochs."""
     pv = _pv()
-    prob, data, work = oracle_problem("c64")
+    prob, data, work = oracle_problem(name)
     plan = pv.Plan(work.geometry, work.n_subsets)
     gp = _gpu_problem(pv, plan, data, work)
     f0 = prob.initial_image().astype(np.float32).astype(np.float64)
     img = _cuda(f0)
     state = pv.State(gp, "saga", img, table="bf16")
     alg = em.SAGA(prob, f0, work.alpha_saga, table="bf16")
+    errs = []
     for t in subset_sequence(7, work.n_subsets, 3 * work.n_subsets):
         _gpu_step(state, "saga", int(t), work)
         f = alg.step(int(t))
-    assert rel_l2(_host(img), f) <= 1e-4
+        errs.append(rel_l2(_host(img), f))
+    phi_gpu, phi_ora = pv.pet_objective(gp.handle, img), prob.objective(f)
+    record_error(test="saga_bf16_table", case=name, method="saga", table="bf16", epochs=3, one_step=errs[0],
+                 trajectory=errs[-1], trajectory_max=max(errs), phi_rel=abs(phi_gpu - phi_ora) / abs(phi_ora))
+    assert errs[0] <= ITERATE_RTOL
+    assert max(errs) <= BF16_TRAJ_RTOL
 
 
 def test_epoch_calls_equal_step_calls():
@@ -291,24 +319,42 @@ def test_full_size_projection_parity(full256):
         _assert_proj(_host(img).reshape(-1, 1), prob.At[t].T @ y[rows])
 
 
-@pytest.mark.parametrize("method", ["osem", "svrem", "saga", "svrg"])
-def test_full_size_one_epoch(full256, method):
+@pytest.mark.parametrize("method,table", [("osem", "fp32"), ("svrem", "fp32"), ("saga", "fp32"),
+                                          ("saga", "bf16"), ("svrg", "fp32")])
+def test_full_size_three_epochs(full256, method, table, record_error):
+    """256x256, 21 subsets, in the launch configuration the benchmark times
+    (captured epochs): the first update, then three epochs, so that SVREM
+    and SVRG take new anchors (SVRG every second epoch) and every SAGA table
+    entry is rewritten, each epoch end within the per-iterate tolerance
+    (BF16 table: its trajectory tolerance), and the objective within 1e-7."""
     pv, prob, data, work, plan = full256
     gp = _gpu_problem(pv, plan, data, work)
     f0 = prob.initial_image().astype(np.float32).astype(np.float64)
     img = _cuda(f0)
-    state = pv.State(gp, method, img)
-    alg = _oracle_alg(prob, method, f0, work)
-    seq = subset_sequence(2000, work.n_subsets, work.n_subsets)
+    state = pv.State(gp, method, img, table=table)
+    alg = (em.SAGA(prob, f0, work.alpha_saga, table=table) if method == "saga"
+           else _oracle_alg(prob, method, f0, work))
+    alpha = {"svrem": work.alpha_svrem, "saga": work.alpha_saga, "svrg": work.alpha_svrg}.get(method, 1.0)
+    eta = {"svrem": work.eta_svrem, "svrg": work.eta_svrg}.get(method, 1)
+    seq = subset_sequence(2000, work.n_subsets, 3 * work.n_subsets)
     _gpu_step(state, method, int(seq[0]), work)
     f = em.osem_step(prob, f0, int(seq[0])) if alg is None else alg.step(int(seq[0]))
-    assert rel_l2(_host(img), f) <= 1e-5
-    state.epoch(seq[1:], alpha={"svrem": work.alpha_svrem, "saga": work.alpha_saga,
-                                "svrg": work.alpha_svrg}.get(method, 1.0),
-                eta={"svrem": work.eta_svrem, "svrg": work.eta_svrg}.get(method, 1))
-    for t in seq[1:]:
-        f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
-    assert rel_l2(_host(img), f) <= 1e-4
+    one = rel_l2(_host(img), f)
+    assert one <= ITERATE_RTOL
+    ns = work.n_subsets
+    errs = []
+    for e in range(3):
+        part = seq[max(1, e * ns):(e + 1) * ns]
+        state.epoch(part, alpha=alpha, eta=eta)
+        for t in part:
+            f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
+        errs.append(rel_l2(_host(img), f))
+        assert errs[-1] <= (BF16_TRAJ_RTOL if table == "bf16" else ITERATE_RTOL), f"epoch {e}: {errs[-1]:.3e}"
+    phi_gpu, phi_ora = pv.pet_objective(gp.handle, img), prob.objective(f)
+    record_error(test="full_size_three_epochs", case=work.name, method=method, table=table, epochs=3,
+                 one_step=one, trajectory=errs[-1], trajectory_max=max(errs),
+                 phi_rel=abs(phi_gpu - phi_ora) / abs(phi_ora))
+    assert phi_gpu == pytest.approx(phi_ora, rel=1e-7)
 
 
 def test_full_size_stack_projection():
@@ -403,7 +449,7 @@ def potential_case(request):
 
 
 @pytest.mark.parametrize("method", ["osem", "svrem", "saga", "svrg"])
-def test_edge_preserving_potential_updates(potential_case, method):
+def test_edge_preserving_potential_updates(potential_case, method, record_error):
     pv, prob, work, plan, gp = potential_case
     f0 = prob.initial_image().astype(np.float32).astype(np.float64)
     img = _cuda(f0)
@@ -411,12 +457,18 @@ def test_edge_preserving_potential_updates(potential_case, method):
     alg = _oracle_alg(prob, method, f0, work)
     seq = subset_sequence(3000 + METHOD_SEED[method], work.n_subsets, 2 * work.n_subsets)
     f = f0
+    errs = []
     for k, t in enumerate(seq):
         _gpu_step(state, method, int(t), work)
         f = em.osem_step(prob, f, int(t)) if alg is None else alg.step(int(t))
         err = rel_l2(_host(img), f)
-        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
-    assert pv.pet_objective(gp.handle, img) == pytest.approx(prob.objective(f), rel=1e-7)
+        errs.append(err)
+        assert err <= ITERATE_RTOL, f"step {k}: {err:.3e}"
+    phi_gpu, phi_ora = pv.pet_objective(gp.handle, img), prob.objective(f)
+    record_error(test="edge_preserving_potential", case=f"c64 {prob.pen.potential}", method=method, table="fp32",
+                 epochs=2, one_step=errs[0], trajectory=errs[-1], trajectory_max=max(errs),
+                 phi_rel=abs(phi_gpu - phi_ora) / abs(phi_ora))
+    assert phi_gpu == pytest.approx(phi_ora, rel=1e-7)
 
 
 def test_edge_preserving_potential_objective(potential_case):
@@ -427,7 +479,7 @@ def test_edge_preserving_potential_objective(potential_case):
 
 
 @pytest.mark.parametrize("method,alpha0,decay", [("sga", 1.0, 0.0), ("sga", 1.0, 0.001), ("sem", 1.0, 0.001)])
-def test_non_vr_baseline_updates(case, method, alpha0, decay):
+def test_non_vr_baseline_updates(case, method, alpha0, decay, record_error):
     """The paper's baselines on the same kernels (§5.1): SGA, the subset
     BSREM (SGA with alpha_k = (0.001 k + 1)^-1) and SEM, against the oracle."""
     pv, prob, data, work, plan = case
@@ -438,11 +490,16 @@ def test_non_vr_baseline_updates(case, method, alpha0, decay):
     sched = lambda k: alpha0 / (decay * k + 1.0)
     alg = em.SGA(prob, f0, sched) if method == "sga" else em.SEM(prob, f0, sched)
     seq = subset_sequence(4000, work.n_subsets, 2 * work.n_subsets)
+    errs = []
     for k, t in enumerate(seq):
         state.epoch([int(t)], alpha=alpha0, decay=decay)
         f = alg.step(int(t))
         err = rel_l2(_host(img), f)
-        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+        errs.append(err)
+        assert err <= ITERATE_RTOL, f"step {k}: {err:.3e}"
+    label = "bsrem" if (method == "sga" and decay > 0) else method
+    record_error(test="non_vr_baseline", case=work.name, method=label, table="fp32", epochs=2,
+                 one_step=errs[0], trajectory=errs[-1], trajectory_max=max(errs))
     assert _host(img).min() >= 0.0
 
 
@@ -465,20 +522,20 @@ def test_iterate_preconditioner_updates(case, method):
         state.epoch([int(t)], alpha=alpha, eta=work.eta_svrg)
         f = alg.step(int(t))
         err = rel_l2(_host(img), f)
-        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+        assert err <= ITERATE_RTOL, f"step {k}: {err:.3e}"
     # back to the constant preconditioner of the starting image for one epoch
     state.set_preconditioner("constant")
     alg.precond = "constant"
     state.epoch(seq[:work.n_subsets], alpha=alpha, eta=work.eta_svrg)
     for t in seq[:work.n_subsets]:
         f = alg.step(int(t))
-    assert rel_l2(_host(img), f) <= 1e-4
+    assert rel_l2(_host(img), f) <= ITERATE_RTOL
     assert _host(img).min() >= 0.0
     with pytest.raises(pv.PetError):
         pv.State(gp, "osem", _cuda(f0)).set_preconditioner("iterate")
 
 
-def test_sagaem_updates(case):
+def test_sagaem_updates(case, record_error):
     """SAGA on the EM statistic (§2.3 remark) against the oracle."""
     pv, prob, data, work, plan = case
     gp = _gpu_problem(pv, plan, data, work)
@@ -486,8 +543,12 @@ def test_sagaem_updates(case):
     img = _cuda(f0)
     state = pv.State(gp, "sagaem", img)
     alg = em.SAGAEM(prob, f0, 0.7)
+    errs = []
     for k, t in enumerate(subset_sequence(4100, work.n_subsets, 2 * work.n_subsets)):
         state.epoch([int(t)], alpha=0.7)
         f = alg.step(int(t))
         err = rel_l2(_host(img), f)
-        assert err <= (1e-5 if k == 0 else 1e-4), f"step {k}: {err:.3e}"
+        errs.append(err)
+        assert err <= ITERATE_RTOL, f"step {k}: {err:.3e}"
+    record_error(test="sagaem", case=work.name, method="sagaem", table="fp32", epochs=2,
+                 one_step=errs[0], trajectory=errs[-1], trajectory_max=max(errs))

@@ -101,7 +101,7 @@ def test_noalloc_nonpositive_mean_with_counts_gives_minus_infinity():
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     pv = _pv()
     from paper_2106_03172_gb300.phantoms import Geometry
-    geom = Geometry(1024, 1024, 1024, 1465)
+    geom = Geometry(1024, 1024, 1024, 4096)            # 4.2M rays: 262144 block partials at 16 chunks
     plan = pv.Plan(geom, 1)
     img = torch.ones(geom.n_pixels, device="cuda")
     counts = torch.ones(geom.n_rays, device="cuda")
