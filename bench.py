@@ -74,10 +74,14 @@ def parse_args():
                     help="run the four methods as one batch (one launch per phase) instead of four streams")
     ap.add_argument("--on", default="c256", help="converge workload: the problem the methods are compared on")
     ap.add_argument("--epochs", type=int, default=40, help="converge workload: update epochs per method")
+    ap.add_argument("--step-epochs", type=int, default=50,
+                    help="update epochs of each method per step (50: the 256^2 configuration's run length)")
+    ap.add_argument("--legs", default="batched,batch64,stack,serve,parity",
+                    help="short extra measurements after the headline (comma list, or 'none')")
     return ap.parse_args()
 
 
-def workload_config(work):
+def workload_config(work, epochs=50):
     g = work.geometry
     return {
         "workload": f"{work.name}: {g.nx}x{g.ny}" + (f"x{g.nz} volume ({g.n_rings} rings {g.ring_mm:g} mm apart, "
@@ -87,9 +91,9 @@ def workload_config(work):
                     f"{g.n_bins} bins, {work.n_subsets} angle-interleaved subsets, {work.counts:.0e} counts, "
                     f"{int(round(work.bg_frac * 100))}% background, {work.potential}"
                     + (f" (delta={work.delta:g})" if work.potential != "quadratic" else "") + f" beta={work.beta}",
-        "step": f"one epoch each of OSEM, SVREM(alpha={work.alpha_svrem}, eta={work.eta_svrem}), "
+        "step": f"{epochs} update epochs each of OSEM, SVREM(alpha={work.alpha_svrem}, eta={work.eta_svrem}), "
                 f"SAGA(alpha={work.alpha_saga}, fp32 table), SVRG(alpha={work.alpha_svrg}, eta={work.eta_svrg}), "
-                "each followed by its FP64 objective",
+                "each epoch followed by its FP64 objective",
         "l2": "flushed between steps (256 MiB write outside the timed events)",
         "n_subsets": work.n_subsets,
         "image": [g.ny, g.nx],
@@ -297,25 +301,51 @@ def measured_hbm_peak():
         return 6800.0, "of fallback (6.8 TB/s)"
 
 
-def dram_traffic_record(kind: int, workload: str = "c256"):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary (profiles/roofline_traffic.txt), or None when that summary was
-    taken on other kernel sources, another workload, or does not cover this
-    kernel kind."""
+def sm_max_mhz() -> float:
+    """Maximum SM clock of the GB300s (MEASURED_PEAKS.json), else the
+    device's reported maximum, else 2070 MHz."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except (OSError, ValueError, KeyError):
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits", "-i", "0"],
+                             capture_output=True, text=True, timeout=10).stdout.strip().splitlines()
+        return float(out[0])
+    except Exception:
+        return 2070.0
+
+
+def _profile_record(workload: str):
+    """Fields of profiles/roofline_traffic.txt, or {} when the record is for
+    another workload or was taken on other projector sources."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return {}
     rec = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             key, val = line.split(":", 1)
             rec[key.strip()] = val.strip()
-    key = f"kind{kind}_dram_bytes_per_launch"
-    if rec.get("workload", "c256") != workload:
-        return None
-    if rec.get("source_sha256") != kernel_source_digest() or key not in rec:
-        return None
-    return float(rec[key])
+    if rec.get("workload", "c256") != workload or rec.get("source_sha256") != kernel_source_digest():
+        return {}
+    return rec
+
+
+def ncu_issue_record(kind: int, workload: str = "c256"):
+    """ncu issue-active fraction (smsp__issue_active, of peak sustained active)
+    of the dominant kernel kind from the committed record, or None."""
+    val = _profile_record(workload).get(f"kind{kind}_issue_active_pct")
+    return float(val) / 100.0 if val is not None else None
+
+
+def dram_traffic_record(kind: int, workload: str = "c256"):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/roofline_traffic.txt), or None when that summary was
+    taken on other kernel sources, another workload, or does not cover this
+    kernel kind."""
+    val = _profile_record(workload).get(f"kind{kind}_dram_bytes_per_launch")
+    return float(val) if val is not None else None
 
 
 # --------------------------------------------------------------------------- objective gap
@@ -429,13 +459,14 @@ def run_ours(args):
 
     side = {m: torch.cuda.Stream() for m in METHODS}
     batch = petvr.Batch([states[m] for m in METHODS]) if args.batch else None
+    E = max(1, args.step_epochs)
 
-    def one_step(step, concurrent=True):
-        """The four reconstructions are independent: by default one batched
-        launch per phase covers all four (pet_batch_epoch); otherwise each
-        runs on its own stream (forked from and joined back into the timing
-        stream)."""
-        seqs = seqs_for_step(step, ns)
+    def one_epoch(ep, concurrent=True):
+        """One update epoch of each of the four independent reconstructions,
+        each followed by its objective: by default each runs on its own stream
+        (forked from and joined back into the timing stream); with --batch one
+        persistent batched launch per phase covers all four."""
+        seqs = seqs_for_step(ep, ns)
         if batch is not None and concurrent:
             batch.epoch(seqs, [a[m][0] for m in METHODS], [a[m][1] for m in METHODS], stream=stream)
             batch.objective_async(phi, stream=stream)
@@ -452,9 +483,24 @@ def run_ours(args):
                 stream.wait_stream(side[m])
         return seqs
 
+    def one_step(step, concurrent=True):
+        """One step: E update epochs of each method (epoch indices step*E ...)."""
+        for e in range(E):
+            one_epoch(step * E + e, concurrent)
+
+    def count_step():
+        """Subset forward+back pairs of the next step's E epochs (anchor passes
+        included), advancing the host's update counters."""
+        total = 0
+        for _ in range(E):
+            p, _ = rep.step_pairs()
+            total += p
+            rep.advance()
+        return total
+
     for w in range(args.warmup):
         one_step(w)
-        rep.advance()
+        count_step()
     torch.cuda.synchronize()
 
     # ---- timed region (kernel-only: inputs resident in HBM)
@@ -469,12 +515,10 @@ def run_ours(args):
     launches0 = petvr.pet_kernel_launches()
     for k in range(args.steps):
         flush.zero_()
-        p, _ = rep.step_pairs()
-        pairs += p
+        pairs += count_step()
         events[k][0].record(stream)
         one_step(args.warmup + k)
         events[k][1].record(stream)
-        rep.advance()
     torch.cuda.synchronize()
     launches = petvr.pet_kernel_launches() - launches0
     clk = clocks.stop()
@@ -485,8 +529,8 @@ def run_ours(args):
     phi_host = phi.cpu().numpy()
     value, total_max, pairs_all = combine_ranks(total_ms, float(pairs), device="cuda")
 
-    # ---- profiled pass: per-kernel durations for the roofline
-    n_prof = min(args.steps, 8)
+    # ---- profiled pass: per-kernel durations for the roofline (a few epochs, methods one after another)
+    n_prof = min(E, 4)
     fk, bk = (("ring_forward_kernel", "ring_back_column_kernel" if geom.nz <= 8 else "ring_back_kernel")
               if geom.multiring else
               ("forward_stack_kernel", "back_stack_kernel") if geom.nz > 1 else ("forward_tile_kernel", "back_tile_kernel"))
@@ -501,10 +545,11 @@ def run_ours(args):
     upd_bytes = {"osem": 12, "svrem": 32, "saga": 32, "svrg": 20}
     petvr.pet_profile_reset()
     petvr.pet_profile_enable(True)
+    prof_base = (args.warmup + args.steps) * E
     for k in range(n_prof):
         flush.zero_()
         p, anchors = rep.step_pairs()
-        seqs = one_step(args.warmup + args.steps + k, concurrent=False)
+        seqs = one_epoch(prof_base + k, concurrent=False)
         for i, m in enumerate(METHODS):
             for t in seqs[i]:
                 rays = plan.subset_lines(int(t)) * (1 if geom.multiring else geom.nz)
@@ -531,14 +576,22 @@ def run_ours(args):
     for v in kinds.values():
         v["share"] = v["total_ms"] / tot
     dom = max(kinds, key=lambda k: kinds[k]["total_ms"])
-    peak_alu = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    n_sms = props.multi_processor_count
+    sm_mhz = sm_max_mhz()
+    peak_alu = n_sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
     achieved = alg_flops[dom] / (kinds[dom]["total_ms"] / 1e3) / 1e12
     traffic = dram_traffic_record(dom, work.name)
+    issue = ncu_issue_record(dom, work.name)
     roofline = {"bound": "alu", "kernel": kinds[dom]["name"], "achieved": achieved, "peak": peak_alu,
                 "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal max clock)",
+                "peak_source": f"{n_sms} SMs (this device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                               f"{sm_mhz:g} MHz (maximum SM clock)",
                 "algorithmic_bytes_per_launch": alg_bytes[dom] / max(1, kinds[dom]["launches"]),
                 "hbm_achieved_gbs": alg_bytes[dom] / (kinds[dom]["total_ms"] / 1e3) / 1e9,
+                "issue_active_frac": issue,
+                "issue_active_source": "ncu smsp__issue_active of this kernel on this workload "
+                                       "(profiles/roofline_traffic.txt; null when the sources changed since)",
                 "kernels": {v["name"]: {k2: v[k2] for k2 in ("launches", "avg_us", "share")}
                             for v in kinds.values()}}
     hbm_peak, hbm_src = measured_hbm_peak()
@@ -555,21 +608,20 @@ def run_ours(args):
     # outside them.
     e2e_events = []
     e2e_pairs = 0
+    e2e_base = (prof_base + n_prof + E - 1) // E
     for k in range(args.steps):
         flush.zero_()
-        p, _ = rep.step_pairs()
-        e2e_pairs += p
+        e2e_pairs += count_step()
         s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s_ev.record(stream)
         g_dev.copy_(g_host, non_blocking=True)
         petvr.pet_problem_update(prob.handle, g_dev, None, data["w"])
-        one_step(args.warmup + args.steps + n_prof + k)
+        one_step(e2e_base + k)
         for i, m in enumerate(METHODS):
             img_host[i].copy_(imgs[m], non_blocking=True)
         phi_host_buf.copy_(phi, non_blocking=True)
         e_ev.record(stream)
         e2e_events.append((s_ev, e_ev))
-        rep.advance()
     torch.cuda.synchronize()
     e2e_ms = [s_ev.elapsed_time(e_ev) for s_ev, e_ev in e2e_events]
     e2e_value, _, _ = combine_ranks(float(sum(e2e_ms)), float(e2e_pairs), device="cuda")
@@ -579,18 +631,21 @@ def run_ours(args):
     # ---- reconstructions to a 1e-4 relative objective gap (Phi* from the oracle)
     phi_star, phi_src = phi_star_for(work, data)
     recon = (measure_recon(torch, petvr, prob, states, imgs, work, phi_star, n_rec=args.recon)
-             if phi_star is not None else None)
+             if phi_star is not None and args.recon > 0 else None)
     recon_line = {"gap": GAP, "phi_star": phi_star, "phi_star_source": phi_src,
                   "start": "constant image + one unpenalised OSEM epoch (counted in the latency)",
                   "per_method": recon}
 
     unit = "subset fwd+back projections/s"
+    legs = {}
+    if rank == 0 and world == 1:
+        legs = run_legs(args, torch, petvr, work, data, prob, f0, value, stream, flush)
     line = {
         "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
         "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ellipse phantom, Poisson counts)",
-        "config": dict(workload_config(work), parallelism=f"replicas x{world}",
+        "config": dict(workload_config(work, E), parallelism=f"replicas x{world}",
                        concurrency="one batch (pet_batch_epoch)" if args.batch else "four streams",
                        launch_shapes={"forward_band_chunks": tuning[0], "back_run_pixels": tuning[1],
                                       "source": tune_src}),
@@ -603,18 +658,153 @@ def run_ours(args):
         "recon": recon_line,
         "objective_last_step": [float(x) for x in phi_host[:, 0]],
     }
+    line.update(legs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, cpairs, setup = oracle_steps(work, data, 2, min_seconds=12.0)
         line["cpu_baseline"] = {
             "value": sum(cpairs) / sum(times), "unit": unit, "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} bench steps of the FP64 oracle (about {sum(times):.0f} s; system matrix build "
-                      f"and warm start, {setup:.1f} s, untimed)"}
+            "sample": f"{len(times)} epochs of each of the four methods (each followed by its objective) of the "
+                      f"FP64 oracle, one thread (about {sum(times):.0f} s; system matrix build and warm start, "
+                      f"{setup:.1f} s, untimed)"}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+# --------------------------------------------------------------------------- short legs after the headline
+
+def _sub_bench(extra, timeout=600):
+    """Run this script in a child process (same GPU, this process idle) and
+    return its JSON line, or {"error": ...}."""
+    cmd = [sys.executable, os.path.abspath(__file__)] + extra
+    try:
+        res = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout} s: {' '.join(extra)}"}
+    lines = [ln for ln in res.stdout.strip().splitlines() if ln.startswith("{")]
+    if res.returncode != 0 or not lines:
+        return {"error": f"rc={res.returncode}: {res.stderr.strip().splitlines()[-1:] or ''}"}
+    return json.loads(lines[-1])
+
+
+def leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush, steps=3, epochs=10):
+    """The same four reconstructions as one persistent batch (pet_batch_epoch:
+    one resident grid per phase for all four), timed like the headline."""
+    imgs = {m: f0.clone() for m in METHODS}
+    states = {m: petvr.State(prob, m, imgs[m]) for m in METHODS}
+    batch = petvr.Batch([states[m] for m in METHODS])
+    a = alphas(work)
+    phi = torch.zeros(4, 3, dtype=torch.float64, device="cuda")
+    rep = Replica(work)
+    ns = work.n_subsets
+
+    def step(k):
+        pairs = 0
+        for e in range(epochs):
+            p, _ = rep.step_pairs()
+            pairs += p
+            rep.advance()
+            batch.epoch(seqs_for_step(50000 + k * epochs + e, ns), [a[m][0] for m in METHODS],
+                        [a[m][1] for m in METHODS], stream=stream)
+            batch.objective_async(phi, stream=stream)
+        return pairs
+
+    step(0)
+    torch.cuda.synchronize()
+    ms, pairs = [], 0
+    for k in range(1, steps + 1):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pairs += step(k)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    total = sum(x.elapsed_time(y) for x, y in ms)
+    value = pairs / (total / 1e3)
+    return {"value": value, "unit": "subset fwd+back projections/s", "ms_per_epoch": total / (steps * epochs),
+            "vs_four_streams": value / streams_value,
+            "how": f"{steps} steps of {epochs} epochs of the four methods as one batch (persistent phases), "
+                   "objectives batched too; L2 flushed between steps"}
+
+
+def leg_parity(torch, petvr, work, data, prob):
+    """Untimed checker: the FP64 oracle on this workload from the same start,
+    against the GPU, per result: the warm start, then for each method the
+    first update and one epoch (relative L2) and the objective after it."""
+    from oracle import em
+    from oracle.em import build_problem
+    from paper_2106_03172_gb300.phantoms import subset_sequence
+    t0 = time.perf_counter()
+    ora = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta, work.potential, work.delta)
+    f0_ora = ora.initial_image()
+    geom, ns = work.geometry, work.n_subsets
+    f0 = torch.empty(geom.n_pixels * geom.nz, device="cuda")
+    petvr.pet_warm_start(prob.handle, f0)
+    torch.cuda.synchronize()
+    got0 = f0.double().cpu().numpy().reshape(f0_ora.shape)
+
+    def rel(x, y):
+        return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+    out = {"warm_start": rel(got0, f0_ora)}
+    f_start = got0                                      # both sides continue from the GPU's FP32 warm start
+    a = alphas(work)
+    seq = subset_sequence(2000, ns, ns)
+    for label, m, table in (("osem", "osem", "fp32"), ("svrem", "svrem", "fp32"), ("saga", "saga", "fp32"),
+                            ("saga_bf16", "saga", "bf16"), ("svrg", "svrg", "fp32")):
+        img = torch.from_numpy(f_start.astype(np.float32).ravel()).cuda()
+        st = petvr.State(prob, m, img, table=table)
+        alg = {"osem": None, "svrem": lambda: em.SVREM(ora, f_start, *a["svrem"]),
+               "saga": lambda: em.SAGA(ora, f_start, a["saga"][0], table=table),
+               "svrg": lambda: em.SVRG(ora, f_start, *a["svrg"])}[m]
+        alg = alg() if alg else None
+        f = f_start
+        errs = []
+        for t in seq:
+            st.epoch([int(t)], alpha=a[m][0], eta=a[m][1])
+            f = em.osem_step(ora, f, int(t)) if alg is None else alg.step(int(t))
+            torch.cuda.synchronize()
+            errs.append(rel(img.double().cpu().numpy().reshape(f.shape), f))
+        phi_gpu = petvr.pet_objective(prob.handle, img)
+        phi_ora = ora.objective(f)
+        out[label] = {"first_update": errs[0], "epoch_max": max(errs), "epoch_end": errs[-1],
+                      "phi_rel": abs(phi_gpu - phi_ora) / abs(phi_ora)}
+    out["how"] = ("FP64 oracle (oracle/) from the GPU's FP32 warm start, the same subset sequence; relative L2 of "
+                  "every iterate of one epoch against the oracle's, |dPhi|/|Phi| at its end; BF16 table against "
+                  "the oracle's BF16 rounding")
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
+def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, flush):
+    """Short measurements after the headline, each reported under its own key."""
+    want = set() if args.legs == "none" else {x.strip() for x in args.legs.split(",") if x.strip()}
+    legs = {}
+    if "batched" in want and not work.geometry.multiring and work.geometry.nz == 1:
+        legs["batched_four_methods"] = leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush)
+    if "batch64" in want:
+        legs["batch64"] = _sub_bench(["--workload", "batch64", "--steps", "3", "--warmup", "1"])
+    if "stack" in want:
+        sub = _sub_bench(["--workload", "c128x47", "--steps", "3", "--warmup", "1", "--step-epochs", "2",
+                          "--legs", "none", "--no-cpu-baseline", "--recon", "0"])
+        legs["c128x47"] = {k: sub.get(k) for k in ("value", "unit", "ms_per_step", "error") if k in sub}
+        if "roofline" in sub:
+            legs["c128x47"]["roofline_frac"] = sub["roofline"].get("frac")
+            legs["c128x47"]["achieved_tflops"] = sub["roofline"].get("achieved")
+    if "serve" in want:
+        sub = _sub_bench(["--workload", "serve", "--requests", "30"])
+        legs["serve30"] = {k: sub.get(k) for k in ("value", "unit", "latency", "speedup_vs_plain",
+                                                   "p50_speedup_vs_plain", "bit_identical_to_plain", "error")
+                           if k in sub}
+        if "plain" in sub:
+            legs["serve30"]["plain_latency"] = sub["plain"]["latency"]
+    if "parity" in want:
+        legs["parity_vs_oracle"] = leg_parity(torch, petvr, work, data, prob)
+    return legs
 
 
 def run_batch64(args):
@@ -719,8 +909,46 @@ def run_batch64(args):
                         "note": "2 flops per system-matrix nonzero per projection"},
         "bit_identical_to_sequential": bool(same),
     }
+    line["recon"] = batch64_recon(torch, petvr, works, [make_data(w, 100 + i) for i, w in enumerate(works)])
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batch64_recon(torch, petvr, works, datas, max_epochs=200):
+    """Reconstructions of the 64 members to the 1e-4 relative gap (each
+    against its own Phi* from the FP64 oracle, tests/golden/phi_star.json):
+    all 64 admitted at once and advanced as one batch (serving.Server, three
+    updates per tick, objectives checked every epoch), against the plain
+    per-reconstruction path, one member after another (serve_plain).  Both
+    return the same image for every member."""
+    import hashlib
+
+    from paper_2106_03172_gb300.serving import Request, Server, latency_summary, serve_plain
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "phi_star.json")))
+    phis = []
+    for i, d in enumerate(datas):
+        ent = golden.get(f"batch64_{i}")
+        sha = hashlib.sha256(d["g"].astype("<f4").tobytes()).hexdigest()
+        if not ent or ent["counts_sha256"] != sha:
+            return {"unavailable": f"no stored Phi* for member {i} (tests/golden/make_phi_star.py batch64_0-64)"}
+        phis.append(ent["phi_star"])
+
+    def requests():
+        return [Request(i, w, d["g"], d["w"], phi, arrival=0.0, seed=9000 + i, algo="saga")
+                for i, (w, d, phi) in enumerate(zip(works, datas, phis))]
+
+    srv = Server(budget_bytes=16 << 30, max_slots=64, gap=GAP, max_epochs=max_epochs, tick=3, window=4)
+    srv.prepare(works)
+    torch.cuda.synchronize()
+    done = srv.serve(requests())
+    plain = serve_plain(requests(), gap=GAP, max_epochs=max_epochs)
+    same = all(x.epochs == y.epochs and np.array_equal(x.image, y.image) for x, y in zip(done, plain))
+    b, p = latency_summary(done), latency_summary(plain)
+    return {"gap": GAP, "batched": b, "plain": p, "speedup_reached_per_s": b["reached_per_s"] / p["reached_per_s"],
+            "bit_identical_to_plain": bool(same),
+            "how": "64 SAGA (BF16 table) reconstructions from their warm starts, all arriving at once: one batch "
+                   "(serving.Server: 3 updates per tick, host check every 4 ticks) against one after another "
+                   "through each member's own epochs (serve_plain); Phi* per member from the FP64 oracle"}
 
 
 def _server_stats(srv):

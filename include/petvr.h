@@ -317,13 +317,20 @@ pet_status pet_state_objective_async(pet_state *state, double *d_phi, void *stre
 /* ---- batches: many reconstructions per launch ------------------------------ */
 
 /* Group n existing states (any algorithms; single-slice plans of any sizes;
- * each state at most once) so that their updates run together: every update
- * of pet_batch_epoch launches one forward projection and one back projection
- * + update kernel per launch shape for all members (the batched form of the
- * reconstructions, with per-member geometry, data and subset indices).  Each
- * member's result is bit-identical to running its own epoch call with the
- * same subset sequence.  The batch borrows the states, which must outlive it;
- * a state in a batch may still be used on its own between batch calls. */
+ * each state at most once) so that their updates run together (the batched
+ * form of the reconstructions, with per-member geometry, data and subset
+ * indices).  Every update of pet_batch_epoch runs as persistent phases: one
+ * resident grid, sized to the GPU, claims the forward-projection work items
+ * of every member (ray blocks of the member's current subset, and of all its
+ * views where its anchor pass is due); then one resident grid per potential
+ * class claims the back-projection + update items (16 x 16 tiles, and the
+ * anchor passes' (subset, tile) items).  An update with anchors due runs the
+ * anchor back projections beside the other members' updates, then the anchor
+ * finishes, then the anchored members' updates.  Each member's result is
+ * bit-identical to running its own epoch call with the same subset sequence
+ * (each work item is one block of the member's own launch).  The batch
+ * borrows the states, which must outlive it; a state in a batch may still be
+ * used on its own between batch calls. */
 pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out);
 pet_status pet_batch_destroy(pet_batch *batch);
 

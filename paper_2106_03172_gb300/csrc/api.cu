@@ -1147,7 +1147,10 @@ pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream)
 pet_status pet_batch_destroy(pet_batch *b) {
     if (!b) return PET_OK;
     dfree(b->d_members);
-    dfree(b->d_idx);
+    dfree(b->d_segs);
+    dfree(b->d_claims);
+    dfree(b->d_obj_segs);
+    dfree(b->d_obj_claim);
     dfree(b->d_seqs);
     dfree(b->d_alphas);
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
@@ -1176,49 +1179,36 @@ pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out
     if (!b) return set_error(PET_ERR_OOM, "host allocation failed");
     b->states.assign(states, states + n);
     b->members.resize(n);
-    // group members by launch shape
-    std::vector<int> idx;
-    // kind 0: subset forwards (band chunks), 1: back projections (run length),
-    // 2: full-data objective forwards (their band chunks)
-    auto value_of = [](int kind, const pet_plan *pl) {
-        return kind == 0 ? choose_group(pl) : kind == 1 ? pl->back_run : full_group(pl);
-    };
-    auto add_groups = [&](int kind) {
-        std::vector<int> values;
-        for (pet_state *st : b->states) {
-            const int v = value_of(kind, st->prob->plan);
-            if (std::find(values.begin(), values.end(), v) == values.end()) values.push_back(v);
-        }
-        for (int v : values) {
-            pet_batch::Group g{v, (int)idx.size(), 0, 0, 0};
-            for (int j = 0; j < n; ++j) {
-                const pet_plan *pl = b->states[j]->prob->plan;
-                if (value_of(kind, pl) != v) continue;
-                idx.push_back(j);
-                ++g.count;
-                const int gx = kind == 0 ? forward_blocks(max_sub_rays(pl), 1, v)
-                               : kind == 1 ? ((pl->nx + 15) / 16) * ((pl->ny + 15) / 16)
-                                           : forward_blocks(pl->M, 1, v);
-                g.grid_x = std::max(g.grid_x, gx);
-                g.max_views = std::max(g.max_views, pl->max_sub_views);
-            }
-            (kind == 0 ? b->fwd_groups : kind == 1 ? b->back_groups : b->obj_groups).push_back(g);
-        }
-    };
-    add_groups(0);
-    add_groups(1);
-    add_groups(2);
     pet_status e;
-    if ((e = dalloc(&b->d_members, (size_t)n, "batch members")) != PET_OK ||
-        (e = dalloc(&b->d_idx, idx.size(), "batch index")) != PET_OK) {
+    if ((e = dalloc(&b->d_members, (size_t)n, "batch members")) != PET_OK) {
         pet_batch_destroy(b);
         return e;
     }
-    b->h_idx = idx;
-    const cudaError_t ce = cudaMemcpy(b->d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice);
+    // the objective pass: one segment per member (its full-data forward blocks), longest items first
+    std::vector<WorkSeg> obj;
+    for (int j = 0; j < n; ++j) {
+        const pet_plan *pl = b->states[j]->prob->plan;
+        obj.push_back({j, WK_FWD_OBJECTIVE, 0, forward_blocks(pl->M, 1, full_group(pl)), full_group(pl), 0});
+    }
+    std::stable_sort(obj.begin(), obj.end(), [&](const WorkSeg &x, const WorkSeg &y) {
+        const pet_plan *px = b->states[x.member]->prob->plan, *py = b->states[y.member]->prob->plan;
+        return (std::max(px->nx, px->ny) + x.shape - 1) / x.shape > (std::max(py->nx, py->ny) + y.shape - 1) / y.shape;
+    });
+    for (WorkSeg &g : obj) {
+        g.first = b->n_obj_items;
+        b->n_obj_items += g.count;
+    }
+    b->n_obj_segs = n;
+    if ((e = dalloc(&b->d_obj_segs, (size_t)n, "batch objective segments")) != PET_OK ||
+        (e = dalloc(&b->d_obj_claim, 1, "batch objective claim")) != PET_OK) {
+        pet_batch_destroy(b);
+        return e;
+    }
+    const cudaError_t ce = cudaMemcpy(b->d_obj_segs, obj.data(), sizeof(WorkSeg) * obj.size(),
+                                      cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
         pet_batch_destroy(b);
-        return cuda_ok(ce, "batch index upload");
+        return cuda_ok(ce, "batch objective segment upload");
     }
     *out = b;
     return PET_OK;
@@ -1253,6 +1243,7 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.img = st->img;
     m.alt = st->alt;
     m.ratio = st->ratio;
+    m.ratio_full = st->ratio_full;
     m.s_hat = st->s_hat;
     m.f_anc = st->f_anc;
     m.s_anc = st->s_anc;
@@ -1269,7 +1260,88 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
     m.part = st->d_part;
 }
 
-// All launches of one batched epoch on stream s.
+// Work segments of the persistent phases of n_iter batched updates (into
+// b->h_segs and b->phases).  Per update:
+//   forward: every member's subset rays, plus the rays of every view of the
+//     members whose anchor pass is due (anchor items first: they are the
+//     longest, so the dynamic claim order leaves short items for the tail);
+//   at an anchor update: a back phase with the anchor back projections and
+//     the other members' updates, the anchor finishes, then a back phase with
+//     the anchored members' updates; otherwise one back phase with every
+//     member's update.
+// Back phases are split by potential class (the quadratic epilogue and the
+// edge-preserving one are different kernels), longest tiles first.
+void build_batch_phases(pet_batch *b, int n_iter, const std::vector<std::vector<uint8_t>> &anchors) {
+    const int n = (int)b->states.size();
+    b->h_segs.clear();
+    b->phases.assign((size_t)n_iter, {});
+    int claim = 0;
+    auto tiles_of = [](const pet_plan *pl) { return ((pl->nx + 15) / 16) * ((pl->ny + 15) / 16); };
+    auto major_of = [](const pet_plan *pl) { return std::max(pl->nx, pl->ny); };
+    auto emit = [&](int i, int kind, std::vector<WorkSeg> &segs, int genpot) {
+        if (segs.empty()) return;
+        pet_batch::Phase ph{kind, (int)b->h_segs.size(), (int)segs.size(), 0, 256, genpot, claim++};
+        for (WorkSeg &g : segs) {
+            g.first = ph.n_items;
+            ph.n_items += g.count;
+            if (kind == 1)
+                ph.threads = std::max(ph.threads, back_block_threads(g.shape,
+                                                                     b->states[g.member]->prob->plan->max_sub_views));
+            b->h_segs.push_back(g);
+        }
+        b->phases[(size_t)i].push_back(ph);
+    };
+    for (int i = 0; i < n_iter; ++i) {
+        bool any = false;
+        std::vector<WorkSeg> fa, fu;
+        for (int j = 0; j < n; ++j) {
+            const pet_plan *pl = b->states[j]->prob->plan;
+            if (anchors[j][i]) {
+                any = true;
+                fa.push_back({j, WK_FWD_ANCHOR, 0, forward_blocks(pl->M, 1, full_group(pl)), full_group(pl), 0});
+            }
+            fu.push_back({j, WK_FWD_UPDATE, 0, forward_blocks(max_sub_rays(pl), 1, choose_group(pl)),
+                          choose_group(pl), 0});
+        }
+        // bands per chunk decide an item's length
+        auto longer_fwd = [&](const WorkSeg &x, const WorkSeg &y) {
+            const int lx = (major_of(b->states[x.member]->prob->plan) + x.shape - 1) / x.shape;
+            const int ly = (major_of(b->states[y.member]->prob->plan) + y.shape - 1) / y.shape;
+            return lx > ly;
+        };
+        std::stable_sort(fa.begin(), fa.end(), longer_fwd);
+        std::stable_sort(fu.begin(), fu.end(), longer_fwd);
+        fa.insert(fa.end(), fu.begin(), fu.end());
+        emit(i, 0, fa, 0);
+        // views per subset decide a back item's length
+        auto longer_back = [&](const WorkSeg &x, const WorkSeg &y) {
+            return b->states[x.member]->prob->plan->max_sub_views > b->states[y.member]->prob->plan->max_sub_views;
+        };
+        for (int pass = any ? 0 : 1; pass < 2; ++pass) {
+            for (int gp = 0; gp < 2; ++gp) {
+                std::vector<WorkSeg> anc, upd;
+                for (int j = 0; j < n; ++j) {
+                    const pet_state *st = b->states[j];
+                    const pet_plan *pl = st->prob->plan;
+                    const int member_gp = st->prob->pen.potential != PET_POT_QUADRATIC ? 1 : 0;
+                    if (pass == 0 && anchors[j][i] && gp == 0)
+                        anc.push_back({j, WK_BACK_ANCHOR, 0, tiles_of(pl) * pl->ns, pl->back_run, tiles_of(pl)});
+                    const bool update_here = any ? ((pass == 0) != (anchors[j][i] != 0)) : true;
+                    if (update_here && member_gp == gp)
+                        upd.push_back({j, WK_BACK_UPDATE, 0, tiles_of(pl), pl->back_run, tiles_of(pl)});
+                }
+                std::stable_sort(anc.begin(), anc.end(), longer_back);
+                std::stable_sort(upd.begin(), upd.end(), longer_back);
+                anc.insert(anc.end(), upd.begin(), upd.end());
+                emit(i, 1, anc, gp);
+            }
+            if (pass == 0) b->phases[(size_t)i].push_back({2, 0, 0, 0, 0, 0, -1});   // the anchor finishes
+        }
+    }
+    b->n_claims = claim;
+}
+
+// All launches of one batched epoch on stream s (phases from build_batch_phases).
 pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<std::vector<uint8_t>> &anchors,
                                cudaStream_t s) {
     const int n = (int)b->states.size();
@@ -1280,6 +1352,7 @@ pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<s
             PET_TRY(cuda_ok(cudaMemcpyAsync(st->alt, st->img, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
                             "cudaMemcpyAsync"));
         }
+    PET_TRY(launch_zero_ints(b->d_claims, b->n_claims, s));
     for (int i = 0; i < n_iter; ++i) {
         const bool in_is_img = ((i % 2) == 0) != odd;
         for (int j = 0; j < n; ++j) {
@@ -1288,29 +1361,31 @@ pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<s
                 PET_TRY(sem_init(st, in_is_img ? st->img : st->alt, s));
                 st->s_hat_ready = true;
             }
-            if (!anchors[j][i]) continue;
-            const pet_plan *pl = st->prob->plan;
-            const long long plane = plane_of(pl);
-            const float *in = in_is_img ? st->img : st->alt;
-            if (st->algo == PET_ALGO_SVREM) {
-                PET_TRY(anchor_pass(st, in, st->ratio_full, s));
-                PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, in, st->f_anc, st->s_anc,
-                                                   st->s_hat, !st->s_hat_ready, s));
-                st->s_hat_ready = true;
-            } else {
-                PET_TRY(anchor_pass(st, in, st->ratio_full, s));
-                PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
-            }
         }
-        for (const auto &g : b->fwd_groups)
-            PET_TRY(launch_batch_forward(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, i,
-                                         in_is_img ? 1 : 0, s));
-        for (const auto &g : b->back_groups) {
-            bool general = false;
-            for (int q = 0; q < g.count; ++q)
-                general |= b->states[b->h_idx[g.offset + q]]->prob->pen.potential != PET_POT_QUADRATIC;
-            PET_TRY(launch_batch_back(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, g.max_views, i,
-                                      in_is_img ? 1 : 0, general, s));
+        for (const pet_batch::Phase &ph : b->phases[(size_t)i]) {
+            if (ph.kind == 0) {
+                PET_TRY(launch_persistent_forward(b->d_members, b->d_segs + ph.seg_off, ph.n_segs, ph.n_items, i,
+                                                  in_is_img ? 1 : 0, b->d_claims + ph.claim, false, s));
+            } else if (ph.kind == 1) {
+                PET_TRY(launch_persistent_back(b->d_members, b->d_segs + ph.seg_off, ph.n_segs, ph.n_items, i,
+                                               in_is_img ? 1 : 0, b->d_claims + ph.claim, ph.genpot != 0, ph.threads,
+                                               s));
+            } else {
+                for (int j = 0; j < n; ++j) {
+                    if (!anchors[j][i]) continue;
+                    pet_state *st = b->states[j];
+                    const pet_plan *pl = st->prob->plan;
+                    const long long plane = plane_of(pl);
+                    const float *in = in_is_img ? st->img : st->alt;
+                    if (st->algo == PET_ALGO_SVREM) {
+                        PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, in, st->f_anc, st->s_anc,
+                                                           st->s_hat, !st->s_hat_ready, s));
+                        st->s_hat_ready = true;
+                    } else {
+                        PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
+                    }
+                }
+            }
         }
     }
     return PET_OK;
@@ -1379,6 +1454,34 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
                 key.push_back((int64_t)j * (1LL << 32) + i);
             }
     }
+    build_batch_phases(b, n_iter, anchors);
+    if ((int)b->h_segs.size() > b->seg_cap || b->n_claims > b->claim_cap) {
+        WorkSeg *grown = nullptr;
+        int *grown_c = nullptr;
+        const size_t segs = std::max((size_t)b->seg_cap, b->h_segs.size());
+        const size_t claims = (size_t)std::max(b->claim_cap, b->n_claims);
+        PET_TRY(dalloc(&grown, segs, "batch work segments"));
+        if (dalloc(&grown_c, claims, "batch claim counters") != PET_OK) {
+            dfree(grown);
+            return PET_ERR_OOM;
+        }
+        // the old buffers may still be read by enqueued work: release them after the stream drains
+        if (b->d_segs) {
+            PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+            dfree(b->d_segs);
+            dfree(b->d_claims);
+        }
+        b->d_segs = grown;
+        b->d_claims = grown_c;
+        b->seg_cap = (int)segs;
+        b->claim_cap = (int)claims;
+        // captured epochs hold the old pointers
+        for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+        b->graphs.clear();
+    }
+    PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_segs, b->h_segs.data(), sizeof(WorkSeg) * b->h_segs.size(),
+                                    cudaMemcpyHostToDevice, s),
+                    "batch work segment copy"));
     pet_status rc;
     if (direct) {
         rc = enqueue_batch_epoch(b, n_iter, anchors, s);
@@ -1413,8 +1516,9 @@ pet_status pet_batch_objective_async(pet_batch *b, double *d_phi, void *stream) 
     PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_members, b->members.data(), sizeof(BatchMember) * n, cudaMemcpyHostToDevice,
                                     s),
                     "batch member copy"));
-    for (const auto &g : b->obj_groups)
-        PET_TRY(launch_batch_objective(b->d_members, b->d_idx + g.offset, g.count, g.value, g.grid_x, 0, s));
+    PET_TRY(launch_zero_ints(b->d_obj_claim, 1, s));
+    PET_TRY(launch_persistent_forward(b->d_members, b->d_obj_segs, b->n_obj_segs, b->n_obj_items, 0, 1,
+                                      b->d_obj_claim, true, s));
     return launch_batch_objective_finish(b->d_members, n, pen_blocks, s);
 }
 

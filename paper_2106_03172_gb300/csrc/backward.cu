@@ -25,6 +25,8 @@
 //          (the anchor's penalty terms cancel against those inside q~) (§4)
 //   ANCHOR B_t = b for every subset t at once (grid.y = t)
 //   SAGA_INIT table_t = b - sens_t - (beta/N_s) grad R(f) for every t.
+#include <algorithm>
+
 #include "epilogue.cuh"
 
 namespace petvr {
@@ -34,6 +36,9 @@ namespace {
 constexpr int kTile = 16;           // single slice: a block owns a kTile x kTile tile (kTile^2 == kBlock)
 constexpr int kChunk = 16;          // views per shared-memory pass
 constexpr int kTileBlockMax = 1024; // threads of a tile block: kTile * kTile / run per view of a chunk
+constexpr int kPersistentBackMax = 512;  // threads of a persistent back block (a run-4 tile with more
+                                         // than 8 views per chunk loops over its runs twice)
+constexpr int kPersistentBackRegs = 48;  // four 288-thread blocks per SM
 static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
 
 // Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
@@ -102,14 +107,28 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
             float *pp = s_part + ql * kTile * kTile + lbase;
             const float2 *ucv = a.uc + v * a.nb;
             const float *rv = a.r + (vb + q0 + ql - r_view0) * a.nb;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float2 u = __ldg(ucv + j);
-                float fl, w0, w1;
-                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
-                const int c = (int)fl + (int)u.x - m0rel;
-                const float r = __ldg(rv + j);
-                if ((unsigned)c < (unsigned)mlen) pp[c * lstep] += w0 * r;
-                if (w1 > 0.0f && (unsigned)(c + 1) < (unsigned)mlen) pp[(c + 1) * lstep] += w1 * r;
+            // kCand candidates at a time: their offsets and ratios are loaded
+            // together (indices past jhi repeat jhi and are not added), then the
+            // pieces are added in candidate order, as one at a time would
+            constexpr int kCand = 4;
+            for (int j0 = jlo; j0 <= jhi; j0 += kCand) {
+                float2 u[kCand];
+                float r[kCand];
+#pragma unroll
+                for (int b = 0; b < kCand; ++b) {
+                    const int j = min(j0 + b, jhi);
+                    u[b] = __ldg(ucv + j);
+                    r[b] = __ldg(rv + j);
+                }
+#pragma unroll
+                for (int b = 0; b < kCand; ++b) {
+                    if (j0 + b > jhi) break;
+                    float fl, w0, w1;
+                    band_split(vp, band_point(vp, u[b].y, kc), band_point(vp, u[b].y, kc + 1.0f), fl, w0, w1);
+                    const int c = (int)fl + (int)u[b].x - m0rel;
+                    if ((unsigned)c < (unsigned)mlen) pp[c * lstep] += w0 * r[b];
+                    if (w1 > 0.0f && (unsigned)(c + 1) < (unsigned)mlen) pp[(c + 1) * lstep] += w1 * r[b];
+                }
             }
         }
         __syncthreads();
@@ -118,12 +137,14 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
         __syncthreads();
     }
     pdl_wait();   // returns at once after the wait above; covers an empty subset
-    if (threadIdx.x >= kTile * kTile) return;
-    const int ix = x0 + (threadIdx.x % kTile);
-    const int iy = y0 + (threadIdx.x / kTile);
-    if (ix >= a.nx || iy >= a.ny) return;
-    const int n = iy * a.nx + ix;
-    apply_epilogue<EPI, TQ, GENPOT>(a, t, n, n, ix, iy, 0, acc);
+    if (threadIdx.x < kTile * kTile) {
+        const int ix = x0 + (threadIdx.x % kTile);
+        const int iy = y0 + (threadIdx.x / kTile);
+        if (ix < a.nx && iy < a.ny) {
+            const int n = iy * a.nx + ix;
+            apply_epilogue<EPI, TQ, GENPOT>(a, t, n, n, ix, iy, 0, acc);
+        }
+    }
 }
 
 template <int EPI, typename TQ, int kRun, bool GENPOT>
@@ -132,61 +153,124 @@ __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs
     back_tile_body<EPI, TQ, kRun, GENPOT>(a, t, blockIdx.x);
 }
 
-// Batched back projection + update: blockIdx.y picks the member, whose
-// algorithm and table type select the epilogue; same body as the single
-// launch, so each member's update is bit-identical to an unbatched one.
+// Member update of one tile: the member's algorithm and table type select
+// the epilogue (the single-state launch's template arguments).
 template <int kRun, bool GENPOT>
-__global__ void __launch_bounds__(kTileBlockMax) batch_back_kernel(const BatchMember *ms, const int *idx, int iter,
-                                                                   int in_is_img) {
-    const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
-    const int tiles = ((m.nx + kTile - 1) / kTile) * ((m.ny + kTile - 1) / kTile);
-    if ((int)blockIdx.x >= tiles) return;
-    BackArgs b{};
-    b.views = m.views;
-    b.uc = m.uc;
-    b.order = m.order;
-    b.sub_off = m.sub_off;
-    b.t_dev = m.seq + iter;
-    b.nx = m.nx;
-    b.ny = m.ny;
-    b.nz = 1;
-    b.nb = m.nb;
-    b.ns = m.ns;
-    b.run = kRun;
-    b.r = m.ratio;
-    b.f = in_is_img ? m.img : m.alt;
-    b.f_out = in_is_img ? m.alt : m.img;
-    b.sens_t = m.sens_t;
-    b.sens = m.sens;
-    b.beta = m.beta;
-    b.pot = m.pot;
-    b.delta = m.delta;
-    b.alpha = m.alpha;
-    b.alpha_dev = m.alphas ? m.alphas + iter : nullptr;
-    b.s_hat = m.s_hat;
-    b.f_anc = m.f_anc;
-    b.s_anc = m.s_anc;
-    b.B = m.B;
-    b.d = m.d;
-    b.table = m.table;
-    b.qbar = m.qbar;
-    b.qtil = m.qtil;
-    const int t = __ldg(m.seq + iter);
-    switch (m.algo) {
-        case PET_ALGO_OSEM: back_tile_body<EPI_OSEM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
-        case PET_ALGO_SVREM: back_tile_body<EPI_SVREM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
+__device__ __forceinline__ void member_update_tile(int algo, int table_dtype, const BackArgs &b, int t, int tile) {
+    switch (algo) {
+        case PET_ALGO_OSEM: back_tile_body<EPI_OSEM, float, kRun, GENPOT>(b, t, tile); break;
+        case PET_ALGO_SVREM: back_tile_body<EPI_SVREM, float, kRun, GENPOT>(b, t, tile); break;
         case PET_ALGO_SAGA:
-            if (m.table_dtype == PET_TABLE_BF16)
-                back_tile_body<EPI_SAGA, __nv_bfloat16, kRun, GENPOT>(b, t, blockIdx.x);
+            if (table_dtype == PET_TABLE_BF16)
+                back_tile_body<EPI_SAGA, __nv_bfloat16, kRun, GENPOT>(b, t, tile);
             else
-                back_tile_body<EPI_SAGA, float, kRun, GENPOT>(b, t, blockIdx.x);
+                back_tile_body<EPI_SAGA, float, kRun, GENPOT>(b, t, tile);
             break;
-        case PET_ALGO_SGA: back_tile_body<EPI_SGA, float, kRun, GENPOT>(b, t, blockIdx.x); break;
-        case PET_ALGO_SEM: back_tile_body<EPI_SEM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
-        case PET_ALGO_SAGAEM: back_tile_body<EPI_SAGAEM, float, kRun, GENPOT>(b, t, blockIdx.x); break;
-        default: back_tile_body<EPI_SVRG, float, kRun, GENPOT>(b, t, blockIdx.x); break;
+        case PET_ALGO_SGA: back_tile_body<EPI_SGA, float, kRun, GENPOT>(b, t, tile); break;
+        case PET_ALGO_SEM: back_tile_body<EPI_SEM, float, kRun, GENPOT>(b, t, tile); break;
+        case PET_ALGO_SAGAEM: back_tile_body<EPI_SAGAEM, float, kRun, GENPOT>(b, t, tile); break;
+        default: back_tile_body<EPI_SVRG, float, kRun, GENPOT>(b, t, tile); break;
     }
 }
+
+// Persistent batched back projection + update: a resident grid whose blocks
+// claim work items until the list is exhausted.  An item is one tile of a
+// member's update (WK_BACK_UPDATE) or one (subset, tile) of a member's anchor
+// back projection (WK_BACK_ANCHOR), run by the same body with the same run
+// length as the member's own launches, so results are bit-identical to them.
+// Thread 0 claims the item and writes its arguments to shared memory; the
+// segment table is staged in shared memory once per block.
+// GENPOT: the members of this launch use an edge-preserving potential.
+template <bool GENPOT>
+__global__ void __maxnreg__(kPersistentBackRegs)
+    persistent_back_kernel(const BatchMember *ms, const WorkSeg *segs, int n_segs, int n_items, int iter,
+                           int in_is_img, int *claim) {
+    __shared__ WorkSeg s_segs[kSegSmem];
+    __shared__ BackArgs s_b;
+    __shared__ int s_item, s_t, s_tile, s_kind, s_shape, s_algo, s_tq;
+    for (int i = threadIdx.x; i < n_segs && i < kSegSmem; i += blockDim.x) s_segs[i] = segs[i];
+    const WorkSeg *tab = n_segs <= kSegSmem ? s_segs : segs;
+    // the segment table and member descriptors were copied in before the
+    // kernel ahead of this one; the claim counter was zeroed by a kernel, so
+    // wait for the kernel ahead before the first claim
+    pdl_wait();
+    pdl_trigger();
+    // the first item of each block is its own index; later ones are claimed
+    // (the counter counts claims beyond the grid's first items)
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int g = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(claim, 1);
+            s_item = g;
+            if (g < n_items) {
+                const WorkSeg sg = tab[find_segment(tab, n_segs, g)];
+                const BatchMember &m = ms[sg.member];
+                BackArgs b{};
+                b.views = m.views;
+                b.uc = m.uc;
+                b.order = m.order;
+                b.sub_off = m.sub_off;
+                b.nx = m.nx;
+                b.ny = m.ny;
+                b.nz = 1;
+                b.nb = m.nb;
+                b.ns = m.ns;
+                b.run = sg.shape;
+                const int local = g - sg.first;
+                if (sg.kind == WK_BACK_ANCHOR) {
+                    const int t = local / sg.tiles;
+                    b.r = m.ratio_full;
+                    b.r_view0 = 0;
+                    b.out = const_cast<float *>(m.B);
+                    s_t = t;
+                    s_tile = local - t * sg.tiles;
+                } else {
+                    b.t_dev = m.seq + iter;
+                    b.r = m.ratio;
+                    b.f = in_is_img ? m.img : m.alt;
+                    b.f_out = in_is_img ? m.alt : m.img;
+                    b.sens_t = m.sens_t;
+                    b.sens = m.sens;
+                    b.beta = m.beta;
+                    b.pot = m.pot;
+                    b.delta = m.delta;
+                    b.alpha = m.alpha;
+                    b.alpha_dev = m.alphas ? m.alphas + iter : nullptr;
+                    b.s_hat = m.s_hat;
+                    b.f_anc = m.f_anc;
+                    b.s_anc = m.s_anc;
+                    b.B = m.B;
+                    b.d = m.d;
+                    b.table = m.table;
+                    b.qbar = m.qbar;
+                    b.qtil = m.qtil;
+                    s_t = __ldg(m.seq + iter);
+                    s_tile = local;
+                }
+                s_b = b;
+                s_kind = sg.kind;
+                s_shape = sg.shape;
+                s_algo = m.algo;
+                s_tq = m.table_dtype;
+            }
+        }
+        __syncthreads();
+        if (s_item >= n_items) break;
+        const int t = s_t, tile = s_tile;
+        if (s_kind == WK_BACK_ANCHOR) {
+            if (s_shape == 4)
+                back_tile_body<EPI_ANCHOR, float, 4, false>(s_b, t, tile);
+            else
+                back_tile_body<EPI_ANCHOR, float, 8, false>(s_b, t, tile);
+        } else if (s_shape == 4) {
+            member_update_tile<4, GENPOT>(s_algo, s_tq, s_b, t, tile);
+        } else {
+            member_update_tile<8, GENPOT>(s_algo, s_tq, s_b, t, tile);
+        }
+    }
+}
+
+size_t back_smem_bytes() { return (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int)); }
 
 // Single-slice back-projection launch of one epilogue / table type / potential.
 struct TileBack {
@@ -212,18 +296,31 @@ struct TileBack {
 
 }  // namespace
 
-pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
-                             int max_views, int iter, int in_is_img, bool general_potential, cudaStream_t s) {
-    if (n_members == 0 || tiles == 0) return PET_OK;
-    const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
-    const int per_view = kTile * (kTile / run);
-    const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
-    const dim3 grid((unsigned)tiles, (unsigned)n_members);
-    void (*k)(const BatchMember *, const int *, int, int) =
-        general_potential ? (run == 4 ? batch_back_kernel<4, true> : batch_back_kernel<8, true>)
-                          : (run == 4 ? batch_back_kernel<4, false> : batch_back_kernel<8, false>);
-    launch_dependent(k, grid, dim3((unsigned)threads), smem, s, d_members, d_idx, iter, in_is_img);
-    return check_launch("batch_back_kernel");
+int back_block_threads(int run, int max_views) {
+    const int per_view = kTile * (kTile / (run == 4 ? 4 : 8));
+    return std::min(kPersistentBackMax, std::max(kTile * kTile, per_view * std::min(max_views, kChunk)));
+}
+
+pet_status launch_persistent_back(const BatchMember *d_members, const WorkSeg *d_segs, int n_segs, int n_items,
+                                  int iter, int in_is_img, int *claim, bool general_potential, int threads,
+                                  cudaStream_t s) {
+    if (n_items <= 0) return PET_OK;
+    void (*k)(const BatchMember *, const WorkSeg *, int, int, int, int, int *) =
+        general_potential ? persistent_back_kernel<true> : persistent_back_kernel<false>;
+    const size_t smem = back_smem_bytes();
+    if (threads < kTile * kTile || threads > kPersistentBackMax)
+        return set_error(PET_ERR_INVALID, "back: block size");
+    static int resident[2][kPersistentBackMax + 1] = {};   // blocks per SM by potential class and block size
+    int &per_sm = resident[general_potential ? 1 : 0][threads];
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k, threads, smem) != cudaSuccess ||
+         per_sm < 1))
+        per_sm = 1;
+    const int grid = std::min(n_items, per_sm * sm_count());
+    ProfileScope prof(1, s);
+    launch_dependent(k, dim3((unsigned)grid), dim3((unsigned)threads), smem, s, d_members, d_segs, n_segs, n_items,
+                     iter, in_is_img, claim);
+    return check_launch("persistent_back_kernel");
 }
 
 pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subsets_grid,

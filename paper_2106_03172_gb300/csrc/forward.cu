@@ -17,6 +17,8 @@
 // a.t_dev is set, read on the device from the subset offsets, so that one
 // captured launch serves any subset; the grid then covers the largest subset
 // and surplus threads only take part in the reduction.
+#include <algorithm>
+
 #include "petvr_internal.cuh"
 
 namespace petvr {
@@ -106,8 +108,6 @@ __device__ __forceinline__ void forward_tile_body(const FwdArgs &a, const int bx
                 // With one pixel of margin on each side both pieces of every
                 // band are inside the image, and the offsets need no checks
                 // (they equal the checked ones).
-                // (The batched kernels leave it out: they keep 40 registers,
-                // and both branches give the same sums.)
                 bool interior = false;
                 if (INTERIOR) {
                     const float vend = band_point(vp, u.y, kc + (float)kBatch);
@@ -220,30 +220,88 @@ __global__ void __launch_bounds__(kBlock, fwd_min_blocks<CHUNKS, LL>()) forward_
     forward_tile_body<CHUNKS, MODE, LL>(a, blockIdx.x);
 }
 
-// Batched forward: blockIdx.y picks the member (through idx), whose subset
-// index for update `iter` is read on the device; same body as the single
-// launch, so each member's ratios are bit-identical to an unbatched update.
-template <int CHUNKS>
-__global__ void __launch_bounds__(kBlock) batch_forward_kernel(const BatchMember *ms, const int *idx, int iter,
-                                                               int in_is_img) {
-    const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
-    FwdArgs a{};
-    a.views = m.views;
-    a.uc = m.uc;
-    a.order = m.order;
-    a.sub_off = m.sub_off;
-    a.t_dev = m.seq + iter;
-    a.nx = m.nx;
-    a.ny = m.ny;
-    a.nz = 1;
-    a.nb = m.nb;
-    a.img = in_is_img ? m.img : m.alt;
-    a.g = m.g;
-    a.w = m.w;
-    a.w_scalar = m.w_scalar;
-    a.out = m.ratio;
-    a.status = m.status;
-    forward_tile_body<CHUNKS, FWD_RATIO, false, false>(a, blockIdx.x);
+// Persistent batched forward: a resident grid whose blocks claim work items
+// (WorkSeg lists) until the list is exhausted.  An item is one block of the
+// single-state forward launch of that member and kind, run by the same body
+// with the same band-chunk count, so every ratio (and every log-likelihood
+// block partial) is bit-identical to the member's own launches.  Thread 0
+// claims the item and writes its arguments to shared memory (the body reads
+// them there, as the single launch reads its kernel parameters); the segment
+// table is staged in shared memory once per block.  The body's shared arrays
+// are free again once the next claim's barrier has passed.
+template <int MODE, bool LL>
+__global__ void __launch_bounds__(kBlock, 6)
+    persistent_forward_kernel(const BatchMember *ms, const WorkSeg *segs, int n_segs, int n_items, int iter,
+                              int in_is_img, int *claim) {
+    __shared__ WorkSeg s_segs[kSegSmem];
+    __shared__ FwdArgs s_a;
+    __shared__ int s_item, s_bx, s_shape;
+    for (int i = threadIdx.x; i < n_segs && i < kSegSmem; i += blockDim.x) s_segs[i] = segs[i];
+    const WorkSeg *tab = n_segs <= kSegSmem ? s_segs : segs;
+    // the segment table and member descriptors were copied in before the
+    // kernel ahead of this one; the claim counter was zeroed by a kernel, so
+    // wait for the kernel ahead before the first claim
+    pdl_wait();
+    pdl_trigger();
+    // the first item of each block is its own index; later ones are claimed
+    // (the counter counts claims beyond the grid's first items)
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int g = round == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(claim, 1);
+            s_item = g;
+            if (g < n_items) {
+                const WorkSeg sg = tab[find_segment(tab, n_segs, g)];
+                const BatchMember &m = ms[sg.member];
+                FwdArgs a{};
+                a.views = m.views;
+                a.uc = m.uc;
+                a.order = m.order;
+                a.nx = m.nx;
+                a.ny = m.ny;
+                a.nz = 1;
+                a.nb = m.nb;
+                a.g = m.g;
+                a.w = m.w;
+                a.w_scalar = m.w_scalar;
+                a.status = m.status;
+                if (sg.kind == WK_FWD_UPDATE) {
+                    a.sub_off = m.sub_off;
+                    a.t_dev = m.seq + iter;
+                    a.img = in_is_img ? m.img : m.alt;
+                    a.out = m.ratio;
+                } else if (sg.kind == WK_FWD_ANCHOR) {
+                    a.v_begin = 0;
+                    a.v_end = m.na;
+                    a.img = in_is_img ? m.img : m.alt;
+                    a.out = m.ratio_full;
+                } else {
+                    a.v_begin = 0;
+                    a.v_end = m.na;
+                    a.img = m.img;
+                    a.ll_partials = m.part;
+                }
+                s_a = a;
+                s_bx = g - sg.first;
+                s_shape = sg.shape;
+            }
+        }
+        __syncthreads();
+        if (s_item >= n_items) break;
+        const int bx = s_bx;
+        if (s_shape == 8)
+            forward_tile_body<8, MODE, LL>(s_a, bx);
+        else if (s_shape == 16)
+            forward_tile_body<16, MODE, LL>(s_a, bx);
+        else
+            forward_tile_body<32, MODE, LL>(s_a, bx);
+    }
+}
+
+int resident_blocks(const void *kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
 }
 
 // Nonzeros of the rays of a view range: band pieces of positive length that
@@ -307,58 +365,39 @@ pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaS
     return check_launch("count_nnz_kernel");
 }
 
-pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
-                                int blocks, int iter, int in_is_img, cudaStream_t s) {
-    if (n_members == 0 || blocks == 0) return PET_OK;
-    const dim3 grid((unsigned)blocks, (unsigned)n_members);
-    void (*k)(const BatchMember *, const int *, int, int) = nullptr;
-    switch (chunks) {
-        case 8: k = batch_forward_kernel<8>; break;
-        case 16: k = batch_forward_kernel<16>; break;
-        case 32: k = batch_forward_kernel<32>; break;
-        default: return set_error(PET_ERR_INVALID, "batch forward: unsupported chunk count");
-    }
-    launch_dependent(k, grid, dim3(kBlock), 0, s, d_members, d_idx, iter, in_is_img);
-    return check_launch("batch_forward_kernel");
+int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        return v;
+    }();
+    return n;
 }
 
-// Batched full-data objective pass: log-likelihood partials of every member's
-// current image over all its rays (blockIdx.y = member), into member.part.
-template <int CHUNKS>
-__global__ void __launch_bounds__(kBlock) batch_objective_kernel(const BatchMember *ms, const int *idx) {
-    const BatchMember &m = ms[__ldg(idx + blockIdx.y)];
-    if ((int)blockIdx.x >= m.n_ll) return;
-    FwdArgs a{};
-    a.views = m.views;
-    a.uc = m.uc;
-    a.order = m.order;
-    a.v_begin = 0;
-    a.v_end = m.na;
-    a.nx = m.nx;
-    a.ny = m.ny;
-    a.nz = 1;
-    a.nb = m.nb;
-    a.img = m.img;
-    a.g = m.g;
-    a.w = m.w;
-    a.w_scalar = m.w_scalar;
-    a.ll_partials = m.part;
-    a.status = m.status;
-    forward_tile_body<CHUNKS, FWD_NONE, true, false>(a, blockIdx.x);
+pet_status launch_persistent_forward(const BatchMember *d_members, const WorkSeg *d_segs, int n_segs, int n_items,
+                                     int iter, int in_is_img, int *claim, bool objective, cudaStream_t s) {
+    if (n_items <= 0) return PET_OK;
+    void (*k)(const BatchMember *, const WorkSeg *, int, int, int, int, int *) =
+        objective ? persistent_forward_kernel<FWD_NONE, true> : persistent_forward_kernel<FWD_RATIO, false>;
+    static const int resident[2] = {
+        resident_blocks((const void *)persistent_forward_kernel<FWD_RATIO, false>, kBlock, 0),
+        resident_blocks((const void *)persistent_forward_kernel<FWD_NONE, true>, kBlock, 0)};
+    const int grid = std::min(n_items, resident[objective ? 1 : 0] * sm_count());
+    ProfileScope prof(objective ? 3 : 0, s);
+    launch_dependent(k, dim3((unsigned)grid), dim3(kBlock), 0, s, d_members, d_segs, n_segs, n_items, iter,
+                     in_is_img, claim);
+    return check_launch("persistent_forward_kernel");
 }
 
-pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
-                                  int fwd_blocks, int pen_blocks, cudaStream_t s) {
-    (void)pen_blocks;
-    if (n_members == 0 || fwd_blocks == 0) return PET_OK;
-    const dim3 grid((unsigned)fwd_blocks, (unsigned)n_members);
-    switch (chunks) {
-        case 8: batch_objective_kernel<8><<<grid, kBlock, 0, s>>>(d_members, d_idx); break;
-        case 16: batch_objective_kernel<16><<<grid, kBlock, 0, s>>>(d_members, d_idx); break;
-        case 32: batch_objective_kernel<32><<<grid, kBlock, 0, s>>>(d_members, d_idx); break;
-        default: return set_error(PET_ERR_INVALID, "batch objective: unsupported chunk count");
-    }
-    return check_launch("batch_objective_kernel");
+__global__ void zero_ints_kernel(int *p, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
+}
+
+pet_status launch_zero_ints(int *p, int n, cudaStream_t s) {
+    if (n <= 0) return PET_OK;
+    zero_ints_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, n);
+    return check_launch("zero_ints_kernel");
 }
 
 // Below this many blocks a multi-ring forward launch is too small to fill a

@@ -350,6 +350,7 @@ struct BatchMember {
     int *status;
     int algo, table_dtype;
     float *img, *alt, *ratio;
+    float *ratio_full;     // anchor-pass ratio over all views (SVREM, SVRG), subset-major
     float *s_hat;
     const float *f_anc, *s_anc, *B, *d;
     void *table;
@@ -363,6 +364,49 @@ struct BatchMember {
     double *part;          // objective partials of this member
     double *phi;           // objective output {Phi, L, R}
 };
+
+// ---------------------------------------------------------------------------
+// Persistent batched kernels: one resident grid per phase of a batched update
+// (the subset forward projections, the anchor passes, the back projections +
+// updates) pulls work items from a list.  The list is a sequence of segments,
+// each a run of items of one member and one kind; an item is one block's
+// worth of the single-state kernels (a block of rays of a forward pass, a
+// 16 x 16 tile of a back projection), so every member gets bit-identical
+// results to its own epoch calls.  Blocks claim items in list order with an
+// atomic counter (zeroed before each phase's launch); nothing waits on
+// another block, so the only ordering is the kernel boundary between phases.
+// ---------------------------------------------------------------------------
+enum WorkKind {
+    WK_FWD_UPDATE = 0,     // rays of the member's current subset -> ratio (subset index on the device)
+    WK_FWD_ANCHOR = 1,     // rays of every view -> ratio_full (anchor pass)
+    WK_FWD_OBJECTIVE = 2,  // rays of every view -> log-likelihood block partials
+    WK_BACK_UPDATE = 3,    // tile of the member's update (its method's epilogue)
+    WK_BACK_ANCHOR = 4,    // (subset, tile) of the anchor back projection -> B
+};
+
+struct WorkSeg {
+    int member;   // index into the batch's member descriptors
+    int kind;     // WorkKind
+    int first;    // list index of the segment's first item
+    int count;    // items in the segment
+    int shape;    // forward: band chunks per ray; back: pixels per run
+    int tiles;    // back: tiles per subset (anchor item = t * tiles + tile)
+};
+
+// Segments a persistent block stages in shared memory (longer tables are
+// searched in global memory).
+constexpr int kSegSmem = 160;
+
+// Segment holding list item g (segments are sorted by `first`).
+__device__ __forceinline__ int find_segment(const WorkSeg *segs, int n_segs, int g) {
+    int lo = 0, hi = n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 
 // ---------------------------------------------------------------------------
 // Host objects.
@@ -444,15 +488,24 @@ struct pet_batch {
     std::vector<pet_state *> states;
     std::vector<petvr::BatchMember> members;   // host copy; uploaded before every call
     petvr::BatchMember *d_members = nullptr;
-    int *d_idx = nullptr;           // member indices: forward, back, then objective groups
-    std::vector<int> h_idx;
-    struct Group {
-        int value;                  // forward / objective: band chunks; back: run length
-        int offset, count;          // slice of d_idx
-        int grid_x;                 // forward blocks / back tiles to cover every member
-        int max_views;
+    // persistent phases of the current call: per update, the launches in order
+    struct Phase {
+        int kind;                   // 0 forward, 1 back + update (GENPOT 0/1 in `genpot`), 2 anchor finishes
+        int seg_off, n_segs, n_items;
+        int threads;                // back: block size
+        int genpot;                 // back: general-potential epilogues
+        int claim;                  // claim counter slot
     };
-    std::vector<Group> fwd_groups, back_groups, obj_groups;
+    std::vector<std::vector<Phase>> phases;   // [n_iter]
+    std::vector<petvr::WorkSeg> h_segs;
+    petvr::WorkSeg *d_segs = nullptr;
+    int seg_cap = 0;
+    int *d_claims = nullptr;        // claim counters of the current call's phases
+    int claim_cap = 0;
+    int n_claims = 0;
+    petvr::WorkSeg *d_obj_segs = nullptr;   // objective pass: every member's rays (fixed at creation)
+    int n_obj_segs = 0, n_obj_items = 0;
+    int *d_obj_claim = nullptr;
     bool graphs_on = true;
     int *d_seqs = nullptr;          // [n][seq_cap] subset indices of the current call
     float *d_alphas = nullptr;      // [n][seq_cap] step sizes of the current call
@@ -500,14 +553,18 @@ pet_status launch_objective_finish(const pet_problem *p, const float *img, int n
 pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const float *img, int n_ll_blocks,
                                        double *part, double *d_out, cudaStream_t s);
 pet_status launch_count_nnz(const FwdArgs &a, unsigned long long *d_count, cudaStream_t s);
-pet_status launch_batch_forward(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
-                                int blocks, int iter, int in_is_img, cudaStream_t s);
-pet_status launch_batch_objective(const BatchMember *d_members, const int *d_idx, int n_members, int chunks,
-                                  int fwd_blocks, int pen_blocks, cudaStream_t s);
+// Persistent phases (forward.cu / backward.cu): objective = false runs the
+// ratio kinds (WK_FWD_UPDATE, WK_FWD_ANCHOR), true the log-likelihood kind.
+pet_status launch_persistent_forward(const BatchMember *d_members, const WorkSeg *d_segs, int n_segs, int n_items,
+                                     int iter, int in_is_img, int *claim, bool objective, cudaStream_t s);
+pet_status launch_persistent_back(const BatchMember *d_members, const WorkSeg *d_segs, int n_segs, int n_items,
+                                  int iter, int in_is_img, int *claim, bool general_potential, int threads,
+                                  cudaStream_t s);
+pet_status launch_zero_ints(int *p, int n, cudaStream_t s);
+int back_block_threads(int run, int max_views);   // block size a back projection of this shape needs
+int sm_count();
 pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_members, int pen_blocks,
                                          cudaStream_t s);
-pet_status launch_batch_back(const BatchMember *d_members, const int *d_idx, int n_members, int run, int tiles,
-                             int max_views, int iter, int in_is_img, bool general_potential, cudaStream_t s);
 pet_status launch_svrem_anchor_finish(const float *B, int ns, long long plane, int nz, const float *f,
                                       float *f_anc, float *s_anc, float *s_hat, bool init, cudaStream_t s);
 pet_status launch_svrg_anchor_finish(const float *B, int ns, long long plane, int nz,

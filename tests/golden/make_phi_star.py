@@ -4,6 +4,10 @@ the generated counts so a consumer can tell whether its inputs are the ones
 these values belong to.  Calls only the oracle and the input generator.
 
     python tests/golden/make_phi_star.py [workload ...]
+
+The members of the 64-reconstruction batch (batched_workloads(0, 64), member j
+with data seed 100 + j) are named batch64_<j>; ``batch64_<a>-<b>`` solves
+members a..b-1.
 """
 import hashlib
 import json
@@ -15,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle.em import build_problem, map_reference  # noqa: E402
-from paper_2106_03172_gb300.phantoms import WORKLOADS, make_data, serving_pool  # noqa: E402
+from paper_2106_03172_gb300.phantoms import WORKLOADS, batched_workloads, make_data, serving_pool  # noqa: E402
 
 OUT = os.path.join(HERE, "phi_star.json")
 
@@ -38,14 +42,36 @@ def _store(name, entry):
     os.replace(tmp, OUT)
 
 
-def main(names):
+BATCH64 = batched_workloads(0, 64)
+
+
+def _expand(names):
+    out = []
     for name in names:
-        work = WORKLOADS.get(name) or SERVING_POOL[name]
-        data = make_data(work, 0)
+        if name.startswith("batch64_") and "-" in name:
+            a, b = name[len("batch64_"):].split("-")
+            out += [f"batch64_{j}" for j in range(int(a), int(b))]
+        else:
+            out.append(name)
+    return out
+
+
+def _workload(name):
+    """(workload, data seed) of a name."""
+    if name.startswith("batch64_"):
+        j = int(name[len("batch64_"):])
+        return BATCH64[j], 100 + j
+    return WORKLOADS.get(name) or SERVING_POOL[name], 0
+
+
+def main(names):
+    for name in _expand(names):
+        work, seed = _workload(name)
+        data = make_data(work, seed)
         prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta, work.potential, work.delta)
         t = time.time()
         _, phi, kkt = map_reference(prob)
-        entry = {"seed": 0, "phi_star": phi, "kkt_residual": kkt,
+        entry = {"seed": seed, "phi_star": phi, "kkt_residual": kkt,
                  "counts_sha256": counts_sha256(data["g"]),
                  "solver": "scipy L-BFGS-B on the FP64 oracle objective",
                  "seconds": round(time.time() - t, 1)}

@@ -78,3 +78,48 @@ def test_batch_rejects_bad_input():
     plan3, gp3, f3, _ = _setup(pv, "ring2")
     with pytest.raises(pv.PetError):
         pv.Batch([pv.State(gp3, "saga", f3.clone())])
+
+
+def test_batch_mixed_potentials_and_many_members():
+    """A batch whose members use both the quadratic and an edge-preserving
+    potential (two back-projection launches per phase), with 170 members so
+    that the work lists outgrow the segment table a block stages in shared
+    memory: every member still matches its own epochs bit for bit."""
+    pv = _pv()
+    from paper_2106_03172_gb300.phantoms import Geometry, Workload, make_data
+    geoms = [Geometry(16, 16, 8, 23), Geometry(20, 12, 9, 25, bin_mm=1.5), Geometry(24, 24, 10, 35)]
+    algos = ["osem", "saga", "svrg", "svrem", "sga"]
+    members = []
+    for j in range(170):
+        geom = geoms[j % 3]
+        pot = "logcosh" if j % 4 == 1 else "quadratic"
+        work = Workload(f"m{j}", geom, n_subsets=2 + j % 3, counts=2e4, bg_frac=0.1, beta=0.3 if pot != "quadratic"
+                        else 0.02, n_ellipses=3)
+        data = make_data(work, 300 + j)
+        plan = pv.Plan(geom, work.n_subsets)
+        gp = pv.Problem(plan, torch.from_numpy(data["g"].ravel()).cuda(), None, data["w"], work.beta,
+                        potential=pot, delta=0.1)
+        f0 = torch.empty(geom.n_pixels, device="cuda")
+        pv.pet_warm_start(gp.handle, f0)
+        a, b = f0.clone(), f0.clone()
+        algo = algos[j % len(algos)]
+        members.append((work, plan, gp, a, b, pv.State(gp, algo, a), pv.State(gp, algo, b), algo))
+    batch = pv.Batch([m[6] for m in members])
+    rng = np.random.default_rng(9)
+    alphas = [0.7 if m[7] == "svrem" else 1.0 for m in members]
+    etas = [1 for _ in members]
+    for n_iter in (5, 6):
+        seqs = [rng.integers(0, m[0].n_subsets, n_iter) for m in members]
+        batch.epoch(seqs, alphas, etas)
+        for m, q, al, et in zip(members, seqs, alphas, etas):
+            m[5].epoch(q, alpha=al, eta=et)
+        torch.cuda.synchronize()
+        for m in members:
+            assert torch.equal(m[3], m[4]), (n_iter, m[0].name, m[7])
+    phi_b = torch.empty(len(members), 3, dtype=torch.float64, device="cuda")
+    phi_s = torch.empty(len(members), 3, dtype=torch.float64, device="cuda")
+    batch.objective_async(phi_b)
+    for j, m in enumerate(members):
+        m[5].objective_async(phi_s[j])
+    torch.cuda.synchronize()
+    assert torch.equal(phi_b, phi_s)
