@@ -107,28 +107,14 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
             float *pp = s_part + ql * kTile * kTile + lbase;
             const float2 *ucv = a.uc + v * a.nb;
             const float *rv = a.r + (vb + q0 + ql - r_view0) * a.nb;
-            // kCand candidates at a time: their offsets and ratios are loaded
-            // together (indices past jhi repeat jhi and are not added), then the
-            // pieces are added in candidate order, as one at a time would
-            constexpr int kCand = 4;
-            for (int j0 = jlo; j0 <= jhi; j0 += kCand) {
-                float2 u[kCand];
-                float r[kCand];
-#pragma unroll
-                for (int b = 0; b < kCand; ++b) {
-                    const int j = min(j0 + b, jhi);
-                    u[b] = __ldg(ucv + j);
-                    r[b] = __ldg(rv + j);
-                }
-#pragma unroll
-                for (int b = 0; b < kCand; ++b) {
-                    if (j0 + b > jhi) break;
-                    float fl, w0, w1;
-                    band_split(vp, band_point(vp, u[b].y, kc), band_point(vp, u[b].y, kc + 1.0f), fl, w0, w1);
-                    const int c = (int)fl + (int)u[b].x - m0rel;
-                    if ((unsigned)c < (unsigned)mlen) pp[c * lstep] += w0 * r[b];
-                    if (w1 > 0.0f && (unsigned)(c + 1) < (unsigned)mlen) pp[(c + 1) * lstep] += w1 * r[b];
-                }
+            for (int j = jlo; j <= jhi; ++j) {
+                const float2 u = __ldg(ucv + j);
+                float fl, w0, w1;
+                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
+                const int c = (int)fl + (int)u.x - m0rel;
+                const float r = __ldg(rv + j);
+                if ((unsigned)c < (unsigned)mlen) pp[c * lstep] += w0 * r;
+                if (w1 > 0.0f && (unsigned)(c + 1) < (unsigned)mlen) pp[(c + 1) * lstep] += w1 * r;
             }
         }
         __syncthreads();
