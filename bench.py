@@ -534,8 +534,9 @@ def run_ours(args):
     fk, bk = (("ring_forward_kernel", "ring_back_column_kernel" if geom.nz <= 8 else "ring_back_kernel")
               if geom.multiring else
               ("forward_stack_kernel", "back_stack_kernel") if geom.nz > 1 else ("forward_tile_kernel", "back_tile_kernel"))
+    bk_all = bk if (geom.multiring or geom.nz > 1) else "back_tile_wide_kernel"
     kinds_named = {0: f"{fk} (subset update, ratio)", 1: f"{bk} (update epilogue)",
-                   2: f"{bk} (anchor, all subsets)", 3: f"{fk} (all rays: anchor/objective)"}
+                   2: f"{bk_all} (anchor, all subsets)", 3: f"{fk} (all rays: anchor/objective)"}
     alg_flops = {k: 0.0 for k in kinds_named}
     alg_bytes = {k: 0.0 for k in kinds_named}
     N, M = geom.n_pixels * geom.nz, geom.n_rays * geom.n_pairs * slices   # image and sinogram floats

@@ -647,12 +647,18 @@ pet_status pet_plan_autotune(pet_plan *pl, int32_t *h_fwd_chunks, int32_t *h_bac
         }
         pl->fwd_chunks = best_c;
         best_ms = 1e30f;
-        for (int r : {4, 8}) {
+        // 4-pixel runs need blocks twice as wide as 8-pixel runs, so fewer fit
+        // beside other streams' kernels and the all-subset launches (anchors,
+        // table fills) slow down: measured on the 256^2 four-stream step, run 4
+        // took its subset back projections from 9.6 to 10.4 us and its anchor
+        // from 47 to 93 us, and the step from 28.2 to 40.6 ms.  Timed alone the
+        // two are close, so run 4 is taken only when it is clearly faster.
+        for (int r : {8, 4}) {
             if (st != PET_OK) break;
             pl->back_run = r;
             float ms = 0.0f;
             if ((st = time_pass(false, &ms)) != PET_OK) break;
-            if (ms < best_ms) best_ms = ms, best_r = r;
+            if (ms < best_ms * (r == 4 ? 0.85f : 1.0f)) best_ms = ms, best_r = r;
         }
         pl->back_run = best_r;
         cleanup();

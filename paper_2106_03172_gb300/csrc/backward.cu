@@ -39,6 +39,15 @@ constexpr int kTileBlockMax = 1024; // threads of a tile block: kTile * kTile / 
 constexpr int kPersistentBackMax = 512;  // threads of a persistent back block (a run-4 tile with more
                                          // than 8 views per chunk loops over its runs twice)
 constexpr int kPersistentBackRegs = 48;  // four 288-thread blocks per SM
+// The all-subset launches (anchor passes, table fills), the full-data
+// statistic and plain back projections run in back_tile_wide_kernel, capped at
+// 48 registers: four 288-thread blocks per SM where the compiler's own choice
+// (57) leaves three.  The subset updates keep theirs (42).
+constexpr bool wide_epilogue(int epi) {
+    return epi == EPI_ANCHOR || epi == EPI_SAGA_INIT || epi == EPI_SAGAEM_INIT || epi == EPI_SEM_INIT ||
+           epi == EPI_PLAIN;
+}
+constexpr int kWideRegs = 48;
 static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
 
 // Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
@@ -135,6 +144,12 @@ __device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, c
 
 template <int EPI, typename TQ, int kRun, bool GENPOT>
 __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {
+    const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
+    back_tile_body<EPI, TQ, kRun, GENPOT>(a, t, blockIdx.x);
+}
+
+template <int EPI, typename TQ, int kRun, bool GENPOT>
+__global__ void __maxnreg__(kWideRegs) back_tile_wide_kernel(const BackArgs a) {
     const int t = a.t_dev ? __ldg(a.t_dev) : a.t0 + (int)blockIdx.y;
     back_tile_body<EPI, TQ, kRun, GENPOT>(a, t, blockIdx.x);
 }
@@ -269,12 +284,17 @@ struct TileBack {
     pet_status run() const {
         const int tiles = ((a.nx + kTile - 1) / kTile) * ((a.ny + kTile - 1) / kTile);
         const dim3 grid((unsigned)tiles, (unsigned)ny_grid);
-        const size_t smem = (size_t)kChunk * (kTile * kTile * sizeof(float) + sizeof(ViewParams) + sizeof(int));
+        const size_t smem = back_smem_bytes();
         // one thread per run: kTile * kTile / run runs per view of the largest chunk
         const int run = a.run == 4 ? 4 : 8;
         const int per_view = kTile * (kTile / run);
         const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
-        launch_dependent(run == 4 ? back_tile_kernel<EPI, TQ, 4, GENPOT> : back_tile_kernel<EPI, TQ, 8, GENPOT>,
+        void (*k)(BackArgs) = nullptr;
+        if constexpr (wide_epilogue(EPI))
+            k = run == 4 ? back_tile_wide_kernel<EPI, TQ, 4, GENPOT> : back_tile_wide_kernel<EPI, TQ, 8, GENPOT>;
+        else
+            k = run == 4 ? back_tile_kernel<EPI, TQ, 4, GENPOT> : back_tile_kernel<EPI, TQ, 8, GENPOT>;
+        launch_dependent(k,
                          grid, dim3((unsigned)threads), smem, s, a);
         return check_launch("back_tile_kernel");
     }
