@@ -282,7 +282,7 @@ def kernel_source_digest() -> str:
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("forward.cu", "backward.cu", "epilogue.cuh", "petvr_internal.cuh"):
+    for name in ("forward.cu", "backward.cu", "bodies.cuh", "epilogue.cuh", "petvr_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2106_03172_gb300", "csrc", name)) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
@@ -691,12 +691,13 @@ def _sub_bench(extra, timeout=600):
     return json.loads(lines[-1])
 
 
-def leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush, steps=3, epochs=10):
-    """The same four reconstructions as one persistent batch (pet_batch_epoch:
-    one resident grid per phase for all four), timed like the headline."""
+def leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush, steps=3, epochs=10, mode="phases"):
+    """The same four reconstructions as one batch (pet_batch_epoch: persistent
+    phases, or one dependency-driven launch per call), timed like the headline."""
     imgs = {m: f0.clone() for m in METHODS}
     states = {m: petvr.State(prob, m, imgs[m]) for m in METHODS}
     batch = petvr.Batch([states[m] for m in METHODS])
+    batch.set_mode(mode)
     a = alphas(work)
     phi = torch.zeros(4, 3, dtype=torch.float64, device="cuda")
     rep = Replica(work)
@@ -724,11 +725,12 @@ def leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush, step
         e1.record(stream)
         ms.append((e0, e1))
     torch.cuda.synchronize()
+    batch.sync()
     total = sum(x.elapsed_time(y) for x, y in ms)
     value = pairs / (total / 1e3)
     return {"value": value, "unit": "subset fwd+back projections/s", "ms_per_epoch": total / (steps * epochs),
             "vs_four_streams": value / streams_value,
-            "how": f"{steps} steps of {epochs} epochs of the four methods as one batch (persistent phases), "
+            "how": f"{steps} steps of {epochs} epochs of the four methods as one batch ({mode}), "
                    "objectives batched too; L2 flushed between steps"}
 
 
@@ -786,7 +788,9 @@ def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, fl
     want = set() if args.legs == "none" else {x.strip() for x in args.legs.split(",") if x.strip()}
     legs = {}
     if "batched" in want and not work.geometry.multiring and work.geometry.nz == 1:
-        legs["batched_four_methods"] = leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush)
+        legs["batched_four_methods"] = {
+            mode: leg_batched(torch, petvr, prob, f0, work, streams_value, stream, flush, mode=mode)
+            for mode in ("phases", "dataflow")}
     if "batch64" in want:
         legs["batch64"] = _sub_bench(["--workload", "batch64", "--steps", "3", "--warmup", "1"])
     if "stack" in want:
@@ -831,11 +835,14 @@ def run_batch64(args):
         prob = petvr.Problem(plan, torch.from_numpy(data["g"].ravel()).cuda(), None, data["w"], w.beta)
         img = torch.empty(w.geometry.n_pixels, device="cuda")
         petvr.pet_warm_start(prob.handle, img)
-        solo_img = img.clone()
-        members.append({"work": w, "plan": plan, "prob": prob, "img": img, "solo_img": solo_img,
+        solo_img, df_img = img.clone(), img.clone()
+        members.append({"work": w, "plan": plan, "prob": prob, "img": img, "solo_img": solo_img, "df_img": df_img,
                         "state": petvr.State(prob, "saga", img, table="bf16"),
-                        "solo": petvr.State(prob, "saga", solo_img, table="bf16")})
+                        "solo": petvr.State(prob, "saga", solo_img, table="bf16"),
+                        "df": petvr.State(prob, "saga", df_img, table="bf16")})
     batch = petvr.Batch([m["state"] for m in members])
+    batch_df = petvr.Batch([m["df"] for m in members])
+    batch_df.set_mode("dataflow")
     n_iter = 21
     phi = torch.zeros(len(members), 3, dtype=torch.float64, device="cuda")
     phi_solo = torch.zeros(len(members), 3, dtype=torch.float64, device="cuda")
@@ -848,6 +855,10 @@ def run_batch64(args):
     def step_batched(step):
         batch.epoch(seqs(step), [1.0] * len(members), [1] * len(members), stream=stream)
         batch.objective_async(phi, stream=stream)
+
+    def step_dataflow(step):
+        batch_df.epoch(seqs(step), [1.0] * len(members), [1] * len(members), stream=stream)
+        batch_df.objective_async(phi, stream=stream)
 
     def step_solo(step):
         for j, (m, q) in enumerate(zip(members, seqs(step))):
@@ -876,9 +887,11 @@ def run_batch64(args):
     clk = clocks.stop()
     launches = petvr.pet_kernel_launches() - launches0
     t_solo = timed(step_solo, 0)
-    # same subset sequences in both runs: the results must agree bit for bit
+    t_df = timed(step_dataflow, 0)
+    batch_df.sync()
+    # same subset sequences in all runs: the results must agree bit for bit
     torch.cuda.synchronize()
-    same = all(torch.equal(m["img"], m["solo_img"]) for m in members)
+    same = all(torch.equal(m["img"], m["solo_img"]) and torch.equal(m["df_img"], m["solo_img"]) for m in members)
     pairs_step = len(members) * n_iter
     value = pairs_step * args.steps / (sum(t_batch) / 1e3)
     # algorithmic work of the timed steps: 2 nnz(A_t) per update (forward + back), nnz(A) per objective
@@ -906,6 +919,8 @@ def run_batch64(args):
         "sequential": {"value": solo_value, "ms_per_step": float(np.mean(t_solo)),
                        "how": "the same 64 states stepped one after another on one stream (graph per state)"},
         "speedup_vs_sequential": value / solo_value,
+        "dataflow": {"value": pairs_step * args.steps / (sum(t_df) / 1e3), "ms_per_step": float(np.mean(t_df)),
+                     "how": "the same batch as one dependency-driven launch per call (pet_batch_set_mode dataflow)"},
         "algorithmic": {"nonzeros_per_step": nnz_steps / args.steps, "achieved_tflops": flops,
                         "note": "2 flops per system-matrix nonzero per projection"},
         "bit_identical_to_sequential": bool(same),

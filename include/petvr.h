@@ -60,6 +60,8 @@ enum { PET_ALGO_OSEM = 0, PET_ALGO_SVREM = 1, PET_ALGO_SAGA = 2, PET_ALGO_SVRG =
 enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
 /* Preconditioner of SAGA and SVRG (pet_state_set_preconditioner). */
 enum { PET_PRECOND_CONSTANT = 0, PET_PRECOND_ITERATE = 1 };
+/* How pet_batch_epoch runs a batch's updates (pet_batch_set_mode). */
+enum { PET_BATCH_PHASES = 0, PET_BATCH_DATAFLOW = 1 };
 /* Potentials of the pairwise penalty (Table 1, t = f_n - f_j, delta > 0):
  * quadratic t^2/2; Huber t^2/2 for |t| <= delta else delta|t| - delta^2/2;
  * log cosh delta^2 log cosh(t/delta); hyperbola delta^2 (sqrt(1+(t/delta)^2) - 1)
@@ -350,6 +352,34 @@ pet_status pet_batch_epoch(pet_batch *batch, const int32_t *h_subset_seqs, int32
 /* Objectives {Phi, L, R} of every member's current image into d_phi
  * (device, [n][3] doubles), enqueued only. */
 pet_status pet_batch_objective_async(pet_batch *batch, double *d_phi, void *stream);
+
+/* How pet_batch_epoch runs the updates (the same results either way, bit for
+ * bit, and the same as each member's own epoch calls):
+ *   PET_BATCH_PHASES (default): per update, persistent phases separated by
+ *     kernel boundaries (see pet_batch_create);
+ *   PET_BATCH_DATAFLOW: one launch for the whole call.  Its resident grid
+ *     claims the stages of every update of every member from one work list in
+ *     which each stage waits only for the earlier stages of its own member
+ *     (the previous update's back projection, its own forward projection, the
+ *     anchor pass when due), so the members' phases overlap instead of meeting
+ *     at a kernel boundary after every phase.  The waits are bounded (see
+ *     pet_batch_set_wait_limit).  Applies when every member uses the same
+ *     potential class (quadratic, or edge-preserving); otherwise the batch
+ *     runs in phases. */
+pet_status pet_batch_set_mode(pet_batch *batch, int32_t mode);
+
+/* PET_BATCH_DATAFLOW only: how many times a block polls (with a short sleep
+ * between polls: a few seconds at the default 2^22) for a stage it waits for
+ * before it gives up: the kernel then latches PET_ERR_TIMEOUT in the batch's
+ * status word, the remaining work items skip their work and the launch ends;
+ * the members' iterates are then not valid.  0 fails any wait that is not
+ * already satisfied (a way to exercise that path).  polls < 0 is refused. */
+pet_status pet_batch_set_wait_limit(pet_batch *batch, int64_t polls);
+
+/* Synchronise `stream` and read the batch's status word: PET_ERR_TIMEOUT if a
+ * dependency wait ran out since the last call (the word is then cleared),
+ * PET_OK otherwise. */
+pet_status pet_batch_sync(pet_batch *batch, void *stream);
 
 /* The paper's non-variance-reduced baselines on the same kernels (§5.1),
  * with step alpha_k = alpha0 / (decay k + 1), k the state's update counter:

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpetvr.so")
-SOURCES = ["api.cu", "forward.cu", "backward.cu", "volume.cu", "volume_back.cu", "misc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "forward.cu", "backward.cu", "dataflow.cu", "volume.cu", "volume_back.cu", "misc.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v",
          "--expt-relaxed-constexpr"]

@@ -1157,6 +1157,9 @@ pet_status pet_batch_destroy(pet_batch *b) {
     dfree(b->d_claims);
     dfree(b->d_obj_segs);
     dfree(b->d_obj_claim);
+    dfree(b->d_df);
+    dfree(b->d_df_done);
+    dfree(b->d_status);
     dfree(b->d_seqs);
     dfree(b->d_alphas);
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
@@ -1168,6 +1171,38 @@ pet_status pet_batch_destroy(pet_batch *b) {
 pet_status pet_batch_set_graphs(pet_batch *b, int32_t on) {
     if (!b) return set_error(PET_ERR_INVALID, "null batch");
     b->graphs_on = on != 0;
+    return PET_OK;
+}
+
+pet_status pet_batch_set_mode(pet_batch *b, int32_t mode) {
+    if (!b) return set_error(PET_ERR_INVALID, "null batch");
+    if (mode != PET_BATCH_PHASES && mode != PET_BATCH_DATAFLOW) return set_error(PET_ERR_INVALID, "unknown batch mode");
+    b->mode = mode;
+    return PET_OK;
+}
+
+pet_status pet_batch_set_wait_limit(pet_batch *b, int64_t polls) {
+    if (!b) return set_error(PET_ERR_INVALID, "null batch");
+    if (polls < 0) return set_error(PET_ERR_INVALID, "the wait limit must be >= 0");
+    b->wait_limit = polls;
+    // the limit is a kernel argument of the captured epochs
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    return PET_OK;
+}
+
+pet_status pet_batch_sync(pet_batch *b, void *stream) {
+    if (!b) return set_error(PET_ERR_INVALID, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    PET_TRY(cuda_ok(cudaMemcpyAsync(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy"));
+    PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    if (h != 0) {
+        PET_TRY(cuda_ok(cudaMemsetAsync(b->d_status, 0, sizeof(int), s), "status reset"));
+        PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+        return set_error((pet_status)h, "a dependency wait of the batched epoch ran out (PET_ERR_TIMEOUT); the "
+                                        "members' iterates are not valid");
+    }
     return PET_OK;
 }
 
@@ -1206,7 +1241,9 @@ pet_status pet_batch_create(pet_state *const *states, int32_t n, pet_batch **out
     }
     b->n_obj_segs = n;
     if ((e = dalloc(&b->d_obj_segs, (size_t)n, "batch objective segments")) != PET_OK ||
-        (e = dalloc(&b->d_obj_claim, 1, "batch objective claim")) != PET_OK) {
+        (e = dalloc(&b->d_obj_claim, 1, "batch objective claim")) != PET_OK ||
+        (e = dalloc(&b->d_status, 1, "batch status")) != PET_OK ||
+        (e = cuda_ok(cudaMemset(b->d_status, 0, sizeof(int)), "batch status reset")) != PET_OK) {
         pet_batch_destroy(b);
         return e;
     }
@@ -1347,6 +1384,96 @@ void build_batch_phases(pet_batch *b, int n_iter, const std::vector<std::vector<
     b->n_claims = claim;
 }
 
+// The dependency-driven epoch's work list (into b->h_df): every stage of every
+// member, merged stage by stage across members (each member's k-th stage
+// before any member's (k+1)-th), with each stage's needs (see dataflow.cu).
+// Returns the block size and whether the members use an edge-preserving
+// potential (all must share one potential class).
+int build_batch_dataflow(pet_batch *b, int n_iter, const std::vector<std::vector<uint8_t>> &anchors, bool *genpot) {
+    const int n = (int)b->states.size();
+    struct Stage {
+        DfSeg seg;
+        int dep0, dep1;   // indices into the member's own stage list (-1: none)
+    };
+    std::vector<std::vector<Stage>> lists((size_t)n);
+    int threads = 256;
+    *genpot = b->states[0]->prob->pen.potential != PET_POT_QUADRATIC;
+    for (int j = 0; j < n; ++j) {
+        const pet_state *st = b->states[j];
+        const pet_plan *pl = st->prob->plan;
+        const int tiles = ((pl->nx + 15) / 16) * ((pl->ny + 15) / 16);
+        threads = std::max(threads, back_block_threads(pl->back_run, pl->max_sub_views));
+        bool ready = st->s_hat_ready;
+        int prev_b = -1;
+        auto add = [&](int kind, int count, int shape, int iter, int flag, int d0, int d1) {
+            DfSeg g{j, kind, 0, count, shape, tiles, iter, flag, -1, 0, -1, 0};
+            lists[(size_t)j].push_back({g, d0, d1});
+            return (int)lists[(size_t)j].size() - 1;
+        };
+        for (int i = 0; i < n_iter; ++i) {
+            int fin = -1;
+            if (anchors[j][i]) {
+                const int af = add(DF_FWD_ANCHOR, forward_blocks(pl->M, 1, full_group(pl)), full_group(pl), i, 0,
+                                   prev_b, -1);
+                const int ab = add(DF_BACK_ANCHOR, tiles * pl->ns, pl->back_run, i, 0, af, -1);
+                fin = add(DF_FINISH, (int)((plane_of(pl) + 255) / 256), 0, i,
+                          st->algo == PET_ALGO_SVREM && !ready ? 1 : 0, ab, -1);
+                if (st->algo == PET_ALGO_SVREM) ready = true;
+            }
+            const int f = add(DF_FWD_UPDATE, forward_blocks(max_sub_rays(pl), 1, choose_group(pl)),
+                              choose_group(pl), i, 0, prev_b, -1);
+            prev_b = add(DF_BACK_UPDATE, tiles, pl->back_run, i, 0, f, fin);
+        }
+    }
+    // merge stage by stage; map each member's stage indices to list positions
+    std::vector<std::vector<int>> pos((size_t)n);
+    for (int j = 0; j < n; ++j) pos[(size_t)j].assign(lists[(size_t)j].size(), -1);
+    b->h_df.clear();
+    size_t longest = 0;
+    for (const auto &l : lists) longest = std::max(longest, l.size());
+    int items = 0;
+    for (size_t k = 0; k < longest; ++k)
+        for (int j = 0; j < n; ++j) {
+            if (k >= lists[(size_t)j].size()) continue;
+            Stage &stg = lists[(size_t)j][k];
+            stg.seg.first = items;
+            items += stg.seg.count;
+            if (stg.dep0 >= 0) {
+                stg.seg.dep0 = pos[(size_t)j][(size_t)stg.dep0];
+                stg.seg.need0 = lists[(size_t)j][(size_t)stg.dep0].seg.count;
+            }
+            if (stg.dep1 >= 0) {
+                stg.seg.dep1 = pos[(size_t)j][(size_t)stg.dep1];
+                stg.seg.need1 = lists[(size_t)j][(size_t)stg.dep1].seg.count;
+            }
+            pos[(size_t)j][k] = (int)b->h_df.size();
+            b->h_df.push_back(stg.seg);
+        }
+    return threads;
+}
+
+// The dependency-driven epoch on stream s: the iterate copy (odd update
+// counts), SEM statistics due, the counters' reset, then one launch.
+pet_status enqueue_batch_dataflow(pet_batch *b, int32_t n_iter, int threads, bool genpot, cudaStream_t s) {
+    const bool odd = (n_iter % 2) == 1;
+    if (odd)
+        for (pet_state *st : b->states) {
+            const long long plane = plane_of(st->prob->plan);
+            PET_TRY(cuda_ok(cudaMemcpyAsync(st->alt, st->img, (size_t)plane * 4, cudaMemcpyDeviceToDevice, s),
+                            "cudaMemcpyAsync"));
+        }
+    for (pet_state *st : b->states)
+        if (st->algo == PET_ALGO_SEM && !st->s_hat_ready) {
+            PET_TRY(sem_init(st, odd ? st->alt : st->img, s));
+            st->s_hat_ready = true;
+        }
+    const int n_segs = (int)b->h_df.size();
+    const DfSeg &last = b->h_df.back();
+    PET_TRY(launch_zero_ints(b->d_df_done, n_segs + 1, s));
+    return launch_dataflow_epoch(b->d_members, b->d_df, n_segs, last.first + last.count, odd ? 1 : 0, b->d_df_done,
+                                 b->d_status, b->wait_limit, genpot, threads, s);
+}
+
 // All launches of one batched epoch on stream s (phases from build_batch_phases).
 pet_status enqueue_batch_epoch(pet_batch *b, int32_t n_iter, const std::vector<std::vector<uint8_t>> &anchors,
                                cudaStream_t s) {
@@ -1459,6 +1586,59 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
                 anchors[j][i] = 1;
                 key.push_back((int64_t)j * (1LL << 32) + i);
             }
+    }
+    bool uniform_potential = true;
+    for (int j = 1; j < n; ++j)
+        uniform_potential &= (b->states[j]->prob->pen.potential != PET_POT_QUADRATIC) ==
+                             (b->states[0]->prob->pen.potential != PET_POT_QUADRATIC);
+    if (b->mode == PET_BATCH_DATAFLOW && uniform_potential) {
+        bool genpot = false;
+        const int threads = build_batch_dataflow(b, n_iter, anchors, &genpot);
+        const int n_segs = (int)b->h_df.size();
+        if (n_segs > b->df_cap || n_segs + 1 > b->df_done_cap) {
+            DfSeg *grown = nullptr;
+            int *grown_d = nullptr;
+            PET_TRY(dalloc(&grown, (size_t)n_segs, "dataflow segments"));
+            if (dalloc(&grown_d, (size_t)n_segs + 1, "dataflow counters") != PET_OK) {
+                dfree(grown);
+                return PET_ERR_OOM;
+            }
+            if (b->d_df) {
+                PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+                dfree(b->d_df);
+                dfree(b->d_df_done);
+            }
+            b->d_df = grown;
+            b->d_df_done = grown_d;
+            b->df_cap = n_segs;
+            b->df_done_cap = n_segs + 1;
+            for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+            b->graphs.clear();
+        }
+        PET_TRY(cuda_ok(cudaMemcpyAsync(b->d_df, b->h_df.data(), sizeof(DfSeg) * n_segs, cudaMemcpyHostToDevice, s),
+                        "dataflow segment copy"));
+        pet_status rc;
+        key.push_back(-1);   // this mode's graphs apart from the phases'
+        if (direct) {
+            rc = enqueue_batch_dataflow(b, n_iter, threads, genpot, s);
+        } else {
+            pet_state holder{};
+            holder.cap = b->cap;
+            holder.graphs.swap(b->graphs);
+            rc = run_graph(&holder, key, s,
+                           [&](cudaStream_t cs) { return enqueue_batch_dataflow(b, n_iter, threads, genpot, cs); });
+            b->graphs.swap(holder.graphs);
+            b->cap = holder.cap;
+            holder.cap = nullptr;
+        }
+        if (rc == PET_OK)
+            for (int j = 0; j < n; ++j) {
+                pet_state *st = b->states[j];
+                if (st->algo == PET_ALGO_SVREM)
+                    for (int i = 0; i < n_iter; ++i) st->s_hat_ready |= anchors[j][i] != 0;
+                st->k += n_iter;
+            }
+        return rc;
     }
     build_batch_phases(b, n_iter, anchors);
     if ((int)b->h_segs.size() > b->seg_cap || b->n_claims > b->claim_cap) {

@@ -27,18 +27,12 @@
 //   SAGA_INIT table_t = b - sens_t - (beta/N_s) grad R(f) for every t.
 #include <algorithm>
 
-#include "epilogue.cuh"
+#include "bodies.cuh"
 
 namespace petvr {
 
 namespace {
 
-constexpr int kTile = 16;           // single slice: a block owns a kTile x kTile tile (kTile^2 == kBlock)
-constexpr int kChunk = 16;          // views per shared-memory pass
-constexpr int kTileBlockMax = 1024; // threads of a tile block: kTile * kTile / run per view of a chunk
-constexpr int kPersistentBackMax = 512;  // threads of a persistent back block (a run-4 tile with more
-                                         // than 8 views per chunk loops over its runs twice)
-constexpr int kPersistentBackRegs = 48;  // four 288-thread blocks per SM
 // The all-subset launches (anchor passes, table fills), the full-data
 // statistic and plain back projections run in back_tile_wide_kernel, capped at
 // 48 registers: four 288-thread blocks per SM where the compiler's own choice
@@ -49,98 +43,6 @@ constexpr bool wide_epilogue(int epi) {
 }
 constexpr int kWideRegs = 48;
 static_assert(kTile * kTile == kBlock, "one pixel of the tile per thread");
-
-// Single-slice path: a block owns a kTile x kTile pixel tile.  For each view,
-// the tile's bands are cut into runs of kRun pixels along the view's minor
-// axis; one thread walks the rays that can cross a run in band order and
-// adds each ray's two band pieces into per-view partial sums in shared
-// memory (every (view, pixel) slot has exactly one writer, so no atomics).
-// Then each thread sums its pixel's partials over the views in a fixed order
-// and applies the update.  Each ray-band split is evaluated once per run
-// instead of once per pixel it touches.  Views are processed in chunks of
-// kChunk to bound shared memory.
-template <int EPI, typename TQ, int kRun, bool GENPOT>
-__device__ __forceinline__ void back_tile_body(const BackArgs &a, const int t, const int bx) {
-    extern __shared__ unsigned char smem_raw[];
-    const int vb = __ldg(a.sub_off + t);
-    const int nv = __ldg(a.sub_off + t + 1) - vb;
-    float *s_part = reinterpret_cast<float *>(smem_raw);                       // [kChunk][kTile*kTile]
-    ViewParams *s_views = reinterpret_cast<ViewParams *>(s_part + kChunk * kTile * kTile);   // [kChunk]
-    int *s_vid = reinterpret_cast<int *>(s_views + kChunk);
-    const int r_view0 = a.t_dev ? vb : a.r_view0;
-    const int nthr = blockDim.x;                  // >= kTile * kTile; one run per thread when nv <= nthr / 32
-
-    const int tiles_x = (a.nx + kTile - 1) / kTile;
-    const int x0 = (bx % tiles_x) * kTile;
-    const int y0 = (bx / tiles_x) * kTile;
-    constexpr int kRunsPerBand = kTile / kRun;
-    constexpr int kRunsPerView = kTile * kRunsPerBand;
-
-    float acc = 0.0f;
-    for (int q0 = 0; q0 < nv; q0 += kChunk) {
-        const int nq = min(kChunk, nv - q0);
-        for (int q = threadIdx.x; q < nq; q += nthr) {
-            const int v = __ldg(a.order + vb + q0 + q);
-            s_vid[q] = v;
-            s_views[q] = a.views[v];
-        }
-        for (int e = threadIdx.x; e < nq * kTile * kTile; e += nthr) s_part[e] = 0.0f;
-        __syncthreads();
-        if (q0 == 0) {
-            // the staging above read plan constants only; the ratios and the
-            // images below come from earlier kernels
-            pdl_wait();
-            pdl_trigger();
-        }
-        for (int run = threadIdx.x; run < nq * kRunsPerView; run += nthr) {
-            const int ql = run / kRunsPerView;
-            const int rem = run - ql * kRunsPerView;
-            const int band = rem / kRunsPerBand;          // band offset inside the tile
-            const int seg = rem - band * kRunsPerBand;
-            const ViewParams vp = s_views[ql];
-            const int v = s_vid[ql];
-            const int k = (vp.col ? x0 : y0) + band;      // major index
-            const int mstart = (vp.col ? y0 : x0) + seg * kRun;
-            const int n_major = vp.col ? a.nx : a.ny;
-            const int n_minor = vp.col ? a.ny : a.nx;
-            const int mlen = min(kRun, n_minor - mstart);
-            if (k >= n_major || mlen <= 0) continue;
-            const int m0rel = mstart - (n_minor >> 1);
-            const float kc = (float)k - 0.5f * (float)n_major;
-            int jlo, jhi;
-            candidate_bins(vp, kc, (float)m0rel, (float)(m0rel + mlen), a.nb, jlo, jhi);
-            // local pixel index of minor offset c inside the run: row-driven runs
-            // go along x, column-driven runs along y
-            const int lbase = vp.col ? (seg * kRun) * kTile + band : band * kTile + seg * kRun;
-            const int lstep = vp.col ? kTile : 1;
-            float *pp = s_part + ql * kTile * kTile + lbase;
-            const float2 *ucv = a.uc + v * a.nb;
-            const float *rv = a.r + (vb + q0 + ql - r_view0) * a.nb;
-            for (int j = jlo; j <= jhi; ++j) {
-                const float2 u = __ldg(ucv + j);
-                float fl, w0, w1;
-                band_split(vp, band_point(vp, u.y, kc), band_point(vp, u.y, kc + 1.0f), fl, w0, w1);
-                const int c = (int)fl + (int)u.x - m0rel;
-                const float r = __ldg(rv + j);
-                if ((unsigned)c < (unsigned)mlen) pp[c * lstep] += w0 * r;
-                if (w1 > 0.0f && (unsigned)(c + 1) < (unsigned)mlen) pp[(c + 1) * lstep] += w1 * r;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < kTile * kTile)
-            for (int ql = 0; ql < nq; ++ql) acc += s_part[ql * kTile * kTile + threadIdx.x];
-        __syncthreads();
-    }
-    pdl_wait();   // returns at once after the wait above; covers an empty subset
-    if (threadIdx.x < kTile * kTile) {
-        const int ix = x0 + (threadIdx.x % kTile);
-        const int iy = y0 + (threadIdx.x / kTile);
-        if (ix < a.nx && iy < a.ny) {
-            const int n = iy * a.nx + ix;
-            apply_epilogue<EPI, TQ, GENPOT>(a, t, n, n, ix, iy, 0, acc);
-        }
-    }
-}
 
 template <int EPI, typename TQ, int kRun, bool GENPOT>
 __global__ void __launch_bounds__(kTileBlockMax) back_tile_kernel(const BackArgs a) {

@@ -15,6 +15,15 @@ constexpr int kBlock = 256;
 constexpr int kLanes = 4;           // multi-ring volumes: lanes per pixel column or voxel
 constexpr float kCandEps = 1e-3f;   // candidate-bin margin (pixels)
 
+// A float that may have been written earlier in the same kernel launch by
+// another block (COH: a plain load, ordered by the reader's acquire) or that is
+// read-only for the launch (the read-only data path).
+template <bool COH>
+__device__ __forceinline__ float ld_data(const float *p) {
+    if (COH) return *p;
+    return __ldg(p);
+}
+
 struct Stencil {
     float cnt;   // sum_j d_nj, d_nj = gamma(f_n - f_j) (quadratic: the number of in-image neighbours)
     float sum;   // sum_j d_nj f_j
@@ -25,18 +34,18 @@ struct Stencil {
 // axial neighbours of a volume when `axial`): surrogate weights and penalty
 // gradient at f^k (out-of-image neighbours are dropped).  GENPOT selects the
 // edge-preserving potentials (runtime pot); otherwise quadratic.
-template <bool GENPOT>
+template <bool GENPOT, bool COH = false>
 __device__ __forceinline__ Stencil stencil4(const float *f, int ix, int iy, int nx, int ny, int nz, int z,
                                             float fk, int pot, float delta, int axial = 0) {
     const bool hl = ix > 0, hr = ix + 1 < nx, hd = iy > 0, hu = iy + 1 < ny;
     const bool hb = axial && z > 0, ht = axial && z + 1 < nz;        // axial neighbours of a volume
     const long long c = ((long long)iy * nx + ix) * nz + z;
-    const float fl = hl ? __ldg(f + c - nz) : 0.0f;
-    const float fr = hr ? __ldg(f + c + nz) : 0.0f;
-    const float fd = hd ? __ldg(f + c - (long long)nx * nz) : 0.0f;
-    const float fu = hu ? __ldg(f + c + (long long)nx * nz) : 0.0f;
-    const float fb = hb ? __ldg(f + c - 1) : 0.0f;
-    const float ft = ht ? __ldg(f + c + 1) : 0.0f;
+    const float fl = hl ? ld_data<COH>(f + c - nz) : 0.0f;
+    const float fr = hr ? ld_data<COH>(f + c + nz) : 0.0f;
+    const float fd = hd ? ld_data<COH>(f + c - (long long)nx * nz) : 0.0f;
+    const float fu = hu ? ld_data<COH>(f + c + (long long)nx * nz) : 0.0f;
+    const float fb = hb ? ld_data<COH>(f + c - 1) : 0.0f;
+    const float ft = ht ? ld_data<COH>(f + c + 1) : 0.0f;
     Stencil s{0.0f, 0.0f, 0.0f};
     if (!GENPOT) {
         // missing neighbours add exact zeros
@@ -76,7 +85,7 @@ template <> __device__ __forceinline__ void store_q<__nv_bfloat16>(void *p, long
 }
 
 // Per-pixel update after the gather: b = acc is A_t^T r_t at (pixel n, slice z).
-template <int EPI, typename TQ, bool GENPOT>
+template <int EPI, typename TQ, bool GENPOT, bool COH = false>
 __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long long i, int n, int ix, int iy,
                                                int z, float acc) {
     const long long plane = (long long)a.nx * a.ny * a.nz;
@@ -91,7 +100,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         a.out[(long long)t * plane + i] = acc;
     } else if (EPI == EPI_OSEM) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float bp = a.beta * inv_ns;
         const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
         const float c = bp * fmaf(fk, st.cnt, st.sum) - S;
@@ -103,13 +112,13 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float tau = ns * fk * acc - ns * a.f_anc[i] * Bt + a.s_anc[i];
         const float s = fmaf(alpha, tau, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float S = __ldg(a.sens + sidx);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
     } else if (EPI == EPI_SAGA || EPI == EPI_SAGA_INIT) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float gradR = st.grad;
         const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
         const float q = round_q<TQ>(acc - S - a.beta * inv_ns * gradR);
@@ -127,7 +136,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         }
     } else if (EPI == EPI_SVRG) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float gradR = st.grad;
         const float Bt = a.B[(long long)t * plane + i];
         const float dir = acc - Bt - a.beta * inv_ns * gradR + a.qtil[i];
@@ -141,7 +150,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         a.f_out[i] = fmaxf(fmaf(alpha * dn, dir, fk), 0.0f);
     } else if (EPI == EPI_SGA) {
         const float fk = a.f[i];
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float S = __ldg(a.sens_t + (long long)t * splane + sidx);
         const float dir = acc - S - a.beta * inv_ns * st.grad;      // grad Phi_t
         const float dt = S > 0.0f ? fk / S : 0.0f;                  // d_t(f) = f / A_t^T 1
@@ -150,7 +159,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
         const float fk = a.f[i];
         const float s = fmaf(alpha, (float)a.ns * fk * acc, (1.0f - alpha) * a.s_hat[i]);
         a.s_hat[i] = s;
-        const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+        const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
         const float S = __ldg(a.sens + sidx);
         const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
         a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);
@@ -168,7 +177,7 @@ __device__ __forceinline__ void apply_epilogue(const BackArgs &a, int t, long lo
             const float Tb = a.qbar[i];
             const float s = fmaf(alpha, tau - T_old + Tb, (1.0f - alpha) * a.s_hat[i]);
             a.s_hat[i] = s;
-            const Stencil st = stencil4<GENPOT>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
+            const Stencil st = stencil4<GENPOT, COH>(a.f, ix, iy, a.nx, a.ny, a.nz, z, fk, a.pot, a.delta, a.axial);
             const float S = __ldg(a.sens + sidx);
             const float c = a.beta * fmaf(fk, st.cnt, st.sum) - S;
             a.f_out[i] = m_step_root(s, S, a.beta * st.cnt, c);

@@ -393,6 +393,35 @@ struct WorkSeg {
     int tiles;    // back: tiles per subset (anchor item = t * tiles + tile)
 };
 
+// Dependency-driven batched epoch: one resident grid runs every update of an
+// epoch call for all members.  Its work list holds every stage of every
+// member (subset forward, subset back + update, and at anchor updates the
+// anchor forward, anchor back projection and anchor finish), ordered stage by
+// stage across members.  A segment's items wait (thread 0, bounded) until the
+// segments it depends on - earlier stages of the same member - have counted
+// all their items done; every dependency lies earlier in the list, and items
+// are claimed in list order, so the earliest unfinished item never waits.
+enum DfKind {
+    DF_FWD_UPDATE = 0,   // ray blocks of the member's subset of update `iter` -> ratio
+    DF_FWD_ANCHOR = 1,   // ray blocks of all views -> ratio_full
+    DF_BACK_UPDATE = 2,  // tiles of update `iter` (the member's epilogue)
+    DF_BACK_ANCHOR = 3,  // (subset, tile) items of the anchor back projection -> B
+    DF_FINISH = 4,       // 256-pixel blocks of the anchor finish (SVREM s_anc / SVRG q~)
+};
+
+struct DfSeg {
+    int member;   // index into the batch's member descriptors
+    int kind;     // DfKind
+    int first;    // list index of the segment's first item
+    int count;    // items in the segment
+    int shape;    // forward: band chunks per ray; back: pixels per run
+    int tiles;    // back: tiles per subset
+    int iter;     // the update this stage belongs to
+    int flag;     // DF_FINISH of SVREM: s_hat is initialised from this anchor
+    int dep0, need0;   // segment waited for (-1: none) and its item count
+    int dep1, need1;
+};
+
 // Segments a persistent block stages in shared memory (longer tables are
 // searched in global memory).
 constexpr int kSegSmem = 160;
@@ -503,6 +532,14 @@ struct pet_batch {
     int *d_claims = nullptr;        // claim counters of the current call's phases
     int claim_cap = 0;
     int n_claims = 0;
+    int mode = 0;                   // 0: persistent phases, 1: dependency-driven epoch
+    long long wait_limit = 1LL << 22;        // dependency-driven epoch: polls of a wait before PET_ERR_TIMEOUT
+    std::vector<petvr::DfSeg> h_df;
+    petvr::DfSeg *d_df = nullptr;
+    int df_cap = 0;
+    int *d_df_done = nullptr;       // claim counter, then one done counter per segment
+    int df_done_cap = 0;
+    int *d_status = nullptr;        // the batch's latched device status (PET_ERR_TIMEOUT)
     petvr::WorkSeg *d_obj_segs = nullptr;   // objective pass: every member's rays (fixed at creation)
     int n_obj_segs = 0, n_obj_items = 0;
     int *d_obj_claim = nullptr;
@@ -561,6 +598,10 @@ pet_status launch_persistent_back(const BatchMember *d_members, const WorkSeg *d
                                   int iter, int in_is_img, int *claim, bool general_potential, int threads,
                                   cudaStream_t s);
 pet_status launch_zero_ints(int *p, int n, cudaStream_t s);
+// Dependency-driven batched epoch (dataflow.cu): the whole list in one launch.
+pet_status launch_dataflow_epoch(const BatchMember *d_members, const DfSeg *d_segs, int n_segs, int n_items,
+                                 int odd, int *d_done, int *d_status, long long wait_limit, bool general_potential,
+                                 int threads, cudaStream_t s);
 int back_block_threads(int run, int max_views);   // block size a back projection of this shape needs
 int sm_count();
 pet_status launch_batch_objective_finish(const BatchMember *d_members, int n_members, int pen_blocks,

@@ -68,6 +68,9 @@ _SIGS = {
     "pet_warm_start": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_objective": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),
     "pet_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pet_batch_set_mode": (c_int32, [c_void_p, c_int32]),
+    "pet_batch_set_wait_limit": (c_int32, [c_void_p, ctypes.c_int64]),
+    "pet_batch_sync": (c_int32, [c_void_p, c_void_p]),
     "pet_objective_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
                                         c_void_p]),
     "pet_state_create": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, POINTER(c_size_t),
@@ -412,6 +415,17 @@ class Batch:
 
     def objective_async(self, phi_out, stream=None):
         pet_batch_objective_async(self.handle, phi_out, stream)
+
+    def set_mode(self, mode: str):
+        """'phases' (default) or 'dataflow' (one launch per epoch call)."""
+        _call("pet_batch_set_mode", self.handle, {"phases": 0, "dataflow": 1}[mode])
+
+    def set_wait_limit(self, polls: int):
+        _call("pet_batch_set_wait_limit", self.handle, int(polls))
+
+    def sync(self, stream=None):
+        """Synchronise and raise PetError (PET_ERR_TIMEOUT) if a dataflow wait ran out."""
+        _call("pet_batch_sync", self.handle, _stream(stream))
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

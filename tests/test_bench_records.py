@@ -9,7 +9,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-FILES = ("forward.cu", "backward.cu", "epilogue.cuh", "petvr_internal.cuh")
+FILES = ("forward.cu", "backward.cu", "bodies.cuh", "epilogue.cuh", "petvr_internal.cuh")
 
 
 def _tree(tmp_path):

@@ -35,7 +35,10 @@ MEMBERS = [("c64", "osem", "fp32", 1.0, 1), ("c64", "svrem", "fp32", 0.7, 1), ("
            ("c64", "sagaem", "fp32", 0.7, 1)]
 
 
-def test_batch_equals_individual_epochs():
+@pytest.mark.parametrize("mode", ["phases", "dataflow"])
+def test_batch_equals_individual_epochs(mode):
+    """Both batch modes (persistent phases; one dependency-driven launch per
+    call) give every member exactly its own epochs' iterates and objectives."""
     pv = _pv()
     setups = {"c64": _setup(pv, "c64"), "ragged": _setup(pv, "ragged", run=4), "c256": _setup(pv, "c256")}
     solo, batched, solo_states, batch_states = [], [], [], []
@@ -47,13 +50,14 @@ def test_batch_equals_individual_epochs():
         solo_states.append(pv.State(gp, algo, a, table=table))
         batch_states.append(pv.State(gp, algo, b, table=table))
     batch = pv.Batch(batch_states)
+    batch.set_mode(mode)
     rng = np.random.default_rng(5)
     for n_iter in (7, 4, 21):
         seqs = [rng.integers(0, setups[m[0]][3].n_subsets, n_iter) for m in MEMBERS]
         batch.epoch(seqs, [m[3] for m in MEMBERS], [m[4] for m in MEMBERS])
         for st, q, m in zip(solo_states, seqs, MEMBERS):
             st.epoch(q, alpha=m[3], eta=m[4])
-        torch.cuda.synchronize()
+        batch.sync()
         for a, b, m in zip(solo, batched, MEMBERS):
             assert torch.equal(a, b), (n_iter, m)
     phi_b = torch.empty(len(MEMBERS), 3, dtype=torch.float64, device="cuda")
@@ -123,3 +127,37 @@ def test_batch_mixed_potentials_and_many_members():
         m[5].objective_async(phi_s[j])
     torch.cuda.synchronize()
     assert torch.equal(phi_b, phi_s)
+
+
+def test_dataflow_wait_that_runs_out_latches_timeout():
+    """A dependency wait of the dataflow epoch that runs out latches
+    PET_ERR_TIMEOUT, which pet_batch_sync reports; the launch still ends and
+    the GPU stays usable.  With a limit of 0 polls, the first back-projection
+    items of a 256^2 member (claimed by the grid's first wave while its forward
+    items are still running) fail their wait.  A fresh batch with the default
+    limit then matches the member's own epochs again."""
+    pv = _pv()
+    plan, gp, f0, work = _setup(pv, "c256")
+    img = f0.clone()
+    st = pv.State(gp, "osem", img)
+    batch = pv.Batch([st])
+    batch.set_mode("dataflow")
+    batch.set_wait_limit(0)
+    seq = [np.arange(work.n_subsets) % work.n_subsets]
+    batch.epoch(seq, [1.0], [1])
+    with pytest.raises(pv.PetError) as e:
+        batch.sync()
+    assert e.value.status == 4
+    batch.sync()                                   # the status word was cleared
+    # recovery: fresh states, default limit, bit-identical to solo epochs
+    a, b = f0.clone(), f0.clone()
+    solo, member = pv.State(gp, "svrg", a), pv.State(gp, "svrg", b)
+    batch2 = pv.Batch([member])
+    batch2.set_mode("dataflow")
+    for epoch in range(2):
+        q = np.random.default_rng(epoch).integers(0, work.n_subsets, work.n_subsets)
+        batch2.epoch([q], [2.0], [2])
+        solo.epoch(q, alpha=2.0, eta=2)
+    batch2.sync()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
