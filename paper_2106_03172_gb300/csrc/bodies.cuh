@@ -19,9 +19,13 @@ namespace {
 constexpr int kTile = 16;           // single slice: a block owns a kTile x kTile tile (kTile^2 == kBlock)
 constexpr int kChunk = 16;          // views per shared-memory pass
 constexpr int kTileBlockMax = 1024; // threads of a tile block: kTile * kTile / run per view of a chunk
-constexpr int kPersistentBackMax = 512;  // threads of a persistent back block (a run-4 tile with more
-                                         // than 8 views per chunk loops over its runs twice)
-constexpr int kPersistentBackRegs = 48;  // four 288-thread blocks per SM
+// Threads of a persistent back block: one 256-thread block per tile, whose
+// threads loop over the runs of subsets with more than 8 views (run 8) or 4
+// views (run 4).  Measured on the 64-reconstruction batch (most members need
+// 512 threads for one run per thread): 118k pairs/s at 256 threads (five
+// blocks per SM), 111k at 288-320, 102k at 512 (two blocks per SM).
+constexpr int kPersistentBackMax = 256;
+constexpr int kPersistentBackRegs = 48;  // five 256-thread blocks per SM
 
 // Single-slice forward: a block takes RAYS adjacent rays of the view range
 // and splits each ray's bands into CHUNKS contiguous chunks (RAYS * CHUNKS =
