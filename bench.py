@@ -925,7 +925,8 @@ def run_batch64(args):
                         "note": "2 flops per system-matrix nonzero per projection"},
         "bit_identical_to_sequential": bool(same),
     }
-    line["recon"] = batch64_recon(torch, petvr, works, [make_data(w, 100 + i) for i, w in enumerate(works)])
+    if args.recon > 0:
+        line["recon"] = batch64_recon(torch, petvr, works, [make_data(w, 100 + i) for i, w in enumerate(works)])
     print(json.dumps(line), flush=True)
     return 0
 

@@ -190,7 +190,12 @@ struct TileBack {
         // one thread per run: kTile * kTile / run runs per view of the largest chunk
         const int run = a.run == 4 ? 4 : 8;
         const int per_view = kTile * (kTile / run);
-        const int threads = max(kTile * kTile, per_view * min(max_views, kChunk));
+        // subset launches are latency-bound: one run per thread; the all-subset and
+        // full-data launches are throughput-bound: 256-thread blocks whose threads
+        // loop over the runs, so that more blocks fit per SM (anchor 41.3 -> 39.5 us)
+        const int threads = (wide_epilogue(EPI) && EPI != EPI_PLAIN)
+                                ? kTile * kTile
+                                : max(kTile * kTile, per_view * min(max_views, kChunk));
         void (*k)(BackArgs) = nullptr;
         if constexpr (wide_epilogue(EPI))
             k = run == 4 ? back_tile_wide_kernel<EPI, TQ, 4, GENPOT> : back_tile_wide_kernel<EPI, TQ, 8, GENPOT>;
