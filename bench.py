@@ -595,6 +595,20 @@ def run_ours(args):
                                        "(profiles/roofline_traffic.txt; null when the sources changed since)",
                 "kernels": {v["name"]: {k2: v[k2] for k2 in ("launches", "avg_us", "share")}
                             for v in kinds.values()}}
+    # context for the per-launch durations above: one tiny kernel timed the same way
+    # (events on both sides of a single launch on an idle stream)
+    tiny = torch.zeros(1, device="cuda")
+    floor = []
+    for _ in range(50):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        tiny.add_(1.0)
+        t1.record(stream)
+        t1.synchronize()
+        floor.append(1e3 * t0.elapsed_time(t1))
+    roofline["launch_floor_us"] = float(np.median(floor))
+    roofline["launch_floor_how"] = ("median of 50 one-element kernels, each bracketed by events like the projector "
+                                    "launches of the profiled pass")
     hbm_peak, hbm_src = measured_hbm_peak()
     roofline["hbm_peak_gbs"] = hbm_peak
     roofline["hbm_frac"] = roofline["hbm_achieved_gbs"] / hbm_peak
