@@ -68,6 +68,9 @@ def parse_args():
     ap.add_argument("--max-epochs", type=int, default=200,
                     help="serve workload: epochs after which a request stops without reaching the gap")
     ap.add_argument("--depth", type=int, default=2, help="serve workload, stream server: epochs in flight per request")
+    ap.add_argument("--distinct", action="store_true",
+                    help="serve workload: requests with their own phantoms and counts (the stored-Phi* sample) "
+                         "instead of draws from the request templates")
     ap.add_argument("--server", choices=["streams", "batch"], default="streams",
                     help="serve workload: the server the headline value is taken from (the other is reported too)")
     ap.add_argument("--batch", dest="batch", action="store_true",
@@ -815,12 +818,14 @@ def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, fl
             legs["c128x47"]["roofline_frac"] = sub["roofline"].get("frac")
             legs["c128x47"]["achieved_tflops"] = sub["roofline"].get("achieved")
     if "serve" in want:
-        sub = _sub_bench(["--workload", "serve", "--requests", "30"])
-        legs["serve30"] = {k: sub.get(k) for k in ("value", "unit", "latency", "speedup_vs_plain",
-                                                   "p50_speedup_vs_plain", "bit_identical_to_plain", "error")
-                           if k in sub}
+        sub = _sub_bench(["--workload", "serve", "--requests", "32", "--distinct"])
+        leg = {k: sub.get(k) for k in ("value", "unit", "latency", "speedup_vs_plain", "p50_speedup_vs_plain",
+                                       "bit_identical_to_plain", "error") if k in sub}
         if "plain" in sub:
-            legs["serve30"]["plain_latency"] = sub["plain"]["latency"]
+            leg["plain_latency"] = sub["plain"]["latency"]
+        if "config" in sub:
+            leg["requests"] = sub["config"].get("workload")
+        legs["serve_distinct32"] = leg
     if "parity" in want:
         legs["parity_vs_oracle"] = leg_parity(torch, petvr, work, data, prob)
     return legs
@@ -992,18 +997,22 @@ def _server_stats(srv):
 
 def run_serve(args):
     """Serving: an open-loop Poisson stream of SVREM/SAGA requests, image size
-    uniform over the request templates' sizes (128^2 to 512^2, 1e6-1e8 counts,
-    6/12/21 subsets), each stopped at a relative objective gap of 1e-4 against
-    the FP64 oracle's Phi* of its template; continuous batching with admission
-    by device-memory budget, against the same stream served one request at a
-    time through the plain per-reconstruction path."""
+    uniform in 128^2-512^2, counts log-uniform in 1e6-1e8, 6/12/21 subsets,
+    each stopped at a relative objective gap of 1e-4 against the FP64
+    oracle's Phi* of its data; continuous batching with admission by
+    device-memory budget, against the same stream served one request at a
+    time through the plain per-reconstruction path.  By default requests are
+    drawn from twelve templates (phantom and counts shared by a template's
+    requests, which differ in their subset sequences); with --distinct every
+    request has its own phantom and counts (as many requests as have a stored
+    Phi*)."""
     import hashlib
 
     import torch
 
     from paper_2106_03172_gb300 import build as _build
     from paper_2106_03172_gb300 import petvr
-    from paper_2106_03172_gb300.phantoms import make_data, serving_pool
+    from paper_2106_03172_gb300.phantoms import make_data, serving_pool, serving_requests
     from paper_2106_03172_gb300.serving import (Request, Server, StreamServer, latency_summary, per_template,
                                                 serve_plain)
 
@@ -1011,27 +1020,49 @@ def run_serve(args):
     _build.build()
     petvr.lib()
     golden = json.load(open(os.path.join(ROOT, "tests", "golden", "phi_star.json")))
-    pool, skipped = [], []
-    for w in serving_pool():
-        data = make_data(w, 0)
+
+    def with_phi_star(w, seed):
+        data = make_data(w, seed)
         ent = golden.get(w.name)
         sha = hashlib.sha256(data["g"].astype("<f4").tobytes()).hexdigest()
-        if ent and ent["counts_sha256"] == sha:
-            pool.append((w, data, ent["phi_star"]))
-        else:
-            skipped.append(w.name)
+        return (w, data, ent["phi_star"]) if ent and ent["counts_sha256"] == sha else None
+
     rng = np.random.default_rng(77)
     n_req = args.requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
-    # image size uniform over the pool's sizes, then a template of that size
-    by_size = {}
-    for k, (w, _, _) in enumerate(pool):
-        by_size.setdefault(w.geometry.nx, []).append(k)
-    size_keys = sorted(by_size)
-    picks = []
-    for _ in range(n_req):
-        group = by_size[size_keys[int(rng.integers(len(size_keys)))]]
-        picks.append(group[int(rng.integers(len(group)))])
+    pool, skipped = [], []
+    if args.distinct:
+        # every request its own phantom and counts: the first n_req requests of
+        # the distinct stream, each with the oracle's Phi* of its own data
+        for w, seed in serving_requests(n_req):
+            ent = with_phi_star(w, seed)
+            if ent is None:
+                skipped.append(w.name)
+            else:
+                pool.append(ent)
+        n_req = len(pool)
+        picks = list(range(n_req))
+        arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    else:
+        for w in serving_pool():
+            ent = with_phi_star(w, 0)
+            if ent is None:
+                skipped.append(w.name)
+            else:
+                pool.append(ent)
+        arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+        # image size uniform over the pool's sizes, then a template of that size
+        by_size = {}
+        for k, (w, _, _) in enumerate(pool):
+            by_size.setdefault(w.geometry.nx, []).append(k)
+        size_keys = sorted(by_size)
+        picks = []
+        for _ in range(n_req):
+            group = by_size[size_keys[int(rng.integers(len(size_keys)))]]
+            picks.append(group[int(rng.integers(len(group)))])
+    if n_req == 0:
+        print(json.dumps({"metric": "reconstructions/s to 1e-4 objective gap", "value": None,
+                          "error": f"no request has a stored Phi* (missing: {', '.join(skipped[:8])})"}), flush=True)
+        return 1
 
     def requests():
         return [Request(i, pool[k][0], pool[k][1]["g"], pool[k][1]["w"], pool[k][2], arrival=float(t),
@@ -1070,13 +1101,17 @@ def run_serve(args):
         "value": summ["reached_per_s"], "unit": "reconstructions/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
         "ms_per_step": summ["p50_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (bf16 SAGA tables)", "data": "synthetic (seeded ellipse phantoms, Poisson counts)",
-        "config": {"workload": f"serve: {n_req} requests, Poisson arrivals at {args.rate:g}/s, templates "
-                               f"{', '.join(w.name for w, _, _ in pool)} "
-                               f"({'/'.join(f'{n}^2' for n in sizes)}, SVREM/SAGA), "
+        "config": {"workload": (f"serve: {n_req} distinct requests (own phantom and counts, log-uniform "
+                                f"1e6-1e8), Poisson arrivals at {args.rate:g}/s, "
+                                if args.distinct else
+                                f"serve: {n_req} requests, Poisson arrivals at {args.rate:g}/s, templates "
+                                f"{', '.join(w.name for w, _, _ in pool)} ")
+                               + f"({'/'.join(f'{n}^2' for n in sizes)}, SVREM/SAGA), "
                                f"stop at relative gap {GAP:g} against the oracle's Phi*",
+                   "requests": "distinct" if args.distinct else "templates",
                    "server": args.server, "budget_gib": args.budget_gib, "max_slots": 64, "max_epochs": me,
                    "streams_depth_epochs": args.depth, "batch_tick_updates": 3, "batch_window_ticks": args.window,
-                   "templates_without_phi_star": skipped},
+                   "without_phi_star": skipped},
         "latency": summ, "gpu_launches": int(launches), "clocks": clk,
         "plain": {"latency": plain_summ, "how": "the same requests one at a time in arrival order, each "
                   "through its own State epochs (captured graphs), objective after every epoch"},

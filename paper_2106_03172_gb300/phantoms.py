@@ -31,6 +31,7 @@ __all__ = [
     "ellipsoid_stack_phantom", "ellipsoid_solids", "rasterise", "analytic_sinogram",
     "analytic_lor_sinogram", "rasterise_volume", "make_data",
     "splitmix64", "subset_sequence", "batched_workloads", "serving_workloads", "serving_pool",
+    "serving_requests",
 ]
 
 
@@ -412,6 +413,16 @@ def serving_pool() -> list:
     (seed 3: SVREM with 6 subsets, SAGA with 12)."""
     return (serving_workloads(0, 8) + serving_workloads(5, 2, sizes=(384,), prefix="serve384_")
             + serving_workloads(3, 2, sizes=(512,), prefix="serve512_"))
+
+
+def serving_requests(count: int) -> list:
+    """A stream of distinct requests, each with its own phantom and counts:
+    request i is ``(workload req<i>, data seed 20000 + i)``, the workload drawn
+    as in ``serving_workloads`` (seed 11) with N uniform in {128, 256, 384,
+    512} and counts log-uniform in [1e6, 1e8].  Requests of one size and
+    subset number share a geometry (and so a plan), nothing else."""
+    works = serving_workloads(11, count, sizes=(128, 256, 384, 512), prefix="req")
+    return [(w, 20000 + i) for i, w in enumerate(works)]
 
 
 def batched_workloads(seed: int, count: int) -> list:

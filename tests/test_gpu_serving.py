@@ -120,3 +120,43 @@ def test_admission_respects_the_memory_budget(kind):
     assert srv.stats.peak_bytes <= budget and srv.stats.admissions_deferred > 0
     assert srv.stats.max_active < len(reqs)
     assert srv.active_bytes == 0 and not srv.active
+
+
+@functools.lru_cache(maxsize=None)
+def _distinct(k):
+    """Request k of a stream whose every request has its own phantom and
+    counts (log-uniform in [3e5, 3e6]) on the first template's shape and
+    method, with the oracle's Phi* of its own data."""
+    import dataclasses
+    base = TEMPLATES[0]
+    counts = float(10.0 ** np.random.default_rng(600 + k).uniform(np.log10(3e5), np.log10(3e6)))
+    work = dataclasses.replace(base, name=f"d{k}", counts=counts)
+    data = make_data(work, 700 + k)
+    prob = build_problem(work.geometry, data["g"], data["w"], work.n_subsets, work.beta)
+    _, phi, _ = map_reference(prob)
+    return work, data, phi
+
+
+@pytest.mark.parametrize("kind", ["batch", "streams"])
+def test_distinct_requests_reach_their_own_gap(kind):
+    """Requests that share only a shape (each its own phantom, counts and
+    Phi*) all reach the 1e-4 gap against their own Phi* in the mix, reuse
+    pooled slots across different data, and return what the plain path
+    returns."""
+    from paper_2106_03172_gb300.serving import Request, serve_plain
+
+    def reqs():
+        out = []
+        for k, t in enumerate([0.0, 0.0005, 0.001, 0.0015, 0.002, 0.0025, 0.003, 0.0035]):
+            work, data, phi = _distinct(k)
+            out.append(Request(k, work, data["g"], data["w"], phi, arrival=t, seed=980 + k))
+        return out
+
+    srv = SERVERS[kind](budget_bytes=1 << 34, max_slots=3, max_epochs=60)
+    done = srv.serve(reqs())
+    assert all(r.reached and r.gap <= 1e-4 for r in done), [(r.rid, r.gap) for r in done]
+    # at most three slots at a time, all of one key: every later request reuses one
+    assert srv.stats.slots_created <= 3 and srv.stats.slots_reused == len(done) - srv.stats.slots_created
+    for a, b in zip(done, serve_plain(reqs(), max_epochs=60)):
+        assert a.epochs == b.epochs
+        np.testing.assert_array_equal(a.image, b.image)

@@ -112,3 +112,21 @@ def test_batched_and_served_shapes():
     assert [w.name for w in pool][-4:] == ["serve384_0", "serve384_1", "serve512_0", "serve512_1"]
     assert {(w.geometry.nx, w.methods[0], w.n_subsets) for w in pool[-4:]} == {
         (384, "svrem", 21), (384, "saga", 6), (512, "svrem", 6), (512, "saga", 12)}
+
+
+def test_distinct_serving_requests():
+    """The distinct serving stream: request i is workload req<i> with data
+    seed 20000 + i, sizes drawn from all four of 128^2-512^2 with the stated
+    views and bins, counts log-uniform in [1e6, 1e8] and different per
+    request, and a prefix of a longer stream equal to the shorter one."""
+    from paper_2106_03172_gb300.phantoms import serving_requests
+    want = {128: (179, 183), 256: (358, 367), 384: (538, 549), 512: (720, 733)}
+    reqs = serving_requests(40)
+    assert [w.name for w, _ in reqs] == [f"req{i}" for i in range(40)]
+    assert [s for _, s in reqs] == [20000 + i for i in range(40)]
+    assert {w.geometry.nx for w, _ in reqs} == set(want)
+    for w, _ in reqs:
+        assert (w.geometry.n_angles, w.geometry.n_bins) == want[w.geometry.nx]
+        assert 1e6 <= w.counts <= 1e8 and w.n_subsets in (6, 12, 21) and w.methods[0] in ("svrem", "saga")
+    assert len({w.counts for w, _ in reqs}) == 40
+    assert serving_requests(12) == reqs[:12]
