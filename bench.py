@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--recon", type=int, default=20, help="reconstructions per method for the gap metric")
+    ap.add_argument("--recon", type=int, default=200, help="reconstructions per method for the gap metric")
     ap.add_argument("--tuning", default="", help="pin launch shapes 'chunks,run' instead of autotuning")
     ap.add_argument("--requests", type=int, default=1000, help="serve workload: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
@@ -450,7 +450,9 @@ def run_ours(args):
     petvr.pet_warm_start(prob.handle, f0)
     imgs = {m: f0.clone() for m in METHODS}
     states = {m: petvr.State(prob, m, imgs[m]) for m in METHODS}
-    phi = torch.zeros(4, 3, dtype=torch.float64, device="cuda")
+    E = max(1, args.step_epochs)
+    phi = torch.zeros(4, 3, dtype=torch.float64, device="cuda")          # epoch-call steps: the last objectives
+    phi_run = torch.zeros(4, E, 3, dtype=torch.float64, device="cuda")   # run-call steps: every epoch's
     a = alphas(work)
     # nonzeros of one slice's A_t (a stack repeats them on every slice)
     slices = 1 if geom.multiring else geom.nz
@@ -462,7 +464,6 @@ def run_ours(args):
 
     side = {m: torch.cuda.Stream() for m in METHODS}
     batch = petvr.Batch([states[m] for m in METHODS]) if args.batch else None
-    E = max(1, args.step_epochs)
 
     def one_epoch(ep, concurrent=True):
         """One update epoch of each of the four independent reconstructions,
@@ -486,10 +487,34 @@ def run_ours(args):
                 stream.wait_stream(side[m])
         return seqs
 
+    step_seq_cache = {}
+
+    def step_seqs(step):
+        """Each method's subset sequence of a step's E epochs (the epochs'
+        sequences back to back), made before the step is timed."""
+        if step not in step_seq_cache:
+            per_epoch = [seqs_for_step(step * E + e, ns) for e in range(E)]
+            step_seq_cache[step] = [np.concatenate([q[i] for q in per_epoch]) for i in range(4)]
+        return step_seq_cache[step]
+
     def one_step(step, concurrent=True):
-        """One step: E update epochs of each method (epoch indices step*E ...)."""
-        for e in range(E):
-            one_epoch(step * E + e, concurrent)
+        """One step: E update epochs of each method (epoch indices step*E ...),
+        each epoch followed by its objective.  On four streams each method's
+        step is one pet_state_run call (objective after every N_s updates, an
+        objective's forward pass also giving the next anchor's ratios); with
+        --batch, or on one stream, epoch by epoch."""
+        if batch is not None or not concurrent:
+            for e in range(E):
+                one_epoch(step * E + e, concurrent)
+            return
+        seqs = step_seqs(step)
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        for i, m in enumerate(METHODS):
+            side[m].wait_event(fork)
+            states[m].run(seqs[i], alpha=a[m][0], eta=a[m][1], objective_every=ns, phi=phi_run[i], stream=side[m])
+        for m in METHODS:
+            stream.wait_stream(side[m])
 
     def count_step():
         """Subset forward+back pairs of the next step's E epochs (anchor passes
@@ -517,6 +542,7 @@ def run_ours(args):
     clocks.start()
     launches0 = petvr.pet_kernel_launches()
     for k in range(args.steps):
+        step_seqs(args.warmup + k)
         flush.zero_()
         pairs += count_step()
         events[k][0].record(stream)
@@ -529,7 +555,7 @@ def run_ours(args):
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in events]
     total_ms = float(sum(step_ms))
-    phi_host = phi.cpu().numpy()
+    phi_host = (phi if args.batch else phi_run[:, E - 1, :]).cpu().numpy()
     value, total_max, pairs_all = combine_ranks(total_ms, float(pairs), device="cuda")
 
     # ---- profiled pass: per-kernel durations for the roofline (a few epochs, methods one after another)
@@ -619,7 +645,8 @@ def run_ours(args):
 
     # ---- end to end through the public API with host buffers
     img_host = torch.empty(4, geom.n_pixels * geom.nz, dtype=torch.float32).pin_memory()
-    phi_host_buf = torch.empty(4, 3, dtype=torch.float64).pin_memory()
+    phi_step = phi if args.batch else phi_run                     # the step's objectives (every epoch's with run calls)
+    phi_host_buf = torch.empty(phi_step.shape, dtype=torch.float64).pin_memory()
     # The host enqueues step after step (as a pipeline would); each step's
     # events bracket its counts upload, problem update, epochs, objectives and
     # result downloads on the device, and the L2 flush between steps stays
@@ -628,6 +655,7 @@ def run_ours(args):
     e2e_pairs = 0
     e2e_base = (prof_base + n_prof + E - 1) // E
     for k in range(args.steps):
+        step_seqs(e2e_base + k)
         flush.zero_()
         e2e_pairs += count_step()
         s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -637,7 +665,7 @@ def run_ours(args):
         one_step(e2e_base + k)
         for i, m in enumerate(METHODS):
             img_host[i].copy_(imgs[m], non_blocking=True)
-        phi_host_buf.copy_(phi, non_blocking=True)
+        phi_host_buf.copy_(phi_step, non_blocking=True)
         e_ev.record(stream)
         e2e_events.append((s_ev, e_ev))
     torch.cuda.synchronize()

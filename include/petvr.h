@@ -401,6 +401,29 @@ pet_status pet_sem_epoch(pet_state *state, float alpha0, float decay, const int3
 pet_status pet_sagaem_epoch(pet_state *state, float alpha, const int32_t *h_subset_seq, int32_t n_iter,
                             void *stream);
 
+/* n_iter updates of the state's own algorithm with the objective inside:
+ * the updates of the epoch call of that algorithm (the same sequence rules,
+ * anchors and update counter; step alpha_k = alpha / (decay k + 1) for every
+ * algorithm that takes a step, ignored by OSEM; eta used by SVREM and SVRG
+ * only), and, when objective_every > 0, after every objective_every-th update
+ * of this call the objective {Phi, L, R} (§3, Eq. (PET-MAP)) of the
+ * iterate then reached, written to d_phi[3 j], d_phi[3 j + 1], d_phi[3 j + 2]
+ * for the j-th such point (j from 0; device, 3 * floor(n_iter /
+ * objective_every) doubles, owned by the caller).  The results are those of
+ * the epoch calls with pet_state_objective_async between them, bit for bit.
+ *
+ * Where an objective's iterate is the anchor of the next update (SVREM and
+ * SVRG at k mod (eta N_s) == 0, inside this call), that anchor's full-data
+ * ratios g / (A f + w) are the objective's own forward projection: one
+ * forward pass serves both, and the anchor pass starts from its back
+ * projection.  Across calls nothing is shared (the image may change between
+ * calls).  Graph capture as for the epoch calls (keyed also by
+ * objective_every and d_phi).  objective_every < 0, or objective_every > 0
+ * with d_phi null, is refused with PET_ERR_INVALID; eta < 1 for SVREM/SVRG
+ * and non-finite alpha or decay (decay < 0) as in the epoch calls. */
+pet_status pet_state_run(pet_state *state, const int32_t *h_subset_seq, int32_t n_iter, float alpha, float decay,
+                         int32_t eta, int32_t objective_every, double *d_phi, void *stream);
+
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);
 

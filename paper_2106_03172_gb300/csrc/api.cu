@@ -282,17 +282,21 @@ pet_status state_init(pet_state *st, cudaStream_t s) {
 }
 
 // Phi, L, R of d_img into d_phi (3 doubles), using `part` as block-partial scratch.
+// With `ratio_out`, the same forward pass also writes the full-data ratio
+// g / (A f + w) there (subset-major, as ratio_all): the sums are the ones
+// ratio_all forms, so the ratios are bit-identical to a separate ratio_all.
 pet_status objective_enqueue(const pet_problem *p, const float *d_img, double *d_phi, double *part,
-                             cudaStream_t s) {
+                             cudaStream_t s, float *ratio_out = nullptr) {
     const pet_plan *pl = p->plan;
     FwdArgs a = fwd_args(pl, d_img, -1, false);
     a.g = p->d_g;
     a.w = p->d_w;
     a.w_scalar = p->w_scalar;
     a.ll_partials = part;
+    a.out = ratio_out;
     a.status = p->d_status;
     int n_ll = 0;
-    PET_TRY(launch_forward(a, FWD_NONE, true, full_group(pl), s, &n_ll));
+    PET_TRY(launch_forward(a, ratio_out ? FWD_RATIO : FWD_NONE, true, full_group(pl), s, &n_ll));
     return launch_objective_finish(p, d_img, n_ll, part, d_phi, s);
 }
 
@@ -894,11 +898,13 @@ pet_status pet_state_create(const pet_problem *p, int32_t algo, int32_t table_dt
 namespace {
 
 // Anchor pass at f: B_t = A_t^T r_t(f) for every t, into st->B, one forward
-// launch over all rays and one back launch over all subsets (grid.y = t).
-pet_status anchor_pass(pet_state *st, const float *f, float *ratio_full, cudaStream_t s) {
+// launch over all rays (skipped when `ratios_ready`: ratio_full already holds
+// r(f), written by the objective of f) and one back launch over all subsets
+// (grid.y = t).
+pet_status anchor_pass(pet_state *st, const float *f, float *ratio_full, cudaStream_t s, bool ratios_ready = false) {
     const pet_problem *p = st->prob;
     const pet_plan *pl = p->plan;
-    PET_TRY(ratio_all(p, f, ratio_full, s));
+    if (!ratios_ready) PET_TRY(ratio_all(p, f, ratio_full, s));
     BackArgs b = back_args(pl, ratio_full, -1, false);
     b.t0 = 0;
     b.r_view0 = 0;
@@ -973,26 +979,41 @@ pet_status sem_init(pet_state *st, const float *f, cudaStream_t s) {
     return launch_back(b, EPI_SEM_INIT, PET_TABLE_FP32, 1, s, pl->na);
 }
 
-// The whole epoch's launch sequence (anchors where `anchors[i]`), on stream s.
+// The whole launch sequence of n_iter updates (anchors where `anchors[i]`),
+// on stream s.  With every > 0, the objective of the iterate after update i
+// goes to d_phi[3 j .. 3 j + 2], j = (i + 1) / every - 1, whenever every
+// divides i + 1.  An objective whose iterate is the next update's anchor
+// (SVREM, SVRG) writes that anchor's ratios in the same forward pass, and the
+// anchor pass then starts from its back projection.
 pet_status enqueue_epoch(pet_state *st, int algo, int32_t n_iter, const std::vector<uint8_t> &anchors,
-                         cudaStream_t s) {
+                         cudaStream_t s, int every = 0, double *d_phi = nullptr) {
     const pet_plan *pl = st->prob->plan;
     const long long plane = plane_of(pl);
+    const bool anchored = algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG;
+    bool ratios_ready = false;      // st->ratio_full holds the ratios of the next update's input
     return pingpong(st->img, st->alt, plane, n_iter, s, [&](int i, const float *in, float *outp) {
         if (anchors[i] && algo == PET_ALGO_SVREM) {
-            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+            PET_TRY(anchor_pass(st, in, st->ratio_full, s, ratios_ready));
             PET_TRY(launch_svrem_anchor_finish(st->B, pl->ns, plane, pl->nz, in, st->f_anc, st->s_anc, st->s_hat,
                                                !st->s_hat_ready, s));
             st->s_hat_ready = true;
         } else if (anchors[i] && algo == PET_ALGO_SVRG) {
-            PET_TRY(anchor_pass(st, in, st->ratio_full, s));
+            PET_TRY(anchor_pass(st, in, st->ratio_full, s, ratios_ready));
             PET_TRY(launch_svrg_anchor_finish(st->B, pl->ns, plane, pl->nz, pl->d_sens, st->qtil, s));
         }
+        ratios_ready = false;
         if (algo == PET_ALGO_SEM && !st->s_hat_ready) {
             PET_TRY(sem_init(st, in, s));
             st->s_hat_ready = true;
         }
-        return enqueue_update(st, algo, st->d_seq + i, st->d_alpha + i, in, outp, s);
+        PET_TRY(enqueue_update(st, algo, st->d_seq + i, st->d_alpha + i, in, outp, s));
+        if (every > 0 && (i + 1) % every == 0) {
+            const bool share = anchored && i + 1 < n_iter && anchors[i + 1];
+            PET_TRY(objective_enqueue(st->prob, outp, d_phi + 3LL * ((i + 1) / every - 1), st->d_part, s,
+                                      share ? st->ratio_full : nullptr));
+            ratios_ready = share;
+        }
+        return PET_OK;
     });
 }
 
@@ -1046,7 +1067,7 @@ pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_
 }
 
 pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_iter, float alpha0, float decay,
-                        int32_t eta, cudaStream_t s) {
+                        int32_t eta, cudaStream_t s, int32_t every = 0, double *d_phi = nullptr) {
     if (!st) return set_error(PET_ERR_INVALID, "null state");
     if (st->algo != algo) return set_error(PET_ERR_STATE, "state was created for another algorithm");
     const pet_problem *p = st->prob;
@@ -1090,12 +1111,18 @@ pet_status epoch_common(pet_state *st, int algo, const int32_t *seq, int32_t n_i
     // a first SVREM anchor / SEM start also initialises s_hat: that call is enqueued directly
     const bool first = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SEM) && !st->s_hat_ready;
     if (!use_graphs() || profiling_enabled() || first) {
-        rc = enqueue_epoch(st, algo, n_iter, anchors, s);
+        rc = enqueue_epoch(st, algo, n_iter, anchors, s, every, d_phi);
     } else {
         std::vector<int64_t> key = {n_iter, eta};
+        if (every > 0) {                    // objectives inside: a separate graph per output buffer
+            key.push_back(-2);
+            key.push_back(every);
+            key.push_back((int64_t)(intptr_t)d_phi);
+        }
         for (int i = 0; i < n_iter; ++i)
             if (anchors[i]) key.push_back(i);
-        rc = run_graph(st, key, s, [&](cudaStream_t cs) { return enqueue_epoch(st, algo, n_iter, anchors, cs); });
+        rc = run_graph(st, key, s,
+                       [&](cudaStream_t cs) { return enqueue_epoch(st, algo, n_iter, anchors, cs, every, d_phi); });
     }
     if (rc == PET_OK) st->k += n_iter;
     return rc;
@@ -1135,6 +1162,19 @@ pet_status pet_sem_epoch(pet_state *st, float alpha0, float decay, const int32_t
 
 pet_status pet_sagaem_epoch(pet_state *st, float alpha, const int32_t *seq, int32_t n_iter, void *stream) {
     return epoch_common(st, PET_ALGO_SAGAEM, seq, n_iter, alpha, 0.0f, 1, (cudaStream_t)stream);
+}
+
+pet_status pet_state_run(pet_state *st, const int32_t *seq, int32_t n_iter, float alpha, float decay, int32_t eta,
+                         int32_t objective_every, double *d_phi, void *stream) {
+    if (!st) return set_error(PET_ERR_INVALID, "null state");
+    if (objective_every < 0) return set_error(PET_ERR_INVALID, "objective_every must be >= 0");
+    if (objective_every > 0 && !d_phi) return set_error(PET_ERR_INVALID, "null d_phi with objective_every > 0");
+    const int algo = st->algo;
+    // the epoch calls' conventions: OSEM takes no step size, only SVREM and SVRG an anchor period
+    const bool stepped = algo != PET_ALGO_OSEM;
+    return epoch_common(st, algo, seq, n_iter, stepped ? alpha : 0.0f, stepped ? decay : 0.0f,
+                        (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) ? eta : 1, (cudaStream_t)stream,
+                        objective_every, d_phi);
 }
 
 pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream) {

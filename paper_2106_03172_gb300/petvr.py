@@ -95,6 +95,8 @@ _SIGS = {
     "pet_sagaem_epoch": (c_int32, [c_void_p, c_float, c_void_p, c_int32, c_void_p]),
     "pet_state_sync": (c_int32, [c_void_p, c_void_p]),
     "pet_state_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "pet_state_run": (c_int32, [c_void_p, c_void_p, c_int32, c_float, c_float, c_int32, c_int32, c_void_p,
+                                c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
     "pet_last_error": (ctypes.c_char_p, []),
 }
@@ -305,6 +307,17 @@ def pet_sagaem_epoch(state, alpha: float, seq, stream=None):
     _call("pet_sagaem_epoch", state, alpha, arr, n, _stream(stream))
 
 
+def pet_state_run(state, seq, alpha: float = 1.0, decay: float = 0.0, eta: int = 1, objective_every: int = 0,
+                  phi_out: torch.Tensor | None = None, stream=None):
+    """n_iter updates of the state's algorithm with the objective after every
+    ``objective_every``-th update into ``phi_out`` (float64, 3 per point)."""
+    arr, n = _seq(seq)
+    if objective_every > 0 and (phi_out is None or phi_out.numel() < 3 * (n // objective_every)):
+        raise ValueError("phi_out needs 3 float64 per objective point")
+    _call("pet_state_run", state, arr, n, alpha, decay, eta, objective_every,
+          _dev(phi_out, torch.float64), _stream(stream))
+
+
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):
     """Enqueue Phi, L, R of the state's current image into ``phi_out`` (3 float64)."""
     _call("pet_state_objective_async", state, _dev(phi_out, torch.float64), _stream(stream))
@@ -455,6 +468,12 @@ class State:
             pet_saga_epoch(self.handle, alpha, seq, stream)
         else:
             pet_svrg_epoch(self.handle, alpha, eta, seq, stream)
+
+    def run(self, seq, alpha: float = 1.0, eta: int = 1, objective_every: int = 0, phi=None, stream=None,
+            decay: float = 0.0):
+        """The updates of ``epoch`` with the objective after every
+        ``objective_every``-th one written into ``phi`` ([points, 3] float64)."""
+        pet_state_run(self.handle, seq, alpha, decay, eta, objective_every, phi, stream)
 
     def reset(self, stream=None):
         pet_state_reset(self.handle, stream)

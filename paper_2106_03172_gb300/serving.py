@@ -129,7 +129,7 @@ class ServerStats:
     slots_created: int = 0
     slots_reused: int = 0
     slots_released: int = 0
-    epochs_launched: int = 0
+    epochs_launched: int = 0    # request epochs enqueued (a batch counts each member's)
     extra: dict = field(default_factory=dict)
 
 
@@ -314,6 +314,8 @@ class Server(_Base):
                 for s in self.active:
                     s.pos += self.tick
                     ns = s.req.work.n_subsets
+                    if s.pos % ns == 0:
+                        self.stats.epochs_launched += 1
                     if s.pos % ns == 0 and s.pos <= self.max_epochs * ns:   # an epoch of this request ended
                         row = len(checks)
                         s.state.objective_async(self._phi[row], stream=stream)

@@ -108,3 +108,14 @@ def test_noalloc_objective_refuses_bad_arguments(lib):
     for bg in (math.nan, math.inf, -math.inf):
         st, msg = call(*fake, bg=bg)
         assert st == PET_ERR_INVALID and "background" in msg, (bg, msg)
+
+
+def test_state_run_refuses_bad_objective_arguments(lib):
+    """pet_state_run checks objective_every and d_phi before it reads the
+    state; the stand-in handle below is never dereferenced."""
+    from ctypes import c_float
+    fake = c_void_p(0x1000)
+    seq = (ctypes.c_int32 * 2)(0, 0)
+    for every, phi, needle in ((-1, c_void_p(0x2000), "objective_every"), (3, None, "d_phi")):
+        st = lib.pet_state_run(fake, seq, 2, c_float(1.0), c_float(0.0), 1, every, phi, None)
+        assert st == PET_ERR_INVALID and needle in lib.pet_last_error().decode()
