@@ -79,7 +79,7 @@ def parse_args():
     ap.add_argument("--epochs", type=int, default=40, help="converge workload: update epochs per method")
     ap.add_argument("--step-epochs", type=int, default=50,
                     help="update epochs of each method per step (50: the 256^2 configuration's run length)")
-    ap.add_argument("--legs", default="batched,batch64,stack,serve,parity",
+    ap.add_argument("--legs", default="batched,batch64,stack,ring,serve,parity",
                     help="short extra measurements after the headline (comma list, or 'none')")
     return ap.parse_args()
 
@@ -845,6 +845,13 @@ def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, fl
         if "roofline" in sub:
             legs["c128x47"]["roofline_frac"] = sub["roofline"].get("frac")
             legs["c128x47"]["achieved_tflops"] = sub["roofline"].get("achieved")
+    if "ring" in want:
+        sub = _sub_bench(["--workload", "ring2_128", "--steps", "3", "--warmup", "1", "--step-epochs", "2",
+                          "--legs", "none", "--no-cpu-baseline", "--recon", "0"])
+        legs["ring2_128"] = {k: sub.get(k) for k in ("value", "unit", "ms_per_step", "error") if k in sub}
+        if "roofline" in sub:
+            legs["ring2_128"]["roofline_frac"] = sub["roofline"].get("frac")
+            legs["ring2_128"]["achieved_tflops"] = sub["roofline"].get("achieved")
     if "serve" in want:
         sub = _sub_bench(["--workload", "serve", "--requests", "32", "--distinct"])
         leg = {k: sub.get(k) for k in ("value", "unit", "latency", "speedup_vs_plain", "p50_speedup_vs_plain",
