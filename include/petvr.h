@@ -301,8 +301,11 @@ pet_status pet_state_set_preconditioner(pet_state *state, int32_t kind);
  * where anchors fall) and replayed on later calls with the same key, so the
  * first call with a new key costs a capture.  All calls on one state must be
  * ordered on one stream, and a state's first call with a new key should not
- * come while `stream` is itself being captured.  Setting the environment
- * variable PETVR_NO_GRAPHS=1 issues the launches directly instead. */
+ * come while `stream` is itself being captured.  A state (and a batch) keeps
+ * at most 64 captured graphs; past that the least recently launched one is
+ * destroyed (freed by the driver once any launch of it completes).  Setting
+ * the environment variable PETVR_NO_GRAPHS=1 issues the launches directly
+ * instead. */
 pet_status pet_osem_epoch(pet_state *state, const int32_t *h_subset_seq, int32_t n_iter, void *stream);
 pet_status pet_svrem_epoch(pet_state *state, float alpha, int32_t eta, const int32_t *h_subset_seq,
                            int32_t n_iter, void *stream);

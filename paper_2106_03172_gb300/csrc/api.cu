@@ -1025,6 +1025,13 @@ bool use_graphs() {
     return on;
 }
 
+// Executable graphs a state (or a batch) keeps: a caller that passes a new
+// output buffer on every call (the buffer is a kernel argument, so part of
+// the key) would otherwise grow the cache without bound.  The least recently
+// launched graph is destroyed first; one still in flight is freed by the
+// driver once its launch completes.
+constexpr size_t kMaxGraphs = 64;
+
 // Capture `enqueue` once on the state's private stream, cache the executable
 // graph under `key`, and launch it on `s`.
 template <class Enqueue>
@@ -1058,9 +1065,17 @@ pet_status run_graph(pet_state *st, const std::vector<int64_t> &key, cudaStream_
         const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         PET_TRY(cuda_ok(ie, "graph instantiate"));
-        st->graphs.push_back({key, exec, kernels});
+        if (st->graphs.size() >= kMaxGraphs) {
+            auto lru = st->graphs.begin();
+            for (auto it = st->graphs.begin(); it != st->graphs.end(); ++it)
+                if (it->last_use < lru->last_use) lru = it;
+            cudaGraphExecDestroy(lru->exec);
+            st->graphs.erase(lru);
+        }
+        st->graphs.push_back({key, exec, kernels, 0});
         hit = &st->graphs.back();
     }
+    hit->last_use = ++st->graph_tick;
     PET_TRY(cuda_ok(cudaGraphLaunch(hit->exec, s), "graph launch"));
     g_launches.fetch_add(hit->kernels);
     return PET_OK;
@@ -1665,9 +1680,11 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
             pet_state holder{};
             holder.cap = b->cap;
             holder.graphs.swap(b->graphs);
+            holder.graph_tick = b->graph_tick;
             rc = run_graph(&holder, key, s,
                            [&](cudaStream_t cs) { return enqueue_batch_dataflow(b, n_iter, threads, genpot, cs); });
             b->graphs.swap(holder.graphs);
+            b->graph_tick = holder.graph_tick;
             b->cap = holder.cap;
             holder.cap = nullptr;
         }
@@ -1717,8 +1734,10 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
         pet_state holder{};
         holder.cap = b->cap;
         holder.graphs.swap(b->graphs);
+        holder.graph_tick = b->graph_tick;
         rc = run_graph(&holder, key, s, [&](cudaStream_t cs) { return enqueue_batch_epoch(b, n_iter, anchors, cs); });
         b->graphs.swap(holder.graphs);
+        b->graph_tick = holder.graph_tick;
         b->cap = holder.cap;
         holder.cap = nullptr;
     }

@@ -508,8 +508,10 @@ struct pet_state {
         std::vector<int64_t> key;
         cudaGraphExec_t exec;
         uint64_t kernels;           // kernel nodes, counted at capture
+        uint64_t last_use;          // graph_tick of its latest launch
     };
-    std::vector<Graph> graphs;      // captured epochs / objectives
+    std::vector<Graph> graphs;      // captured epochs / objectives, at most kMaxGraphs (least recently used go)
+    uint64_t graph_tick = 0;
     uint64_t graph_version = 0;     // problem version the captured graphs were made with
 };
 
@@ -549,6 +551,7 @@ struct pet_batch {
     int seq_cap = 0;
     cudaStream_t cap = nullptr;
     std::vector<pet_state::Graph> graphs;
+    uint64_t graph_tick = 0;        // LRU clock of `graphs` (kept across the holder swaps)
 };
 
 namespace petvr {

@@ -70,3 +70,26 @@ def test_run_without_objectives_and_bad_arguments():
         sb.run(seq, alpha=0.7, objective_every=ns, phi=torch.zeros(1, 3, dtype=torch.float64, device="cuda"))
     with pytest.raises(pv.PetError):
         sb.run(seq, alpha=0.7, eta=0, objective_every=ns, phi=torch.zeros(2, 3, dtype=torch.float64, device="cuda"))
+
+
+def test_many_output_buffers_evict_graphs_without_changing_results():
+    """Each new output buffer is a new captured graph; past the cache's 64
+    graphs the least recently used are destroyed (some still in flight),
+    and every call still writes what the epoch calls give."""
+    pv, plan, gp, f0, work = _setup("c64")
+    ns = work.n_subsets
+    a, b = f0.clone(), f0.clone()
+    sa, sb = pv.State(gp, "svrg", a), pv.State(gp, "svrg", b)
+    want, got = [], []
+    for j in range(90):
+        seq = np.random.default_rng(300 + j).integers(0, ns, ns)
+        pa = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
+        pb = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
+        sa.epoch(seq, alpha=2.0, eta=2)
+        sa.objective_async(pa[0])
+        sb.run(seq, alpha=2.0, eta=2, objective_every=ns, phi=pb)
+        want.append(pa)
+        got.append(pb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert torch.equal(torch.cat(want), torch.cat(got))
