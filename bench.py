@@ -170,7 +170,7 @@ class ClockSampler:
             os.close(fd)
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.idx)], stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -178,7 +178,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.06)                # one more sample interval, so a short region is not cut short
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -439,6 +439,33 @@ def measure_recon(torch, petvr, prob, states, imgs, work, phi_star: float, n_rec
         out[m] = {"recon_per_s": n_rec / (t0.elapsed_time(t1) / 1e3), "p50_ms": float(np.percentile(lat, 50)),
                   "p99_ms": float(np.percentile(lat, 99)), "epochs_mean": float(np.mean(epochs)),
                   "reached": reached, "n": n_rec, "epochs_in_flight": depth}
+    return out
+
+
+def recon_executor(torch, petvr, prob, work, phi_star: float, n_rec: int, workers: int, max_epochs: int = 60):
+    """The reconstructions of measure_recon (same subset sequences) through
+    the library's executor (pet_run_to_gap): `workers` worker states, each on
+    its own stream, the host's gap check after every epoch done in C++.
+    Latency from a job's start to the host reading its last objective;
+    recon_per_s over the call's wall time."""
+    from paper_2106_03172_gb300.phantoms import subset_sequences
+    ns = work.n_subsets
+    n = work.geometry.n_pixels * work.geometry.nz
+    a = alphas(work)
+    seeds = np.arange(n_rec, dtype=np.uint64)[:, None] * np.uint64(1000) + np.uint64(90000) + \
+        np.arange(max_epochs, dtype=np.uint64)[None, :]
+    seqs = subset_sequences(seeds.ravel(), ns, ns).reshape(n_rec, max_epochs * ns)
+    out = {}
+    for m in METHODS:
+        states = [petvr.State(prob, m, torch.empty(n, device="cuda")) for _ in range(workers)]
+        petvr.pet_run_to_gap(states, seqs[:min(n_rec, 2 * workers)], max_epochs, phi_star, GAP,
+                             alpha=a[m][0], eta=a[m][1])          # graphs captured, streams warm
+        t = time.perf_counter()
+        epochs, gaps, ms = petvr.pet_run_to_gap(states, seqs, max_epochs, phi_star, GAP, alpha=a[m][0], eta=a[m][1])
+        wall = time.perf_counter() - t
+        out[m] = {"recon_per_s": int((gaps <= GAP).sum()) / wall, "p50_ms": float(np.percentile(ms, 50)),
+                  "p99_ms": float(np.percentile(ms, 99)), "epochs_mean": float(np.mean(epochs)),
+                  "reached": int((gaps <= GAP).sum()), "n": n_rec, "workers": workers}
     return out
 
 
@@ -715,9 +742,11 @@ def run_ours(args):
     # epoch after each gap costs throughput)
     recon2 = (measure_recon(torch, petvr, prob, states, imgs, work, phi_star, n_rec=args.recon, depth=2)
               if phi_star is not None and args.recon > 0 else None)
+    recon_ex = ({f"workers_{k}": recon_executor(torch, petvr, prob, work, phi_star, args.recon, k) for k in (1, 8)}
+                if phi_star is not None and args.recon > 0 else None)
     recon_line = {"gap": GAP, "phi_star": phi_star, "phi_star_source": phi_src,
                   "start": "constant image + one unpenalised OSEM epoch (counted in the latency)",
-                  "per_method": recon, "two_epochs_in_flight": recon2}
+                  "per_method": recon, "two_epochs_in_flight": recon2, "executor": recon_ex}
 
     unit = "subset fwd+back projections/s"
     legs = {}

@@ -205,7 +205,9 @@ pet_status pet_problem_update(pet_problem *problem, const float *d_counts, const
 
 /* Warm start (every method of §5.1 starts from one OSEM epoch): write the constant
  * image f_u = sum_m max(g_m - w_m, 0) / sum_n (A^T 1)_n into d_img, then run
- * one unpenalised OSEM epoch in cyclic subset order on it. */
+ * one unpenalised OSEM epoch in cyclic subset order on it.  Its scratch is the
+ * problem's own, so warm starts of one problem must be ordered on one stream
+ * (pet_run_to_gap warm-starts its workers with their states' own scratch). */
 pet_status pet_warm_start(const pet_problem *problem, float *d_img, void *stream);
 
 /* Objective Phi(f) = sum_m (g_m log yhat_m - yhat_m) - beta R(f), with
@@ -426,6 +428,39 @@ pet_status pet_sagaem_epoch(pet_state *state, float alpha, const int32_t *h_subs
  * and non-finite alpha or decay (decay < 0) as in the epoch calls. */
 pet_status pet_state_run(pet_state *state, const int32_t *h_subset_seq, int32_t n_iter, float alpha, float decay,
                          int32_t eta, int32_t objective_every, double *d_phi, void *stream);
+
+/* Executor: n_jobs reconstructions of one problem and method, each run to a
+ * relative objective gap (phi_star - Phi(f)) / |phi_star| <= gap (§5.1, the
+ * paper's convergence measure, with phi_star the caller's reference optimum)
+ * or to max_epochs epochs, up to n_workers at a time.  The workers are
+ * distinct states of one problem and algorithm, each with its own image; each
+ * runs on a CUDA stream of its own that the call creates.  Job j takes the
+ * next free worker: the warm start of pet_warm_start into the worker's image
+ * (with the worker's own scratch), the state's reset (pet_state_reset), then
+ * epochs of the worker's algorithm (the epoch calls' updates, step alpha_k =
+ * alpha / (decay k + 1) where the algorithm takes one, eta for SVREM and
+ * SVRG), the j-th subset sequence h_seqs[j * max_epochs * N_s ...] (host,
+ * max_epochs * N_s indices per job), each epoch followed by its objective,
+ * which the host reads before it launches the job's next epoch or retires it.
+ * The workers start after the work already enqueued on `stream`; the call
+ * returns when every job is done (synchronising).
+ *
+ * Per job (host arrays of n_jobs): h_epochs[j] the epochs run, h_gap[j] the
+ * relative gap after the last one, h_ms[j] the host time from the job's start
+ * (its warm start enqueued) to the host reading its last objective.  With
+ * d_results (device, n_jobs times the image size, or null) each job's final
+ * image is copied there.  A job's results are those of the same warm start,
+ * reset, epoch calls and objective calls on one stream, bit for bit.  SAGA and
+ * SAGA-EM resets fill their tables through the problem's scratch and run one
+ * after another.  Refused with PET_ERR_INVALID before any CUDA call: no or
+ * null workers, workers of different problems or algorithms, repeated workers
+ * or images, n_jobs < 0, max_epochs < 1, null host arrays (n_jobs > 0), a
+ * non-finite or zero phi_star, a negative or non-finite gap, alpha/decay/eta
+ * as in the epoch calls, a subset index outside [0, N_s).  A device-side
+ * numeric error latched meanwhile is returned at the end (PET_ERR_NUMERIC). */
+pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t n_jobs, const int32_t *h_seqs,
+                          int32_t max_epochs, float alpha, float decay, int32_t eta, double phi_star, double gap,
+                          float *d_results, int32_t *h_epochs, double *h_gap, double *h_ms, void *stream);
 
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);

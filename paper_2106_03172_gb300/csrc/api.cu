@@ -1,10 +1,12 @@
 // Host side of the C ABI declared in include/petvr.h: argument checking,
 // geometry tables, object lifetime and the per-update launch sequences.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 
 #include "petvr_internal.cuh"
 
@@ -279,6 +281,24 @@ pet_status state_init(pet_state *st, cudaStream_t s) {
     PET_TRY(launch_back(b, EPI_SAGA_INIT, st->table_dtype, pl->ns, s, pl->max_sub_views));
     return launch_saga_finish(st->table, st->table_dtype, pl->ns, Nz, pl->nz, st->img, pl->d_sens, st->qbar, st->d,
                               s);
+}
+
+// The warm start (a constant image, then one unpenalised OSEM epoch in cyclic
+// subset order) into d_img, with `alt` (the image's size), `ratio` (a subset's
+// rays) and `sums` (nz + 1 doubles; null: the problem's) as scratch: a state's
+// own buffers let states of one problem warm-start on several streams at once.
+pet_status warm_start_into(const pet_problem *p, float *d_img, float *alt, float *ratio, double *sums,
+                           cudaStream_t s) {
+    const pet_plan *pl = p->plan;
+    PET_TRY(launch_uniform_image(p, d_img, s, sums));
+    return pingpong(d_img, alt, plane_of(pl), pl->ns, s, [&](int i, const float *in, float *outp) {
+        PET_TRY(ratio_subset(p, in, i, ratio, s));
+        BackArgs b = back_args(pl, ratio, i, false);
+        b.f = in;
+        b.f_out = outp;
+        b.beta = 0.0f;
+        return launch_back(b, EPI_OSEM, PET_TABLE_FP32, 1, s, pl->max_sub_views);
+    });
 }
 
 // Phi, L, R of d_img into d_phi (3 doubles), using `part` as block-partial scratch.
@@ -773,17 +793,7 @@ pet_status pet_problem_update(pet_problem *p, const float *d_counts, const float
 
 pet_status pet_warm_start(const pet_problem *p, float *d_img, void *stream) {
     if (!p || !d_img) return set_error(PET_ERR_INVALID, "null argument");
-    const pet_plan *pl = p->plan;
-    cudaStream_t s = (cudaStream_t)stream;
-    PET_TRY(launch_uniform_image(p, d_img, s));
-    return pingpong(d_img, p->d_alt, plane_of(pl), pl->ns, s, [&](int i, const float *in, float *outp) {
-        PET_TRY(ratio_subset(p, in, i, p->d_ratio, s));
-        BackArgs b = back_args(pl, p->d_ratio, i, false);
-        b.f = in;
-        b.f_out = outp;
-        b.beta = 0.0f;
-        return launch_back(b, EPI_OSEM, PET_TABLE_FP32, 1, s, pl->max_sub_views);
-    });
+    return warm_start_into(p, d_img, p->d_alt, p->d_ratio, nullptr, (cudaStream_t)stream);
 }
 
 pet_status pet_objective_async(const pet_problem *p, const float *d_img, double *d_phi, void *stream) {
@@ -1201,6 +1211,157 @@ pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream)
     return run_graph(st, key, s, [&](cudaStream_t cs) {
         return objective_enqueue(st->prob, st->img, d_phi, st->d_part, cs);
     });
+}
+
+// ---- executor: many reconstructions to an objective gap ------------------------
+
+pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t n_jobs, const int32_t *h_seqs,
+                          int32_t max_epochs, float alpha, float decay, int32_t eta, double phi_star, double gap,
+                          float *d_results, int32_t *h_epochs, double *h_gap, double *h_ms, void *stream) {
+    if (!workers || n_workers < 1) return set_error(PET_ERR_INVALID, "need at least one worker state");
+    if (n_jobs < 0 || max_epochs < 1) return set_error(PET_ERR_INVALID, "n_jobs must be >= 0 and max_epochs >= 1");
+    if (n_jobs > 0 && (!h_seqs || !h_epochs || !h_gap || !h_ms)) return set_error(PET_ERR_INVALID, "null argument");
+    if (!std::isfinite(phi_star) || phi_star == 0.0 || !std::isfinite(gap) || gap < 0.0)
+        return set_error(PET_ERR_INVALID, "phi_star must be finite and nonzero, gap finite and >= 0");
+    for (int w = 0; w < n_workers; ++w) {
+        if (!workers[w]) return set_error(PET_ERR_INVALID, "null worker state");
+        if (workers[w]->prob != workers[0]->prob || workers[w]->algo != workers[0]->algo)
+            return set_error(PET_ERR_INVALID, "worker states must share one problem and one algorithm");
+        for (int v = 0; v < w; ++v)
+            if (workers[v] == workers[w] || workers[v]->img == workers[w]->img)
+                return set_error(PET_ERR_INVALID, "worker states must be distinct, with distinct images");
+    }
+    const pet_problem *p = workers[0]->prob;
+    const pet_plan *pl = p->plan;
+    const int algo = workers[0]->algo;
+    const bool stepped = algo != PET_ALGO_OSEM;
+    const float a0 = stepped ? alpha : 0.0f, dc = stepped ? decay : 0.0f;
+    const int et = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) ? eta : 1;
+    if (!std::isfinite(a0) || !std::isfinite(dc) || dc < 0.0f)
+        return set_error(PET_ERR_INVALID, "alpha must be finite and decay >= 0");
+    if (et < 1) return set_error(PET_ERR_INVALID, "eta must be >= 1");
+    const long long per_job = (long long)max_epochs * pl->ns;
+    for (long long i = 0; i < (long long)n_jobs * per_job; ++i)
+        if (h_seqs[i] < 0 || h_seqs[i] >= pl->ns)
+            return set_error(PET_ERR_INVALID, "subset index out of range at position " + std::to_string(i));
+    if (n_jobs == 0) return PET_OK;
+
+    using clock = std::chrono::steady_clock;
+    struct Slot {
+        pet_state *st;
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        double *d_phi = nullptr;
+        int job = -1, epoch = 0;
+        clock::time_point t0;
+    };
+    const int n_slots = std::min(n_workers, n_jobs);
+    std::vector<Slot> slots((size_t)n_slots);
+    double *h_phi = nullptr, *d_phi = nullptr;
+    cudaEvent_t entry = nullptr, shared = nullptr;
+    // a SAGA / SAGA-EM state's reset fills its table through the problem's own
+    // full-data ratio buffer: those resets run one after another
+    const bool shared_init = algo == PET_ALGO_SAGA || algo == PET_ALGO_SAGAEM;
+    bool shared_recorded = false;
+    const long long plane = plane_of(pl);
+    pet_status rc = PET_OK;
+    auto cleanup = [&]() {
+        for (Slot &sl : slots) {
+            if (sl.s) cudaStreamSynchronize(sl.s);
+            if (sl.ev) cudaEventDestroy(sl.ev);
+            if (sl.s) cudaStreamDestroy(sl.s);
+        }
+        if (entry) cudaEventDestroy(entry);
+        if (shared) cudaEventDestroy(shared);
+        if (h_phi) cudaFreeHost(h_phi);
+        dfree(d_phi);
+    };
+    auto fail = [&](pet_status st) {
+        cleanup();
+        return st;
+    };
+    if ((rc = cuda_ok(cudaMallocHost(&h_phi, sizeof(double) * 3 * n_slots), "pinned objectives")) != PET_OK)
+        return fail(rc);
+    if ((rc = dalloc(&d_phi, (size_t)3 * n_slots, "objectives")) != PET_OK) return fail(rc);
+    // the workers start after what the caller enqueued on `stream`
+    if ((rc = cuda_ok(cudaEventCreateWithFlags(&entry, cudaEventDisableTiming), "event")) != PET_OK) return fail(rc);
+    if ((rc = cuda_ok(cudaEventRecord(entry, (cudaStream_t)stream), "event record")) != PET_OK) return fail(rc);
+    if ((rc = cuda_ok(cudaEventCreateWithFlags(&shared, cudaEventDisableTiming), "event")) != PET_OK) return fail(rc);
+    for (int w = 0; w < n_slots; ++w) {
+        Slot &sl = slots[(size_t)w];
+        sl.st = workers[w];
+        sl.d_phi = d_phi + 3 * w;
+        if ((rc = cuda_ok(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking), "worker stream")) != PET_OK ||
+            (rc = cuda_ok(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming), "event")) != PET_OK ||
+            (rc = cuda_ok(cudaStreamWaitEvent(sl.s, entry, 0), "stream wait")) != PET_OK)
+            return fail(rc);
+    }
+    // one epoch of slot `w`'s job, its objective, the objective's copy to the host, and the slot's event
+    auto launch_epoch = [&](int w) -> pet_status {
+        Slot &sl = slots[(size_t)w];
+        const int32_t *seq = h_seqs + (long long)sl.job * per_job + (long long)sl.epoch * pl->ns;
+        PET_TRY(epoch_common(sl.st, algo, seq, pl->ns, a0, dc, et, sl.s));
+        PET_TRY(pet_state_objective_async(sl.st, sl.d_phi, sl.s));
+        PET_TRY(cuda_ok(cudaMemcpyAsync(h_phi + 3 * w, sl.d_phi, sizeof(double) * 3, cudaMemcpyDeviceToHost, sl.s),
+                        "objective copy"));
+        return cuda_ok(cudaEventRecord(sl.ev, sl.s), "event record");
+    };
+    int next = 0;
+    // a job starts with the warm start of the worker's image (with the worker's own scratch) and a state reset
+    auto start_job = [&](int w) -> pet_status {
+        Slot &sl = slots[(size_t)w];
+        sl.job = next++;
+        sl.epoch = 0;
+        sl.t0 = clock::now();
+        PET_TRY(warm_start_into(p, sl.st->img, sl.st->alt, sl.st->ratio, sl.st->d_part, sl.s));
+        if (shared_init && shared_recorded) PET_TRY(cuda_ok(cudaStreamWaitEvent(sl.s, shared, 0), "stream wait"));
+        PET_TRY(state_init(sl.st, sl.s));
+        if (shared_init) {
+            PET_TRY(cuda_ok(cudaEventRecord(shared, sl.s), "event record"));
+            shared_recorded = true;
+        }
+        return launch_epoch(w);
+    };
+    int active = 0;
+    for (int w = 0; w < n_slots; ++w) {
+        if ((rc = start_job(w)) != PET_OK) return fail(rc);
+        ++active;
+    }
+    while (active > 0) {
+        bool progressed = false;
+        for (int w = 0; w < n_slots; ++w) {
+            Slot &sl = slots[(size_t)w];
+            if (sl.job < 0) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev);
+            if (q == cudaErrorNotReady) continue;
+            if ((rc = cuda_ok(q, "event query")) != PET_OK) return fail(rc);
+            progressed = true;
+            ++sl.epoch;
+            const double g = (phi_star - h_phi[3 * w]) / std::fabs(phi_star);
+            if (g <= gap || sl.epoch >= max_epochs || !std::isfinite(g)) {
+                const int j = sl.job;
+                h_epochs[j] = sl.epoch;
+                h_gap[j] = g;
+                h_ms[j] = std::chrono::duration<double, std::milli>(clock::now() - sl.t0).count();
+                if (d_results &&
+                    (rc = cuda_ok(cudaMemcpyAsync(d_results + (long long)j * plane, sl.st->img,
+                                                  sizeof(float) * (size_t)plane, cudaMemcpyDeviceToDevice, sl.s),
+                                  "result copy")) != PET_OK)
+                    return fail(rc);
+                sl.job = -1;
+                if (next < n_jobs) {
+                    if ((rc = start_job(w)) != PET_OK) return fail(rc);
+                } else {
+                    --active;
+                }
+            } else if ((rc = launch_epoch(w)) != PET_OK) {
+                return fail(rc);
+            }
+        }
+        if (!progressed) std::this_thread::yield();
+    }
+    cleanup();
+    return read_status(p, (cudaStream_t)stream);
 }
 
 // ---- batches ------------------------------------------------------------------

@@ -293,14 +293,15 @@ pet_status launch_sum_sens(const float *sens_t, float *sens, int ns, int N, cuda
     return check_launch("sum_sens_kernel");
 }
 
-pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s) {
+pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s, double *sums) {
     const pet_plan *pl = p->plan;
+    if (!sums) sums = p->d_scalar + 4;
     uniform_sums_kernel<<<pl->nz + 1, kBlock, 0, s>>>(p->d_g, p->d_w, p->w_scalar, (long long)pl->M, pl->nz,
-                                                     pl->d_sens, pl->N, p->d_scalar + 4);
+                                                     pl->d_sens, pl->N, sums);
     pet_status st = check_launch("uniform_sums_kernel");
     if (st != PET_OK) return st;
     const long long plane = (long long)pl->N * pl->nz;
-    uniform_fill_kernel<<<blocks_for(plane), kBlock, 0, s>>>(img, plane, pl->nz, p->d_scalar + 4);
+    uniform_fill_kernel<<<blocks_for(plane), kBlock, 0, s>>>(img, plane, pl->nz, sums);
     return check_launch("uniform_fill_kernel");
 }
 

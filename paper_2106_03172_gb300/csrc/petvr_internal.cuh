@@ -587,7 +587,9 @@ pet_status launch_back(const BackArgs &a, int epi, int table_dtype, int n_subset
 pet_status launch_permute_sino(const float *src, float *dst, const int *order, int na, int nb, int nz,
                                cudaStream_t s);
 pet_status launch_sum_sens(const float *sens_t, float *sens, int ns, int N, cudaStream_t s);
-pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s);
+// `sums`: nz + 1 doubles of scratch (null: the problem's own, which concurrent
+// warm starts of one problem must not share)
+pet_status launch_uniform_image(const pet_problem *p, float *img, cudaStream_t s, double *sums = nullptr);
 pet_status launch_objective_finish(const pet_problem *p, const float *img, int n_ll_blocks,
                                    double *part, double *d_out, cudaStream_t s);
 pet_status launch_objective_finish_raw(int nx, int ny, int nz, float beta, const float *img, int n_ll_blocks,

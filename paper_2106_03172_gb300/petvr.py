@@ -97,6 +97,8 @@ _SIGS = {
     "pet_state_objective_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pet_state_run": (c_int32, [c_void_p, c_void_p, c_int32, c_float, c_float, c_int32, c_int32, c_void_p,
                                 c_void_p]),
+    "pet_run_to_gap": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_int32, c_float, c_float, c_int32,
+                                 c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
     "pet_last_error": (ctypes.c_char_p, []),
 }
@@ -316,6 +318,24 @@ def pet_state_run(state, seq, alpha: float = 1.0, decay: float = 0.0, eta: int =
         raise ValueError("phi_out needs 3 float64 per objective point")
     _call("pet_state_run", state, arr, n, alpha, decay, eta, objective_every,
           _dev(phi_out, torch.float64), _stream(stream))
+
+
+def pet_run_to_gap(workers, seqs, max_epochs: int, phi_star: float, gap: float = 1e-4, alpha: float = 1.0,
+                   decay: float = 0.0, eta: int = 1, results: torch.Tensor | None = None, stream=None):
+    """Run len(seqs) reconstructions to the gap on the worker States (see the
+    C header).  ``seqs``: int32 array [jobs, max_epochs * N_s].  Returns
+    (epochs, gap, ms) numpy arrays, one entry per job."""
+    import numpy as np
+    q = np.ascontiguousarray(seqs, dtype=np.int32)
+    n_jobs = q.shape[0] if q.ndim == 2 else 0
+    arr = (c_void_p * max(1, len(workers)))(*[w.handle for w in workers])
+    epochs = np.zeros(max(1, n_jobs), dtype=np.int32)
+    gaps = np.zeros(max(1, n_jobs), dtype=np.float64)
+    ms = np.zeros(max(1, n_jobs), dtype=np.float64)
+    _call("pet_run_to_gap", arr, len(workers), n_jobs, c_void_p(q.ctypes.data) if n_jobs else None, max_epochs,
+          alpha, decay, eta, phi_star, gap, _dev(results), c_void_p(epochs.ctypes.data), c_void_p(gaps.ctypes.data),
+          c_void_p(ms.ctypes.data), _stream(stream))
+    return epochs[:n_jobs], gaps[:n_jobs], ms[:n_jobs]
 
 
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):

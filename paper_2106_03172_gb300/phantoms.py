@@ -31,7 +31,7 @@ __all__ = [
     "ellipsoid_stack_phantom", "ellipsoid_solids", "rasterise", "analytic_sinogram",
     "analytic_lor_sinogram", "rasterise_volume", "make_data",
     "splitmix64", "subset_sequence", "batched_workloads", "serving_workloads", "serving_pool",
-    "serving_requests",
+    "serving_requests", "subset_sequences",
 ]
 
 
@@ -382,6 +382,22 @@ def subset_sequence(seed: int, n_subsets: int, length: int) -> np.ndarray:
         raise ValueError("n_subsets must be positive and length nonnegative")
     vals = splitmix64(seed, length)
     return np.array([int(((v >> 11) * n_subsets) >> 53) for v in vals], dtype=np.int32)
+
+
+def subset_sequences(seeds, n_subsets: int, length: int) -> np.ndarray:
+    """``subset_sequence(seed, n_subsets, length)`` for every seed at once, as
+    rows of an int32 array: the same SplitMix64 steps in unsigned 64-bit
+    array arithmetic (products wrap modulo 2^64 as the definition has them)."""
+    if n_subsets <= 0 or length < 0:
+        raise ValueError("n_subsets must be positive and length nonnegative")
+    seeds = np.asarray(seeds, dtype=np.uint64).reshape(-1, 1)
+    steps = np.arange(1, length + 1, dtype=np.uint64).reshape(1, -1)
+    with np.errstate(over="ignore"):
+        z = seeds + steps * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (((z >> np.uint64(11)) * np.uint64(n_subsets)) >> np.uint64(53)).astype(np.int32)
 
 
 def serving_workloads(seed: int, count: int, sizes=(128, 256), prefix: str = "serve") -> list:

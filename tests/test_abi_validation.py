@@ -119,3 +119,27 @@ def test_state_run_refuses_bad_objective_arguments(lib):
     for every, phi, needle in ((-1, c_void_p(0x2000), "objective_every"), (3, None, "d_phi")):
         st = lib.pet_state_run(fake, seq, 2, c_float(1.0), c_float(0.0), 1, every, phi, None)
         assert st == PET_ERR_INVALID and needle in lib.pet_last_error().decode()
+
+
+def test_executor_refuses_bad_arguments_before_reading_states(lib):
+    """pet_run_to_gap's argument checks that come before it reads any worker
+    state (the stand-in handle below is never dereferenced)."""
+    from ctypes import c_double, c_float, c_int32
+    w = (c_void_p * 1)(0x1000)
+    seq = (c_int32 * 4)(0, 0, 0, 0)
+    ep = (c_int32 * 1)()
+    gp = (c_double * 1)()
+    ms = (c_double * 1)()
+
+    def call(workers=w, n_workers=1, n_jobs=1, seqs=seq, max_epochs=2, phi_star=1.0, gap=1e-4, outs=True):
+        o = (ep, gp, ms) if outs else (None, None, None)
+        st = lib.pet_run_to_gap(workers, n_workers, n_jobs, seqs, max_epochs, c_float(1.0), c_float(0.0), 1,
+                                c_double(phi_star), c_double(gap), None, *o, None)
+        return st, lib.pet_last_error().decode()
+
+    for kw, needle in (({"workers": None}, "worker"), ({"n_workers": 0}, "worker"), ({"n_jobs": -1}, "n_jobs"),
+                       ({"max_epochs": 0}, "max_epochs"), ({"seqs": None}, "null"), ({"outs": False}, "null"),
+                       ({"phi_star": 0.0}, "phi_star"), ({"phi_star": float("nan")}, "phi_star"),
+                       ({"gap": -1.0}, "gap"), ({"gap": float("inf")}, "gap")):
+        st, msg = call(**kw)
+        assert st == PET_ERR_INVALID and needle in msg, (kw, msg)

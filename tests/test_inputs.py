@@ -130,3 +130,16 @@ def test_distinct_serving_requests():
         assert 1e6 <= w.counts <= 1e8 and w.n_subsets in (6, 12, 21) and w.methods[0] in ("svrem", "saga")
     assert len({w.counts for w, _ in reqs}) == 40
     assert serving_requests(12) == reqs[:12]
+
+
+def test_subset_sequences_equal_the_scalar_definition():
+    """The array form of the subset sequences gives, row by row, what
+    subset_sequence gives (seeds across the 64-bit range, several subset
+    numbers, the wrap of the state and the products)."""
+    from paper_2106_03172_gb300.phantoms import subset_sequence, subset_sequences
+    seeds = [0, 1, 90000, 2**63 + 5, 2**64 - 1, 123456789]
+    for ns in (1, 6, 21, 1024):
+        rows = subset_sequences(seeds, ns, 50)
+        assert rows.dtype == np.int32 and rows.shape == (len(seeds), 50)
+        for s, row in zip(seeds, rows):
+            assert np.array_equal(row, subset_sequence(s, ns, 50)), (s, ns)
