@@ -462,6 +462,23 @@ pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t 
                           int32_t max_epochs, float alpha, float decay, int32_t eta, double phi_star, double gap,
                           float *d_results, int32_t *h_epochs, double *h_gap, double *h_ms, void *stream);
 
+/* The executor for reconstructions that each have their own state (any
+ * problems, plans and algorithms, e.g. a batch of independent
+ * reconstructions): job j runs on states[j] (which keeps its final image)
+ * with its own subset sequence h_seqs[j] (host, max_epochs * N_s indices of
+ * its plan), step h_alpha[j] / (h_decay[j] k + 1), anchor period h_eta[j]
+ * (as the epoch calls take them) and reference optimum h_phi_star[j], up to
+ * n_streams jobs at a time, each on a stream the call creates; otherwise as
+ * pet_run_to_gap (warm start, reset, epochs with the objective after each
+ * until the gap or max_epochs; outputs h_epochs, h_gap, h_ms per job;
+ * synchronising).  Refused with PET_ERR_INVALID: null arrays, states or
+ * sequences, repeated states or images, n_streams < 1, and the argument
+ * checks of pet_run_to_gap per job. */
+pet_status pet_run_jobs_to_gap(pet_state *const *states, const int32_t *const *h_seqs, const float *h_alpha,
+                               const float *h_decay, const int32_t *h_eta, const double *h_phi_star, int32_t n_jobs,
+                               int32_t n_streams, int32_t max_epochs, double gap, int32_t *h_epochs, double *h_gap,
+                               double *h_ms, void *stream);
+
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);
 

@@ -1215,55 +1215,63 @@ pet_status pet_state_objective_async(pet_state *st, double *d_phi, void *stream)
 
 // ---- executor: many reconstructions to an objective gap ------------------------
 
-pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t n_jobs, const int32_t *h_seqs,
-                          int32_t max_epochs, float alpha, float decay, int32_t eta, double phi_star, double gap,
-                          float *d_results, int32_t *h_epochs, double *h_gap, double *h_ms, void *stream) {
-    if (!workers || n_workers < 1) return set_error(PET_ERR_INVALID, "need at least one worker state");
-    if (n_jobs < 0 || max_epochs < 1) return set_error(PET_ERR_INVALID, "n_jobs must be >= 0 and max_epochs >= 1");
-    if (n_jobs > 0 && (!h_seqs || !h_epochs || !h_gap || !h_ms)) return set_error(PET_ERR_INVALID, "null argument");
-    if (!std::isfinite(phi_star) || phi_star == 0.0 || !std::isfinite(gap) || gap < 0.0)
-        return set_error(PET_ERR_INVALID, "phi_star must be finite and nonzero, gap finite and >= 0");
-    for (int w = 0; w < n_workers; ++w) {
-        if (!workers[w]) return set_error(PET_ERR_INVALID, "null worker state");
-        if (workers[w]->prob != workers[0]->prob || workers[w]->algo != workers[0]->algo)
-            return set_error(PET_ERR_INVALID, "worker states must share one problem and one algorithm");
-        for (int v = 0; v < w; ++v)
-            if (workers[v] == workers[w] || workers[v]->img == workers[w]->img)
-                return set_error(PET_ERR_INVALID, "worker states must be distinct, with distinct images");
-    }
-    const pet_problem *p = workers[0]->prob;
-    const pet_plan *pl = p->plan;
-    const int algo = workers[0]->algo;
-    const bool stepped = algo != PET_ALGO_OSEM;
-    const float a0 = stepped ? alpha : 0.0f, dc = stepped ? decay : 0.0f;
-    const int et = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) ? eta : 1;
-    if (!std::isfinite(a0) || !std::isfinite(dc) || dc < 0.0f)
-        return set_error(PET_ERR_INVALID, "alpha must be finite and decay >= 0");
-    if (et < 1) return set_error(PET_ERR_INVALID, "eta must be >= 1");
-    const long long per_job = (long long)max_epochs * pl->ns;
-    for (long long i = 0; i < (long long)n_jobs * per_job; ++i)
-        if (h_seqs[i] < 0 || h_seqs[i] >= pl->ns)
-            return set_error(PET_ERR_INVALID, "subset index out of range at position " + std::to_string(i));
-    if (n_jobs == 0) return PET_OK;
+}  // extern "C"
 
+namespace petvr {
+namespace {
+
+// One reconstruction of the executor: the state it runs on (a worker's, or
+// its own), its subset sequence (max_epochs * N_s indices), its step and its
+// reference optimum.
+struct GapJob {
+    pet_state *st;
+    const int32_t *seq;
+    float a0, dc;
+    int eta;
+    double phi_star;
+};
+
+// The step conventions of the epoch calls for a state's algorithm, checked.
+pet_status job_steps(int algo, float alpha, float decay, int32_t eta, GapJob &j) {
+    const bool stepped = algo != PET_ALGO_OSEM;
+    j.a0 = stepped ? alpha : 0.0f;
+    j.dc = stepped ? decay : 0.0f;
+    j.eta = (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) ? eta : 1;
+    if (!std::isfinite(j.a0) || !std::isfinite(j.dc) || j.dc < 0.0f)
+        return set_error(PET_ERR_INVALID, "alpha must be finite and decay >= 0");
+    if (j.eta < 1) return set_error(PET_ERR_INVALID, "eta must be >= 1");
+    return PET_OK;
+}
+
+// Runs the jobs to the gap on n_slots streams of its own.  Worker-pool mode
+// (workers non-null): slot w runs its jobs on workers[w] and copies each
+// job's final image to results (when non-null); otherwise each job runs on
+// its own state, which keeps the final image.  The host loop: a job starts
+// with the warm start (the state's own scratch) and the state's reset, then
+// one epoch and its objective at a time, each read back to pinned host memory
+// behind an event; the host polls the events, and after each objective either
+// launches the job's next epoch or records the job and starts the next one on
+// that slot.  Resets that fill a SAGA / SAGA-EM table go through their
+// problem's full-data ratio buffer, so those of one problem are chained by an
+// event.  Synchronising; the slots start after the work enqueued on `caller`.
+pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const *workers, float *results,
+                        int max_epochs, double gap, int32_t *h_epochs, double *h_gap, double *h_ms,
+                        cudaStream_t caller) {
     using clock = std::chrono::steady_clock;
+    const int n_jobs = (int)jobs.size();
     struct Slot {
-        pet_state *st;
+        pet_state *worker = nullptr;
         cudaStream_t s = nullptr;
         cudaEvent_t ev = nullptr;
         double *d_phi = nullptr;
         int job = -1, epoch = 0;
         clock::time_point t0;
     };
-    const int n_slots = std::min(n_workers, n_jobs);
     std::vector<Slot> slots((size_t)n_slots);
+    std::vector<std::pair<const pet_problem *, cudaEvent_t>> chains;    // SAGA / SAGA-EM resets per problem
+    std::vector<const pet_problem *> chained;                           // problems whose chain has an event
     double *h_phi = nullptr, *d_phi = nullptr;
-    cudaEvent_t entry = nullptr, shared = nullptr;
-    // a SAGA / SAGA-EM state's reset fills its table through the problem's own
-    // full-data ratio buffer: those resets run one after another
-    const bool shared_init = algo == PET_ALGO_SAGA || algo == PET_ALGO_SAGAEM;
-    bool shared_recorded = false;
-    const long long plane = plane_of(pl);
+    cudaEvent_t entry = nullptr;
     pet_status rc = PET_OK;
     auto cleanup = [&]() {
         for (Slot &sl : slots) {
@@ -1271,8 +1279,8 @@ pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t 
             if (sl.ev) cudaEventDestroy(sl.ev);
             if (sl.s) cudaStreamDestroy(sl.s);
         }
+        for (auto &c : chains) cudaEventDestroy(c.second);
         if (entry) cudaEventDestroy(entry);
-        if (shared) cudaEventDestroy(shared);
         if (h_phi) cudaFreeHost(h_phi);
         dfree(d_phi);
     };
@@ -1283,43 +1291,52 @@ pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t 
     if ((rc = cuda_ok(cudaMallocHost(&h_phi, sizeof(double) * 3 * n_slots), "pinned objectives")) != PET_OK)
         return fail(rc);
     if ((rc = dalloc(&d_phi, (size_t)3 * n_slots, "objectives")) != PET_OK) return fail(rc);
-    // the workers start after what the caller enqueued on `stream`
     if ((rc = cuda_ok(cudaEventCreateWithFlags(&entry, cudaEventDisableTiming), "event")) != PET_OK) return fail(rc);
-    if ((rc = cuda_ok(cudaEventRecord(entry, (cudaStream_t)stream), "event record")) != PET_OK) return fail(rc);
-    if ((rc = cuda_ok(cudaEventCreateWithFlags(&shared, cudaEventDisableTiming), "event")) != PET_OK) return fail(rc);
+    if ((rc = cuda_ok(cudaEventRecord(entry, caller), "event record")) != PET_OK) return fail(rc);
     for (int w = 0; w < n_slots; ++w) {
         Slot &sl = slots[(size_t)w];
-        sl.st = workers[w];
+        sl.worker = workers ? workers[w] : nullptr;
         sl.d_phi = d_phi + 3 * w;
         if ((rc = cuda_ok(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking), "worker stream")) != PET_OK ||
             (rc = cuda_ok(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming), "event")) != PET_OK ||
             (rc = cuda_ok(cudaStreamWaitEvent(sl.s, entry, 0), "stream wait")) != PET_OK)
             return fail(rc);
     }
-    // one epoch of slot `w`'s job, its objective, the objective's copy to the host, and the slot's event
     auto launch_epoch = [&](int w) -> pet_status {
         Slot &sl = slots[(size_t)w];
-        const int32_t *seq = h_seqs + (long long)sl.job * per_job + (long long)sl.epoch * pl->ns;
-        PET_TRY(epoch_common(sl.st, algo, seq, pl->ns, a0, dc, et, sl.s));
-        PET_TRY(pet_state_objective_async(sl.st, sl.d_phi, sl.s));
+        const GapJob &j = jobs[(size_t)sl.job];
+        const int ns = j.st->prob->plan->ns;
+        PET_TRY(epoch_common(j.st, j.st->algo, j.seq + (long long)sl.epoch * ns, ns, j.a0, j.dc, j.eta, sl.s));
+        PET_TRY(pet_state_objective_async(j.st, sl.d_phi, sl.s));
         PET_TRY(cuda_ok(cudaMemcpyAsync(h_phi + 3 * w, sl.d_phi, sizeof(double) * 3, cudaMemcpyDeviceToHost, sl.s),
                         "objective copy"));
         return cuda_ok(cudaEventRecord(sl.ev, sl.s), "event record");
     };
     int next = 0;
-    // a job starts with the warm start of the worker's image (with the worker's own scratch) and a state reset
     auto start_job = [&](int w) -> pet_status {
         Slot &sl = slots[(size_t)w];
         sl.job = next++;
         sl.epoch = 0;
         sl.t0 = clock::now();
-        PET_TRY(warm_start_into(p, sl.st->img, sl.st->alt, sl.st->ratio, sl.st->d_part, sl.s));
-        if (shared_init && shared_recorded) PET_TRY(cuda_ok(cudaStreamWaitEvent(sl.s, shared, 0), "stream wait"));
-        PET_TRY(state_init(sl.st, sl.s));
-        if (shared_init) {
-            PET_TRY(cuda_ok(cudaEventRecord(shared, sl.s), "event record"));
-            shared_recorded = true;
+        GapJob &j = jobs[(size_t)sl.job];
+        if (sl.worker) j.st = sl.worker;
+        pet_state *st = j.st;
+        const pet_problem *p = st->prob;
+        PET_TRY(warm_start_into(p, st->img, st->alt, st->ratio, st->d_part, sl.s));
+        const bool shared = st->algo == PET_ALGO_SAGA || st->algo == PET_ALGO_SAGAEM;
+        cudaEvent_t chain = nullptr;
+        if (shared) {
+            for (auto &c : chains)
+                if (c.first == p) chain = c.second;
+            if (!chain) {
+                PET_TRY(cuda_ok(cudaEventCreateWithFlags(&chain, cudaEventDisableTiming), "event"));
+                chains.push_back({p, chain});
+            } else {
+                PET_TRY(cuda_ok(cudaStreamWaitEvent(sl.s, chain, 0), "stream wait"));
+            }
         }
+        PET_TRY(state_init(st, sl.s));
+        if (shared) PET_TRY(cuda_ok(cudaEventRecord(chain, sl.s), "event record"));
         return launch_epoch(w);
     };
     int active = 0;
@@ -1337,17 +1354,19 @@ pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t 
             if ((rc = cuda_ok(q, "event query")) != PET_OK) return fail(rc);
             progressed = true;
             ++sl.epoch;
-            const double g = (phi_star - h_phi[3 * w]) / std::fabs(phi_star);
+            const GapJob &j = jobs[(size_t)sl.job];
+            const double g = (j.phi_star - h_phi[3 * w]) / std::fabs(j.phi_star);
             if (g <= gap || sl.epoch >= max_epochs || !std::isfinite(g)) {
-                const int j = sl.job;
-                h_epochs[j] = sl.epoch;
-                h_gap[j] = g;
-                h_ms[j] = std::chrono::duration<double, std::milli>(clock::now() - sl.t0).count();
-                if (d_results &&
-                    (rc = cuda_ok(cudaMemcpyAsync(d_results + (long long)j * plane, sl.st->img,
-                                                  sizeof(float) * (size_t)plane, cudaMemcpyDeviceToDevice, sl.s),
-                                  "result copy")) != PET_OK)
-                    return fail(rc);
+                h_epochs[sl.job] = sl.epoch;
+                h_gap[sl.job] = g;
+                h_ms[sl.job] = std::chrono::duration<double, std::milli>(clock::now() - sl.t0).count();
+                if (sl.worker && results) {
+                    const long long plane = plane_of(j.st->prob->plan);
+                    if ((rc = cuda_ok(cudaMemcpyAsync(results + (long long)sl.job * plane, j.st->img,
+                                                      sizeof(float) * (size_t)plane, cudaMemcpyDeviceToDevice, sl.s),
+                                      "result copy")) != PET_OK)
+                        return fail(rc);
+                }
                 sl.job = -1;
                 if (next < n_jobs) {
                     if ((rc = start_job(w)) != PET_OK) return fail(rc);
@@ -1361,7 +1380,93 @@ pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t 
         if (!progressed) std::this_thread::yield();
     }
     cleanup();
-    return read_status(p, (cudaStream_t)stream);
+    // numeric errors latched by any job's problem
+    for (const GapJob &j : jobs) {
+        bool seen = false;
+        for (const GapJob &i : jobs) {
+            if (&i == &j) break;
+            if (i.st->prob == j.st->prob) seen = true;
+        }
+        if (!seen) PET_TRY(read_status(j.st->prob, caller));
+    }
+    return PET_OK;
+}
+
+pet_status check_gap_args(int32_t n_jobs, int32_t max_epochs, double gap, const void *seqs, const int32_t *h_epochs,
+                          const double *h_gap, const double *h_ms) {
+    if (n_jobs < 0 || max_epochs < 1) return set_error(PET_ERR_INVALID, "n_jobs must be >= 0 and max_epochs >= 1");
+    if (n_jobs > 0 && (!seqs || !h_epochs || !h_gap || !h_ms)) return set_error(PET_ERR_INVALID, "null argument");
+    if (!std::isfinite(gap) || gap < 0.0) return set_error(PET_ERR_INVALID, "gap must be finite and >= 0");
+    return PET_OK;
+}
+
+pet_status check_job_seq(const pet_plan *pl, const int32_t *seq, long long n, long long job) {
+    for (long long i = 0; i < n; ++i)
+        if (seq[i] < 0 || seq[i] >= pl->ns)
+            return set_error(PET_ERR_INVALID, "subset index out of range in job " + std::to_string(job) +
+                                                  " at position " + std::to_string(i));
+    return PET_OK;
+}
+
+}  // namespace
+}  // namespace petvr
+
+extern "C" {
+
+pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t n_jobs, const int32_t *h_seqs,
+                          int32_t max_epochs, float alpha, float decay, int32_t eta, double phi_star, double gap,
+                          float *d_results, int32_t *h_epochs, double *h_gap, double *h_ms, void *stream) {
+    if (!workers || n_workers < 1) return set_error(PET_ERR_INVALID, "need at least one worker state");
+    PET_TRY(check_gap_args(n_jobs, max_epochs, gap, h_seqs, h_epochs, h_gap, h_ms));
+    if (!std::isfinite(phi_star) || phi_star == 0.0)
+        return set_error(PET_ERR_INVALID, "phi_star must be finite and nonzero");
+    for (int w = 0; w < n_workers; ++w) {
+        if (!workers[w]) return set_error(PET_ERR_INVALID, "null worker state");
+        if (workers[w]->prob != workers[0]->prob || workers[w]->algo != workers[0]->algo)
+            return set_error(PET_ERR_INVALID, "worker states must share one problem and one algorithm");
+        for (int v = 0; v < w; ++v)
+            if (workers[v] == workers[w] || workers[v]->img == workers[w]->img)
+                return set_error(PET_ERR_INVALID, "worker states must be distinct, with distinct images");
+    }
+    const pet_plan *pl = workers[0]->prob->plan;
+    GapJob proto{nullptr, nullptr, 0.0f, 0.0f, 1, phi_star};
+    PET_TRY(job_steps(workers[0]->algo, alpha, decay, eta, proto));
+    const long long per_job = (long long)max_epochs * pl->ns;
+    PET_TRY(check_job_seq(pl, h_seqs, (long long)n_jobs * per_job, 0));
+    if (n_jobs == 0) return PET_OK;
+    std::vector<GapJob> jobs((size_t)n_jobs, proto);
+    for (int j = 0; j < n_jobs; ++j) jobs[(size_t)j].seq = h_seqs + (long long)j * per_job;
+    return drive_to_gap(jobs, std::min(n_workers, n_jobs), workers, d_results, max_epochs, gap, h_epochs, h_gap,
+                        h_ms, (cudaStream_t)stream);
+}
+
+pet_status pet_run_jobs_to_gap(pet_state *const *states, const int32_t *const *h_seqs, const float *h_alpha,
+                               const float *h_decay, const int32_t *h_eta, const double *h_phi_star, int32_t n_jobs,
+                               int32_t n_streams, int32_t max_epochs, double gap, int32_t *h_epochs, double *h_gap,
+                               double *h_ms, void *stream) {
+    PET_TRY(check_gap_args(n_jobs, max_epochs, gap, h_seqs, h_epochs, h_gap, h_ms));
+    if (n_streams < 1) return set_error(PET_ERR_INVALID, "n_streams must be >= 1");
+    if (n_jobs > 0 && (!states || !h_alpha || !h_decay || !h_eta || !h_phi_star))
+        return set_error(PET_ERR_INVALID, "null argument");
+    std::vector<GapJob> jobs((size_t)n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        if (!states[j] || !h_seqs[j]) return set_error(PET_ERR_INVALID, "null state or sequence of job " + std::to_string(j));
+        if (!std::isfinite(h_phi_star[j]) || h_phi_star[j] == 0.0)
+            return set_error(PET_ERR_INVALID, "phi_star of job " + std::to_string(j) + " must be finite and nonzero");
+        for (int i = 0; i < j; ++i)
+            if (states[i] == states[j] || states[i]->img == states[j]->img)
+                return set_error(PET_ERR_INVALID, "jobs must have distinct states with distinct images");
+        GapJob &g = jobs[(size_t)j];
+        g.st = states[j];
+        g.seq = h_seqs[j];
+        g.phi_star = h_phi_star[j];
+        PET_TRY(job_steps(states[j]->algo, h_alpha[j], h_decay[j], h_eta[j], g));
+        const pet_plan *pl = states[j]->prob->plan;
+        PET_TRY(check_job_seq(pl, h_seqs[j], (long long)max_epochs * pl->ns, j));
+    }
+    if (n_jobs == 0) return PET_OK;
+    return drive_to_gap(jobs, std::min(n_streams, n_jobs), nullptr, nullptr, max_epochs, gap, h_epochs, h_gap, h_ms,
+                        (cudaStream_t)stream);
 }
 
 // ---- batches ------------------------------------------------------------------

@@ -99,6 +99,8 @@ _SIGS = {
                                 c_void_p]),
     "pet_run_to_gap": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_int32, c_float, c_float, c_int32,
                                  c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pet_run_jobs_to_gap": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                      c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
     "pet_last_error": (ctypes.c_char_p, []),
 }
@@ -336,6 +338,28 @@ def pet_run_to_gap(workers, seqs, max_epochs: int, phi_star: float, gap: float =
           alpha, decay, eta, phi_star, gap, _dev(results), c_void_p(epochs.ctypes.data), c_void_p(gaps.ctypes.data),
           c_void_p(ms.ctypes.data), _stream(stream))
     return epochs[:n_jobs], gaps[:n_jobs], ms[:n_jobs]
+
+
+def pet_run_jobs_to_gap(states, seqs, alphas, etas, phi_stars, max_epochs: int, gap: float = 1e-4,
+                        decays=None, n_streams: int = 8, stream=None):
+    """Run job j on States[j] to the gap (see the C header).  ``seqs[j]``:
+    max_epochs * N_s indices of that state's plan.  Returns (epochs, gap, ms)."""
+    import numpy as np
+    n = len(states)
+    qs = [np.ascontiguousarray(q, dtype=np.int32) for q in seqs]
+    h_states = (c_void_p * max(1, n))(*[st.handle for st in states])
+    h_seqs = (c_void_p * max(1, n))(*[q.ctypes.data for q in qs])
+    a = np.ascontiguousarray(alphas, dtype=np.float32)
+    d = np.ascontiguousarray(decays if decays is not None else [0.0] * n, dtype=np.float32)
+    e = np.ascontiguousarray(etas, dtype=np.int32)
+    ps = np.ascontiguousarray(phi_stars, dtype=np.float64)
+    epochs = np.zeros(max(1, n), dtype=np.int32)
+    gaps = np.zeros(max(1, n), dtype=np.float64)
+    ms = np.zeros(max(1, n), dtype=np.float64)
+    ptr = lambda x: c_void_p(x.ctypes.data)   # noqa: E731
+    _call("pet_run_jobs_to_gap", h_states, h_seqs, ptr(a), ptr(d), ptr(e), ptr(ps), n, n_streams, max_epochs, gap,
+          ptr(epochs), ptr(gaps), ptr(ms), _stream(stream))
+    return epochs[:n], gaps[:n], ms[:n]
 
 
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):

@@ -143,3 +143,26 @@ def test_executor_refuses_bad_arguments_before_reading_states(lib):
                        ({"gap": -1.0}, "gap"), ({"gap": float("inf")}, "gap")):
         st, msg = call(**kw)
         assert st == PET_ERR_INVALID and needle in msg, (kw, msg)
+
+
+def test_jobs_executor_refuses_bad_arguments_before_reading_states(lib):
+    """pet_run_jobs_to_gap's checks before it reads any state."""
+    from ctypes import c_double, c_float, c_int32
+    st = (c_void_p * 1)(0x1000)
+    sq = (c_void_p * 1)(0x2000)
+    a = (c_float * 1)(1.0)
+    d = (c_float * 1)(0.0)
+    e = (c_int32 * 1)(1)
+    ps = (c_double * 1)(1.0)
+    outs = ((c_int32 * 1)(), (c_double * 1)(), (c_double * 1)())
+
+    def call(states=st, seqs=sq, n_jobs=1, n_streams=2, max_epochs=2, gap=1e-4, alpha=a, phi=ps):
+        r = lib.pet_run_jobs_to_gap(states, seqs, alpha, d, e, phi, n_jobs, n_streams, max_epochs, c_double(gap),
+                                    *outs, None)
+        return r, lib.pet_last_error().decode()
+
+    for kw, needle in (({"states": None}, "null"), ({"seqs": None}, "null"), ({"alpha": None}, "null"),
+                       ({"phi": None}, "null"), ({"n_jobs": -1}, "n_jobs"), ({"n_streams": 0}, "n_streams"),
+                       ({"max_epochs": 0}, "max_epochs"), ({"gap": float("nan")}, "gap")):
+        r, msg = call(**kw)
+        assert r == PET_ERR_INVALID and needle in msg, (kw, msg)

@@ -93,3 +93,30 @@ def test_executor_refuses_mixed_or_repeated_workers():
         pv.pet_run_to_gap([s1], seqs + work.n_subsets, 2, 1.0e6)
     e, g, ms = pv.pet_run_to_gap([s1], np.zeros((0, 2 * work.n_subsets), dtype=np.int32), 2, 1.0e6)
     assert len(e) == 0
+
+
+def test_jobs_on_their_own_states_equal_one_job_at_a_time():
+    """pet_run_jobs_to_gap: jobs of different problems, plans and algorithms,
+    each on its own state, up to three at a time; every job gives the epochs,
+    gap and final image of the same calls made one job at a time."""
+    from paper_2106_03172_gb300 import petvr as pv
+    spec = [("c64", "svrem", "fp32", 0.7, 1), ("ragged", "saga", "fp32", 1.0, 1), ("c64", "osem", "fp32", 1.0, 1),
+            ("ragged", "svrg", "fp32", 2.0, 2), ("c64", "sagaem", "fp32", 0.7, 1), ("c64", "saga", "bf16", 1.0, 1),
+            ("ragged", "svrem", "fp32", 0.7, 1)]
+    setups = {name: _setup(name) for name in ("c64", "ragged")}
+    states, seqs, want = [], [], []
+    for k, (name, algo, table, alpha, eta) in enumerate(spec):
+        _, gp, n, work = setups[name]
+        ns = work.n_subsets
+        q = np.random.default_rng(40 + k).integers(0, ns, MAX_EPOCHS * ns).astype(np.int32)
+        seqs.append(q)
+        states.append(pv.State(gp, algo, torch.empty(n, device="cuda"), table=table))
+        want.append(_one_at_a_time(pv, gp, n, algo, table, [q], ns, alpha, eta, 0.0, _phi_star(name))[0])
+    epochs, gaps, ms = pv.pet_run_jobs_to_gap(states, seqs, [s[3] for s in spec], [s[4] for s in spec],
+                                              [_phi_star(s[0]) for s in spec], MAX_EPOCHS, GAP, n_streams=3)
+    for j, (e, g, im) in enumerate(want):
+        assert epochs[j] == e and gaps[j] == g, (j, epochs[j], e, gaps[j], g)
+        assert torch.equal(states[j].img, im), j
+    assert np.all(ms > 0)
+    with pytest.raises(pv.PetError):                 # one state for two jobs
+        pv.pet_run_jobs_to_gap([states[0], states[0]], seqs[:1] * 2, [0.7] * 2, [1] * 2, [1.0e6] * 2, MAX_EPOCHS)
