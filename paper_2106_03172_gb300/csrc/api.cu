@@ -1432,7 +1432,7 @@ pet_status pet_run_to_gap(pet_state *const *workers, int32_t n_workers, int32_t 
     GapJob proto{nullptr, nullptr, 0.0f, 0.0f, 1, phi_star};
     PET_TRY(job_steps(workers[0]->algo, alpha, decay, eta, proto));
     const long long per_job = (long long)max_epochs * pl->ns;
-    PET_TRY(check_job_seq(pl, h_seqs, (long long)n_jobs * per_job, 0));
+    for (int j = 0; j < n_jobs; ++j) PET_TRY(check_job_seq(pl, h_seqs + (long long)j * per_job, per_job, j));
     if (n_jobs == 0) return PET_OK;
     std::vector<GapJob> jobs((size_t)n_jobs, proto);
     for (int j = 0; j < n_jobs; ++j) jobs[(size_t)j].seq = h_seqs + (long long)j * per_job;
