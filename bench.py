@@ -457,7 +457,7 @@ def recon_executor(torch, petvr, prob, work, phi_star: float, n_rec: int, worker
     seqs = subset_sequences(seeds.ravel(), ns, ns).reshape(n_rec, max_epochs * ns)
     out = {}
     for m in METHODS:
-        states = [petvr.State(prob, m, torch.empty(n, device="cuda")) for _ in range(workers)]
+        states = [petvr.State(prob, m, torch.zeros(n, device="cuda")) for _ in range(workers)]
         petvr.pet_run_to_gap(states, seqs[:min(n_rec, 2 * workers)], max_epochs, phi_star, GAP,
                              alpha=a[m][0], eta=a[m][1])          # graphs captured, streams warm
         t = time.perf_counter()
@@ -924,6 +924,8 @@ def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, fl
                                        "bit_identical_to_plain", "error") if k in sub}
         if "plain" in sub:
             leg["plain_latency"] = sub["plain"]["latency"]
+        if "native_loop" in sub:
+            leg["native_loop_latency"] = sub["native_loop"]["latency"]
         if "config" in sub:
             leg["requests"] = sub["config"].get("workload")
         legs["serve_distinct96"] = leg
@@ -1125,7 +1127,7 @@ def batch64_executor(torch, petvr, works, datas, phis, plain, max_epochs, n_stre
         plan = tuned_plan(w)
         prob = petvr.Problem(plan, torch.from_numpy(np.ascontiguousarray(d["g"]).ravel()).cuda(), None, d["w"],
                              w.beta)
-        st = petvr.State(prob, "saga", torch.empty(w.geometry.n_pixels, device="cuda"), table="bf16")
+        st = petvr.State(prob, "saga", torch.zeros(w.geometry.n_pixels, device="cuda"), table="bf16")
         keep.append((plan, prob))
         states.append(st)
         seqs.append(subset_sequence(9000 + i, w.n_subsets, max_epochs * w.n_subsets))
@@ -1172,7 +1174,7 @@ def run_serve(args):
     from paper_2106_03172_gb300 import petvr
     from paper_2106_03172_gb300.phantoms import make_data, serving_pool, serving_requests
     from paper_2106_03172_gb300.serving import (Request, Server, StreamServer, latency_summary, per_template,
-                                                serve_plain)
+                                                serve_native, serve_plain)
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     _build.build()
@@ -1246,11 +1248,14 @@ def run_serve(args):
         del srv
     srv, done, clk, launches = runs[args.server]
     summ = latency_summary(done)
+    # the same stream through the library's own host loop (pet_serve_jobs)
+    native_done = serve_native(requests(), gap=GAP, max_epochs=args.max_epochs, n_streams=64)
+    native = latency_summary(native_done)
     # the same stream through the plain per-reconstruction path, one request at a time
     plain = serve_plain(requests(), gap=GAP, max_epochs=args.max_epochs)
     plain_summ = latency_summary(plain)
     same = all(a.epochs == b.epochs and np.array_equal(a.image, b.image)
-               for _, d, _, _ in runs.values() for a, b in zip(d, plain))
+               for d in [r[1] for r in runs.values()] + [native_done] for a, b in zip(d, plain))
     sizes = sorted({w.geometry.nx for w, _, _ in pool})
     other = [k for k in order if k != args.server][0]
     o_srv, o_done, _, _ = runs[other]
@@ -1279,6 +1284,8 @@ def run_serve(args):
         "bit_identical_to_plain": bool(same),
         "server_stats": _server_stats(srv),
         "other_server": {"server": other, "latency": latency_summary(o_done), "stats": _server_stats(o_srv)},
+        "native_loop": {"latency": native, "how": "pet_serve_jobs: the requests' problems and states made up front, "
+                        "then the library's C++ loop starts each once it has arrived and one of 64 streams is free"},
     }
     print(json.dumps(line), flush=True)
     return 0

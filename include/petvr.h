@@ -479,6 +479,19 @@ pet_status pet_run_jobs_to_gap(pet_state *const *states, const int32_t *const *h
                                int32_t n_streams, int32_t max_epochs, double gap, int32_t *h_epochs, double *h_gap,
                                double *h_ms, void *stream);
 
+/* pet_run_jobs_to_gap for jobs that arrive over time: job j may start only
+ * once h_arrival_s[j] seconds (finite, >= 0, nondecreasing in j) have passed
+ * since the call, and jobs start in index order on the first free stream.
+ * Outputs per job: h_epochs, h_gap as above, and h_start_ms[j], h_done_ms[j]:
+ * when it started and when the host read its last objective, in milliseconds
+ * since the call (its latency is h_done_ms[j] - 1000 h_arrival_s[j]).  The host
+ * loop waits for arrivals by spinning.  Argument errors as for
+ * pet_run_jobs_to_gap, and bad arrival times, with PET_ERR_INVALID. */
+pet_status pet_serve_jobs(pet_state *const *states, const int32_t *const *h_seqs, const float *h_alpha,
+                          const float *h_decay, const int32_t *h_eta, const double *h_phi_star,
+                          const double *h_arrival_s, int32_t n_jobs, int32_t n_streams, int32_t max_epochs, double gap,
+                          int32_t *h_epochs, double *h_gap, double *h_start_ms, double *h_done_ms, void *stream);
+
 /* Synchronise `stream` and return any latched device-side error. */
 pet_status pet_state_sync(pet_state *state, void *stream);
 

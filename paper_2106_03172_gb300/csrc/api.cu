@@ -1256,9 +1256,16 @@ pet_status job_steps(int algo, float alpha, float decay, int32_t eta, GapJob &j)
 // event.  Synchronising; the slots start after the work enqueued on `caller`.
 pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const *workers, float *results,
                         int max_epochs, double gap, int32_t *h_epochs, double *h_gap, double *h_ms,
-                        cudaStream_t caller) {
+                        cudaStream_t caller, const double *arrival_s = nullptr, double *h_start_ms = nullptr,
+                        double *h_done_ms = nullptr) {
     using clock = std::chrono::steady_clock;
     const int n_jobs = (int)jobs.size();
+    const clock::time_point t_call = clock::now();
+    auto since_call_ms = [&](clock::time_point t) {
+        return std::chrono::duration<double, std::milli>(t - t_call).count();
+    };
+    // arrival_s: job j may start only once arrival_s[j] seconds have passed since the call (nondecreasing)
+    auto arrived = [&](int j) { return !arrival_s || since_call_ms(clock::now()) >= 1e3 * arrival_s[j]; };
     struct Slot {
         pet_state *worker = nullptr;
         cudaStream_t s = nullptr;
@@ -1318,6 +1325,7 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
         sl.job = next++;
         sl.epoch = 0;
         sl.t0 = clock::now();
+        if (h_start_ms) h_start_ms[sl.job] = since_call_ms(sl.t0);
         GapJob &j = jobs[(size_t)sl.job];
         if (sl.worker) j.st = sl.worker;
         pet_state *st = j.st;
@@ -1340,12 +1348,15 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
         return launch_epoch(w);
     };
     int active = 0;
-    for (int w = 0; w < n_slots; ++w) {
-        if ((rc = start_job(w)) != PET_OK) return fail(rc);
-        ++active;
-    }
-    while (active > 0) {
+    while (active > 0 || next < n_jobs) {
         bool progressed = false;
+        // free slots take the jobs that have arrived, in order
+        for (int w = 0; w < n_slots && next < n_jobs; ++w) {
+            if (slots[(size_t)w].job >= 0 || !arrived(next)) continue;
+            if ((rc = start_job(w)) != PET_OK) return fail(rc);
+            ++active;
+            progressed = true;
+        }
         for (int w = 0; w < n_slots; ++w) {
             Slot &sl = slots[(size_t)w];
             if (sl.job < 0) continue;
@@ -1357,9 +1368,11 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
             const GapJob &j = jobs[(size_t)sl.job];
             const double g = (j.phi_star - h_phi[3 * w]) / std::fabs(j.phi_star);
             if (g <= gap || sl.epoch >= max_epochs || !std::isfinite(g)) {
+                const clock::time_point t_done = clock::now();
                 h_epochs[sl.job] = sl.epoch;
                 h_gap[sl.job] = g;
-                h_ms[sl.job] = std::chrono::duration<double, std::milli>(clock::now() - sl.t0).count();
+                h_ms[sl.job] = std::chrono::duration<double, std::milli>(t_done - sl.t0).count();
+                if (h_done_ms) h_done_ms[sl.job] = since_call_ms(t_done);
                 if (sl.worker && results) {
                     const long long plane = plane_of(j.st->prob->plan);
                     if ((rc = cuda_ok(cudaMemcpyAsync(results + (long long)sl.job * plane, j.st->img,
@@ -1368,10 +1381,10 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
                         return fail(rc);
                 }
                 sl.job = -1;
-                if (next < n_jobs) {
+                --active;
+                if (next < n_jobs && arrived(next)) {
                     if ((rc = start_job(w)) != PET_OK) return fail(rc);
-                } else {
-                    --active;
+                    ++active;
                 }
             } else if ((rc = launch_epoch(w)) != PET_OK) {
                 return fail(rc);
@@ -1467,6 +1480,40 @@ pet_status pet_run_jobs_to_gap(pet_state *const *states, const int32_t *const *h
     if (n_jobs == 0) return PET_OK;
     return drive_to_gap(jobs, std::min(n_streams, n_jobs), nullptr, nullptr, max_epochs, gap, h_epochs, h_gap, h_ms,
                         (cudaStream_t)stream);
+}
+
+pet_status pet_serve_jobs(pet_state *const *states, const int32_t *const *h_seqs, const float *h_alpha,
+                          const float *h_decay, const int32_t *h_eta, const double *h_phi_star,
+                          const double *h_arrival_s, int32_t n_jobs, int32_t n_streams, int32_t max_epochs, double gap,
+                          int32_t *h_epochs, double *h_gap, double *h_start_ms, double *h_done_ms, void *stream) {
+    if (n_jobs > 0 && (!h_arrival_s || !h_start_ms || !h_done_ms)) return set_error(PET_ERR_INVALID, "null argument");
+    for (int j = 0; j < n_jobs; ++j)
+        if (!std::isfinite(h_arrival_s[j]) || h_arrival_s[j] < 0.0 || (j > 0 && h_arrival_s[j] < h_arrival_s[j - 1]))
+            return set_error(PET_ERR_INVALID, "arrival times must be finite, >= 0 and nondecreasing");
+    std::vector<double> ms((size_t)std::max(1, (int)n_jobs));
+    PET_TRY(check_gap_args(n_jobs, max_epochs, gap, h_seqs, h_epochs, h_gap, ms.data()));
+    if (n_streams < 1) return set_error(PET_ERR_INVALID, "n_streams must be >= 1");
+    if (n_jobs > 0 && (!states || !h_alpha || !h_decay || !h_eta || !h_phi_star))
+        return set_error(PET_ERR_INVALID, "null argument");
+    std::vector<GapJob> jobs((size_t)n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        if (!states[j] || !h_seqs[j]) return set_error(PET_ERR_INVALID, "null state or sequence of job " + std::to_string(j));
+        if (!std::isfinite(h_phi_star[j]) || h_phi_star[j] == 0.0)
+            return set_error(PET_ERR_INVALID, "phi_star of job " + std::to_string(j) + " must be finite and nonzero");
+        for (int i = 0; i < j; ++i)
+            if (states[i] == states[j] || states[i]->img == states[j]->img)
+                return set_error(PET_ERR_INVALID, "jobs must have distinct states with distinct images");
+        GapJob &g = jobs[(size_t)j];
+        g.st = states[j];
+        g.seq = h_seqs[j];
+        g.phi_star = h_phi_star[j];
+        PET_TRY(job_steps(states[j]->algo, h_alpha[j], h_decay[j], h_eta[j], g));
+        const pet_plan *pl = states[j]->prob->plan;
+        PET_TRY(check_job_seq(pl, h_seqs[j], (long long)max_epochs * pl->ns, j));
+    }
+    if (n_jobs == 0) return PET_OK;
+    return drive_to_gap(jobs, std::min(n_streams, n_jobs), nullptr, nullptr, max_epochs, gap, h_epochs, h_gap,
+                        ms.data(), (cudaStream_t)stream, h_arrival_s, h_start_ms, h_done_ms);
 }
 
 // ---- batches ------------------------------------------------------------------

@@ -101,6 +101,8 @@ _SIGS = {
                                  c_double, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pet_run_jobs_to_gap": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                       c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pet_serve_jobs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                 c_int32, c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
     "pet_last_error": (ctypes.c_char_p, []),
 }
@@ -360,6 +362,30 @@ def pet_run_jobs_to_gap(states, seqs, alphas, etas, phi_stars, max_epochs: int, 
     _call("pet_run_jobs_to_gap", h_states, h_seqs, ptr(a), ptr(d), ptr(e), ptr(ps), n, n_streams, max_epochs, gap,
           ptr(epochs), ptr(gaps), ptr(ms), _stream(stream))
     return epochs[:n], gaps[:n], ms[:n]
+
+
+def pet_serve_jobs(states, seqs, alphas, etas, phi_stars, arrivals_s, max_epochs: int, gap: float = 1e-4,
+                   decays=None, n_streams: int = 8, stream=None):
+    """Jobs that arrive over time (see the C header).  Returns (epochs, gap,
+    start_ms, done_ms), times in milliseconds since the call."""
+    import numpy as np
+    n = len(states)
+    qs = [np.ascontiguousarray(q, dtype=np.int32) for q in seqs]
+    h_states = (c_void_p * max(1, n))(*[st.handle for st in states])
+    h_seqs = (c_void_p * max(1, n))(*[q.ctypes.data for q in qs])
+    a = np.ascontiguousarray(alphas, dtype=np.float32)
+    d = np.ascontiguousarray(decays if decays is not None else [0.0] * n, dtype=np.float32)
+    e = np.ascontiguousarray(etas, dtype=np.int32)
+    ps = np.ascontiguousarray(phi_stars, dtype=np.float64)
+    arr = np.ascontiguousarray(arrivals_s, dtype=np.float64)
+    epochs = np.zeros(max(1, n), dtype=np.int32)
+    gaps = np.zeros(max(1, n), dtype=np.float64)
+    t_start = np.zeros(max(1, n), dtype=np.float64)
+    t_done = np.zeros(max(1, n), dtype=np.float64)
+    ptr = lambda x: c_void_p(x.ctypes.data)   # noqa: E731
+    _call("pet_serve_jobs", h_states, h_seqs, ptr(a), ptr(d), ptr(e), ptr(ps), ptr(arr), n, n_streams, max_epochs,
+          gap, ptr(epochs), ptr(gaps), ptr(t_start), ptr(t_done), _stream(stream))
+    return epochs[:n], gaps[:n], t_start[:n], t_done[:n]
 
 
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):

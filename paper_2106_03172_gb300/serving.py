@@ -450,6 +450,39 @@ class StreamServer(_Base):
         return requests
 
 
+def serve_native(requests, gap: float = 1e-4, max_epochs: int = 60, n_streams: int = 64):
+    """The stream server's policy with the host loop in the library
+    (pet_serve_jobs): every request gets its own problem and state up front
+    (no memory budget: admission is limited by the streams alone), then the
+    library starts each request once it has arrived and a stream is free, runs
+    its epochs with the objective after each, and retires it at the gap or at
+    max_epochs, from C++.  A request's subset sequence, launch shapes and
+    result are those of the other paths."""
+    reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+    plans, keep, states, seqs = {}, [], [], []
+    for r in reqs:
+        key = _Base._plan_key(r.work)
+        if key not in plans:
+            plans[key] = tuned_plan(r.work)
+        counts = torch.from_numpy(np.ascontiguousarray(r.counts, dtype=np.float32).ravel()).cuda()
+        problem = petvr.Problem(plans[key], counts, None, r.w, r.work.beta)
+        state = petvr.State(problem, r.algo, torch.zeros(r.work.geometry.n_pixels, device="cuda"),
+                            table=_table(r.algo))
+        keep.append(problem)
+        states.append(state)
+        seqs.append(subset_sequence(r.seed, r.work.n_subsets, max_epochs * r.work.n_subsets))
+    torch.cuda.synchronize()
+    epochs, gaps, t_start, t_done = petvr.pet_serve_jobs(
+        states, seqs, [STEP[r.algo][0] for r in reqs], [STEP[r.algo][1] for r in reqs],
+        [r.phi_star for r in reqs], [r.arrival for r in reqs], max_epochs, gap, n_streams=n_streams)
+    for r, st, e, g, t0, t1 in zip(reqs, states, epochs, gaps, t_start, t_done):
+        r.epochs, r.gap = int(e), float(g)
+        r.reached = r.gap <= gap
+        r.admitted, r.done = float(t0) / 1e3, float(t1) / 1e3
+        r.image = st.img.cpu().numpy()
+    return requests
+
+
 def serve_plain(requests, gap: float = 1e-4, max_epochs: int = 60, clock=time.perf_counter):
     """The plain per-reconstruction path, for comparison with the servers:
     requests are taken in arrival order, one at a time, each run epoch by

@@ -160,3 +160,24 @@ def test_distinct_requests_reach_their_own_gap(kind):
     for a, b in zip(done, serve_plain(reqs(), max_epochs=60)):
         assert a.epochs == b.epochs
         np.testing.assert_array_equal(a.image, b.image)
+
+
+def test_native_loop_gives_the_plain_results():
+    """serve_native (the library's arrival-gated host loop, pet_serve_jobs)
+    returns, request by request, the epochs and images of the plain path,
+    and starts no request before its arrival."""
+    from paper_2106_03172_gb300.serving import Request, serve_native, serve_plain
+
+    def reqs():
+        out = []
+        for k, t in enumerate([0.0, 0.0005, 0.001, 0.02, 0.021, 0.05]):
+            work, data, phi = _template(k % len(TEMPLATES))
+            out.append(Request(k, work, data["g"], data["w"], phi, arrival=t, seed=990 + k))
+        return out
+
+    native = serve_native(reqs(), max_epochs=40, n_streams=3)
+    plain = serve_plain(reqs(), max_epochs=40)
+    for a, b in zip(native, plain):
+        assert a.epochs == b.epochs and a.reached == b.reached
+        np.testing.assert_array_equal(a.image, b.image)
+        assert a.admitted >= a.arrival and a.done > a.admitted
