@@ -618,6 +618,40 @@ def run_ours(args):
     phi_host = (phi if args.batch else phi_run[:, E - 1, :]).cpu().numpy()
     value, total_max, pairs_all = combine_ranks(total_ms, float(pairs), device="cuda")
 
+    # ---- where a step's time goes (after the timed region): each method's step alone on the GPU, then the
+    # four together with an event at the end of each method's stream
+    breakdown = None
+    if batch is None:
+        b0 = args.warmup + args.steps
+        alone = {}
+        seqs = step_seqs(b0)
+        for i, m in enumerate(METHODS):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            states[m].run(seqs[i], alpha=a[m][0], eta=a[m][1], objective_every=ns, phi=phi_run[i], stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            alone[m] = e0.elapsed_time(e1)
+        count_step()
+        seqs = step_seqs(b0 + 1)
+        flush.zero_()
+        fork = torch.cuda.Event(enable_timing=True)
+        fork.record(stream)
+        ends = {}
+        for i, m in enumerate(METHODS):
+            side[m].wait_event(fork)
+            states[m].run(seqs[i], alpha=a[m][0], eta=a[m][1], objective_every=ns, phi=phi_run[i], stream=side[m])
+            ends[m] = torch.cuda.Event(enable_timing=True)
+            ends[m].record(side[m])
+        for m in METHODS:
+            stream.wait_stream(side[m])
+        torch.cuda.synchronize()
+        count_step()
+        breakdown = {"alone_ms": alone, "together_end_ms": {m: fork.elapsed_time(ends[m]) for m in METHODS},
+                     "how": "one step of each method's run call alone on the GPU, then one step of all four on "
+                            "their streams with an event at the end of each (after the timed region)"}
+
     # ---- profiled pass: per-kernel durations for the roofline (a few epochs, methods one after another)
     n_prof = min(E, 4)
     fk, bk = (("ring_forward_kernel", "ring_back_column_kernel" if geom.nz <= 8 else "ring_back_kernel")
@@ -766,6 +800,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": roofline,
+        "step_breakdown": breakdown,
         "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "recon": recon_line,
         "objective_last_step": [float(x) for x in phi_host[:, 0]],
