@@ -485,7 +485,8 @@ pet_status pet_run_jobs_to_gap(pet_state *const *states, const int32_t *const *h
  * Outputs per job: h_epochs, h_gap as above, and h_start_ms[j], h_done_ms[j]:
  * when it started and when the host read its last objective, in milliseconds
  * since the call (its latency is h_done_ms[j] - 1000 h_arrival_s[j]).  The host
- * loop waits for arrivals by spinning.  Argument errors as for
+ * loop sleeps while no job runs and the next is more than 2 ms away, and spins
+ * otherwise.  Argument errors as for
  * pet_run_jobs_to_gap, and bad arrival times, with PET_ERR_INVALID. */
 pet_status pet_serve_jobs(pet_state *const *states, const int32_t *const *h_seqs, const float *h_alpha,
                           const float *h_decay, const int32_t *h_eta, const double *h_phi_star,

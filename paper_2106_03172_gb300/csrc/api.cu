@@ -1390,7 +1390,15 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
                 return fail(rc);
             }
         }
-        if (!progressed) std::this_thread::yield();
+        if (!progressed) {
+            // nothing running and the next job far off: sleep until shortly before it arrives
+            const double ahead_ms = (active == 0 && next < n_jobs && arrival_s)
+                                        ? 1e3 * arrival_s[next] - since_call_ms(clock::now()) : 0.0;
+            if (ahead_ms > 2.0)
+                std::this_thread::sleep_for(std::chrono::microseconds((long long)(1e3 * (ahead_ms - 1.0))));
+            else
+                std::this_thread::yield();
+        }
     }
     cleanup();
     // numeric errors latched by any job's problem
