@@ -1284,7 +1284,8 @@ def run_serve(args):
     srv, done, clk, launches = runs[args.server]
     summ = latency_summary(done)
     # the same stream through the library's own host loop (pet_serve_jobs)
-    native_done = serve_native(requests(), gap=GAP, max_epochs=args.max_epochs, n_streams=64)
+    native_done, native_stats = serve_native(requests(), gap=GAP, max_epochs=args.max_epochs, n_streams=64,
+                                             budget_bytes=budget)
     native = latency_summary(native_done)
     # the same stream through the plain per-reconstruction path, one request at a time
     plain = serve_plain(requests(), gap=GAP, max_epochs=args.max_epochs)
@@ -1319,8 +1320,9 @@ def run_serve(args):
         "bit_identical_to_plain": bool(same),
         "server_stats": _server_stats(srv),
         "other_server": {"server": other, "latency": latency_summary(o_done), "stats": _server_stats(o_srv)},
-        "native_loop": {"latency": native, "how": "pet_serve_jobs: the requests' problems and states made up front, "
-                        "then the library's C++ loop starts each once it has arrived and one of 64 streams is free"},
+        "native_loop": {"latency": native, "stats": native_stats,
+                        "how": "pet_serve_requests: the whole loop in C++, each request admitted once it has arrived, "
+                               "one of 64 streams is free and its slot fits the same device-memory budget"},
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -488,6 +488,53 @@ pet_status pet_run_jobs_to_gap(pet_state *const *states, const int32_t *const *h
  * loop sleeps while no job runs and the next is more than 2 ms away, and spins
  * otherwise.  Argument errors as for
  * pet_run_jobs_to_gap, and bad arrival times, with PET_ERR_INVALID. */
+/* A request of pet_serve_requests (host data; the plan is the caller's). */
+typedef struct {
+    const pet_plan *plan;
+    const float *h_counts;   /* host float32 counts, the plan's sinogram layout (as pet_problem_create) */
+    float bg;                /* uniform background per bin */
+    pet_penalty penalty;
+    int32_t algo, table_dtype;
+    const int32_t *h_seq;    /* max_epochs * N_s subset indices of the plan */
+    float alpha, decay;      /* step alpha / (decay k + 1), as the epoch calls take it */
+    int32_t eta;             /* SVREM / SVRG anchor period */
+    double phi_star;         /* reference optimum of the request's objective */
+    double arrival_s;        /* seconds after the call; nondecreasing over the requests */
+    float *h_image;          /* host, the plan's image size: the result; or null */
+} pet_request;
+
+/* What pet_serve_requests did with its device-memory budget. */
+typedef struct {
+    size_t peak_bytes;       /* most bytes its slots held at once */
+    int32_t slots_created, slots_reused, slots_evicted, admissions_deferred;
+} pet_serve_stats;
+
+/* A request stream served to the objective gap with admission by a device
+ * memory budget, the whole loop in C++: request j is admitted once
+ * arrival_s seconds have passed since the call, a stream of the n_streams the
+ * call creates is free, and a slot fits the budget; a slot is a problem
+ * (pet_problem_create on the request's counts, uploaded through a staging
+ * buffer), a state (pet_state_create) and an image, and is kept after the
+ * request ends for the next request of the same plan, algorithm, table and
+ * penalty (pet_problem_update with the new counts and background), or freed,
+ * least recently used first, when an admission needs its bytes.  A slot's
+ * bytes are pet_problem_bytes + pet_plan_state_bytes + its staging and image.
+ * While the next request does not fit, it and those after it wait (in order)
+ * for a running request to end.  Each request then runs as a job of
+ * pet_serve_jobs (warm start, reset, epochs with the objective after each,
+ * until the gap or max_epochs) and its final image is copied to h_image.
+ * Outputs per request: h_epochs, h_gap, h_start_ms, h_done_ms as for
+ * pet_serve_jobs; *stats for the call.  Synchronising.  Refused with
+ * PET_ERR_INVALID before any CUDA call: null arrays, a request with a null
+ * plan, counts or sequence, an unknown algorithm or table type, a non-finite
+ * background, a non-finite or zero phi_star, bad arrival times, alpha/decay/
+ * eta as in the epoch calls, a subset index out of range, or a request whose
+ * slot alone exceeds the budget.  A numeric error latched by a request's
+ * problem is returned when its slot is freed or at the end. */
+pet_status pet_serve_requests(const pet_request *reqs, int32_t n, int32_t n_streams, size_t budget_bytes,
+                              int32_t max_epochs, double gap, int32_t *h_epochs, double *h_gap, double *h_start_ms,
+                              double *h_done_ms, pet_serve_stats *stats, void *stream);
+
 pet_status pet_serve_jobs(pet_state *const *states, const int32_t *const *h_seqs, const float *h_alpha,
                           const float *h_decay, const int32_t *h_eta, const double *h_phi_star,
                           const double *h_arrival_s, int32_t n_jobs, int32_t n_streams, int32_t max_epochs, double gap,

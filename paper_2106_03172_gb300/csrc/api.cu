@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -1254,10 +1255,18 @@ pet_status job_steps(int algo, float alpha, float decay, int32_t eta, GapJob &j)
 // that slot.  Resets that fill a SAGA / SAGA-EM table go through their
 // problem's full-data ratio buffer, so those of one problem are chained by an
 // event.  Synchronising; the slots start after the work enqueued on `caller`.
+// Slot hooks of a caller that owns the jobs' states: `acquire` gives job j its
+// state (ok = false: not now, the job waits at the head of the queue) just
+// before it starts on `s`; `release` runs on the job's end, after its last
+// objective was read.
+using AcquireFn = std::function<pet_status(int, cudaStream_t, bool &)>;
+using ReleaseFn = std::function<pet_status(int, cudaStream_t)>;
+
 pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const *workers, float *results,
                         int max_epochs, double gap, int32_t *h_epochs, double *h_gap, double *h_ms,
                         cudaStream_t caller, const double *arrival_s = nullptr, double *h_start_ms = nullptr,
-                        double *h_done_ms = nullptr) {
+                        double *h_done_ms = nullptr, const AcquireFn *acquire = nullptr,
+                        const ReleaseFn *release = nullptr) {
     using clock = std::chrono::steady_clock;
     const int n_jobs = (int)jobs.size();
     const clock::time_point t_call = clock::now();
@@ -1353,6 +1362,11 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
         // free slots take the jobs that have arrived, in order
         for (int w = 0; w < n_slots && next < n_jobs; ++w) {
             if (slots[(size_t)w].job >= 0 || !arrived(next)) continue;
+            if (acquire) {
+                bool ok = false;
+                if ((rc = (*acquire)(next, slots[(size_t)w].s, ok)) != PET_OK) return fail(rc);
+                if (!ok) break;
+            }
             if ((rc = start_job(w)) != PET_OK) return fail(rc);
             ++active;
             progressed = true;
@@ -1380,9 +1394,10 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
                                       "result copy")) != PET_OK)
                         return fail(rc);
                 }
+                if (release && (rc = (*release)(sl.job, sl.s)) != PET_OK) return fail(rc);
                 sl.job = -1;
                 --active;
-                if (next < n_jobs && arrived(next)) {
+                if (!acquire && next < n_jobs && arrived(next)) {
                     if ((rc = start_job(w)) != PET_OK) return fail(rc);
                     ++active;
                 }
@@ -1401,6 +1416,7 @@ pet_status drive_to_gap(std::vector<GapJob> &jobs, int n_slots, pet_state *const
         }
     }
     cleanup();
+    if (acquire) return PET_OK;    // the caller owns (and checks) the jobs' problems
     // numeric errors latched by any job's problem
     for (const GapJob &j : jobs) {
         bool seen = false;
@@ -1522,6 +1538,158 @@ pet_status pet_serve_jobs(pet_state *const *states, const int32_t *const *h_seqs
     if (n_jobs == 0) return PET_OK;
     return drive_to_gap(jobs, std::min(n_streams, n_jobs), nullptr, nullptr, max_epochs, gap, h_epochs, h_gap,
                         ms.data(), (cudaStream_t)stream, h_arrival_s, h_start_ms, h_done_ms);
+}
+
+pet_status pet_serve_requests(const pet_request *reqs, int32_t n, int32_t n_streams, size_t budget_bytes,
+                              int32_t max_epochs, double gap, int32_t *h_epochs, double *h_gap, double *h_start_ms,
+                              double *h_done_ms, pet_serve_stats *stats, void *stream) {
+    std::vector<double> ms((size_t)std::max(1, (int)n));
+    PET_TRY(check_gap_args(n, max_epochs, gap, reqs, h_epochs, h_gap, ms.data()));
+    if (n_streams < 1) return set_error(PET_ERR_INVALID, "n_streams must be >= 1");
+    if (n > 0 && (!h_start_ms || !h_done_ms || !stats)) return set_error(PET_ERR_INVALID, "null argument");
+    std::vector<GapJob> jobs((size_t)n);
+    std::vector<size_t> need((size_t)n);
+    for (int j = 0; j < n; ++j) {
+        const pet_request &r = reqs[j];
+        const std::string at = " of request " + std::to_string(j);
+        if (!r.plan || !r.h_counts || !r.h_seq) return set_error(PET_ERR_INVALID, "null plan, counts or sequence" + at);
+        if (r.algo < PET_ALGO_OSEM || r.algo > PET_ALGO_SAGAEM) return set_error(PET_ERR_INVALID, "unknown algorithm" + at);
+        if (r.table_dtype != PET_TABLE_FP32 && r.table_dtype != PET_TABLE_BF16)
+            return set_error(PET_ERR_INVALID, "unknown table type" + at);
+        if (!std::isfinite(r.bg)) return set_error(PET_ERR_INVALID, "background must be finite" + at);
+        if (!std::isfinite(r.phi_star) || r.phi_star == 0.0)
+            return set_error(PET_ERR_INVALID, "phi_star must be finite and nonzero" + at);
+        if (!std::isfinite(r.arrival_s) || r.arrival_s < 0.0 || (j > 0 && r.arrival_s < reqs[j - 1].arrival_s))
+            return set_error(PET_ERR_INVALID, "arrival times must be finite, >= 0 and nondecreasing");
+        GapJob &g = jobs[(size_t)j];
+        g.st = nullptr;
+        g.seq = r.h_seq;
+        g.phi_star = r.phi_star;
+        PET_TRY(job_steps(r.algo, r.alpha, r.decay, r.eta, g));
+        PET_TRY(check_job_seq(r.plan, r.h_seq, (long long)max_epochs * r.plan->ns, j));
+        size_t pb = 0, sb = 0;
+        PET_TRY(pet_problem_bytes(r.plan, 0, &pb));
+        PET_TRY(pet_plan_state_bytes(r.plan, r.algo, r.table_dtype, &sb));
+        need[(size_t)j] = pb + sb + sizeof(float) * ((size_t)r.plan->M * sino_inner(r.plan) + (size_t)plane_of(r.plan));
+        if (need[(size_t)j] > budget_bytes) return set_error(PET_ERR_INVALID, "request larger than the budget" + at);
+    }
+    *stats = pet_serve_stats{};
+    if (n == 0) return PET_OK;
+
+    // the slot pool: a request's problem, state, image and counts staging, kept after the request for
+    // the next one of the same plan, algorithm, table and penalty
+    struct Pooled {
+        const pet_request *key;
+        pet_problem *p = nullptr;
+        pet_state *st = nullptr;
+        float *img = nullptr, *stage = nullptr;
+        size_t bytes = 0;
+        int job = -1;
+        uint64_t used = 0;
+    };
+    std::vector<Pooled> pool;
+    size_t used_bytes = 0;
+    uint64_t tick = 0;
+    int last_deferred = -1;
+    auto same_kind = [](const pet_request &a, const pet_request &b) {
+        return a.plan == b.plan && a.algo == b.algo && a.table_dtype == b.table_dtype &&
+               a.penalty.potential == b.penalty.potential && a.penalty.beta == b.penalty.beta &&
+               a.penalty.delta == b.penalty.delta;
+    };
+    auto destroy = [&](Pooled &q) -> pet_status {
+        pet_status st = PET_OK;
+        if (q.p) st = read_status(q.p, (cudaStream_t)stream);     // a numeric error latched by its requests
+        pet_state_destroy(q.st);
+        pet_problem_destroy(q.p);
+        dfree(q.img);
+        dfree(q.stage);
+        used_bytes -= q.bytes;
+        return st;
+    };
+    auto upload = [&](Pooled &q, const pet_request &r, cudaStream_t s) -> pet_status {
+        const size_t count = (size_t)r.plan->M * sino_inner(r.plan);
+        return cuda_ok(cudaMemcpyAsync(q.stage, r.h_counts, sizeof(float) * count, cudaMemcpyHostToDevice, s),
+                       "counts upload");
+    };
+    const AcquireFn acquire = [&](int j, cudaStream_t s, bool &ok) -> pet_status {
+        const pet_request &r = reqs[j];
+        ok = false;
+        for (Pooled &q : pool)
+            if (q.job < 0 && same_kind(*q.key, r)) {
+                PET_TRY(upload(q, r, s));
+                PET_TRY(pet_problem_update(q.p, q.stage, nullptr, r.bg, s));
+                q.job = j;
+                q.used = ++tick;
+                jobs[(size_t)j].st = q.st;
+                ++stats->slots_reused;
+                ok = true;
+                return PET_OK;
+            }
+        // make room: free pooled slots, least recently used first
+        while (used_bytes + need[(size_t)j] > budget_bytes) {
+            Pooled *lru = nullptr;
+            for (Pooled &q : pool)
+                if (q.job < 0 && (!lru || q.used < lru->used)) lru = &q;
+            if (!lru) break;
+            const pet_status st = destroy(*lru);
+            pool.erase(pool.begin() + (lru - pool.data()));
+            ++stats->slots_evicted;
+            PET_TRY(st);
+        }
+        if (used_bytes + need[(size_t)j] > budget_bytes) {          // wait for a running request to end
+            if (last_deferred != j) ++stats->admissions_deferred;
+            last_deferred = j;
+            return PET_OK;
+        }
+        Pooled q;
+        q.key = &r;
+        q.bytes = need[(size_t)j];
+        const pet_plan *pl = r.plan;
+        pet_status st = dalloc(&q.stage, (size_t)pl->M * sino_inner(pl), "counts staging");
+        if (st == PET_OK) st = dalloc(&q.img, (size_t)plane_of(pl), "image");
+        if (st == PET_OK) st = upload(q, r, s);
+        if (st == PET_OK) st = pet_problem_create(pl, q.stage, nullptr, r.bg, &r.penalty, &q.p, s);
+        if (st == PET_OK) st = pet_state_create(q.p, r.algo, r.table_dtype, q.img, nullptr, &q.st, s);
+        if (st != PET_OK) {
+            pet_state_destroy(q.st);
+            pet_problem_destroy(q.p);
+            dfree(q.img);
+            dfree(q.stage);
+            return st;
+        }
+        q.job = j;
+        q.used = ++tick;
+        used_bytes += q.bytes;
+        stats->peak_bytes = std::max(stats->peak_bytes, used_bytes);
+        ++stats->slots_created;
+        jobs[(size_t)j].st = q.st;
+        pool.push_back(q);
+        ok = true;
+        return PET_OK;
+    };
+    const ReleaseFn release = [&](int j, cudaStream_t s) -> pet_status {
+        for (Pooled &q : pool)
+            if (q.job == j) {
+                if (reqs[j].h_image) {
+                    PET_TRY(cuda_ok(cudaMemcpyAsync(reqs[j].h_image, q.img, sizeof(float) * (size_t)plane_of(q.key->plan),
+                                                    cudaMemcpyDeviceToHost, s), "image download"));
+                    PET_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+                }
+                q.job = -1;
+                return PET_OK;
+            }
+        return set_error(PET_ERR_STATE, "released a request that holds no slot");
+    };
+    std::vector<double> arrivals((size_t)n);
+    for (int j = 0; j < n; ++j) arrivals[(size_t)j] = reqs[j].arrival_s;
+    pet_status rc = drive_to_gap(jobs, std::min((int)n_streams, (int)n), nullptr, nullptr, max_epochs, gap, h_epochs,
+                                 h_gap, ms.data(), (cudaStream_t)stream, arrivals.data(), h_start_ms, h_done_ms,
+                                 &acquire, &release);
+    for (Pooled &q : pool) {
+        const pet_status st = destroy(q);
+        if (rc == PET_OK) rc = st;
+    }
+    return rc;
 }
 
 // ---- batches ------------------------------------------------------------------

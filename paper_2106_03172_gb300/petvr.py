@@ -47,6 +47,18 @@ class pet_penalty(ctypes.Structure):
     _fields_ = [("potential", c_int32), ("beta", c_float), ("delta", c_float)]
 
 
+class pet_request(ctypes.Structure):
+    _fields_ = [("plan", c_void_p), ("h_counts", c_void_p), ("bg", c_float), ("penalty", pet_penalty),
+                ("algo", c_int32), ("table_dtype", c_int32), ("h_seq", c_void_p), ("alpha", c_float),
+                ("decay", c_float), ("eta", c_int32), ("phi_star", c_double), ("arrival_s", c_double),
+                ("h_image", c_void_p)]
+
+
+class pet_serve_stats(ctypes.Structure):
+    _fields_ = [("peak_bytes", c_size_t), ("slots_created", c_int32), ("slots_reused", c_int32),
+                ("slots_evicted", c_int32), ("admissions_deferred", c_int32)]
+
+
 _SIGS = {
     "pet_plan_create": (c_int32, [POINTER(pet_geometry), POINTER(pet_subsets), POINTER(c_void_p)]),
     "pet_plan_destroy": (None, [c_void_p]),
@@ -103,6 +115,8 @@ _SIGS = {
                                       c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pet_serve_jobs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                  c_int32, c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pet_serve_requests": (c_int32, [c_void_p, c_int32, c_int32, c_size_t, c_int32, c_double, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "pet_kernel_launches": (c_uint64, []),
     "pet_last_error": (ctypes.c_char_p, []),
 }
@@ -386,6 +400,40 @@ def pet_serve_jobs(states, seqs, alphas, etas, phi_stars, arrivals_s, max_epochs
     _call("pet_serve_jobs", h_states, h_seqs, ptr(a), ptr(d), ptr(e), ptr(ps), ptr(arr), n, n_streams, max_epochs,
           gap, ptr(epochs), ptr(gaps), ptr(t_start), ptr(t_done), _stream(stream))
     return epochs[:n], gaps[:n], t_start[:n], t_done[:n]
+
+
+def pet_serve_requests(requests, n_streams: int, budget_bytes: int, max_epochs: int, gap: float = 1e-4,
+                       stream=None):
+    """Serve a request stream with admission by a device-memory budget (see
+    the C header).  ``requests``: dicts with plan (Plan), counts (float32
+    array), bg, beta, potential, delta, algo, table, seq (int array), alpha,
+    decay, eta, phi_star, arrival_s.  Returns (epochs, gap, start_ms, done_ms,
+    images, stats dict)."""
+    import numpy as np
+    n = len(requests)
+    keep = []
+    arr = (pet_request * max(1, n))()
+    images = []
+    for i, r in enumerate(requests):
+        counts = np.ascontiguousarray(r["counts"], dtype=np.float32).ravel()
+        seq = np.ascontiguousarray(r["seq"], dtype=np.int32)
+        img = np.zeros(r["n_image"], dtype=np.float32)
+        keep += [counts, seq]
+        images.append(img)
+        arr[i] = pet_request(r["plan"].handle.value, counts.ctypes.data, r["bg"],
+                             pet_penalty(POTENTIAL[r.get("potential", "quadratic")], r["beta"], r.get("delta", 1.0)),
+                             ALGO[r["algo"]], TABLE[r.get("table", "fp32")], seq.ctypes.data, r.get("alpha", 1.0),
+                             r.get("decay", 0.0), r.get("eta", 1), r["phi_star"], r["arrival_s"], img.ctypes.data)
+    epochs = np.zeros(max(1, n), dtype=np.int32)
+    gaps = np.zeros(max(1, n), dtype=np.float64)
+    t_start = np.zeros(max(1, n), dtype=np.float64)
+    t_done = np.zeros(max(1, n), dtype=np.float64)
+    st = pet_serve_stats()
+    ptr = lambda x: c_void_p(x.ctypes.data)   # noqa: E731
+    _call("pet_serve_requests", arr, n, n_streams, budget_bytes, max_epochs, gap, ptr(epochs), ptr(gaps),
+          ptr(t_start), ptr(t_done), byref(st), _stream(stream))
+    stats = {k: getattr(st, k) for k, _ in pet_serve_stats._fields_}
+    return epochs[:n], gaps[:n], t_start[:n], t_done[:n], images, stats
 
 
 def pet_state_objective_async(state, phi_out: torch.Tensor, stream=None):

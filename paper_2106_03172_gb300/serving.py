@@ -450,37 +450,38 @@ class StreamServer(_Base):
         return requests
 
 
-def serve_native(requests, gap: float = 1e-4, max_epochs: int = 60, n_streams: int = 64):
-    """The stream server's policy with the host loop in the library
-    (pet_serve_jobs): every request gets its own problem and state up front
-    (no memory budget: admission is limited by the streams alone), then the
-    library starts each request once it has arrived and a stream is free, runs
-    its epochs with the objective after each, and retires it at the gap or at
-    max_epochs, from C++.  A request's subset sequence, launch shapes and
-    result are those of the other paths."""
+def serve_native(requests, gap: float = 1e-4, max_epochs: int = 60, n_streams: int = 64,
+                 budget_bytes: int = 1 << 30):
+    """The stream server's policy with the whole loop in the library
+    (pet_serve_requests): a request is admitted once it has arrived, one of
+    `n_streams` streams is free and its slot fits the device-memory budget
+    (problem, state, image and counts staging; slots are pooled by plan,
+    method, table and penalty and freed least recently used first), then runs
+    its epochs with the objective after each until the gap or max_epochs, all
+    from C++.  A request's subset sequence, launch shapes and result are
+    those of the other paths.  Returns the requests (filled in) and the
+    call's slot statistics."""
     reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
-    plans, keep, states, seqs = {}, [], [], []
+    plans, specs = {}, []
     for r in reqs:
         key = _Base._plan_key(r.work)
         if key not in plans:
             plans[key] = tuned_plan(r.work)
-        counts = torch.from_numpy(np.ascontiguousarray(r.counts, dtype=np.float32).ravel()).cuda()
-        problem = petvr.Problem(plans[key], counts, None, r.w, r.work.beta)
-        state = petvr.State(problem, r.algo, torch.zeros(r.work.geometry.n_pixels, device="cuda"),
-                            table=_table(r.algo))
-        keep.append(problem)
-        states.append(state)
-        seqs.append(subset_sequence(r.seed, r.work.n_subsets, max_epochs * r.work.n_subsets))
+        alpha, eta = STEP[r.algo]
+        specs.append({"plan": plans[key], "counts": r.counts, "bg": r.w, "beta": r.work.beta, "algo": r.algo,
+                      "table": _table(r.algo), "seq": subset_sequence(r.seed, r.work.n_subsets,
+                                                                       max_epochs * r.work.n_subsets),
+                      "alpha": alpha, "eta": eta, "phi_star": r.phi_star, "arrival_s": r.arrival,
+                      "n_image": r.work.geometry.n_pixels})
     torch.cuda.synchronize()
-    epochs, gaps, t_start, t_done = petvr.pet_serve_jobs(
-        states, seqs, [STEP[r.algo][0] for r in reqs], [STEP[r.algo][1] for r in reqs],
-        [r.phi_star for r in reqs], [r.arrival for r in reqs], max_epochs, gap, n_streams=n_streams)
-    for r, st, e, g, t0, t1 in zip(reqs, states, epochs, gaps, t_start, t_done):
+    epochs, gaps, t_start, t_done, images, stats = petvr.pet_serve_requests(specs, n_streams, budget_bytes,
+                                                                           max_epochs, gap)
+    for r, e, g, t0, t1, im in zip(reqs, epochs, gaps, t_start, t_done, images):
         r.epochs, r.gap = int(e), float(g)
         r.reached = r.gap <= gap
         r.admitted, r.done = float(t0) / 1e3, float(t1) / 1e3
-        r.image = st.img.cpu().numpy()
-    return requests
+        r.image = im
+    return requests, stats
 
 
 def serve_plain(requests, gap: float = 1e-4, max_epochs: int = 60, clock=time.perf_counter):

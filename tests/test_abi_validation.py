@@ -166,3 +166,34 @@ def test_jobs_executor_refuses_bad_arguments_before_reading_states(lib):
                        ({"max_epochs": 0}, "max_epochs"), ({"gap": float("nan")}, "gap")):
         r, msg = call(**kw)
         assert r == PET_ERR_INVALID and needle in msg, (kw, msg)
+
+
+def test_serve_requests_refuses_bad_arguments_before_any_cuda_call(lib):
+    """pet_serve_requests's checks on the call's own arguments and on each
+    request's host fields (the stand-in plan is read only for its subset
+    number after these checks, so it is never reached here)."""
+    from ctypes import c_double, c_int32, c_size_t
+    req = (petvr.pet_request * 1)()
+    seq = (c_int32 * 4)(0, 0, 0, 0)
+    counts = (ctypes.c_float * 4)()
+    req[0].plan, req[0].h_counts, req[0].h_seq = 0x1000, ctypes.addressof(counts), ctypes.addressof(seq)
+    req[0].phi_star, req[0].arrival_s, req[0].algo = 1.0, 0.0, 0
+    outs = ((c_int32 * 1)(), (c_double * 1)(), (c_double * 1)(), (c_double * 1)())
+    st = petvr.pet_serve_stats()
+
+    def call(reqs=req, n=1, n_streams=2, max_epochs=2, stats=True):
+        r = lib.pet_serve_requests(reqs, n, n_streams, c_size_t(1 << 20), max_epochs, c_double(1e-4), *outs,
+                                   byref(st) if stats else None, None)
+        return r, lib.pet_last_error().decode()
+
+    for kw, needle in (({"reqs": None}, "null"), ({"n": -1}, "n_jobs"), ({"n_streams": 0}, "n_streams"),
+                       ({"max_epochs": 0}, "max_epochs"), ({"stats": False}, "null")):
+        r, msg = call(**kw)
+        assert r == PET_ERR_INVALID and needle in msg, (kw, msg)
+    for field, value, needle in (("algo", 9, "algorithm"), ("table_dtype", 5, "table"), ("bg", float("nan"), "background"),
+                                 ("phi_star", 0.0, "phi_star"), ("arrival_s", -1.0, "arrival")):
+        old = getattr(req[0], field)
+        setattr(req[0], field, value)
+        r, msg = call()
+        setattr(req[0], field, old)
+        assert r == PET_ERR_INVALID and needle in msg, (field, msg)

@@ -175,9 +175,40 @@ def test_native_loop_gives_the_plain_results():
             out.append(Request(k, work, data["g"], data["w"], phi, arrival=t, seed=990 + k))
         return out
 
-    native = serve_native(reqs(), max_epochs=40, n_streams=3)
+    native, stats = serve_native(reqs(), max_epochs=40, n_streams=3)
     plain = serve_plain(reqs(), max_epochs=40)
     for a, b in zip(native, plain):
         assert a.epochs == b.epochs and a.reached == b.reached
         np.testing.assert_array_equal(a.image, b.image)
         assert a.admitted >= a.arrival and a.done > a.admitted
+    assert stats["slots_created"] + stats["slots_reused"] == len(native)
+
+
+def test_native_loop_respects_the_memory_budget():
+    """With a budget of two and a half of the largest slots the library's
+    loop defers admissions, evicts pooled slots of other kinds to make room,
+    never holds more than the budget, and still returns the plain path's
+    results."""
+    from paper_2106_03172_gb300 import petvr
+    from paper_2106_03172_gb300.serving import Request, _table, serve_native, serve_plain
+
+    def reqs():
+        out = []
+        for k in range(8):
+            work, data, phi = _template(k % len(TEMPLATES))
+            out.append(Request(k, work, data["g"], data["w"], phi, arrival=0.0, seed=970 + k))
+        return out
+
+    slot = 0
+    for work in TEMPLATES:                     # a slot: problem, state, counts staging and image
+        plan = petvr.Plan(work.geometry, work.n_subsets)
+        algo = work.methods[0]
+        slot = max(slot, petvr.pet_problem_bytes(plan.handle, False)
+                   + petvr.pet_plan_state_bytes(plan.handle, algo, _table(algo))
+                   + 4 * (work.geometry.n_rays + work.geometry.n_pixels))
+    budget = int(2.5 * slot)
+    native, stats = serve_native(reqs(), max_epochs=40, n_streams=4, budget_bytes=budget)
+    assert stats["peak_bytes"] <= budget and stats["admissions_deferred"] > 0 and stats["slots_evicted"] > 0, stats
+    for a, b in zip(native, serve_plain(reqs(), max_epochs=40)):
+        assert a.epochs == b.epochs
+        np.testing.assert_array_equal(a.image, b.image)
