@@ -61,7 +61,7 @@ enum { PET_TABLE_FP32 = 0, PET_TABLE_BF16 = 1 };
 /* Preconditioner of SAGA and SVRG (pet_state_set_preconditioner). */
 enum { PET_PRECOND_CONSTANT = 0, PET_PRECOND_ITERATE = 1 };
 /* How pet_batch_epoch runs a batch's updates (pet_batch_set_mode). */
-enum { PET_BATCH_PHASES = 0, PET_BATCH_DATAFLOW = 1 };
+enum { PET_BATCH_PHASES = 0, PET_BATCH_DATAFLOW = 1, PET_BATCH_STREAMS = 2 };
 /* Potentials of the pairwise penalty (Table 1, t = f_n - f_j, delta > 0):
  * quadratic t^2/2; Huber t^2/2 for |t| <= delta else delta|t| - delta^2/2;
  * log cosh delta^2 log cosh(t/delta); hyperbola delta^2 (sqrt(1+(t/delta)^2) - 1)
@@ -370,7 +370,11 @@ pet_status pet_batch_objective_async(pet_batch *batch, double *d_phi, void *stre
  *     at a kernel boundary after every phase.  The waits are bounded (see
  *     pet_batch_set_wait_limit).  Applies when every member uses the same
  *     potential class (quadratic, or edge-preserving); otherwise the batch
- *     runs in phases. */
+ *     runs in phases;
+ *   PET_BATCH_STREAMS: every member's own epoch call (and objective call),
+ *     its captured graphs, member j on stream j mod k of k <= 8 streams the
+ *     batch creates on first use, which wait for `stream` and which `stream`
+ *     then waits for. */
 pet_status pet_batch_set_mode(pet_batch *batch, int32_t mode);
 
 /* PET_BATCH_DATAFLOW only: how many times a block polls (with a short sleep

@@ -1708,6 +1708,12 @@ pet_status pet_batch_destroy(pet_batch *b) {
     dfree(b->d_alphas);
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t sd : b->side) {
+        cudaStreamSynchronize(sd);
+        cudaStreamDestroy(sd);
+    }
+    for (cudaEvent_t e : b->side_ev) cudaEventDestroy(e);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     delete b;
     return PET_OK;
 }
@@ -1720,7 +1726,8 @@ pet_status pet_batch_set_graphs(pet_batch *b, int32_t on) {
 
 pet_status pet_batch_set_mode(pet_batch *b, int32_t mode) {
     if (!b) return set_error(PET_ERR_INVALID, "null batch");
-    if (mode != PET_BATCH_PHASES && mode != PET_BATCH_DATAFLOW) return set_error(PET_ERR_INVALID, "unknown batch mode");
+    if (mode != PET_BATCH_PHASES && mode != PET_BATCH_DATAFLOW && mode != PET_BATCH_STREAMS)
+        return set_error(PET_ERR_INVALID, "unknown batch mode");
     b->mode = mode;
     return PET_OK;
 }
@@ -1858,6 +1865,36 @@ void fill_member(BatchMember &m, const pet_state *st, float alpha, const int *se
 //     member's update.
 // Back phases are split by potential class (the quadratic epilogue and the
 // edge-preserving one are different kernels), longest tiles first.
+// PET_BATCH_STREAMS: the batch's own streams (up to 8), created on first use;
+// fork makes them wait for `s`, join makes `s` wait for them.
+constexpr int kBatchSideStreams = 8;
+
+pet_status batch_fork(pet_batch *b, cudaStream_t s) {
+    if (b->side.empty()) {
+        const int k = std::max(1, std::min((int)b->states.size(), kBatchSideStreams));
+        PET_TRY(cuda_ok(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "event"));
+        for (int i = 0; i < k; ++i) {
+            cudaStream_t sd = nullptr;
+            cudaEvent_t e = nullptr;
+            PET_TRY(cuda_ok(cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking), "batch stream"));
+            b->side.push_back(sd);
+            PET_TRY(cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"));
+            b->side_ev.push_back(e);
+        }
+    }
+    PET_TRY(cuda_ok(cudaEventRecord(b->fork_ev, s), "event record"));
+    for (cudaStream_t sd : b->side) PET_TRY(cuda_ok(cudaStreamWaitEvent(sd, b->fork_ev, 0), "stream wait"));
+    return PET_OK;
+}
+
+pet_status batch_join(pet_batch *b, cudaStream_t s) {
+    for (size_t i = 0; i < b->side.size(); ++i) {
+        PET_TRY(cuda_ok(cudaEventRecord(b->side_ev[i], b->side[i]), "event record"));
+        PET_TRY(cuda_ok(cudaStreamWaitEvent(s, b->side_ev[i], 0), "stream wait"));
+    }
+    return PET_OK;
+}
+
 void build_batch_phases(pet_batch *b, int n_iter, const std::vector<std::vector<uint8_t>> &anchors) {
     const int n = (int)b->states.size();
     b->h_segs.clear();
@@ -2086,6 +2123,19 @@ pet_status pet_batch_epoch(pet_batch *b, const int32_t *h_seqs, int32_t n_iter, 
             return set_error(PET_ERR_INVALID, "eta must be >= 1");
     }
     if (n_iter == 0) return PET_OK;
+    if (b->mode == PET_BATCH_STREAMS) {
+        // every member's own epoch call (its captured graphs), member j on the batch's stream j mod k
+        PET_TRY(batch_fork(b, s));
+        for (int j = 0; j < n; ++j) {
+            pet_state *st = b->states[j];
+            const int algo = st->algo;
+            PET_TRY(epoch_common(st, algo, h_seqs + (size_t)j * n_iter, n_iter,
+                                 algo == PET_ALGO_OSEM ? 0.0f : h_alpha[j], 0.0f,
+                                 (algo == PET_ALGO_SVREM || algo == PET_ALGO_SVRG) ? h_eta[j] : 1,
+                                 b->side[(size_t)j % b->side.size()]));
+        }
+        return batch_join(b, s);
+    }
     const size_t need = (size_t)n * n_iter;
     if ((int)need > b->seq_cap) {
         int *grown = nullptr;
@@ -2239,6 +2289,12 @@ pet_status pet_batch_objective_async(pet_batch *b, double *d_phi, void *stream) 
     if (!b || !d_phi) return set_error(PET_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)b->states.size();
+    if (b->mode == PET_BATCH_STREAMS) {
+        PET_TRY(batch_fork(b, s));
+        for (int j = 0; j < n; ++j)
+            PET_TRY(pet_state_objective_async(b->states[j], d_phi + 3 * j, b->side[(size_t)j % b->side.size()]));
+        return batch_join(b, s);
+    }
     // descriptors with the output slots (the subset sequences are not read here)
     int pen_blocks = 0;
     for (int j = 0; j < n; ++j) {

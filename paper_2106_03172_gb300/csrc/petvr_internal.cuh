@@ -534,7 +534,10 @@ struct pet_batch {
     int *d_claims = nullptr;        // claim counters of the current call's phases
     int claim_cap = 0;
     int n_claims = 0;
-    int mode = 0;                   // 0: persistent phases, 1: dependency-driven epoch
+    int mode = 0;                   // 0: persistent phases, 1: dependency-driven epoch, 2: member graphs on streams
+    std::vector<cudaStream_t> side; // mode 2: the batch's own streams, member j on side[j % side.size()]
+    std::vector<cudaEvent_t> side_ev;
+    cudaEvent_t fork_ev = nullptr;
     long long wait_limit = 1LL << 22;        // dependency-driven epoch: polls of a wait before PET_ERR_TIMEOUT
     std::vector<petvr::DfSeg> h_df;
     petvr::DfSeg *d_df = nullptr;

@@ -548,8 +548,9 @@ class Batch:
         pet_batch_objective_async(self.handle, phi_out, stream)
 
     def set_mode(self, mode: str):
-        """'phases' (default) or 'dataflow' (one launch per epoch call)."""
-        _call("pet_batch_set_mode", self.handle, {"phases": 0, "dataflow": 1}[mode])
+        """'phases' (default), 'dataflow' (one launch per epoch call) or
+        'streams' (the members' own graphs on the batch's streams)."""
+        _call("pet_batch_set_mode", self.handle, {"phases": 0, "dataflow": 1, "streams": 2}[mode])
 
     def set_wait_limit(self, polls: int):
         _call("pet_batch_set_wait_limit", self.handle, int(polls))

@@ -35,7 +35,7 @@ MEMBERS = [("c64", "osem", "fp32", 1.0, 1), ("c64", "svrem", "fp32", 0.7, 1), ("
            ("c64", "sagaem", "fp32", 0.7, 1)]
 
 
-@pytest.mark.parametrize("mode", ["phases", "dataflow"])
+@pytest.mark.parametrize("mode", ["phases", "dataflow", "streams"])
 def test_batch_equals_individual_epochs(mode):
     """Both batch modes (persistent phases; one dependency-driven launch per
     call) give every member exactly its own epochs' iterates and objectives."""
