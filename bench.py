@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--distinct", action="store_true",
                     help="serve workload: requests with their own phantoms and counts (the stored-Phi* sample) "
                          "instead of draws from the request templates")
-    ap.add_argument("--server", choices=["streams", "batch"], default="streams",
+    ap.add_argument("--server", choices=["native", "streams", "batch"], default="native",
                     help="serve workload: the server the headline value is taken from (the other is reported too)")
     ap.add_argument("--batch", dest="batch", action="store_true",
                     help="run the four methods as one batch (one launch per phase) instead of four streams")
@@ -1262,7 +1262,7 @@ def run_serve(args):
                                                depth=args.depth),
                "batch": lambda: Server(budget_bytes=budget, max_slots=64, gap=GAP, max_epochs=me, tick=3,
                                        window=args.window)}
-    order = [args.server] + [k for k in servers if k != args.server]
+    order = ([args.server] if args.server in servers else []) + [k for k in servers if k != args.server]
     runs = {}
     for kind in order:
         srv = servers[kind]()
@@ -1274,20 +1274,23 @@ def run_serve(args):
         clk = clocks.stop()
         runs[kind] = (srv, done, clk, petvr.pet_kernel_launches() - launches0)
         del srv
-    srv, done, clk, launches = runs[args.server]
-    summ = latency_summary(done)
-    # the same stream through the library's own host loop (pet_serve_jobs)
+    # the same stream through the library's own serving loop (pet_serve_requests, same budget)
+    clocks = ClockSampler(visible_index(torch))
+    launches0 = petvr.pet_kernel_launches()
+    clocks.start()
     native_done, native_stats = serve_native(requests(), gap=GAP, max_epochs=args.max_epochs, n_streams=64,
                                              budget_bytes=budget)
+    runs["native"] = (None, native_done, clocks.stop(), petvr.pet_kernel_launches() - launches0)
     native = latency_summary(native_done)
+    srv, done, clk, launches = runs[args.server]
+    summ = latency_summary(done)
     # the same stream through the plain per-reconstruction path, one request at a time
     plain = serve_plain(requests(), gap=GAP, max_epochs=args.max_epochs)
     plain_summ = latency_summary(plain)
     same = all(a.epochs == b.epochs and np.array_equal(a.image, b.image)
-               for d in [r[1] for r in runs.values()] + [native_done] for a, b in zip(d, plain))
+               for d in [r[1] for r in runs.values()] for a, b in zip(d, plain))
     sizes = sorted({w.geometry.nx for w, _, _ in pool})
-    other = [k for k in order if k != args.server][0]
-    o_srv, o_done, _, _ = runs[other]
+    others = [k for k in ("streams", "batch") if k != args.server]
     line = {
         "metric": "subset fwd+back projections/s and reconstructions/s to 1e-4 objective gap; p50/p99",
         "value": summ["reached_per_s"], "unit": "reconstructions/s", "n_gpus": 1, "steps": n_req, "warmup": 0,
@@ -1311,8 +1314,9 @@ def run_serve(args):
         "speedup_vs_plain": summ["reached_per_s"] / plain_summ["reached_per_s"],
         "p50_speedup_vs_plain": plain_summ["p50_ms"] / summ["p50_ms"],
         "bit_identical_to_plain": bool(same),
-        "server_stats": _server_stats(srv),
-        "other_server": {"server": other, "latency": latency_summary(o_done), "stats": _server_stats(o_srv)},
+        "server_stats": native_stats if srv is None else _server_stats(srv),
+        "other_servers": {k: {"latency": latency_summary(runs[k][1]), "stats": _server_stats(runs[k][0])}
+                          for k in others},
         "native_loop": {"latency": native, "stats": native_stats,
                         "how": "pet_serve_requests: the whole loop in C++, each request admitted once it has arrived, "
                                "one of 64 streams is free and its slot fits the same device-memory budget"},
