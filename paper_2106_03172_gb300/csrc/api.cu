@@ -1255,9 +1255,11 @@ pet_status job_steps(int algo, float alpha, float decay, int32_t eta, GapJob &j)
 // that slot.  Resets that fill a SAGA / SAGA-EM table go through their
 // problem's full-data ratio buffer, so those of one problem are chained by an
 // event.  Synchronising; the slots start after the work enqueued on `caller`.
-// Slot hooks of a caller that owns the jobs' states: `acquire` gives job j its
-// state (ok = false: not now, the job waits at the head of the queue) just
-// before it starts on `s`; `release` runs on the job's end, after its last
+// With arrival_s, job j starts only once arrival_s[j] seconds have passed
+// since the call (h_start_ms / h_done_ms: times since the call).  With the
+// hooks, the caller owns the jobs' states: `acquire` gives job j its state
+// (ok = false: not now, the job waits at the head of the queue) just before
+// it starts on stream `s`; `release` runs at the job's end, after its last
 // objective was read.
 using AcquireFn = std::function<pet_status(int, cudaStream_t, bool &)>;
 using ReleaseFn = std::function<pet_status(int, cudaStream_t)>;
