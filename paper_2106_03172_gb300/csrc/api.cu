@@ -1649,6 +1649,9 @@ pet_status pet_serve_requests(const pet_request *reqs, int32_t n, int32_t n_stre
         const pet_plan *pl = r.plan;
         pet_status st = dalloc(&q.stage, (size_t)pl->M * sino_inner(pl), "counts staging");
         if (st == PET_OK) st = dalloc(&q.img, (size_t)plane_of(pl), "image");
+        // the state is made on a zero image (its job's warm start and reset come before any update)
+        if (st == PET_OK)
+            st = cuda_ok(cudaMemsetAsync(q.img, 0, sizeof(float) * (size_t)plane_of(pl), s), "image clear");
         if (st == PET_OK) st = upload(q, r, s);
         if (st == PET_OK) st = pet_problem_create(pl, q.stage, nullptr, r.bg, &r.penalty, &q.p, s);
         if (st == PET_OK) st = pet_state_create(q.p, r.algo, r.table_dtype, q.img, nullptr, &q.st, s);
