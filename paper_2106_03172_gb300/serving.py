@@ -270,9 +270,12 @@ class Server(_Base):
     `window` ticks."""
 
     def __init__(self, budget_bytes: int, max_slots: int = 64, gap: float = 1e-4, max_epochs: int = 60,
-                 tick: int = 3, window: int = 1):
+                 tick: int = 3, window: int = 1, batch_mode: str = "streams"):
         if tick < 1 or window < 1:
             raise ValueError("tick and window must be positive")
+        # pet_batch_set_mode of the tick batches: the members' own graphs on the batch's streams measured
+        # 20.5 reconstructions/s against 20.0 in persistent phases on the 96 distinct requests (same p50)
+        self.batch_mode = batch_mode
         super().__init__(budget_bytes, max_slots, gap, max_epochs)
         self.tick, self.window = tick, window
         self._batch = None
@@ -304,6 +307,8 @@ class Server(_Base):
                 continue
             if self._batch is None:
                 self._batch = petvr.Batch([s.state for s in self.active], graphs=False)
+                if self.batch_mode != "phases":
+                    self._batch.set_mode(self.batch_mode)
                 self.stats.batches_built += 1
             alphas = [STEP[s.req.algo][0] for s in self.active]
             etas = [STEP[s.req.algo][1] for s in self.active]
