@@ -15,9 +15,10 @@ timed once per request shape (tuned_plan) and shared by every path.
 Two ways to let the work of concurrent requests overlap on the device:
 
 * ``Server`` (one batch): all admitted requests advance together; every tick
-  runs `tick` updates of every active state in one batched launch per phase
-  (pet_batch_epoch), so requests that arrive while others run join the next
-  tick and share its kernels.  The host meets the device once per `window`
+  runs `tick` updates of every active state through one pet_batch_epoch call
+  (by default in the streams batch mode, the members' own graphs on the
+  batch's streams; or in persistent phases, one batched launch per phase), so
+  requests that arrive while others run join the next tick.  The host meets the device once per `window`
   ticks: it enqueues the window's ticks back to back, synchronises once,
   reads every epoch-end objective of the window in order, retires finished
   requests and admits new ones.  A request that finished early in a window
