@@ -954,7 +954,7 @@ def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, fl
             legs["ring2_128"]["roofline_frac"] = sub["roofline"].get("frac")
             legs["ring2_128"]["achieved_tflops"] = sub["roofline"].get("achieved")
     if "serve" in want:
-        sub = _sub_bench(["--workload", "serve", "--requests", "96", "--distinct"])
+        sub = _sub_bench(["--workload", "serve", "--requests", "192", "--distinct"])
         leg = {k: sub.get(k) for k in ("value", "unit", "latency", "speedup_vs_plain", "p50_speedup_vs_plain",
                                        "bit_identical_to_plain", "error") if k in sub}
         if "plain" in sub:
@@ -963,7 +963,7 @@ def run_legs(args, torch, petvr, work, data, prob, f0, streams_value, stream, fl
             leg["native_loop_latency"] = sub["native_loop"]["latency"]
         if "config" in sub:
             leg["requests"] = sub["config"].get("workload")
-        legs["serve_distinct96"] = leg
+        legs["serve_distinct192"] = leg
     if "parity" in want:
         legs["parity_vs_oracle"] = leg_parity(torch, petvr, work, data, prob)
     return legs
