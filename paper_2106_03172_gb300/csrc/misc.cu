@@ -258,15 +258,21 @@ int choose_group(const pet_plan *plan) {
 // kernel is bound by instruction issue rather than latency, and each thread's
 // fixed work (ray set-up, chunk reduction, epilogue) is better spread over
 // more bands: the chunk count is halved from the plan's, down to 16, while the
-// grid keeps at least kLargeGrid blocks (8 chunks measured slower again on a
-// 256^2 image: too few warps left to hide the load latency).  Stacks and
-// multi-ring plans keep theirs.
+// grid keeps at least kLargeGrid blocks and a chunk keeps at most kFullBands
+// bands (8 chunks measured slower again on a 256^2 image: too few warps left
+// to hide the load latency; on 512^2 images, 32 bands per chunk made the full
+// pass 547 us against 426 us at the plan's 32 chunks, while 384^2 images, 24
+// bands per chunk at 16 chunks, took 155 us against 168 us at 32).  Stacks
+// and multi-ring plans keep theirs.
 constexpr int kLargeGrid = 8 * 152;
+constexpr int kFullBands = 24;
 
 int full_group(const pet_plan *plan) {
     int g = choose_group(plan);
     if (plan->nz != 1 || plan->ring) return g;
-    while (g > 16 && forward_blocks(plan->M, 1, g / 2) >= kLargeGrid) g /= 2;
+    const int major = std::max(plan->nx, plan->ny);
+    while (g > 16 && forward_blocks(plan->M, 1, g / 2) >= kLargeGrid && (major + g / 2 - 1) / (g / 2) <= kFullBands)
+        g /= 2;
     return g;
 }
 
