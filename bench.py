@@ -96,7 +96,8 @@ def workload_config(work, epochs=50):
                     + (f" (delta={work.delta:g})" if work.potential != "quadratic" else "") + f" beta={work.beta}",
         "step": f"{epochs} update epochs each of OSEM, SVREM(alpha={work.alpha_svrem}, eta={work.eta_svrem}), "
                 f"SAGA(alpha={work.alpha_saga}, fp32 table), SVRG(alpha={work.alpha_svrg}, eta={work.eta_svrg}), "
-                "each epoch followed by its FP64 objective",
+                "each epoch followed by its FP64 objective; each method's step one pet_state_run call on its own "
+                "stream (an objective's forward pass also gives the next SVREM/SVRG anchor's ratios)",
         "l2": "flushed between steps (256 MiB write outside the timed events)",
         "n_subsets": work.n_subsets,
         "image": [g.ny, g.nx],
@@ -806,6 +807,8 @@ def run_ours(args):
         "objective_last_step": [float(x) for x in phi_host[:, 0]],
     }
     line.update(legs)
+    if args.batch:      # the batched step runs epoch by epoch through pet_batch_epoch
+        line["config"]["step"] = line["config"]["step"].split(";")[0] + "; one pet_batch_epoch call per epoch"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, cpairs, setup = oracle_steps(work, data, 2, min_seconds=12.0)
         line["cpu_baseline"] = {
